@@ -1,0 +1,194 @@
+/*
+ * rich.h - C ABI of the GB300 moving-Voronoi-mesh hydrodynamics sweep.
+ *
+ * One time step of the moving-mesh Godunov scheme of Yalinewich, Steinberg &
+ * Sari, "RICH: Open Source Hydrodynamic Simulation on a Moving Voronoi Mesh"
+ * (arXiv:1410.3219), Section 2, with the "extrapolated fluxes" time
+ * advancement of Section 2.3:
+ *
+ *   a0  host: ghost images + Delaunay triangulation by point insertion with
+ *       exact, tie-broken in-circle predicates (Section 2.1)
+ *   a1  Voronoi geometry: circumcentres, areas, centres of mass, edge lengths,
+ *       midpoints, normals, c_ij (quantities defined under Eq. 1)
+ *   a2  primitive variables rho, v, p and sound speed (ideal gas)
+ *   a3  Green-Gauss gradients (Eq. 1)
+ *   a4  AREPO limiter (Eqs. 3-5), TESS limiter (Eq. 6), per-cell switch (Eqs. 7-8)
+ *   a5  mesh-point velocities with cell rounding (Section 6)
+ *   a6  Courant time step (Section 2.3)
+ *   a7  per edge: linear extrapolation (Eq. 2), half-step prediction, boost
+ *       into the moving edge's frame (Section 1), rotation, HLLC (Section 2.4)
+ *   a8  conservative update U_i -= dt * sum_j L_ij F_ij (Section 5)
+ *   a9  advance the mesh-generating points
+ *
+ * Steps a1-a9 run as CUDA kernels on the device (sm_103a); a0 runs on the host.
+ *
+ * Conventions
+ *  - All arrays passed in or out are HOST arrays unless a name says "device".
+ *    The library copies on entry and exit; the caller keeps ownership.
+ *  - Per-cell arrays are indexed by the caller's point order (the library
+ *    renumbers cells internally along a Hilbert curve and maps back).
+ *  - Return value: RICH_OK (0) or a negative RICH_E* code; rich_strerror()
+ *    gives a message, rich_last_error() the detail of the last failure on the
+ *    calling thread.  No C++ exception crosses this boundary.
+ *  - A rich_sim is used by one host thread at a time.
+ */
+#ifndef RICH_H
+#define RICH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RICH_OK 0
+#define RICH_EINVAL -1     /* bad argument: n < 3, point outside the box, rho/p <= 0, NaN, gamma <= 1 */
+#define RICH_EDUPLICATE -2 /* two generating points coincide */
+#define RICH_ETESS -3      /* tessellation failed (inconsistent connectivity) */
+#define RICH_ETOOFEW -4    /* too few points for the ghost band to close every cell */
+#define RICH_ENEGATIVE -5  /* a step produced m <= 0, thermal energy <= 0, or a point left a walled box;
+                              the state stays at the last good step */
+#define RICH_ENAN -6       /* a step produced a non-finite value; state kept as for RICH_ENEGATIVE */
+#define RICH_ENOMEM -7     /* device or host allocation failed */
+#define RICH_ECUDA -8      /* CUDA runtime error (see rich_last_error) */
+#define RICH_ENODEV -9     /* no CUDA device */
+#define RICH_ESTATE -10    /* call not valid in the current state */
+
+#define RICH_BC_REFLECTIVE 0 /* rigid walls (mirror ghosts) */
+#define RICH_BC_PERIODIC 1
+
+#define RICH_MESH_LAGRANGIAN 0 /* w = v plus the Section 6 rounding velocity */
+#define RICH_MESH_EULERIAN 1   /* w = 0 */
+
+#define RICH_LIM_SWITCHED 0 /* AREPO, TESS where Eqs. 7-8 flag a shock (paper default) */
+#define RICH_LIM_AREPO 1
+#define RICH_LIM_TESS 2
+
+#define RICH_SCHEME_EXTRAPOLATED 0 /* Section 2.3 "extrapolated fluxes" */
+
+#define RICH_FP64 0 /* every step in FP64 */
+
+typedef struct rich_sim rich_sim;
+
+/* Scheme parameters.  Paper defaults: cfl 0.3 (Section 2.3); theta 0.5,
+   delta_v 0.2, delta_p 0.7 (Section 2.2); chi 0.15, eta 0.02 (Section 6). */
+typedef struct {
+    double gamma;                   /* ideal-gas adiabatic index, > 1 */
+    double cfl;                     /* Courant number */
+    int32_t boundary;               /* RICH_BC_* */
+    double x0, x1, y0, y1;          /* domain box */
+    int32_t motion;                 /* RICH_MESH_* */
+    double chi, eta;                /* cell-rounding speed (units of c_s) and trigger distance (units of R_i) */
+    double theta, delta_v, delta_p; /* TESS factor and shock-switch thresholds */
+    int32_t limiter;                /* RICH_LIM_* */
+    int32_t scheme;                 /* RICH_SCHEME_* */
+    int32_t precision;              /* RICH_FP64 */
+} rich_config;
+
+typedef struct {
+    int64_t steps_done; /* steps completed by this call */
+    double t;           /* simulation time after the call */
+    double dt_last;     /* last time step */
+    double sweep_ms;    /* device time of steps a1-a9 summed over the call (CUDA events) */
+    double tess_ms;     /* host time of a0 summed over the call */
+    double copy_ms;     /* host time spent in host<->device copies and waits */
+    int64_t n_ghost, n_tri, n_edges, n_slots; /* size of the last tessellation */
+} rich_step_info;
+
+/* Fill cfg with the paper's defaults (gamma 5/3, unit periodic box). */
+void rich_default_config(rich_config *cfg);
+
+/* Create a simulation from n generating points (x, y) inside the box and the
+   primitive fields rho, vx, vy, p at those points (the problem statement of
+   Sections 3-4: generating points, primitive fields, gamma, CFL, boundary).
+   Tessellates, computes the initial cell areas and stores the extensive
+   conserved variables (m, momentum, E) = (rho, rho v, p/(gamma-1) + rho|v|^2/2) * A
+   on the device.  Points must lie strictly inside a walled box (periodic:
+   x0 <= x < x1).  *out receives the handle; it owns all device memory and a
+   CUDA stream.  Errors: RICH_EINVAL, RICH_EDUPLICATE, RICH_ETOOFEW,
+   RICH_ENOMEM, RICH_ENODEV, RICH_ECUDA. */
+int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const double *y, const double *rho,
+                   const double *vx, const double *vy, const double *p, rich_sim **out);
+
+/* Advance up to max_steps steps, stopping early once the time reaches t_end
+   (the last step is shortened to land on t_end).  Each step: a0 on the host
+   for the current points, then a1-a9 on the device.  info may be NULL.
+   Errors: RICH_ENEGATIVE / RICH_ENAN (state left at the last good step),
+   RICH_ETESS, RICH_EDUPLICATE, RICH_ECUDA. */
+int rich_step(rich_sim *s, int32_t max_steps, double t_end, rich_step_info *info);
+
+/* Primitive fields and cell areas on the current generating points (each
+   output may be NULL; n must equal the simulation's size).  If the points
+   moved since the last tessellation this tessellates and recomputes the
+   geometry first. */
+int rich_get_state(rich_sim *s, int64_t n, double *x, double *y, double *rho, double *vx, double *vy,
+                   double *p, double *area);
+
+/* Extensive conserved variables and generating points (each may be NULL). */
+int rich_get_conserved(rich_sim *s, int64_t n, double *x, double *y, double *m, double *px, double *py,
+                       double *E);
+
+/* Release the handle and all its device memory.  NULL is ignored. */
+void rich_destroy(rich_sim *s);
+
+const char *rich_strerror(int code);
+const char *rich_last_error(void);
+
+/* ---- pieces of a step, for measurement and inspection ------------------- */
+
+/* Launch all device work of this handle on the given cudaStream_t (NULL:
+   the handle's own stream).  The caller keeps the stream alive. */
+int rich_set_stream(rich_sim *s, void *cuda_stream);
+
+/* a0 for the current points: copy points device->host, tessellate on the
+   host, upload the connectivity.  Synchronous. */
+int rich_tessellate(rich_sim *s, rich_step_info *info);
+
+/* Enqueue a1-a9 for one step on the current connectivity (asynchronous; no
+   host synchronisation).  Requires a current tessellation. */
+int rich_sweep(rich_sim *s, double t_end);
+
+/* Wait for the enqueued sweep, read time step, time and status flags.
+   Returns RICH_ENEGATIVE / RICH_ENAN if the last sweep failed (then the
+   state is rolled back to before that sweep). */
+int rich_sync(rich_sim *s, rich_step_info *info);
+
+/* Per-cell diagnostics of the last sweep, caller's order, n doubles:
+   0 area, 1-2 centre of mass, 3-6 rho vx vy p, 7 c_s, 8-15 unlimited gradient
+   (d/dx, d/dy of rho, vx, vy, p), 16-23 limited gradient, 24-25 w,
+   26 TESS flag, 27-30 alpha (rho, vx, vy, p), 31 dt (same value in every cell). */
+int rich_get_field(rich_sim *s, int32_t field, int64_t n, double *out);
+
+/* Per-stage device times of the last synchronised sweep, from CUDA events
+   recorded on the launching stream between the stages (enabled by
+   rich_set_profiling; off by default).  Stages, in launch order:
+   k_circumcentre, k_edge_geometry, k_cell_geometry, dt_reset (a memset),
+   k_cell_gradient, k_edge_flux, k_cell_update.  *count receives the number of
+   stages; up to cap values (milliseconds) are written to ms. */
+int rich_set_profiling(rich_sim *s, int32_t on);
+int rich_kernel_times(rich_sim *s, int32_t cap, double *ms, int32_t *count);
+const char *rich_kernel_name(int32_t stage);
+
+/* Number of cells of the handle. */
+int64_t rich_num_cells(const rich_sim *s);
+
+/* ---- host-only entry points (no GPU needed) ----------------------------- */
+
+/* Delaunay triangulation of n distinct points with the library's host
+   builder (exact, tie-broken predicates).  Writes up to cap triangles (3
+   point ids each; ids >= n are the corners of the enclosing triangle) and
+   sets *ntri.  Returns RICH_EDUPLICATE, RICH_ETESS or RICH_EINVAL (cap too
+   small, *ntri then holds the size needed). */
+int rich_delaunay_host(int64_t n, const double *x, const double *y, int64_t cap, int32_t *tris, int64_t *ntri);
+
+/* Voronoi neighbour rings of the n real cells of a box with ghosts (host a0
+   only): ptr[n+1] offsets, and for each ring slot the neighbour's position
+   (nbx, nby) and its source cell (caller order) in counter-clockwise order.
+   cap is the capacity of nbx/nby/nbsrc; *nslots receives the size needed. */
+int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const double *y, int64_t cap,
+                    int64_t *ptr, double *nbx, double *nby, int64_t *nbsrc, int64_t *nslots);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

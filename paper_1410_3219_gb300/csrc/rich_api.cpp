@@ -1,0 +1,611 @@
+// C ABI of the library (include/rich.h): owns the device memory of a
+// simulation, runs the host tessellation (a0) and enqueues the device sweep
+// (a1-a9) on a CUDA stream.  There is no CPU fallback: without a CUDA device
+// rich_init_mesh fails with RICH_ENODEV.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rich.h"
+#include "mesh.h"
+#include "sweep.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                            \
+    do {                                                                                          \
+        cudaError_t err_ = (expr);                                                                \
+        if (err_ != cudaSuccess)                                                                  \
+            return fail(err_ == cudaErrorMemoryAllocation ? RICH_ENOMEM : RICH_ECUDA,             \
+                        std::string(#expr) + ": " + cudaGetErrorString(err_));                    \
+    } while (0)
+
+struct DBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~DBuf() { if (p) cudaFree(p); }
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= cap && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = bytes + bytes / 4 + 256;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+double now_ms()
+{
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int mesh_rc(int rc)
+{
+    switch (rc) {
+    case 0: return RICH_OK;
+    case -2: return fail(RICH_EDUPLICATE, "two generating points coincide");
+    case -4: return fail(RICH_ETOOFEW, "too few points: the ghost band cannot close every cell");
+    default: return fail(RICH_ETESS, "tessellation failed");
+    }
+}
+
+bool valid_config(const rich_config *c)
+{
+    return c && c->gamma > 1.0 && std::isfinite(c->gamma) && c->cfl > 0.0 && c->x1 > c->x0 && c->y1 > c->y0 &&
+           (c->boundary == RICH_BC_REFLECTIVE || c->boundary == RICH_BC_PERIODIC) &&
+           (c->motion == RICH_MESH_LAGRANGIAN || c->motion == RICH_MESH_EULERIAN) && c->limiter >= 0 &&
+           c->limiter <= 2 && c->scheme == RICH_SCHEME_EXTRAPOLATED && c->precision == RICH_FP64 && c->chi >= 0 &&
+           c->eta >= 0 && c->theta >= 0 && c->delta_p >= 0 && c->delta_v >= 0;
+}
+
+bool point_inside(const rich_config *c, double x, double y)
+{
+    if (c->boundary == RICH_BC_PERIODIC) return x >= c->x0 && x < c->x1 && y >= c->y0 && y < c->y1;
+    return x > c->x0 && x < c->x1 && y > c->y0 && y < c->y1;
+}
+
+}  // namespace
+
+struct rich_sim {
+    rich_config cfg{};
+    int32_t n = 0;
+    std::vector<int32_t> perm;  // internal -> caller index
+    std::vector<double> hx, hy; // host copy of the points (internal order)
+    rich::Delaunay dt;
+    rich::HostMesh hm;
+    double t = 0.0;
+    int cur = 0;
+    bool tess_current = false;
+    bool pending = false;
+    bool geometry_current = false;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool profiling = false;
+    cudaEvent_t kev[rich::NUM_STAGES + 1] = {};
+    double kms[rich::NUM_STAGES] = {};
+    double last_dt = 0.0;
+    // device buffers
+    DBuf x[2], y[2], U[2];
+    DBuf A, ox, oy, W, cs, g, gl, alpha, wx, wy, tess, cell_ptr, initW;
+    DBuf gx, gy, gsrc, gxf;
+    DBuf tri, ccx, ccy;
+    DBuf slot_nb, slot_tri, slot_edge;
+    DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F;
+    DBuf scal;  // dtmin bits, dt, status
+
+    ~rich_sim()
+    {
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        for (cudaEvent_t e : kev)
+            if (e) cudaEventDestroy(e);
+        if (own_stream) cudaStreamDestroy(own_stream);
+    }
+
+    rich::SweepParams params() const
+    {
+        rich::SweepParams p{};
+        p.gamma = cfg.gamma; p.cfl = cfg.cfl; p.chi = cfg.chi; p.eta = cfg.eta; p.theta = cfg.theta;
+        p.delta_v = cfg.delta_v; p.delta_p = cfg.delta_p;
+        p.x0 = cfg.x0; p.x1 = cfg.x1; p.y0 = cfg.y0; p.y1 = cfg.y1;
+        p.boundary = cfg.boundary; p.motion = cfg.motion; p.limiter = cfg.limiter;
+        p.n = n;
+        p.ng = hm.g;
+        p.T = (int32_t)(hm.tri.size() / 3);
+        p.E = (int32_t)hm.edge_l.size();
+        p.S = (int32_t)hm.slot_nb.size();
+        p.x = x[cur].as<double>(); p.y = y[cur].as<double>();
+        p.xn = x[1 - cur].as<double>(); p.yn = y[1 - cur].as<double>();
+        p.gx = gx.as<double>(); p.gy = gy.as<double>();
+        p.tri = tri.as<int32_t>(); p.cell_ptr = cell_ptr.as<int32_t>();
+        p.slot_nb = slot_nb.as<int32_t>(); p.slot_tri = slot_tri.as<int32_t>(); p.slot_edge = slot_edge.as<int32_t>();
+        p.edge_l = edge_l.as<int32_t>(); p.edge_r = edge_r.as<int32_t>();
+        p.edge_ta = edge_ta.as<int32_t>(); p.edge_tb = edge_tb.as<int32_t>();
+        p.ghost_src = gsrc.as<int32_t>(); p.ghost_xf = gxf.as<int32_t>();
+        p.ccx = ccx.as<double>(); p.ccy = ccy.as<double>();
+        p.eL = eL.as<double>(); p.emlx = emlx.as<double>(); p.emly = emly.as<double>();
+        p.emrx = emrx.as<double>(); p.emry = emry.as<double>();
+        p.enx = enx.as<double>(); p.eny = eny.as<double>(); p.eqx = eqx.as<double>(); p.eqy = eqy.as<double>();
+        p.A = A.as<double>(); p.ox = ox.as<double>(); p.oy = oy.as<double>();
+        p.U = U[cur].as<double>(); p.Un = U[1 - cur].as<double>();
+        p.W = W.as<double>(); p.cs = cs.as<double>(); p.g = g.as<double>(); p.gl = gl.as<double>();
+        p.alpha = alpha.as<double>(); p.wx = wx.as<double>(); p.wy = wy.as<double>();
+        p.tess = tess.as<int32_t>(); p.F = F.as<double>();
+        char *sc = scal.as<char>();
+        p.dtmin_bits = reinterpret_cast<unsigned long long *>(sc);
+        p.dt_out = reinterpret_cast<double *>(sc + 8);
+        p.status = reinterpret_cast<int32_t *>(sc + 16);
+        p.remaining = 0.0;
+        return p;
+    }
+};
+
+namespace {
+
+template <class T> cudaError_t upload(DBuf &b, const std::vector<T> &v, cudaStream_t st)
+{
+    cudaError_t e = b.ensure(sizeof(T) * (v.size() + 1));
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
+}
+
+int alloc_cells(rich_sim *s)
+{
+    const size_t n = (size_t)s->n, d = sizeof(double);
+    for (int k = 0; k < 2; k++) {
+        CUDA_TRY(s->x[k].ensure(n * d));
+        CUDA_TRY(s->y[k].ensure(n * d));
+        CUDA_TRY(s->U[k].ensure(4 * n * d));
+    }
+    CUDA_TRY(s->A.ensure(n * d)); CUDA_TRY(s->ox.ensure(n * d)); CUDA_TRY(s->oy.ensure(n * d));
+    CUDA_TRY(s->W.ensure(4 * n * d)); CUDA_TRY(s->cs.ensure(n * d));
+    CUDA_TRY(s->g.ensure(8 * n * d)); CUDA_TRY(s->gl.ensure(8 * n * d)); CUDA_TRY(s->alpha.ensure(4 * n * d));
+    CUDA_TRY(s->wx.ensure(n * d)); CUDA_TRY(s->wy.ensure(n * d)); CUDA_TRY(s->tess.ensure(n * 4));
+    CUDA_TRY(s->scal.ensure(64));
+    CUDA_TRY(cudaMemsetAsync(s->scal.p, 0, 64, s->stream));
+    return RICH_OK;
+}
+
+// host tessellation of the current points + upload of the connectivity
+int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
+{
+    double t0 = now_ms();
+    if (fetch_points) {
+        CUDA_TRY(cudaMemcpyAsync(s->hx.data(), s->x[s->cur].p, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(s->hy.data(), s->y[s->cur].p, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+    }
+    double t1 = now_ms();
+    rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
+    int rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->dt, s->hm);
+    if (rc) return mesh_rc(rc);
+    double t2 = now_ms();
+    const rich::HostMesh &m = s->hm;
+    const size_t T = m.tri.size() / 3, E = m.edge_l.size(), d = sizeof(double);
+    CUDA_TRY(upload(s->gx, m.gx, s->stream));
+    CUDA_TRY(upload(s->gy, m.gy, s->stream));
+    CUDA_TRY(upload(s->gsrc, m.ghost_src, s->stream));
+    CUDA_TRY(upload(s->gxf, m.ghost_xf, s->stream));
+    CUDA_TRY(upload(s->tri, m.tri, s->stream));
+    CUDA_TRY(upload(s->cell_ptr, m.cell_ptr, s->stream));
+    CUDA_TRY(upload(s->slot_nb, m.slot_nb, s->stream));
+    CUDA_TRY(upload(s->slot_tri, m.slot_tri, s->stream));
+    CUDA_TRY(upload(s->slot_edge, m.slot_edge, s->stream));
+    CUDA_TRY(upload(s->edge_l, m.edge_l, s->stream));
+    CUDA_TRY(upload(s->edge_r, m.edge_r, s->stream));
+    CUDA_TRY(upload(s->edge_ta, m.edge_ta, s->stream));
+    CUDA_TRY(upload(s->edge_tb, m.edge_tb, s->stream));
+    CUDA_TRY(s->ccx.ensure((T + 1) * d)); CUDA_TRY(s->ccy.ensure((T + 1) * d));
+    for (DBuf *b : {&s->eL, &s->emlx, &s->emly, &s->emrx, &s->emry, &s->enx, &s->eny, &s->eqx, &s->eqy})
+        CUDA_TRY(b->ensure((E + 1) * d));
+    CUDA_TRY(s->F.ensure((4 * E + 1) * d));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    double t3 = now_ms();
+    s->tess_current = true;
+    s->geometry_current = false;
+    if (info) {
+        info->tess_ms += t2 - t1;
+        info->copy_ms += (t1 - t0) + (t3 - t2);
+        info->n_ghost = m.g;
+        info->n_tri = (int64_t)T;
+        info->n_edges = (int64_t)E;
+        info->n_slots = (int64_t)m.slot_nb.size();
+    }
+    return RICH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rich_default_config(rich_config *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->gamma = 5.0 / 3.0;
+    c->cfl = 0.3;
+    c->boundary = RICH_BC_PERIODIC;
+    c->x0 = 0.0; c->x1 = 1.0; c->y0 = 0.0; c->y1 = 1.0;
+    c->motion = RICH_MESH_LAGRANGIAN;
+    c->chi = 0.15; c->eta = 0.02;
+    c->theta = 0.5; c->delta_v = 0.2; c->delta_p = 0.7;
+    c->limiter = RICH_LIM_SWITCHED;
+    c->scheme = RICH_SCHEME_EXTRAPOLATED;
+    c->precision = RICH_FP64;
+}
+
+const char *rich_strerror(int code)
+{
+    switch (code) {
+    case RICH_OK: return "ok";
+    case RICH_EINVAL: return "invalid argument";
+    case RICH_EDUPLICATE: return "coincident generating points";
+    case RICH_ETESS: return "tessellation failed";
+    case RICH_ETOOFEW: return "too few points for the ghost band";
+    case RICH_ENEGATIVE: return "non-positive mass or thermal energy, or a point left the box";
+    case RICH_ENAN: return "non-finite value";
+    case RICH_ENOMEM: return "out of memory";
+    case RICH_ECUDA: return "CUDA error";
+    case RICH_ENODEV: return "no CUDA device";
+    case RICH_ESTATE: return "call not valid in the current state";
+    default: return "unknown error";
+    }
+}
+
+const char *rich_last_error(void) { return g_last_error.c_str(); }
+
+int64_t rich_num_cells(const rich_sim *s) { return s ? s->n : -1; }
+
+int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const double *y, const double *rho,
+                   const double *vx, const double *vy, const double *p, rich_sim **out)
+{
+    if (!out) return fail(RICH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!valid_config(cfg)) return fail(RICH_EINVAL, "invalid configuration");
+    if (n < 3 || n > (int64_t)1 << 30) return fail(RICH_EINVAL, "n must be in [3, 2^30]");
+    if (!x || !y || !rho || !vx || !vy || !p) return fail(RICH_EINVAL, "NULL input array");
+    for (int64_t i = 0; i < n; i++) {
+        if (!std::isfinite(x[i]) || !std::isfinite(y[i]) || !point_inside(cfg, x[i], y[i]))
+            return fail(RICH_EINVAL, "point " + std::to_string(i) + " outside the box");
+        if (!(rho[i] > 0) || !(p[i] > 0) || !std::isfinite(rho[i]) || !std::isfinite(p[i]) || !std::isfinite(vx[i]) ||
+            !std::isfinite(vy[i]))
+            return fail(RICH_EINVAL, "bad primitive values at point " + std::to_string(i));
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(RICH_ENODEV, "no CUDA device");
+    rich_sim *s = new (std::nothrow) rich_sim();
+    if (!s) return fail(RICH_ENOMEM, "host allocation");
+    s->cfg = *cfg;
+    s->n = (int32_t)n;
+    // renumber cells along a Hilbert curve for locality
+    rich::hilbert_order(s->n, x, y, s->perm);
+    s->hx.resize(n);
+    s->hy.resize(n);
+    std::vector<double> Wh(4 * (size_t)n);
+    for (int32_t k = 0; k < s->n; k++) {
+        int32_t u = s->perm[k];
+        s->hx[k] = x[u];
+        s->hy[k] = y[u];
+        Wh[k] = rho[u];
+        Wh[n + k] = vx[u];
+        Wh[2 * n + k] = vy[u];
+        Wh[3 * n + k] = p[u];
+    }
+    int rc = RICH_OK;
+    auto bail = [&](int code) { delete s; return code; };
+    if (cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(RICH_ECUDA, "stream creation failed"));
+    s->stream = s->own_stream;
+    if (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess)
+        return bail(fail(RICH_ECUDA, "event creation failed"));
+    if ((rc = alloc_cells(s)) != RICH_OK) return bail(rc);
+    if (s->x[0].ensure(n * 8) != cudaSuccess) return bail(fail(RICH_ENOMEM, "device points"));
+    cudaMemcpyAsync(s->x[0].p, s->hx.data(), n * 8, cudaMemcpyHostToDevice, s->stream);
+    cudaMemcpyAsync(s->y[0].p, s->hy.data(), n * 8, cudaMemcpyHostToDevice, s->stream);
+    if ((rc = tessellate(s, nullptr, false)) != RICH_OK) return bail(rc);
+    if (s->initW.ensure(4 * n * 8) != cudaSuccess) return bail(fail(RICH_ENOMEM, "device primitives"));
+    cudaMemcpyAsync(s->initW.p, Wh.data(), 4 * n * 8, cudaMemcpyHostToDevice, s->stream);
+    rich::SweepParams prm = s->params();
+    prm.Un = s->U[0].as<double>();
+    for (int k = 0; k < rich::GEOMETRY_STAGES; k++) rich::launch_stage(k, prm, s->initW.as<double>(), s->stream);
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(fail(RICH_ECUDA, std::string("init: ") + cudaGetErrorString(e)));
+    s->geometry_current = false;  // W not yet derived from U
+    *out = s;
+    return RICH_OK;
+}
+
+void rich_destroy(rich_sim *s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    delete s;
+}
+
+int rich_set_stream(rich_sim *s, void *stream)
+{
+    if (!s) return fail(RICH_EINVAL, "NULL handle");
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    s->stream = stream ? static_cast<cudaStream_t>(stream) : s->own_stream;
+    return RICH_OK;
+}
+
+int rich_set_profiling(rich_sim *s, int32_t on)
+{
+    if (!s) return fail(RICH_EINVAL, "NULL handle");
+    if (on && !s->kev[0])
+        for (cudaEvent_t &e : s->kev) CUDA_TRY(cudaEventCreate(&e));
+    s->profiling = on != 0;
+    return RICH_OK;
+}
+
+int rich_kernel_times(rich_sim *s, int32_t cap, double *ms, int32_t *count)
+{
+    if (!s || !count) return fail(RICH_EINVAL, "bad arguments");
+    *count = rich::NUM_STAGES;
+    if (!s->profiling) return fail(RICH_ESTATE, "profiling is off");
+    for (int k = 0; k < rich::NUM_STAGES && k < cap; k++) ms[k] = s->kms[k];
+    return RICH_OK;
+}
+
+const char *rich_kernel_name(int32_t k) { return rich::stage_name(k); }
+
+int rich_tessellate(rich_sim *s, rich_step_info *info)
+{
+    if (!s) return fail(RICH_EINVAL, "NULL handle");
+    if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
+    return tessellate(s, info, true);
+}
+
+int rich_sweep(rich_sim *s, double t_end)
+{
+    if (!s) return fail(RICH_EINVAL, "NULL handle");
+    if (!s->tess_current) return fail(RICH_ESTATE, "no current tessellation");
+    if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
+    if (!(t_end > s->t)) return fail(RICH_EINVAL, "t_end must exceed the current time");
+    rich::SweepParams p = s->params();
+    p.remaining = t_end - s->t;
+    CUDA_TRY(cudaEventRecord(s->ev0, s->stream));
+    for (int k = 0; k < rich::NUM_STAGES; k++) {
+        if (s->profiling) CUDA_TRY(cudaEventRecord(s->kev[k], s->stream));
+        rich::launch_stage(k, p, nullptr, s->stream);
+    }
+    if (s->profiling) CUDA_TRY(cudaEventRecord(s->kev[rich::NUM_STAGES], s->stream));
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(s->ev1, s->stream));
+    s->pending = true;
+    return RICH_OK;
+}
+
+int rich_sync(rich_sim *s, rich_step_info *info)
+{
+    if (!s) return fail(RICH_EINVAL, "NULL handle");
+    if (!s->pending) return fail(RICH_ESTATE, "no sweep pending");
+    double t0 = now_ms();
+    double dt = 0.0;
+    int32_t status = 0;
+    char *sc = s->scal.as<char>();
+    CUDA_TRY(cudaMemcpyAsync(&dt, sc + 8, 8, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(&status, sc + 16, 4, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    s->pending = false;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+    if (s->profiling)
+        for (int k = 0; k < rich::NUM_STAGES; k++) {
+            float km = 0.0f;
+            cudaEventElapsedTime(&km, s->kev[k], s->kev[k + 1]);
+            s->kms[k] = km;
+        }
+    if (info) {
+        info->sweep_ms += ms;
+        info->copy_ms += now_ms() - t0;
+    }
+    s->geometry_current = true;  // diagnostics describe this sweep
+    if (status) {
+        CUDA_TRY(cudaMemsetAsync(sc + 16, 0, 4, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (status & rich::ST_NAN) return fail(RICH_ENAN, "non-finite state after the step");
+        if (status & rich::ST_LEFT_BOX) return fail(RICH_ENEGATIVE, "a generating point left the box");
+        return fail(RICH_ENEGATIVE, "non-positive mass or thermal energy after the step");
+    }
+    s->cur = 1 - s->cur;
+    s->last_dt = dt;
+    s->t += dt;
+    s->tess_current = false;
+    if (info) {
+        info->steps_done += 1;
+        info->t = s->t;
+        info->dt_last = dt;
+    }
+    return RICH_OK;
+}
+
+int rich_step(rich_sim *s, int32_t max_steps, double t_end, rich_step_info *info)
+{
+    if (!s) return fail(RICH_EINVAL, "NULL handle");
+    if (info) std::memset(info, 0, sizeof(*info));
+    for (int32_t k = 0; k < max_steps; k++) {
+        if (!(s->t < t_end)) break;
+        int rc;
+        if (!s->tess_current && (rc = tessellate(s, info, true)) != RICH_OK) return rc;
+        if ((rc = rich_sweep(s, t_end)) != RICH_OK) return rc;
+        double before = s->t;
+        if ((rc = rich_sync(s, info)) != RICH_OK) return rc;
+        if (s->last_dt >= t_end - before) s->t = t_end;  // landed on t_end
+        if (info) info->t = s->t;
+    }
+    if (info) {
+        info->t = s->t;
+        info->dt_last = s->last_dt;
+    }
+    return RICH_OK;
+}
+
+static int ensure_geometry(rich_sim *s)
+{
+    if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
+    if (!s->tess_current) {
+        int rc = tessellate(s, nullptr, true);
+        if (rc) return rc;
+    }
+    rich::SweepParams p = s->params();
+    for (int k = 0; k < rich::GEOMETRY_STAGES; k++) rich::launch_stage(k, p, nullptr, s->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return RICH_OK;
+}
+
+static void unpermute(const rich_sim *s, const double *internal, double *out)
+{
+    for (int32_t k = 0; k < s->n; k++) out[s->perm[k]] = internal[k];
+}
+
+static int fetch(rich_sim *s, const void *dev, std::vector<double> &h, size_t count)
+{
+    h.resize(count);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), dev, count * 8, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return RICH_OK;
+}
+
+int rich_get_state(rich_sim *s, int64_t n, double *x, double *y, double *rho, double *vx, double *vy, double *p,
+                   double *area)
+{
+    if (!s || n != s->n) return fail(RICH_EINVAL, "bad handle or size");
+    int rc = ensure_geometry(s);
+    if (rc) return rc;
+    std::vector<double> h;
+    const size_t N = (size_t)s->n;
+    if (x) { if ((rc = fetch(s, s->x[s->cur].p, h, N))) return rc; unpermute(s, h.data(), x); }
+    if (y) { if ((rc = fetch(s, s->y[s->cur].p, h, N))) return rc; unpermute(s, h.data(), y); }
+    double *outs[4] = {rho, vx, vy, p};
+    if (rho || vx || vy || p) {
+        if ((rc = fetch(s, s->W.p, h, 4 * N))) return rc;
+        for (int v = 0; v < 4; v++)
+            if (outs[v]) unpermute(s, h.data() + v * N, outs[v]);
+    }
+    if (area) { if ((rc = fetch(s, s->A.p, h, N))) return rc; unpermute(s, h.data(), area); }
+    return RICH_OK;
+}
+
+int rich_get_conserved(rich_sim *s, int64_t n, double *x, double *y, double *m, double *px, double *py, double *E)
+{
+    if (!s || n != s->n) return fail(RICH_EINVAL, "bad handle or size");
+    if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
+    std::vector<double> h;
+    int rc;
+    const size_t N = (size_t)s->n;
+    if (x) { if ((rc = fetch(s, s->x[s->cur].p, h, N))) return rc; unpermute(s, h.data(), x); }
+    if (y) { if ((rc = fetch(s, s->y[s->cur].p, h, N))) return rc; unpermute(s, h.data(), y); }
+    double *outs[4] = {m, px, py, E};
+    if (m || px || py || E) {
+        if ((rc = fetch(s, s->U[s->cur].p, h, 4 * N))) return rc;
+        for (int v = 0; v < 4; v++)
+            if (outs[v]) unpermute(s, h.data() + v * N, outs[v]);
+    }
+    return RICH_OK;
+}
+
+int rich_get_field(rich_sim *s, int32_t f, int64_t n, double *out)
+{
+    if (!s || n != s->n || !out) return fail(RICH_EINVAL, "bad arguments");
+    if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
+    const size_t N = (size_t)s->n;
+    std::vector<double> h, h2;
+    int rc;
+    // the diagnostics refer to the points before the last completed step
+    const int prev = s->geometry_current && !s->tess_current ? 1 - s->cur : s->cur;
+    if (f == 0) rc = fetch(s, s->A.p, h, N);
+    else if (f == 1 || f == 2) {
+        if ((rc = fetch(s, (f == 1 ? s->ox : s->oy).p, h, N))) return rc;
+        rc = fetch(s, (f == 1 ? s->x[prev] : s->y[prev]).p, h2, N);
+        for (size_t k = 0; k < N; k++) h[k] += h2[k];
+    } else if (f >= 3 && f <= 6) {
+        if ((rc = fetch(s, s->W.p, h2, 4 * N))) return rc;
+        h.assign(h2.begin() + (f - 3) * N, h2.begin() + (f - 2) * N);
+    } else if (f == 7) rc = fetch(s, s->cs.p, h, N);
+    else if (f >= 8 && f <= 23) {
+        const DBuf &b = f < 16 ? s->g : s->gl;
+        int c = (f - 8) % 8;
+        if ((rc = fetch(s, b.p, h2, 8 * N))) return rc;
+        h.assign(h2.begin() + c * N, h2.begin() + (c + 1) * N);
+    } else if (f == 24 || f == 25) rc = fetch(s, (f == 24 ? s->wx : s->wy).p, h, N);
+    else if (f == 26) {
+        std::vector<int32_t> ti(N);
+        CUDA_TRY(cudaMemcpyAsync(ti.data(), s->tess.p, N * 4, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        h.resize(N);
+        for (size_t k = 0; k < N; k++) h[k] = ti[k];
+        rc = RICH_OK;
+    } else if (f >= 27 && f <= 30) {
+        if ((rc = fetch(s, s->alpha.p, h2, 4 * N))) return rc;
+        h.assign(h2.begin() + (f - 27) * N, h2.begin() + (f - 26) * N);
+    } else if (f == 31) {
+        h.assign(N, s->last_dt);
+        rc = RICH_OK;
+    } else
+        return fail(RICH_EINVAL, "unknown field");
+    if (rc) return rc;
+    unpermute(s, h.data(), out);
+    return RICH_OK;
+}
+
+int rich_delaunay_host(int64_t n, const double *x, const double *y, int64_t cap, int32_t *tris, int64_t *ntri)
+{
+    if (n < 1 || !x || !y || !ntri) return fail(RICH_EINVAL, "bad arguments");
+    rich::Delaunay dt;
+    int rc = dt.build(x, y, (int32_t)n);
+    if (rc == -2) return fail(RICH_EDUPLICATE, "two points coincide");
+    if (rc) return fail(RICH_ETESS, "triangulation failed");
+    *ntri = (int64_t)dt.tris.size();
+    if (cap < *ntri || !tris) return fail(RICH_EINVAL, "capacity too small");
+    for (size_t t = 0; t < dt.tris.size(); t++)
+        for (int k = 0; k < 3; k++) tris[3 * t + k] = dt.tris[t].v[k];
+    return RICH_OK;
+}
+
+int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const double *y, int64_t cap, int64_t *ptr,
+                    double *nbx, double *nby, int64_t *nbsrc, int64_t *nslots)
+{
+    if (!valid_config(cfg) || n < 3 || !x || !y || !nslots || !ptr) return fail(RICH_EINVAL, "bad arguments");
+    for (int64_t i = 0; i < n; i++)
+        if (!point_inside(cfg, x[i], y[i])) return fail(RICH_EINVAL, "point outside the box");
+    rich::Delaunay dt;
+    rich::HostMesh m;
+    rich::BoxConfig box{cfg->boundary, cfg->x0, cfg->x1, cfg->y0, cfg->y1};
+    int rc = rich::build_host_mesh(box, (int32_t)n, x, y, dt, m);
+    if (rc) return mesh_rc(rc);
+    *nslots = (int64_t)m.slot_nb.size();
+    for (int64_t i = 0; i <= n; i++) ptr[i] = m.cell_ptr[i];
+    if (cap < *nslots || !nbx || !nby || !nbsrc) return fail(RICH_EINVAL, "capacity too small");
+    for (size_t s = 0; s < m.slot_nb.size(); s++) {
+        int32_t q = m.slot_nb[s];
+        if (q < n) { nbx[s] = x[q]; nby[s] = y[q]; nbsrc[s] = q; }
+        else { nbx[s] = m.gx[q - n]; nby[s] = m.gy[q - n]; nbsrc[s] = m.ghost_src[q - n]; }
+    }
+    return RICH_OK;
+}
+
+}  // extern "C"

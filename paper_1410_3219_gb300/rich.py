@@ -1,0 +1,268 @@
+"""Thin ctypes binding of librich.so (include/rich.h).
+
+The functions carry the names of the C entry points and only marshal
+arguments; every step of the sweep runs in the library's CUDA kernels.  The
+library is loaded on first use; if it is missing, or the machine has no CUDA
+device, the calls raise instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librich.so")
+
+RICH_OK = 0
+ERRORS = {-1: "EINVAL", -2: "EDUPLICATE", -3: "ETESS", -4: "ETOOFEW", -5: "ENEGATIVE", -6: "ENAN",
+          -7: "ENOMEM", -8: "ECUDA", -9: "ENODEV", -10: "ESTATE"}
+
+FIELDS = {"area": 0, "cx": 1, "cy": 2, "rho": 3, "vx": 4, "vy": 5, "p": 6, "cs": 7, "grad": 8,
+          "lgrad": 16, "wx": 24, "wy": 25, "tess": 26, "alpha": 27, "dt": 31}
+
+# names of every entry point declared in include/rich.h
+EXPORTS = ["rich_default_config", "rich_init_mesh", "rich_step", "rich_get_state", "rich_get_conserved",
+           "rich_destroy", "rich_strerror", "rich_last_error", "rich_set_stream", "rich_tessellate",
+           "rich_sweep", "rich_sync", "rich_get_field", "rich_num_cells", "rich_delaunay_host",
+           "rich_rings_host", "rich_set_profiling", "rich_kernel_times", "rich_kernel_name"]
+
+
+class RichError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rich_config(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("boundary", C.c_int32),
+                ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+                ("motion", C.c_int32), ("chi", C.c_double), ("eta", C.c_double),
+                ("theta", C.c_double), ("delta_v", C.c_double), ("delta_p", C.c_double),
+                ("limiter", C.c_int32), ("scheme", C.c_int32), ("precision", C.c_int32)]
+
+    @classmethod
+    def from_dict(cls, d):
+        c = cls()
+        _lib().rich_default_config(C.byref(c))
+        for name, _ in cls._fields_:
+            if name in d:
+                setattr(c, name, d[name])
+        return c
+
+
+class rich_step_info(C.Structure):
+    _fields_ = [("steps_done", C.c_int64), ("t", C.c_double), ("dt_last", C.c_double),
+                ("sweep_ms", C.c_double), ("tess_ms", C.c_double), ("copy_ms", C.c_double),
+                ("n_ghost", C.c_int64), ("n_tri", C.c_int64), ("n_edges", C.c_int64), ("n_slots", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_D = C.POINTER(C.c_double)
+_handle = None
+
+
+def _lib():
+    global _handle
+    if _handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P, I64, I32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        L.rich_default_config.argtypes = [C.POINTER(rich_config)]
+        L.rich_default_config.restype = None
+        L.rich_init_mesh.argtypes = [C.POINTER(rich_config), I64] + [_D] * 6 + [C.POINTER(P)]
+        L.rich_step.argtypes = [P, I32, d, C.POINTER(rich_step_info)]
+        L.rich_get_state.argtypes = [P, I64] + [_D] * 7
+        L.rich_get_conserved.argtypes = [P, I64] + [_D] * 6
+        L.rich_destroy.argtypes = [P]
+        L.rich_destroy.restype = None
+        L.rich_strerror.argtypes = [C.c_int]
+        L.rich_strerror.restype = C.c_char_p
+        L.rich_last_error.argtypes = []
+        L.rich_last_error.restype = C.c_char_p
+        L.rich_set_stream.argtypes = [P, P]
+        L.rich_tessellate.argtypes = [P, C.POINTER(rich_step_info)]
+        L.rich_sweep.argtypes = [P, d]
+        L.rich_sync.argtypes = [P, C.POINTER(rich_step_info)]
+        L.rich_get_field.argtypes = [P, I32, I64, _D]
+        L.rich_num_cells.argtypes = [P]
+        L.rich_num_cells.restype = I64
+        L.rich_delaunay_host.argtypes = [I64, _D, _D, I64, C.POINTER(C.c_int32), C.POINTER(I64)]
+        L.rich_rings_host.argtypes = [C.POINTER(rich_config), I64, _D, _D, I64, C.POINTER(I64), _D, _D,
+                                      C.POINTER(I64), C.POINTER(I64)]
+        L.rich_set_profiling.argtypes = [P, I32]
+        L.rich_kernel_times.argtypes = [P, I32, _D, C.POINTER(I32)]
+        L.rich_kernel_name.argtypes = [I32]
+        L.rich_kernel_name.restype = C.c_char_p
+        _handle = L
+    return _handle
+
+
+def lib():
+    return _lib()
+
+
+def _check(rc):
+    if rc != RICH_OK:
+        raise RichError(rc, _lib().rich_last_error().decode())
+    return rc
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.shape != (n,):
+        raise ValueError("bad array shape")
+    return a
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+# ---- the C entry points -----------------------------------------------------
+
+def rich_init_mesh(cfg, x, y, rho, vx, vy, p):
+    c = cfg if isinstance(cfg, rich_config) else rich_config.from_dict(cfg)
+    n = len(x)
+    arrs = [_f64(a, n) for a in (x, y, rho, vx, vy, p)]
+    h = C.c_void_p()
+    _check(_lib().rich_init_mesh(C.byref(c), n, *[_p(a) for a in arrs], C.byref(h)))
+    return h
+
+
+def rich_step(h, max_steps=1, t_end=float("inf")):
+    info = rich_step_info()
+    _check(_lib().rich_step(h, max_steps, t_end, C.byref(info)))
+    return info.as_dict()
+
+
+def rich_get_state(h, n):
+    out = [np.zeros(n) for _ in range(7)]
+    _check(_lib().rich_get_state(h, n, *[_p(a) for a in out]))
+    return dict(zip(("x", "y", "rho", "vx", "vy", "p", "area"), out))
+
+
+def rich_get_conserved(h, n):
+    out = [np.zeros(n) for _ in range(6)]
+    _check(_lib().rich_get_conserved(h, n, *[_p(a) for a in out]))
+    return dict(zip(("x", "y", "m", "px", "py", "E"), out))
+
+
+def rich_destroy(h):
+    _lib().rich_destroy(h)
+
+
+def rich_set_stream(h, stream_ptr):
+    _check(_lib().rich_set_stream(h, C.c_void_p(stream_ptr)))
+
+
+def rich_tessellate(h):
+    info = rich_step_info()
+    _check(_lib().rich_tessellate(h, C.byref(info)))
+    return info.as_dict()
+
+
+def rich_sweep(h, t_end=float("inf")):
+    _check(_lib().rich_sweep(h, t_end))
+
+
+def rich_sync(h):
+    info = rich_step_info()
+    _check(_lib().rich_sync(h, C.byref(info)))
+    return info.as_dict()
+
+
+def rich_get_field(h, n, name, comp=0):
+    out = np.zeros(n)
+    _check(_lib().rich_get_field(h, FIELDS[name] + comp, n, _p(out)))
+    return out
+
+
+def rich_set_profiling(h, on=True):
+    _check(_lib().rich_set_profiling(h, 1 if on else 0))
+
+
+def rich_kernel_times(h):
+    ms = np.zeros(16)
+    cnt = C.c_int32()
+    _check(_lib().rich_kernel_times(h, 16, _p(ms), C.byref(cnt)))
+    return {rich_kernel_name(k): float(ms[k]) for k in range(cnt.value)}
+
+
+def rich_kernel_name(k):
+    return _lib().rich_kernel_name(k).decode()
+
+
+def rich_delaunay_host(x, y):
+    x, y = _f64(x), _f64(y)
+    n = len(x)
+    cap = 2 * n + 16
+    tris = np.zeros(3 * cap, np.int32)
+    nt = C.c_int64()
+    _check(_lib().rich_delaunay_host(n, _p(x), _p(y), cap, tris.ctypes.data_as(C.POINTER(C.c_int32)),
+                                     C.byref(nt)))
+    return tris[:3 * nt.value].reshape(-1, 3)
+
+
+def rich_rings_host(cfg, x, y):
+    c = cfg if isinstance(cfg, rich_config) else rich_config.from_dict(cfg)
+    x, y = _f64(x), _f64(y)
+    n = len(x)
+    ptr = np.zeros(n + 1, np.int64)
+    ns = C.c_int64()
+    cap = 12 * n + 64
+    nbx, nby, src = np.zeros(cap), np.zeros(cap), np.zeros(cap, np.int64)
+    I64P = C.POINTER(C.c_int64)
+    _check(_lib().rich_rings_host(C.byref(c), n, _p(x), _p(y), cap, ptr.ctypes.data_as(I64P), _p(nbx), _p(nby),
+                                  src.ctypes.data_as(I64P), C.byref(ns)))
+    k = ns.value
+    return ptr, nbx[:k], nby[:k], src[:k]
+
+
+# ---- convenience wrapper ------------------------------------------------------
+
+class Sim:
+    """One simulation owned by the library (device-resident state)."""
+
+    def __init__(self, wl):
+        self.n = len(wl["x"])
+        self.h = rich_init_mesh(wl["cfg"], wl["x"], wl["y"], wl["rho"], wl["vx"], wl["vy"], wl["p"])
+
+    def close(self):
+        if self.h:
+            rich_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, max_steps=1, t_end=float("inf")):
+        return rich_step(self.h, max_steps, t_end)
+
+    def tessellate(self):
+        return rich_tessellate(self.h)
+
+    def sweep(self, t_end=float("inf")):
+        rich_sweep(self.h, t_end)
+
+    def sync(self):
+        return rich_sync(self.h)
+
+    def set_stream(self, ptr):
+        rich_set_stream(self.h, ptr)
+
+    def state(self):
+        return rich_get_state(self.h, self.n)
+
+    def conserved(self):
+        return rich_get_conserved(self.h, self.n)
+
+    def field(self, name, comp=0):
+        return rich_get_field(self.h, self.n, name, comp)
