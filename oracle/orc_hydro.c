@@ -79,6 +79,7 @@ struct orc_sim {
     double *wx, *wy;
     int *tess;
     double dt;
+    double *x_prev, *y_prev;    /* generating points at the start of the last sweep */
 };
 
 static void *xmalloc(size_t n) { void *p = calloc(1, n > 0 ? n : 1); if (!p) abort(); return p; }
@@ -395,6 +396,8 @@ int orc_create(const orc_config *cfg, int n, const double *x, const double *y, c
     s->alpha = xmalloc(sizeof(double) * 4 * n);
     s->wx = xmalloc(sizeof(double) * n); s->wy = xmalloc(sizeof(double) * n);
     s->tess = xmalloc(sizeof(int) * n);
+    s->x_prev = xmalloc(sizeof(double) * n); s->y_prev = xmalloc(sizeof(double) * n);
+    memcpy(s->x_prev, x, sizeof(double) * n); memcpy(s->y_prev, y, sizeof(double) * n);
     int rc = orc_tessellate(s);
     if (rc != ORC_OK) { orc_destroy(s); return rc; }
     /* areas of the initial cells turn the primitive fields into extensive ones */
@@ -424,6 +427,7 @@ void orc_destroy(orc_sim *s)
     free(s->x); free(s->y); free(s->m); free(s->px); free(s->py); free(s->E);
     free(s->A); free(s->ox); free(s->oy); free(s->W); free(s->cs); free(s->g); free(s->gl);
     free(s->alpha); free(s->wx); free(s->wy); free(s->tess);
+    free(s->x_prev); free(s->y_prev);
     free(s);
 }
 
@@ -470,6 +474,8 @@ int orc_sweep(orc_sim *s, double t_end, double *dt_out)
 
     int rc = geometry_and_primitives(s);
     if (rc) return rc;
+    memcpy(s->x_prev, s->x, sizeof(double) * n);
+    memcpy(s->y_prev, s->y, sizeof(double) * n);
     /* Eq. 1: Green-Gauss gradient of each primitive */
     for (int i = 0; i < n; i++) {
         int lo = s->rptr[i], deg = s->rptr[i + 1] - lo;
@@ -635,6 +641,8 @@ int orc_get_primitives(orc_sim *s, double *rho, double *vx, double *vy, double *
     }
     int rc = geometry_and_primitives(s);
     if (rc) return rc;
+    memcpy(s->x_prev, s->x, sizeof(double) * s->n);
+    memcpy(s->y_prev, s->y, sizeof(double) * s->n);
     for (int i = 0; i < s->n; i++) {
         if (rho) rho[i] = s->W[4 * i];
         if (vx) vx[i] = s->W[4 * i + 1];
@@ -697,8 +705,8 @@ int orc_get_cells(const orc_sim *s, int f, double *out)
     for (int i = 0; i < s->n; i++) {
         double v;
         if (f == 0) v = s->A[i];
-        else if (f == 1) v = s->x[i] + s->ox[i];
-        else if (f == 2) v = s->y[i] + s->oy[i];
+        else if (f == 1) v = s->x_prev[i] + s->ox[i];
+        else if (f == 2) v = s->y_prev[i] + s->oy[i];
         else if (f >= 3 && f <= 6) v = s->W[4 * i + f - 3];
         else if (f == 7) v = s->cs[i];
         else if (f >= 8 && f <= 15) v = s->g[8 * i + f - 8];
