@@ -25,7 +25,8 @@
  *
  * Points the paper leaves open and the reading taken here:
  *   - the limiter's max/min include the cell's own value (so alpha is in [0,1])
- *     and alpha is the minimum over all edges of the cell;
+ *     and alpha is the minimum over all edges of the cell; the neighbours of
+ *     Eqs. 3-8 are the cells sharing an edge longer than 1e-9 sqrt(A_i);
  *   - Eq. 7 reads -div(v) > delta_v c_s/R_i with R_i = sqrt(A_i/pi) and div(v)
  *     from the unlimited gradient; Eq. 8 reads "some neighbour has
  *     min(P_i,P_j)/max(P_i,P_j) < delta_p"; the switch applies to all four
@@ -493,18 +494,25 @@ int orc_sweep(orc_sim *s, double t_end, double *dt_out)
         }
         for (int q = 0; q < 8; q++) s->g[8 * i + q] = acc[q] / s->A[i];
     }
-    /* Eqs. 3-8: slope limiter with the shock switch */
+    /* Eqs. 3-8: slope limiter with the shock switch.  Neighbours are the
+       cells sharing a Voronoi edge of positive length: an edge shorter than
+       1e-9 sqrt(A_i) is a point contact (the Delaunay triangulation of
+       co-circular points is not unique, the Voronoi diagram is). */
     for (int i = 0; i < n; i++) {
         int lo = s->rptr[i], deg = s->rptr[i + 1] - lo;
         const double *Wi = &s->W[4 * i];
         const double *gi = &s->g[8 * i];
         double R = sqrt(s->A[i] / M_PI);
+        double Lmin = 1e-9 * sqrt(s->A[i]);
         int shock = -(gi[2] + gi[5]) > c->delta_v * s->cs[i] / R;
         double fmaxv[4], fminv[4];
         for (int v = 0; v < 4; v++) fmaxv[v] = fminv[v] = Wi[v];
         for (int k = 0; k < deg; k++) {
+            slot_geom G;
+            get_slot(s, i, k, &G);
+            if (G.L <= Lmin) continue;
             double Wj[4];
-            view_W(s, s->rnb[lo + k], Wj);
+            view_W(s, G.j, Wj);
             for (int v = 0; v < 4; v++) {
                 if (Wj[v] > fmaxv[v]) fmaxv[v] = Wj[v];
                 if (Wj[v] < fminv[v]) fminv[v] = Wj[v];
@@ -519,6 +527,7 @@ int orc_sweep(orc_sim *s, double t_end, double *dt_out)
             for (int k = 0; k < deg; k++) {
                 slot_geom G;
                 get_slot(s, i, k, &G);
+                if (G.L <= Lmin) continue;
                 double Wj[4];
                 view_W(s, G.j, Wj);
                 double dphi = gi[2 * v] * (G.mx - s->ox[i]) + gi[2 * v + 1] * (G.my - s->oy[i]);

@@ -156,6 +156,10 @@ __global__ void __launch_bounds__(kBlock) k_cell_gradient(SweepParams p)
         double fmx[4] = {Wi[0], Wi[1], Wi[2], Wi[3]};
         double fmn[4] = {Wi[0], Wi[1], Wi[2], Wi[3]};
         bool shock = false;
+        const double A = p.A[i];
+        // Eqs. 3-8 look at the cells sharing an edge longer than 1e-9 sqrt(A):
+        // shorter edges are point contacts whose presence depends on round-off
+        const double Lmin = 1e-9 * sqrt(A);
         for (int32_t s = lo; s < hi; s++) {
             int32_t es = p.slot_edge[s];
             int32_t e = es >> 1;
@@ -170,12 +174,16 @@ __global__ void __launch_bounds__(kBlock) k_cell_gradient(SweepParams p)
                 double d = Wj[v] - Wi[v], a = 0.5 * (Wi[v] + Wj[v]);
                 acc[2 * v] += L * (d * qx + a * nx);
                 acc[2 * v + 1] += L * (d * qy + a * ny);
-                fmx[v] = fmax(fmx[v], Wj[v]);
-                fmn[v] = fmin(fmn[v], Wj[v]);
             }
-            if (fmin(Wi[3], Wj[3]) < p.delta_p * fmax(Wi[3], Wj[3])) shock = true;
+            if (L > Lmin) {
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    fmx[v] = fmax(fmx[v], Wj[v]);
+                    fmn[v] = fmin(fmn[v], Wj[v]);
+                }
+                if (fmin(Wi[3], Wj[3]) < p.delta_p * fmax(Wi[3], Wj[3])) shock = true;
+            }
         }
-        const double A = p.A[i];
         const double invA = 1.0 / A;
         double g[8];
 #pragma unroll
@@ -185,24 +193,62 @@ __global__ void __launch_bounds__(kBlock) k_cell_gradient(SweepParams p)
         if (-(g[2] + g[5]) * R > p.delta_v * cs) shock = true;
         const bool use_tess = p.limiter == 2 || (p.limiter == 0 && shock);
         const double ox = p.ox[i], oy = p.oy[i];
-        double alpha[4] = {1.0, 1.0, 1.0, 1.0};
-        for (int32_t s = lo; s < hi; s++) {
-            int32_t es = p.slot_edge[s];
-            int32_t e = es >> 1;
-            double mx = (es & 1) ? p.emrx[e] : p.emlx[e];
-            double my = (es & 1) ? p.emry[e] : p.emly[e];
-            double offx = mx - ox, offy = my - oy;
-            double Wj[4];
-            if (use_tess) load_W(p, p.slot_nb[s], Wj);
+        // alpha = min(1, min_j psi_ij) without a division per edge.
+        // AREPO (Eqs. 4-5): psi_ij = (phi_max - phi_i)/dphi for dphi > 0, so the
+        // minimum over those edges sits at the largest dphi (likewise for
+        // dphi < 0); one division per sign and variable.
+        // TESS (Eq. 6): psi_ij = max(theta (phi_j - phi_i)/dphi, 0); the
+        // smallest ratio is found by cross-multiplication, divided once.
+        double alpha[4];
+        if (!use_tess) {
+            double dpos[4] = {0, 0, 0, 0}, dneg[4] = {0, 0, 0, 0};
+            for (int32_t s = lo; s < hi; s++) {
+                int32_t es = p.slot_edge[s];
+                int32_t e = es >> 1;
+                if (!(p.eL[e] > Lmin)) continue;
+                double offx = ((es & 1) ? p.emrx[e] : p.emlx[e]) - ox;
+                double offy = ((es & 1) ? p.emry[e] : p.emly[e]) - oy;
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    double dphi = g[2 * v] * offx + g[2 * v + 1] * offy;
+                    dpos[v] = fmax(dpos[v], dphi);
+                    dneg[v] = fmin(dneg[v], dphi);
+                }
+            }
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                double dphi = g[2 * v] * offx + g[2 * v + 1] * offy;
-                double psi;
-                if (dphi == 0.0) psi = 1.0;
-                else if (use_tess) psi = fmax(p.theta * (Wj[v] - Wi[v]) / dphi, 0.0);
-                else if (dphi > 0.0) psi = (fmx[v] - Wi[v]) / dphi;
-                else psi = (fmn[v] - Wi[v]) / dphi;
-                alpha[v] = fmin(alpha[v], psi);
+                double a = 1.0;
+                if (dpos[v] > 0.0) a = fmin(a, (fmx[v] - Wi[v]) / dpos[v]);
+                if (dneg[v] < 0.0) a = fmin(a, (fmn[v] - Wi[v]) / dneg[v]);
+                alpha[v] = a;
+            }
+        } else {
+            double bn[4] = {0, 0, 0, 0}, bd[4] = {0, 0, 0, 0};  // smallest |N|/|D| so far (bd == 0: none)
+            bool zero[4] = {false, false, false, false};
+            for (int32_t s = lo; s < hi; s++) {
+                int32_t es = p.slot_edge[s];
+                int32_t e = es >> 1;
+                if (!(p.eL[e] > Lmin)) continue;
+                double offx = ((es & 1) ? p.emrx[e] : p.emlx[e]) - ox;
+                double offy = ((es & 1) ? p.emry[e] : p.emly[e]) - oy;
+                double Wj[4];
+                load_W(p, p.slot_nb[s], Wj);
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    double dphi = g[2 * v] * offx + g[2 * v + 1] * offy;
+                    if (dphi == 0.0) continue;
+                    double num = Wj[v] - Wi[v];
+                    if (!(num * dphi > 0.0)) { zero[v] = true; continue; }
+                    double an = fabs(num), ad = fabs(dphi);
+                    if (bd[v] == 0.0 || an * bd[v] < bn[v] * ad) { bn[v] = an; bd[v] = ad; }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                double a = 1.0;
+                if (zero[v]) a = 0.0;
+                else if (bd[v] > 0.0) a = fmin(a, p.theta * bn[v] / bd[v]);
+                alpha[v] = a;
             }
         }
 #pragma unroll

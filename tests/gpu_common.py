@@ -8,7 +8,7 @@ TOL = 1e-12
 
 def rel_err(a, b, scale=None):
     a, b = np.asarray(a), np.asarray(b)
-    s = scale if scale is not None else max(np.max(np.abs(b)), 1e-300)
+    s = max(scale if scale is not None else np.max(np.abs(b)), 1e-300)
     return float(np.max(np.abs(a - b)) / s) if a.size else 0.0
 
 
