@@ -172,6 +172,36 @@ const char *rich_kernel_name(int32_t stage);
 /* Number of cells of the handle. */
 int64_t rich_num_cells(const rich_sim *s);
 
+/* ---- time step without allocation ---------------------------------------- */
+
+/* Largest n accepted by rich_courant_dt_noalloc. */
+#define RICH_NOALLOC_MAX_CELLS (1 << 24)
+
+/* The paper has no counterpart to this entry point; it serves callers that
+   cannot allocate GPU memory when they need the time step: code running
+   inside a memory pool or arena that owns the device, code that must not
+   trigger the device synchronisation an allocation or free can cause, and
+   code that is later replayed from a recorded sequence of launches.
+
+   Computes the Courant time step of the sweep (step a6),
+   dt = cfg->cfl * min_i R_i / (c_i + |v_i - w_i|), R_i = sqrt(area_i/pi),
+   c_i = sqrt(gamma p_i/rho_i) (w = 0 for RICH_MESH_EULERIAN, when wx, wy may
+   be NULL), over n cells whose values are DEVICE arrays of doubles owned by
+   the caller, and writes it to the DEVICE double *dt_out, asynchronously on
+   the cudaStream_t stream (NULL: the default stream).  It allocates nothing:
+   its scratch (one partial minimum per block of 256 cells and a completion
+   counter, 512 KiB) is a fixed array in the library's device image, which
+   every GPU that loads the library holds until the process exits.  The first
+   call on each device looks up that array's address (cudaGetSymbolAddress),
+   so make it before any stream capture.  Every call shares the array and
+   clears its counter: calls that overlap on the GPU (other streams, other
+   host threads) race and must not be issued.
+   Returns RICH_EINVAL for a NULL pointer or n outside [1,
+   RICH_NOALLOC_MAX_CELLS], RICH_ECUDA if the set-up or launch fails. */
+int rich_courant_dt_noalloc(const rich_config *cfg, int64_t n, const double *area, const double *rho,
+                            const double *vx, const double *vy, const double *p, const double *wx,
+                            const double *wy, double *dt_out, void *stream);
+
 /* ---- host-only entry points (no GPU needed) ----------------------------- */
 
 /* Delaunay triangulation of n distinct points with the library's host

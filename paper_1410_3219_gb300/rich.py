@@ -26,7 +26,8 @@ FIELDS = {"area": 0, "cx": 1, "cy": 2, "rho": 3, "vx": 4, "vy": 5, "p": 6, "cs":
 EXPORTS = ["rich_default_config", "rich_init_mesh", "rich_step", "rich_get_state", "rich_get_conserved",
            "rich_destroy", "rich_strerror", "rich_last_error", "rich_set_stream", "rich_tessellate",
            "rich_sweep", "rich_sync", "rich_get_field", "rich_num_cells", "rich_delaunay_host",
-           "rich_rings_host", "rich_set_profiling", "rich_kernel_times", "rich_kernel_name"]
+           "rich_rings_host", "rich_set_profiling", "rich_kernel_times", "rich_kernel_name",
+           "rich_courant_dt_noalloc"]
 
 
 class RichError(RuntimeError):
@@ -98,6 +99,7 @@ def _lib():
         L.rich_kernel_times.argtypes = [P, I32, _D, C.POINTER(I32)]
         L.rich_kernel_name.argtypes = [I32]
         L.rich_kernel_name.restype = C.c_char_p
+        L.rich_courant_dt_noalloc.argtypes = [C.POINTER(rich_config), I64] + [P] * 8 + [P]
         _handle = L
     return _handle
 
@@ -195,6 +197,13 @@ def rich_kernel_times(h):
 
 def rich_kernel_name(k):
     return _lib().rich_kernel_name(k).decode()
+
+
+def rich_courant_dt_noalloc(cfg, n, area, rho, vx, vy, p, wx, wy, dt_out, stream=0):
+    """Device pointers (ints) in, device pointer out; see include/rich.h."""
+    c = cfg if isinstance(cfg, rich_config) else rich_config.from_dict(cfg)
+    ptrs = [C.c_void_p(v) if v else None for v in (area, rho, vx, vy, p, wx, wy, dt_out)]
+    _check(_lib().rich_courant_dt_noalloc(C.byref(c), n, *ptrs, C.c_void_p(stream)))
 
 
 def rich_delaunay_host(x, y):
