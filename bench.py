@@ -30,22 +30,47 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s of Voronoi sweep (FP64 vs FP32-split, batched), % HBM roofline; p99"
 UNIT = "cell-updates/s"
 
-# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x
-# 2 flop x 2.070 GHz (max SM clock); a throughput probe measured 1.19 TFLOP/s.
+# Peaks derived from unit counts and clocks (2.070 GHz max SM clock):
+# FP64: 152 SMs x 2 FMA lanes/clk x 2 flop (an FMA probe measured 1.19 TFLOP/s);
+# FP32: 152 SMs x 128 FMA lanes/clk x 2 flop (the probe measured 69.6 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# HBM: measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), and the
+# compulsory traffic of one cell-update with FP64 state and 32-bit indices:
+# read points 16 + U 32 + connectivity ~28, write U 32 + points 16 = 124 B.
+HBM_PEAK_GBS_FALLBACK = 6800.0
+COMPULSORY_BYTES_PER_CELL = 124
 
-# Algorithmic FP64 operations per unit of work of each kernel, counted from
-# the formulas (add, sub, mul, min, max = 1; fused multiply-add = 2; divide
-# and square root = 1).  Units: triangles, edges or cells.
+# Algorithmic operations per unit of work of each kernel, counted from the
+# formulas (add, sub, mul, min, max, compare = 1; fused multiply-add = 2;
+# divide, square root = 1), split by the pipe they run on in each precision.
+# (per unit, unit kind, extra per ring slot)
 FLOPS = {
-    "k_circumcentre": (24, "tri"),
-    "k_edge_geometry": (31, "edge"),
-    "k_cell_geometry": (22, "cell"),       # + 12 per ring slot
-    "k_cell_gradient": (40, "cell"),       # + 83 per ring slot
-    "k_edge_flux": (224, "edge"),
-    "k_cell_update": (20, "cell"),         # + 4 per ring slot
+    "fp64": {
+        "k_circumcentre": ({"fp64": 24}, "tri", {}),
+        "k_edge_geometry": ({"fp64": 31}, "edge", {}),
+        "k_cell_geometry": ({"fp64": 22}, "cell", {"fp64": 12}),
+        "k_cell_gradient": ({"fp64": 40}, "cell", {"fp64": 83}),
+        "k_edge_flux": ({"fp64": 224}, "edge", {}),
+        "k_cell_update": ({"fp64": 20}, "cell", {"fp64": 4}),
+    },
+    "split": {
+        "k_circumcentre": ({"fp64": 24}, "tri", {}),
+        "k_edge_geometry": ({"fp64": 6, "fp32": 25}, "edge", {}),
+        "k_cell_geometry": ({"fp64": 12, "fp32": 10}, "cell", {"fp64": 12}),
+        "k_cell_gradient": ({"fp32": 40}, "cell", {"fp32": 83}),
+        "k_edge_flux": ({"fp32": 224}, "edge", {}),
+        "k_cell_update": ({"fp64": 20}, "cell", {"fp64": 4}),
+    },
 }
-PER_SLOT = {"k_cell_geometry": 12, "k_cell_gradient": 83, "k_cell_update": 4}
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return HBM_PEAK_GBS_FALLBACK, "fallback"
 
 
 def workload(name):
@@ -109,12 +134,39 @@ class Clocks:
                 "power_w_max": max(pw), "reasons": sorted(reasons)}
 
 
-def kernel_flops(name, units):
-    per, kind = FLOPS[name]
-    f = per * units[kind]
-    if name in PER_SLOT:
-        f += PER_SLOT[name] * units["slot"]
-    return f
+def kernel_flops(prec, name, units):
+    per, kind, slot = FLOPS[prec][name]
+    out = {}
+    for pipe in ("fp64", "fp32"):
+        out[pipe] = per.get(pipe, 0) * units[kind] + slot.get(pipe, 0) * units["slot"]
+    return out
+
+
+def roofline_of(prec, kern_means, units, sweep_ms):
+    """Roofline of the dominant kernel: bound by the pipe that carries most
+    of its issue time (FP64 issues at 1/64 of the FP32 rate)."""
+    dom = max(kern_means, key=kern_means.get)
+    fl = kernel_flops(prec, dom, units)
+    t64 = fl["fp64"] / (FP64_PEAK_TFLOPS * 1e12)
+    t32 = fl["fp32"] / (FP32_PEAK_TFLOPS * 1e12)
+    pipe, peak = ("fp64", FP64_PEAK_TFLOPS) if t64 >= t32 else ("fp32", FP32_PEAK_TFLOPS)
+    achieved = fl[pipe] / (kern_means[dom] / 1e3) / 1e12
+    tot = {"fp64": 0, "fp32": 0}
+    for k in FLOPS[prec]:
+        f = kernel_flops(prec, k, units)
+        tot["fp64"] += f["fp64"]
+        tot["fp32"] += f["fp32"]
+    hbm, src = hbm_peak()
+    cells_per_s = units["cell"] / (sweep_ms / 1e3)
+    return {"bound": "alu", "pipe": pipe, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": ("derived: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz" if pipe == "fp64"
+                            else "derived: 152 SMs x 128 FP32 FMA lanes/clk x 2 flop x 2.07 GHz"),
+            "sweep_fp64_tflops": tot["fp64"] / (sweep_ms / 1e3) / 1e12,
+            "sweep_fp32_tflops": tot["fp32"] / (sweep_ms / 1e3) / 1e12,
+            "hbm_frac_compulsory": cells_per_s * COMPULSORY_BYTES_PER_CELL / (hbm * 1e9),
+            "hbm_peak_gbs": hbm, "hbm_peak_source": src,
+            "kernel_ms": kern_means}
 
 
 def run_ours(args):
@@ -134,55 +186,68 @@ def run_ours(args):
     n = len(wl["x"])
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    sim = rich.Sim(wl)
-    sim.set_stream(stream.cuda_stream)
-    rich.rich_set_profiling(sim.h, True)
-
-    def one_step(timed):
-        info = sim.tessellate()
-        with torch.cuda.stream(stream):
-            flush.zero_()
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            sim.sweep()
-            ev1.record(stream)
-        res = sim.sync()
-        ev1.synchronize()
-        return ev0.elapsed_time(ev1), info, res
-
-    for _ in range(args.warmup):
-        one_step(False)
-
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")) if rank == 0 else None
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    if clocks:
-        clocks.start()
-        time.sleep(0.3)
-    sweep_ms, tess_ms, kern = [], [], {}
-    wall0 = time.perf_counter()
-    units = None
-    for _ in range(args.steps):
-        ms, info, res = one_step(True)
-        sweep_ms.append(ms)
-        tess_ms.append(info["tess_ms"])
-        units = {"tri": info["n_tri"], "edge": info["n_edges"], "cell": n, "slot": info["n_slots"]}
-        for k, v in rich.rich_kernel_times(sim.h).items():
-            kern.setdefault(k, []).append(v)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    if ws > 1:
-        dist.barrier()
-    clk = clocks.stop(local) if clocks else None
 
-    total_sweep_s = sum(sweep_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_sweep_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_sweep_s = float(t.item())
-    value = ws * n * args.steps / total_sweep_s
+    def time_precision(prec, with_clocks):
+        w = dict(wl)
+        w["cfg"] = dict(wl["cfg"], precision=1 if prec == "split" else 0)
+        sim = rich.Sim(w)
+        sim.set_stream(stream.cuda_stream)
+        rich.rich_set_profiling(sim.h, True)
+        rich.rich_set_diagnostics(sim.h, False)
+
+        def one_step():
+            info = sim.tessellate()
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                sim.sweep()
+                ev1.record(stream)
+            sim.sync()
+            ev1.synchronize()
+            return ev0.elapsed_time(ev1), info
+
+        for _ in range(args.warmup):
+            one_step()
+        clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{prec}_r{rank}.csv")) \
+            if (rank == 0 and with_clocks) else None
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        sweep_ms, tess_ms, kern = [], [], {}
+        wall0 = time.perf_counter()
+        units = None
+        for _ in range(args.steps):
+            ms, info = one_step()
+            sweep_ms.append(ms)
+            tess_ms.append(info["tess_ms"])
+            units = {"tri": info["n_tri"], "edge": info["n_edges"], "cell": n, "slot": info["n_slots"]}
+            for k, v in rich.rich_kernel_times(sim.h).items():
+                kern.setdefault(k, []).append(v)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if ws > 1:
+            dist.barrier()
+        clk = clocks.stop(local) if clocks else None
+        sim.close()
+        total_s = sum(sweep_ms) / 1e3
+        if ws > 1:
+            t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_s = float(t.item())
+        means = {k: float(np.mean(v)) for k, v in kern.items() if k != "dt_reset"}
+        return {"value": ws * n * args.steps / total_s, "sweep_ms": sweep_ms, "tess_ms": tess_ms, "wall": wall,
+                "units": units, "kernel_means": means, "clocks": clk}
+
+    res64 = time_precision("fp64", True)
+    res32 = time_precision("split", False)
+    sweep_ms, tess_ms, wall, units, clk = (res64["sweep_ms"], res64["tess_ms"], res64["wall"], res64["units"],
+                                           res64["clocks"])
+    value = res64["value"]
 
     # end to end through the public API: rich_step (host tessellation, copies,
     # sweep) plus a host read of the step's result
@@ -208,22 +273,12 @@ def run_ours(args):
     sim2.close()
 
     if rank != 0:
-        sim.close()
         if ws > 1:
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (FP64-ALU bound)
-    means = {k: float(np.mean(v)) for k, v in kern.items() if k != "dt_reset"}
-    dom = max(means, key=means.get)
-    fl = kernel_flops(dom, units)
-    achieved = fl / (means[dom] / 1e3) / 1e12
-    total_fl = sum(kernel_flops(k, units) for k in FLOPS)
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-            "sweep_fp64_tflops": total_fl / (float(np.mean(sweep_ms)) / 1e3) / 1e12,
-            "kernel_ms": means}
+    roof = roofline_of("fp64", res64["kernel_means"], units, float(np.mean(sweep_ms)))
+    roof32 = roofline_of("split", res32["kernel_means"], res32["units"], float(np.mean(res32["sweep_ms"])))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(sweep_ms)),
@@ -239,10 +294,12 @@ def run_ours(args):
                 "steps": e2e_steps},
         "gpu_launches": 6 * args.steps,
         "clocks": clk,
+        "fp32_split": {"value": res32["value"], "unit": UNIT, "dtype": "f32 reconstruction + f64 geometry/state",
+                       "ms_per_step": float(np.mean(res32["sweep_ms"])),
+                       "p99_ms": float(np.percentile(res32["sweep_ms"], 99)), "roofline": roof32},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
-    sim.close()
     print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()

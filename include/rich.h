@@ -66,7 +66,10 @@ extern "C" {
 
 #define RICH_SCHEME_EXTRAPOLATED 0 /* Section 2.3 "extrapolated fluxes" */
 
-#define RICH_FP64 0 /* every step in FP64 */
+#define RICH_FP64 0       /* every step in FP64 */
+#define RICH_FP32_SPLIT 1 /* primitives, gradients, limiter, mesh velocity, edge states and HLLC in
+                             FP32; positions, Voronoi vertices, areas, centres of mass, coordinate
+                             differences and the conserved variables (with the flux sums) in FP64 */
 
 typedef struct rich_sim rich_sim;
 
@@ -82,7 +85,7 @@ typedef struct {
     double theta, delta_v, delta_p; /* TESS factor and shock-switch thresholds */
     int32_t limiter;                /* RICH_LIM_* */
     int32_t scheme;                 /* RICH_SCHEME_* */
-    int32_t precision;              /* RICH_FP64 */
+    int32_t precision;              /* RICH_FP64 | RICH_FP32_SPLIT */
 } rich_config;
 
 typedef struct {
@@ -159,6 +162,11 @@ int rich_sync(rich_sim *s, rich_step_info *info);
    26 TESS flag, 27-30 alpha (rho, vx, vy, p), 31 dt (same value in every cell). */
 int rich_get_field(rich_sim *s, int32_t field, int64_t n, double *out);
 
+/* Write (on, the default) or skip (off) the inspection-only per-cell arrays
+   of a sweep: unlimited gradient, alpha and TESS flag (fields 8-15, 26-30
+   of rich_get_field).  The step's results do not depend on it. */
+int rich_set_diagnostics(rich_sim *s, int32_t on);
+
 /* Per-stage device times of the last synchronised sweep, from CUDA events
    recorded on the launching stream between the stages (enabled by
    rich_set_profiling; off by default).  Stages, in launch order:
@@ -171,6 +179,63 @@ const char *rich_kernel_name(int32_t stage);
 
 /* Number of cells of the handle. */
 int64_t rich_num_cells(const rich_sim *s);
+
+/* ---- batches of independent simulations ---------------------------------- */
+
+/* A batch advances many independent simulations (different sizes, problems
+   and scheme parameters, one precision) with ONE device sweep per step over
+   all their cells: each step tessellates every simulation on a pool of host
+   threads, packs the meshes into one index space with a per-cell simulation
+   id, and runs steps a1-a9 once; every simulation keeps its own time step,
+   end time, step budget and status.  A cell's arithmetic depends only on its
+   own simulation, so results are identical alone and in any mix.  The batch
+   owns its device memory and stream. */
+typedef struct rich_batch rich_batch;
+
+#define RICH_SIM_PENDING 0  /* admitted, not yet stepped */
+#define RICH_SIM_RUNNING 1
+#define RICH_SIM_DONE 2     /* reached t_end or max_steps; state kept for reading */
+#define RICH_SIM_FAILED 3   /* a step or a tessellation failed; last good state kept */
+
+/* max_cells: admission budget (cells of pending + running simulations);
+   device memory grows to about 1 KiB per admitted cell.  host_threads <= 0:
+   one per hardware thread.  Errors: RICH_EINVAL, RICH_ENODEV, RICH_ECUDA. */
+int rich_batch_create(int32_t precision, int64_t max_cells, int32_t host_threads, rich_batch **out);
+
+/* Admit a simulation (arguments as rich_init_mesh, cfg->precision must equal
+   the batch's) that runs until t_end or max_steps steps.  It joins the
+   device sweep at the next rich_batch_step.  *id receives its handle.
+   Errors: RICH_EINVAL, RICH_ENOMEM when the cell budget would be exceeded. */
+int rich_batch_add(rich_batch *b, const rich_config *cfg, int64_t n, const double *x, const double *y,
+                   const double *rho, const double *vx, const double *vy, const double *p, double t_end,
+                   int64_t max_steps, int32_t *id);
+
+/* One step of every pending or running simulation.  info (nullable):
+   steps_done = simulations stepped, sweep_ms = device time of the sweep,
+   tess_ms = host tessellation wall time, copy_ms = other host time. */
+int rich_batch_step(rich_batch *b, rich_step_info *info);
+
+/* State (RICH_SIM_*), error code of a failed simulation, its time and steps
+   taken, and for finished ones the wall time from rich_batch_add to the end
+   of its last step (ms; -1 while running).  Each output may be NULL. */
+int rich_batch_query(rich_batch *b, int32_t id, int32_t *state, int32_t *error, double *t, int64_t *steps,
+                     double *latency_ms);
+
+/* Generating points and extensive conserved variables of a running or
+   finished simulation, caller's point order (each output may be NULL). */
+int rich_batch_get_conserved(rich_batch *b, int32_t id, int64_t n, double *x, double *y, double *m, double *px,
+                             double *py, double *E);
+
+/* Forget a simulation (running ones leave the batch at the next step). */
+int rich_batch_remove(rich_batch *b, int32_t id);
+
+/* As rich_set_diagnostics, for the batch (off by default). */
+int rich_batch_set_diagnostics(rich_batch *b, int32_t on);
+
+/* Cells of pending + running simulations. */
+int64_t rich_batch_cells(const rich_batch *b);
+
+void rich_batch_destroy(rich_batch *b);
 
 /* ---- time step without allocation ---------------------------------------- */
 

@@ -14,8 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librich.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["sweep_fp64.cu", "courant_noalloc.cu"]
-HOST_SOURCES = ["predicates.cpp", "mesh.cpp", "rich_api.cpp"]
+CUDA_SOURCES = ["sweep.cu", "courant_noalloc.cu"]
+HOST_SOURCES = ["predicates.cpp", "mesh.cpp", "rich_api.cpp", "batch.cpp"]
 
 
 def _nvcc():
@@ -36,7 +36,7 @@ def _compile(src):
         cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
                "-Xptxas", "-v", "-c", path, "-o", obj]
     else:
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math",
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-ffp-contract=off", "-fno-fast-math",
                "-I", _cuda_include(), "-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if log:
                 print(log)
     objs = [o for o, _ in results]
-    cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lstdc++"]
+    cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lstdc++", "-lpthread"]
     subprocess.check_call(cmd)
     os.replace(LIB + ".tmp", LIB)
     return LIB

@@ -1,0 +1,66 @@
+// Helpers shared by the C ABI implementations (single simulation and batch):
+// per-thread error text, CUDA error mapping, growable device buffers.
+#pragma once
+
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rich.h"
+
+namespace rich {
+
+int set_error(int code, const std::string &msg);
+
+#define RICH_CUDA_TRY(expr)                                                                       \
+    do {                                                                                          \
+        cudaError_t err_ = (expr);                                                                \
+        if (err_ != cudaSuccess)                                                                  \
+            return ::rich::set_error(err_ == cudaErrorMemoryAllocation ? RICH_ENOMEM : RICH_ECUDA, \
+                                     std::string(#expr) + ": " + cudaGetErrorString(err_));       \
+    } while (0)
+
+// Device allocation that only grows (25% headroom), freed with the owner.
+struct DBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf()
+    {
+        if (p) cudaFree(p);
+    }
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= cap && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = bytes + bytes / 4 + 256;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+template <class T> cudaError_t upload(DBuf &b, const std::vector<T> &v, cudaStream_t st)
+{
+    cudaError_t e = b.ensure(sizeof(T) * (v.size() + 1));
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
+}
+
+inline double now_ms()
+{
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+bool valid_config(const rich_config *c);
+bool point_inside(const rich_config *c, double x, double y);
+
+}  // namespace rich

@@ -1,0 +1,603 @@
+// Batched simulations (include/rich.h, rich_batch_*): many independent
+// moving-mesh simulations of different sizes and parameters advanced
+// together, one device sweep per step over all of them.
+//
+// Every step:
+//   1. the generating points of all running simulations come back to the
+//      host in one copy;
+//   2. each simulation is tessellated on a host worker thread (a0), newly
+//      admitted ones included;
+//   3. the meshes are packed into one index space (cells of simulation k
+//      follow those of k-1; ghosts, triangles, edges and ring slots likewise)
+//      with a per-cell simulation id and a per-simulation parameter table;
+//      when membership changed, the FP64 conserved state is regathered on
+//      the device;
+//   4. newly admitted simulations get their conserved variables from their
+//      initial primitives and first areas (geometry stage in init mode);
+//   5. one sweep (a1-a9) runs over all cells; each simulation keeps its own
+//      time step, remaining time and status flags;
+//   6. simulations that reached t_end or their step budget are copied out
+//      and leave the batch; a failed step rolls back that simulation only.
+// The arithmetic of every cell depends only on its own simulation, so a
+// simulation's results do not depend on what else is in the batch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "api_internal.h"
+#include "mesh.h"
+#include "sweep.cuh"
+#include "threadpool.h"
+
+namespace {
+
+using rich::DBuf;
+using rich::now_ms;
+using rich::upload;
+#define CUDA_TRY RICH_CUDA_TRY
+
+int fail(int code, const std::string &msg) { return rich::set_error(code, msg); }
+
+enum SimState { PENDING = 0, RUNNING = 1, DONE = 2, FAILED = 3, REMOVED = 4 };
+
+struct BatchSim {
+    int32_t id = -1;
+    rich_config cfg{};
+    int32_t n = 0;
+    std::vector<int32_t> perm;  // internal (Hilbert) -> caller index
+    std::vector<double> hx, hy;  // points, internal order
+    std::vector<double> W0;      // initial primitives (4n, component-major) until admitted
+    rich::Delaunay dt;
+    rich::HostMesh hm;
+    int mesh_rc = 0;
+    double t = 0.0, t_end = 0.0, last_dt = 0.0;
+    int64_t steps = 0, max_steps = 0;
+    int state = PENDING;
+    int err = RICH_OK;
+    std::string err_msg;
+    // offsets in the packed arrays of the current step
+    int64_t cell_off = -1, ghost_off = 0, tri_off = 0, edge_off = 0, slot_off = 0;
+    int64_t prev_cell_off = -1;  // offset in the previous packing (-1: not packed)
+    // results of a finished simulation (caller order is applied on read)
+    std::vector<double> fin;  // x, y, m, px, py, E (n each, internal order)
+    double t_submit = 0.0, t_admit = 0.0, t_finish = 0.0;
+};
+
+int mesh_code(int rc, std::string &msg)
+{
+    if (rc == -2) { msg = "two generating points coincide"; return RICH_EDUPLICATE; }
+    if (rc == -4) { msg = "too few points for the ghost band"; return RICH_ETOOFEW; }
+    msg = "tessellation failed";
+    return RICH_ETESS;
+}
+
+}  // namespace
+
+struct rich_batch {
+    int32_t precision = RICH_FP64;
+    int64_t max_cells = 0;
+    int64_t cells_admitted = 0;  // cells of pending + running simulations
+    std::vector<std::unique_ptr<BatchSim>> sims;
+    std::vector<BatchSim *> packed;  // running simulations in packed order (last step)
+    int64_t n_packed = 0;            // cells in the packed arrays
+    rich::ThreadPool pool;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool diagnostics = false;
+    int cur = 0;
+    // device
+    DBuf x[2], y[2], U[2], A, o, W, cs, g, gl, alpha, w, tess, rounding, p64, cell_ptr, cell_inst, initW, src;
+    DBuf gx, gy, gsrc, gxf, tri, ccx, ccy, slot_nb, slot_tri, slot_edge;
+    DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F;
+    DBuf instp, dtmin, dtout, status;
+    // host staging of the packed mesh
+    std::vector<double> h_x, h_y, h_gx, h_gy, h_W0;
+    std::vector<int32_t> h_gsrc, h_gxf, h_tri, h_cell_ptr, h_slot_nb, h_slot_tri, h_slot_edge, h_cell_inst;
+    std::vector<int32_t> h_edge_l, h_edge_r, h_edge_ta, h_edge_tb, h_src;
+    std::vector<rich::InstParams> h_inst;
+    std::vector<double> h_dt;
+    std::vector<int32_t> h_status;
+    int64_t nG = 0, nT = 0, nE = 0, nS = 0;
+
+    explicit rich_batch(int threads) : pool(threads) {}
+    ~rich_batch()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (stream) cudaStreamDestroy(stream);
+    }
+
+    size_t rsize() const { return precision == RICH_FP32_SPLIT ? sizeof(float) : sizeof(double); }
+
+    template <class R> rich::SweepParams<R> params() const
+    {
+        rich::SweepParams<R> p{};
+        p.inst = instp.as<rich::InstParams>();
+        p.cell_inst = cell_inst.as<int32_t>();
+        p.n_inst = (int32_t)packed.size();
+        p.diagnostics = diagnostics ? 1 : 0;
+        p.n = (int32_t)n_packed;
+        p.ng = (int32_t)nG;
+        p.T = (int32_t)nT;
+        p.E = (int32_t)nE;
+        p.S = (int32_t)nS;
+        p.x = x[cur].as<double>(); p.y = y[cur].as<double>();
+        p.xn = x[1 - cur].as<double>(); p.yn = y[1 - cur].as<double>();
+        p.gx = gx.as<double>(); p.gy = gy.as<double>();
+        p.tri = tri.as<int32_t>(); p.cell_ptr = cell_ptr.as<int32_t>();
+        p.slot_nb = slot_nb.as<int32_t>(); p.slot_tri = slot_tri.as<int32_t>(); p.slot_edge = slot_edge.as<int32_t>();
+        p.edge_l = edge_l.as<int32_t>(); p.edge_r = edge_r.as<int32_t>();
+        p.edge_ta = edge_ta.as<int32_t>(); p.edge_tb = edge_tb.as<int32_t>();
+        p.ghost_src = gsrc.as<int32_t>(); p.ghost_xf = gxf.as<int32_t>();
+        p.ccx = ccx.as<double>(); p.ccy = ccy.as<double>(); p.A = A.as<double>();
+        p.eL = eL.as<R>(); p.emlx = emlx.as<R>(); p.emly = emly.as<R>();
+        p.emrx = emrx.as<R>(); p.emry = emry.as<R>();
+        p.enx = enx.as<R>(); p.eny = eny.as<R>(); p.eqx = eqx.as<R>(); p.eqy = eqy.as<R>();
+        p.U = U[cur].as<double>(); p.Un = U[1 - cur].as<double>();
+        p.W = W.as<rich::Vec4<R>>(); p.o = o.as<rich::Vec2<R>>(); p.cs = cs.as<R>();
+        p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
+        p.w = w.as<rich::Vec2<R>>();
+        p.rounding = rounding.as<uint8_t>(); p.p64 = p64.as<double>();
+        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<R>>();
+        p.dtmin_bits = dtmin.as<unsigned long long>();
+        p.dt_out = dtout.as<double>();
+        p.status = status.as<int32_t>();
+        return p;
+    }
+
+    void launch(int k, const double *init_W, double *Un_override = nullptr) const
+    {
+        if (precision == RICH_FP32_SPLIT) {
+            rich::SweepParams<float> p = params<float>();
+            if (Un_override) p.Un = Un_override;
+            rich::launch_stage<float>(k, p, init_W, stream);
+        } else {
+            rich::SweepParams<double> p = params<double>();
+            if (Un_override) p.Un = Un_override;
+            rich::launch_stage<double>(k, p, init_W, stream);
+        }
+    }
+
+    BatchSim *find(int32_t id) const
+    {
+        for (auto &s : sims)
+            if (s->id == id && s->state != REMOVED) return s.get();
+        return nullptr;
+    }
+};
+
+namespace {
+
+rich::InstParams inst_params(const BatchSim &s, bool init)
+{
+    rich::InstParams ip{};
+    const rich_config &c = s.cfg;
+    ip.gamma = c.gamma; ip.cfl = c.cfl; ip.chi = c.chi; ip.eta = c.eta; ip.theta = c.theta;
+    ip.delta_v = c.delta_v; ip.delta_p = c.delta_p;
+    ip.x0 = c.x0; ip.x1 = c.x1; ip.y0 = c.y0; ip.y1 = c.y1;
+    ip.remaining = s.t_end - s.t;
+    ip.boundary = c.boundary; ip.motion = c.motion; ip.limiter = c.limiter;
+    ip.init = init ? 1 : 0;
+    return ip;
+}
+
+// Fill the staging arrays of simulation s (index k in packing order) at its offsets.
+void pack_one(rich_batch *b, BatchSim &s, int32_t k)
+{
+    const rich::HostMesh &m = s.hm;
+    const int32_t n = s.n;
+    const int64_t co = s.cell_off, go = s.ghost_off, to = s.tri_off, eo = s.edge_off, so = s.slot_off;
+    const int64_t N = b->n_packed;
+    auto pid = [&](int32_t q) -> int32_t {
+        return q < n ? (int32_t)(co + q) : (int32_t)(N + go + (q - n));
+    };
+    std::memcpy(&b->h_x[co], s.hx.data(), sizeof(double) * n);
+    std::memcpy(&b->h_y[co], s.hy.data(), sizeof(double) * n);
+    for (int32_t i = 0; i < n; i++) b->h_cell_inst[co + i] = k;
+    for (int32_t q = 0; q < m.g; q++) {
+        b->h_gx[go + q] = m.gx[q];
+        b->h_gy[go + q] = m.gy[q];
+        b->h_gsrc[go + q] = (int32_t)(co + m.ghost_src[q]);
+        b->h_gxf[go + q] = m.ghost_xf[q];
+    }
+    const size_t T = m.tri.size() / 3;
+    for (size_t t = 0; t < 3 * T; t++) b->h_tri[3 * to + t] = pid(m.tri[t]);
+    for (int32_t i = 0; i < n; i++) b->h_cell_ptr[co + i] = (int32_t)(so + m.cell_ptr[i]);
+    const size_t S = m.slot_nb.size();
+    for (size_t q = 0; q < S; q++) {
+        b->h_slot_nb[so + q] = pid(m.slot_nb[q]);
+        b->h_slot_tri[so + q] = (int32_t)(to + m.slot_tri[q]);
+        const int32_t es = m.slot_edge[q];
+        b->h_slot_edge[so + q] = (int32_t)(2 * (eo + (es >> 1)) + (es & 1));
+    }
+    const size_t E = m.edge_l.size();
+    for (size_t e = 0; e < E; e++) {
+        b->h_edge_l[eo + e] = (int32_t)(co + m.edge_l[e]);
+        b->h_edge_r[eo + e] = pid(m.edge_r[e]);
+        b->h_edge_ta[eo + e] = (int32_t)(to + m.edge_ta[e]);
+        b->h_edge_tb[eo + e] = (int32_t)(to + m.edge_tb[e]);
+    }
+    // conserved state: continuing simulations gather from their previous slot
+    for (int32_t i = 0; i < n; i++) b->h_src[co + i] = s.prev_cell_off >= 0 ? (int32_t)(s.prev_cell_off + i) : -1;
+    if (s.state == PENDING)
+        for (int c = 0; c < 4; c++)
+            for (int32_t i = 0; i < n; i++) b->h_W0[(size_t)c * N + co + i] = s.W0[(size_t)c * n + i];
+}
+
+int ensure_device(rich_batch *b)
+{
+    const size_t N = (size_t)b->n_packed, d = sizeof(double), r = b->rsize();
+    const size_t G = (size_t)b->nG, T = (size_t)b->nT, E = (size_t)b->nE, K = b->packed.size();
+    for (int k = 0; k < 2; k++) {
+        CUDA_TRY(b->x[k].ensure(N * d + 8));
+        CUDA_TRY(b->y[k].ensure(N * d + 8));
+        CUDA_TRY(b->U[k].ensure(4 * N * d + 8));
+    }
+    CUDA_TRY(b->A.ensure(N * d + 8)); CUDA_TRY(b->o.ensure(2 * N * r + 16));
+    CUDA_TRY(b->W.ensure(4 * N * r + 32)); CUDA_TRY(b->cs.ensure(N * r + 8));
+    CUDA_TRY(b->g.ensure(8 * N * r + 64)); CUDA_TRY(b->gl.ensure(8 * N * r + 64));
+    CUDA_TRY(b->alpha.ensure(4 * N * r + 32)); CUDA_TRY(b->w.ensure(2 * N * r + 16));
+    CUDA_TRY(b->tess.ensure(N * 4 + 4)); CUDA_TRY(b->rounding.ensure(N + 8)); CUDA_TRY(b->p64.ensure(N * d + 8));
+    CUDA_TRY(b->ccx.ensure(T * d + 8)); CUDA_TRY(b->ccy.ensure(T * d + 8));
+    for (DBuf *e : {&b->eL, &b->emlx, &b->emly, &b->emrx, &b->emry, &b->enx, &b->eny, &b->eqx, &b->eqy})
+        CUDA_TRY(e->ensure(E * r + 8));
+    CUDA_TRY(b->F.ensure(4 * E * r + 32));
+    CUDA_TRY(b->instp.ensure(K * sizeof(rich::InstParams) + 8));
+    CUDA_TRY(b->dtmin.ensure(K * 8 + 8)); CUDA_TRY(b->dtout.ensure(K * 8 + 8)); CUDA_TRY(b->status.ensure(K * 4 + 8));
+    (void)G;
+    return RICH_OK;
+}
+
+void finish_copy_out(rich_batch *b, BatchSim &s, int which)
+{
+    // x, y and U of simulation s from packed buffer set `which` (synchronous)
+    const size_t n = (size_t)s.n, N = (size_t)b->n_packed;
+    s.fin.assign(6 * n, 0.0);
+    cudaMemcpyAsync(&s.fin[0], b->x[which].as<double>() + s.cell_off, n * 8, cudaMemcpyDeviceToHost, b->stream);
+    cudaMemcpyAsync(&s.fin[n], b->y[which].as<double>() + s.cell_off, n * 8, cudaMemcpyDeviceToHost, b->stream);
+    for (int c = 0; c < 4; c++)
+        cudaMemcpyAsync(&s.fin[(2 + c) * n], b->U[which].as<double>() + c * N + s.cell_off, n * 8,
+                        cudaMemcpyDeviceToHost, b->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rich_batch_create(int32_t precision, int64_t max_cells, int32_t host_threads, rich_batch **out)
+{
+    if (!out) return fail(RICH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if ((precision != RICH_FP64 && precision != RICH_FP32_SPLIT) || max_cells < 3 || max_cells > ((int64_t)1 << 30))
+        return fail(RICH_EINVAL, "bad precision or cell budget");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(RICH_ENODEV, "no CUDA device");
+    int threads = host_threads > 0 ? host_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+    rich_batch *b = new (std::nothrow) rich_batch(threads);
+    if (!b) return fail(RICH_ENOMEM, "host allocation");
+    b->precision = precision;
+    b->max_cells = max_cells;
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+        delete b;
+        return fail(RICH_ECUDA, "stream or event creation failed");
+    }
+    *out = b;
+    return RICH_OK;
+}
+
+void rich_batch_destroy(rich_batch *b) { delete b; }
+
+int rich_batch_add(rich_batch *b, const rich_config *cfg, int64_t n, const double *x, const double *y,
+                   const double *rho, const double *vx, const double *vy, const double *p, double t_end,
+                   int64_t max_steps, int32_t *id)
+{
+    if (!b || !id) return fail(RICH_EINVAL, "NULL argument");
+    if (!rich::valid_config(cfg) || cfg->precision != b->precision)
+        return fail(RICH_EINVAL, "invalid configuration or precision differs from the batch");
+    if (n < 3 || n > ((int64_t)1 << 30) || !x || !y || !rho || !vx || !vy || !p) return fail(RICH_EINVAL, "bad arrays");
+    if (!(t_end > 0.0) || max_steps < 1) return fail(RICH_EINVAL, "t_end must be > 0 and max_steps >= 1");
+    for (int64_t i = 0; i < n; i++) {
+        if (!std::isfinite(x[i]) || !std::isfinite(y[i]) || !rich::point_inside(cfg, x[i], y[i]))
+            return fail(RICH_EINVAL, "point " + std::to_string(i) + " outside the box");
+        if (!(rho[i] > 0) || !(p[i] > 0) || !std::isfinite(rho[i]) || !std::isfinite(p[i]) || !std::isfinite(vx[i]) ||
+            !std::isfinite(vy[i]))
+            return fail(RICH_EINVAL, "bad primitive values at point " + std::to_string(i));
+    }
+    if (b->cells_admitted + n > b->max_cells) return fail(RICH_ENOMEM, "the batch's cell budget is full");
+    auto s = std::make_unique<BatchSim>();
+    s->cfg = *cfg;
+    s->n = (int32_t)n;
+    rich::hilbert_order(s->n, x, y, s->perm);
+    s->hx.resize(n);
+    s->hy.resize(n);
+    s->W0.resize(4 * (size_t)n);
+    for (int32_t k = 0; k < s->n; k++) {
+        int32_t u = s->perm[k];
+        s->hx[k] = x[u];
+        s->hy[k] = y[u];
+        s->W0[k] = rho[u];
+        s->W0[n + k] = vx[u];
+        s->W0[2 * n + k] = vy[u];
+        s->W0[3 * n + k] = p[u];
+    }
+    s->t_end = t_end;
+    s->max_steps = max_steps;
+    s->t_submit = now_ms();
+    int32_t next = 0;
+    for (auto &o : b->sims) next = std::max(next, o->id + 1);
+    s->id = next;
+    *id = s->id;
+    b->cells_admitted += n;
+    b->sims.push_back(std::move(s));
+    return RICH_OK;
+}
+
+int rich_batch_step(rich_batch *b, rich_step_info *info)
+{
+    if (!b) return fail(RICH_EINVAL, "NULL handle");
+    if (info) std::memset(info, 0, sizeof(*info));
+    const double t0 = now_ms();
+    // 1. points of the running simulations back to the host
+    if (b->n_packed > 0 && !b->packed.empty()) {
+        std::vector<double> hx(b->n_packed), hy(b->n_packed);
+        CUDA_TRY(cudaMemcpyAsync(hx.data(), b->x[b->cur].p, b->n_packed * 8, cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaMemcpyAsync(hy.data(), b->y[b->cur].p, b->n_packed * 8, cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        for (BatchSim *s : b->packed) {
+            if (s->state != RUNNING) continue;
+            std::memcpy(s->hx.data(), &hx[s->cell_off], sizeof(double) * s->n);
+            std::memcpy(s->hy.data(), &hy[s->cell_off], sizeof(double) * s->n);
+        }
+    }
+    // the simulations of this step: running ones in their previous order, then new ones
+    std::vector<BatchSim *> list;
+    for (BatchSim *s : b->packed)
+        if (s->state == RUNNING) list.push_back(s);
+    for (auto &s : b->sims)
+        if (s->state == PENDING) list.push_back(s.get());
+    for (BatchSim *s : list) s->prev_cell_off = s->state == RUNNING ? s->cell_off : -1;
+    if (list.empty()) {
+        b->packed.clear();
+        b->n_packed = 0;
+        return RICH_OK;
+    }
+    // 2. tessellations in parallel
+    const double t1 = now_ms();
+    b->pool.parallel_for((int64_t)list.size(), [&](int64_t k) {
+        BatchSim *s = list[k];
+        rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
+        s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->dt, s->hm);
+    });
+    const double t2 = now_ms();
+    std::vector<BatchSim *> ok;
+    for (BatchSim *s : list) {
+        if (s->mesh_rc == 0) {
+            ok.push_back(s);
+            continue;
+        }
+        s->err = mesh_code(s->mesh_rc, s->err_msg);
+        if (s->state == RUNNING) {
+            // keep its last good state for the caller
+            s->cell_off = s->prev_cell_off;
+            finish_copy_out(b, *s, b->cur);
+        }
+        s->state = FAILED;
+        s->t_finish = now_ms();
+        b->cells_admitted -= s->n;
+    }
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    // 3. packing offsets
+    const int64_t n_old = b->n_packed;
+    bool same_layout = ok.size() == b->packed.size();
+    int64_t co = 0, go = 0, to = 0, eo = 0, so = 0;
+    for (size_t k = 0; k < ok.size(); k++) {
+        BatchSim *s = ok[k];
+        if (same_layout && (b->packed[k] != s || s->prev_cell_off != co)) same_layout = false;
+        s->cell_off = co; s->ghost_off = go; s->tri_off = to; s->edge_off = eo; s->slot_off = so;
+        co += s->n;
+        go += s->hm.g;
+        to += (int64_t)s->hm.tri.size() / 3;
+        eo += (int64_t)s->hm.edge_l.size();
+        so += (int64_t)s->hm.slot_nb.size();
+    }
+    if (co + go > ((int64_t)1 << 31) - 1 || 3 * to > ((int64_t)1 << 31) - 1 || 2 * eo > ((int64_t)1 << 31) - 1)
+        return fail(RICH_ENOMEM, "batch exceeds 32-bit indexing");
+    b->packed = ok;
+    b->n_packed = co;
+    b->nG = go;
+    b->nT = to;
+    b->nE = eo;
+    b->nS = so;
+    const size_t N = (size_t)co;
+    bool any_pending = false;
+    for (BatchSim *s : ok) any_pending |= s->state == PENDING;
+    b->h_x.resize(N); b->h_y.resize(N); b->h_cell_inst.resize(N); b->h_src.resize(N);
+    b->h_gx.resize(go); b->h_gy.resize(go); b->h_gsrc.resize(go); b->h_gxf.resize(go);
+    b->h_tri.resize(3 * to); b->h_cell_ptr.resize(N + 1);
+    b->h_slot_nb.resize(so); b->h_slot_tri.resize(so); b->h_slot_edge.resize(so);
+    b->h_edge_l.resize(eo); b->h_edge_r.resize(eo); b->h_edge_ta.resize(eo); b->h_edge_tb.resize(eo);
+    if (any_pending) b->h_W0.assign(4 * N, 0.0);
+    b->pool.parallel_for((int64_t)ok.size(), [&](int64_t k) { pack_one(b, *ok[k], (int32_t)k); });
+    b->h_cell_ptr[N] = (int32_t)so;
+    b->h_inst.resize(ok.size());
+    for (size_t k = 0; k < ok.size(); k++) b->h_inst[k] = inst_params(*ok[k], ok[k]->state == PENDING);
+    // 4. device buffers and uploads
+    int rc = ensure_device(b);
+    if (rc) return rc;
+    const int nxt = 1 - b->cur;
+    if (!same_layout && n_old > 0) {
+        // regather the conserved state of continuing simulations into the other buffer
+        CUDA_TRY(upload(b->src, b->h_src, b->stream));
+        rich::launch_repack(b->src.as<int32_t>(), (int32_t)N, (int32_t)n_old, b->U[b->cur].as<double>(),
+                            b->U[nxt].as<double>(), b->stream);
+        CUDA_TRY(cudaGetLastError());
+        b->cur = nxt;
+    }
+    CUDA_TRY(upload(b->x[b->cur], b->h_x, b->stream));
+    CUDA_TRY(upload(b->y[b->cur], b->h_y, b->stream));
+    CUDA_TRY(upload(b->cell_inst, b->h_cell_inst, b->stream));
+    CUDA_TRY(upload(b->gx, b->h_gx, b->stream));
+    CUDA_TRY(upload(b->gy, b->h_gy, b->stream));
+    CUDA_TRY(upload(b->gsrc, b->h_gsrc, b->stream));
+    CUDA_TRY(upload(b->gxf, b->h_gxf, b->stream));
+    CUDA_TRY(upload(b->tri, b->h_tri, b->stream));
+    CUDA_TRY(upload(b->cell_ptr, b->h_cell_ptr, b->stream));
+    CUDA_TRY(upload(b->slot_nb, b->h_slot_nb, b->stream));
+    CUDA_TRY(upload(b->slot_tri, b->h_slot_tri, b->stream));
+    CUDA_TRY(upload(b->slot_edge, b->h_slot_edge, b->stream));
+    CUDA_TRY(upload(b->edge_l, b->h_edge_l, b->stream));
+    CUDA_TRY(upload(b->edge_r, b->h_edge_r, b->stream));
+    CUDA_TRY(upload(b->edge_ta, b->h_edge_ta, b->stream));
+    CUDA_TRY(upload(b->edge_tb, b->h_edge_tb, b->stream));
+    CUDA_TRY(upload(b->instp, b->h_inst, b->stream));
+    CUDA_TRY(cudaMemsetAsync(b->status.p, 0, ok.size() * 4, b->stream));
+    if (any_pending) CUDA_TRY(upload(b->initW, b->h_W0, b->stream));
+    // 5. admission: conserved variables of new simulations from their first geometry
+    if (any_pending) {
+        b->launch(rich::K_CIRCUMCENTRE, nullptr);
+        b->launch(rich::K_CELL_GEOMETRY, b->initW.as<double>(), b->U[b->cur].as<double>());
+        for (BatchSim *s : ok)
+            if (s->state == PENDING) {
+                s->state = RUNNING;
+                s->t_admit = now_ms();
+                s->W0.clear();
+                s->W0.shrink_to_fit();
+            }
+        for (size_t k = 0; k < ok.size(); k++) b->h_inst[k].init = 0;
+        CUDA_TRY(upload(b->instp, b->h_inst, b->stream));
+    }
+    const double t3 = now_ms();
+    // 6. the sweep over every cell of every simulation
+    CUDA_TRY(cudaEventRecord(b->ev0, b->stream));
+    for (int k = 0; k < rich::NUM_STAGES; k++) b->launch(k, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(b->ev1, b->stream));
+    b->h_dt.resize(ok.size());
+    b->h_status.resize(ok.size());
+    CUDA_TRY(cudaMemcpyAsync(b->h_dt.data(), b->dtout.p, ok.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaMemcpyAsync(b->h_status.data(), b->status.p, ok.size() * 4, cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+    // 7. per-simulation bookkeeping; a failed step keeps that simulation's old state
+    const int nxt2 = 1 - b->cur;
+    const double tnow = now_ms();
+    for (size_t k = 0; k < ok.size(); k++) {
+        BatchSim *s = ok[k];
+        if (b->h_status[k]) {
+            s->err = (b->h_status[k] & rich::ST_NAN) ? RICH_ENAN : RICH_ENEGATIVE;
+            s->err_msg = "step rejected (non-finite, non-positive mass or thermal energy, or a point left the box)";
+            finish_copy_out(b, *s, b->cur);
+            s->state = FAILED;
+            s->t_finish = tnow;
+            b->cells_admitted -= s->n;
+            continue;
+        }
+        const double rem = s->t_end - s->t;
+        s->last_dt = b->h_dt[k];
+        s->t = s->last_dt >= rem ? s->t_end : s->t + s->last_dt;
+        s->steps++;
+        if (s->t >= s->t_end || s->steps >= s->max_steps) {
+            finish_copy_out(b, *s, nxt2);
+            s->state = DONE;
+            s->t_finish = tnow;
+            b->cells_admitted -= s->n;
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    b->cur = nxt2;
+    if (info) {
+        info->steps_done = (int64_t)ok.size();
+        info->sweep_ms = ms;
+        info->tess_ms = t2 - t1;
+        info->copy_ms = (t1 - t0) + (t3 - t2) + (now_ms() - tnow);
+        info->n_ghost = b->nG;
+        info->n_tri = b->nT;
+        info->n_edges = b->nE;
+        info->n_slots = b->nS;
+        info->t = 0.0;
+        info->dt_last = 0.0;
+    }
+    return RICH_OK;
+}
+
+int rich_batch_query(rich_batch *b, int32_t id, int32_t *state, int32_t *error, double *t, int64_t *steps,
+                     double *latency_ms)
+{
+    if (!b) return fail(RICH_EINVAL, "NULL handle");
+    BatchSim *s = b->find(id);
+    if (!s) return fail(RICH_EINVAL, "unknown simulation id");
+    if (state) *state = s->state;
+    if (error) *error = s->err;
+    if (t) *t = s->t;
+    if (steps) *steps = s->steps;
+    if (latency_ms)
+        *latency_ms = (s->state == DONE || s->state == FAILED) ? s->t_finish - s->t_submit : -1.0;
+    return RICH_OK;
+}
+
+int rich_batch_get_conserved(rich_batch *b, int32_t id, int64_t n, double *x, double *y, double *m, double *px,
+                             double *py, double *E)
+{
+    if (!b) return fail(RICH_EINVAL, "NULL handle");
+    BatchSim *s = b->find(id);
+    if (!s || n != s->n) return fail(RICH_EINVAL, "unknown simulation id or wrong size");
+    std::vector<double> buf;
+    const double *src = nullptr;
+    if (s->state == DONE || s->state == FAILED) {
+        if (s->fin.empty()) return fail(RICH_ESTATE, "no state recorded");
+        src = s->fin.data();
+    } else if (s->state == RUNNING) {
+        const size_t nn = (size_t)s->n, N = (size_t)b->n_packed;
+        buf.resize(6 * nn);
+        CUDA_TRY(cudaMemcpyAsync(&buf[0], b->x[b->cur].as<double>() + s->cell_off, nn * 8, cudaMemcpyDeviceToHost,
+                                 b->stream));
+        CUDA_TRY(cudaMemcpyAsync(&buf[nn], b->y[b->cur].as<double>() + s->cell_off, nn * 8, cudaMemcpyDeviceToHost,
+                                 b->stream));
+        for (int c = 0; c < 4; c++)
+            CUDA_TRY(cudaMemcpyAsync(&buf[(2 + c) * nn], b->U[b->cur].as<double>() + c * N + s->cell_off, nn * 8,
+                                     cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        src = buf.data();
+    } else {
+        return fail(RICH_ESTATE, "simulation not admitted yet");
+    }
+    double *outs[6] = {x, y, m, px, py, E};
+    for (int f = 0; f < 6; f++) {
+        if (!outs[f]) continue;
+        for (int32_t k = 0; k < s->n; k++) outs[f][s->perm[k]] = src[(size_t)f * s->n + k];
+    }
+    return RICH_OK;
+}
+
+int rich_batch_remove(rich_batch *b, int32_t id)
+{
+    if (!b) return fail(RICH_EINVAL, "NULL handle");
+    BatchSim *s = b->find(id);
+    if (!s) return fail(RICH_EINVAL, "unknown simulation id");
+    if (s->state == PENDING || s->state == RUNNING) b->cells_admitted -= s->n;
+    s->state = REMOVED;
+    s->fin.clear();
+    s->fin.shrink_to_fit();
+    s->hm = rich::HostMesh();
+    s->dt = rich::Delaunay();
+    return RICH_OK;
+}
+
+int rich_batch_set_diagnostics(rich_batch *b, int32_t on)
+{
+    if (!b) return fail(RICH_EINVAL, "NULL handle");
+    b->diagnostics = on != 0;
+    return RICH_OK;
+}
+
+int64_t rich_batch_cells(const rich_batch *b) { return b ? b->cells_admitted : -1; }
+
+}  // extern "C"

@@ -13,50 +13,30 @@
 #include <cuda_runtime.h>
 
 #include "../../include/rich.h"
+#include "api_internal.h"
 #include "mesh.h"
 #include "sweep.cuh"
 
+namespace rich {
 namespace {
-
 thread_local std::string g_last_error;
-
-int fail(int code, const std::string &msg)
+}
+int set_error(int code, const std::string &msg)
 {
     g_last_error = msg;
     return code;
 }
+const char *last_error() { return g_last_error.c_str(); }
+}  // namespace rich
 
-#define CUDA_TRY(expr)                                                                            \
-    do {                                                                                          \
-        cudaError_t err_ = (expr);                                                                \
-        if (err_ != cudaSuccess)                                                                  \
-            return fail(err_ == cudaErrorMemoryAllocation ? RICH_ENOMEM : RICH_ECUDA,             \
-                        std::string(#expr) + ": " + cudaGetErrorString(err_));                    \
-    } while (0)
+namespace {
 
-struct DBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-    ~DBuf() { if (p) cudaFree(p); }
-    cudaError_t ensure(size_t bytes)
-    {
-        if (bytes <= cap && p) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        size_t want = bytes + bytes / 4 + 256;
-        cudaError_t e = cudaMalloc(&p, want);
-        if (e == cudaSuccess) cap = want;
-        return e;
-    }
-    template <class T> T *as() const { return static_cast<T *>(p); }
-};
+using rich::DBuf;
+using rich::now_ms;
+using rich::upload;
+#define CUDA_TRY RICH_CUDA_TRY
 
-double now_ms()
-{
-    using namespace std::chrono;
-    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
-}
+int fail(int code, const std::string &msg) { return rich::set_error(code, msg); }
 
 int mesh_rc(int rc)
 {
@@ -68,12 +48,15 @@ int mesh_rc(int rc)
     }
 }
 
+}  // namespace
+
+namespace rich {
 bool valid_config(const rich_config *c)
 {
     return c && c->gamma > 1.0 && std::isfinite(c->gamma) && c->cfl > 0.0 && c->x1 > c->x0 && c->y1 > c->y0 &&
            (c->boundary == RICH_BC_REFLECTIVE || c->boundary == RICH_BC_PERIODIC) &&
            (c->motion == RICH_MESH_LAGRANGIAN || c->motion == RICH_MESH_EULERIAN) && c->limiter >= 0 &&
-           c->limiter <= 2 && c->scheme == RICH_SCHEME_EXTRAPOLATED && c->precision == RICH_FP64 && c->chi >= 0 &&
+           c->limiter <= 2 && c->scheme == RICH_SCHEME_EXTRAPOLATED && (c->precision == RICH_FP64 || c->precision == RICH_FP32_SPLIT) && c->chi >= 0 &&
            c->eta >= 0 && c->theta >= 0 && c->delta_p >= 0 && c->delta_v >= 0;
 }
 
@@ -83,7 +66,9 @@ bool point_inside(const rich_config *c, double x, double y)
     return x > c->x0 && x < c->x1 && y > c->y0 && y < c->y1;
 }
 
-}  // namespace
+}  // namespace rich
+using rich::point_inside;
+using rich::valid_config;
 
 struct rich_sim {
     rich_config cfg{};
@@ -106,12 +91,15 @@ struct rich_sim {
     double last_dt = 0.0;
     // device buffers
     DBuf x[2], y[2], U[2];
-    DBuf A, ox, oy, W, cs, g, gl, alpha, wx, wy, tess, cell_ptr, initW;
+    DBuf A, o, W, cs, g, gl, alpha, w, tess, cell_ptr, initW, rounding, p64;
+    bool diagnostics = true;
     DBuf gx, gy, gsrc, gxf;
     DBuf tri, ccx, ccy;
     DBuf slot_nb, slot_tri, slot_edge;
     DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F;
-    DBuf scal;  // dtmin bits, dt, status
+    DBuf scal;   // dtmin bits, dt, status
+    DBuf instp;  // one InstParams
+    rich::InstParams inst_host{};  // staging for the parameter upload
 
     ~rich_sim()
     {
@@ -122,13 +110,13 @@ struct rich_sim {
         if (own_stream) cudaStreamDestroy(own_stream);
     }
 
-    rich::SweepParams params() const
+    template <class R> rich::SweepParams<R> params() const
     {
-        rich::SweepParams p{};
-        p.gamma = cfg.gamma; p.cfl = cfg.cfl; p.chi = cfg.chi; p.eta = cfg.eta; p.theta = cfg.theta;
-        p.delta_v = cfg.delta_v; p.delta_p = cfg.delta_p;
-        p.x0 = cfg.x0; p.x1 = cfg.x1; p.y0 = cfg.y0; p.y1 = cfg.y1;
-        p.boundary = cfg.boundary; p.motion = cfg.motion; p.limiter = cfg.limiter;
+        rich::SweepParams<R> p{};
+        p.inst = instp.as<rich::InstParams>();
+        p.cell_inst = nullptr;
+        p.n_inst = 1;
+        p.diagnostics = diagnostics ? 1 : 0;
         p.n = n;
         p.ng = hm.g;
         p.T = (int32_t)(hm.tri.size() / 3);
@@ -142,47 +130,75 @@ struct rich_sim {
         p.edge_l = edge_l.as<int32_t>(); p.edge_r = edge_r.as<int32_t>();
         p.edge_ta = edge_ta.as<int32_t>(); p.edge_tb = edge_tb.as<int32_t>();
         p.ghost_src = gsrc.as<int32_t>(); p.ghost_xf = gxf.as<int32_t>();
-        p.ccx = ccx.as<double>(); p.ccy = ccy.as<double>();
-        p.eL = eL.as<double>(); p.emlx = emlx.as<double>(); p.emly = emly.as<double>();
-        p.emrx = emrx.as<double>(); p.emry = emry.as<double>();
-        p.enx = enx.as<double>(); p.eny = eny.as<double>(); p.eqx = eqx.as<double>(); p.eqy = eqy.as<double>();
-        p.A = A.as<double>(); p.ox = ox.as<double>(); p.oy = oy.as<double>();
+        p.ccx = ccx.as<double>(); p.ccy = ccy.as<double>(); p.A = A.as<double>();
+        p.eL = eL.as<R>(); p.emlx = emlx.as<R>(); p.emly = emly.as<R>();
+        p.emrx = emrx.as<R>(); p.emry = emry.as<R>();
+        p.enx = enx.as<R>(); p.eny = eny.as<R>(); p.eqx = eqx.as<R>(); p.eqy = eqy.as<R>();
         p.U = U[cur].as<double>(); p.Un = U[1 - cur].as<double>();
-        p.W = W.as<double>(); p.cs = cs.as<double>(); p.g = g.as<double>(); p.gl = gl.as<double>();
-        p.alpha = alpha.as<double>(); p.wx = wx.as<double>(); p.wy = wy.as<double>();
-        p.tess = tess.as<int32_t>(); p.F = F.as<double>();
+        p.W = W.as<rich::Vec4<R>>(); p.o = o.as<rich::Vec2<R>>(); p.cs = cs.as<R>();
+        p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
+        p.w = w.as<rich::Vec2<R>>();
+        p.rounding = rounding.as<uint8_t>(); p.p64 = p64.as<double>();
+        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<R>>();
         char *sc = scal.as<char>();
         p.dtmin_bits = reinterpret_cast<unsigned long long *>(sc);
         p.dt_out = reinterpret_cast<double *>(sc + 8);
         p.status = reinterpret_cast<int32_t *>(sc + 16);
-        p.remaining = 0.0;
         return p;
     }
+
+    size_t rsize() const { return cfg.precision == RICH_FP32_SPLIT ? sizeof(float) : sizeof(double); }
+
+    // scheme parameters of this simulation with the time left to t_end
+    rich::InstParams inst_params(double remaining, bool init = false) const
+    {
+        rich::InstParams ip{};
+        ip.init = init ? 1 : 0;
+        ip.gamma = cfg.gamma; ip.cfl = cfg.cfl; ip.chi = cfg.chi; ip.eta = cfg.eta; ip.theta = cfg.theta;
+        ip.delta_v = cfg.delta_v; ip.delta_p = cfg.delta_p;
+        ip.x0 = cfg.x0; ip.x1 = cfg.x1; ip.y0 = cfg.y0; ip.y1 = cfg.y1;
+        ip.remaining = remaining;
+        ip.boundary = cfg.boundary; ip.motion = cfg.motion; ip.limiter = cfg.limiter;
+        return ip;
+    }
+
+    // launch stage k of the sweep in the handle's precision
+    void launch(int k, const double *init_W, double *Un_override = nullptr) const
+    {
+        if (cfg.precision == RICH_FP32_SPLIT) {
+            rich::SweepParams<float> p = params<float>();
+            if (Un_override) p.Un = Un_override;
+            rich::launch_stage<float>(k, p, init_W, stream);
+        } else {
+            rich::SweepParams<double> p = params<double>();
+            if (Un_override) p.Un = Un_override;
+            rich::launch_stage<double>(k, p, init_W, stream);
+        }
+    }
+
+    // the mesh sizes of the current tessellation
+    int32_t nT() const { return (int32_t)(hm.tri.size() / 3); }
+    int32_t nE() const { return (int32_t)hm.edge_l.size(); }
 };
 
 namespace {
 
-template <class T> cudaError_t upload(DBuf &b, const std::vector<T> &v, cudaStream_t st)
-{
-    cudaError_t e = b.ensure(sizeof(T) * (v.size() + 1));
-    if (e != cudaSuccess || v.empty()) return e;
-    return cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
-}
-
 int alloc_cells(rich_sim *s)
 {
-    const size_t n = (size_t)s->n, d = sizeof(double);
+    const size_t n = (size_t)s->n, d = sizeof(double), r = s->rsize();
     for (int k = 0; k < 2; k++) {
         CUDA_TRY(s->x[k].ensure(n * d));
         CUDA_TRY(s->y[k].ensure(n * d));
         CUDA_TRY(s->U[k].ensure(4 * n * d));
     }
-    CUDA_TRY(s->A.ensure(n * d)); CUDA_TRY(s->ox.ensure(n * d)); CUDA_TRY(s->oy.ensure(n * d));
-    CUDA_TRY(s->W.ensure(4 * n * d)); CUDA_TRY(s->cs.ensure(n * d));
-    CUDA_TRY(s->g.ensure(8 * n * d)); CUDA_TRY(s->gl.ensure(8 * n * d)); CUDA_TRY(s->alpha.ensure(4 * n * d));
-    CUDA_TRY(s->wx.ensure(n * d)); CUDA_TRY(s->wy.ensure(n * d)); CUDA_TRY(s->tess.ensure(n * 4));
+    CUDA_TRY(s->A.ensure(n * d)); CUDA_TRY(s->o.ensure(2 * n * r));
+    CUDA_TRY(s->W.ensure(4 * n * r)); CUDA_TRY(s->cs.ensure(n * r));
+    CUDA_TRY(s->g.ensure(8 * n * r)); CUDA_TRY(s->gl.ensure(8 * n * r)); CUDA_TRY(s->alpha.ensure(4 * n * r));
+    CUDA_TRY(s->w.ensure(2 * n * r)); CUDA_TRY(s->tess.ensure(n * 4));
+    CUDA_TRY(s->rounding.ensure(n)); CUDA_TRY(s->p64.ensure(n * d));
     CUDA_TRY(s->scal.ensure(64));
     CUDA_TRY(cudaMemsetAsync(s->scal.p, 0, 64, s->stream));
+    CUDA_TRY(s->instp.ensure(sizeof(rich::InstParams)));
     return RICH_OK;
 }
 
@@ -215,10 +231,11 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     CUDA_TRY(upload(s->edge_r, m.edge_r, s->stream));
     CUDA_TRY(upload(s->edge_ta, m.edge_ta, s->stream));
     CUDA_TRY(upload(s->edge_tb, m.edge_tb, s->stream));
+    const size_t r = s->rsize();
     CUDA_TRY(s->ccx.ensure((T + 1) * d)); CUDA_TRY(s->ccy.ensure((T + 1) * d));
     for (DBuf *b : {&s->eL, &s->emlx, &s->emly, &s->emrx, &s->emry, &s->enx, &s->eny, &s->eqx, &s->eqy})
-        CUDA_TRY(b->ensure((E + 1) * d));
-    CUDA_TRY(s->F.ensure((4 * E + 1) * d));
+        CUDA_TRY(b->ensure((E + 1) * r));
+    CUDA_TRY(s->F.ensure((4 * E + 4) * r));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     double t3 = now_ms();
     s->tess_current = true;
@@ -272,7 +289,7 @@ const char *rich_strerror(int code)
     }
 }
 
-const char *rich_last_error(void) { return g_last_error.c_str(); }
+const char *rich_last_error(void) { return rich::last_error(); }
 
 int64_t rich_num_cells(const rich_sim *s) { return s ? s->n : -1; }
 
@@ -325,9 +342,11 @@ int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const dou
     if ((rc = tessellate(s, nullptr, false)) != RICH_OK) return bail(rc);
     if (s->initW.ensure(4 * n * 8) != cudaSuccess) return bail(fail(RICH_ENOMEM, "device primitives"));
     cudaMemcpyAsync(s->initW.p, Wh.data(), 4 * n * 8, cudaMemcpyHostToDevice, s->stream);
-    rich::SweepParams prm = s->params();
-    prm.Un = s->U[0].as<double>();
-    for (int k = 0; k < rich::GEOMETRY_STAGES; k++) rich::launch_stage(k, prm, s->initW.as<double>(), s->stream);
+    s->inst_host = s->inst_params(0.0, true);
+    if (cudaMemcpyAsync(s->instp.p, &s->inst_host, sizeof(rich::InstParams), cudaMemcpyHostToDevice, s->stream) !=
+        cudaSuccess)
+        return bail(fail(RICH_ECUDA, "parameter upload"));
+    for (int k = 0; k < rich::GEOMETRY_STAGES; k++) s->launch(k, s->initW.as<double>(), s->U[0].as<double>());
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return bail(fail(RICH_ECUDA, std::string("init: ") + cudaGetErrorString(e)));
@@ -348,6 +367,14 @@ int rich_set_stream(rich_sim *s, void *stream)
     if (!s) return fail(RICH_EINVAL, "NULL handle");
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     s->stream = stream ? static_cast<cudaStream_t>(stream) : s->own_stream;
+    return RICH_OK;
+}
+
+int rich_set_diagnostics(rich_sim *s, int32_t on)
+{
+    if (!s) return fail(RICH_EINVAL, "NULL handle");
+    if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
+    s->diagnostics = on != 0;
     return RICH_OK;
 }
 
@@ -384,12 +411,13 @@ int rich_sweep(rich_sim *s, double t_end)
     if (!s->tess_current) return fail(RICH_ESTATE, "no current tessellation");
     if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
     if (!(t_end > s->t)) return fail(RICH_EINVAL, "t_end must exceed the current time");
-    rich::SweepParams p = s->params();
-    p.remaining = t_end - s->t;
+    CUDA_TRY(cudaStreamSynchronize(s->stream));  // the staging struct may be in flight
+    s->inst_host = s->inst_params(t_end - s->t);
+    CUDA_TRY(cudaMemcpyAsync(s->instp.p, &s->inst_host, sizeof(rich::InstParams), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(cudaEventRecord(s->ev0, s->stream));
     for (int k = 0; k < rich::NUM_STAGES; k++) {
         if (s->profiling) CUDA_TRY(cudaEventRecord(s->kev[k], s->stream));
-        rich::launch_stage(k, p, nullptr, s->stream);
+        s->launch(k, nullptr);
     }
     if (s->profiling) CUDA_TRY(cudaEventRecord(s->kev[rich::NUM_STAGES], s->stream));
     CUDA_TRY(cudaGetLastError());
@@ -470,8 +498,7 @@ static int ensure_geometry(rich_sim *s)
         int rc = tessellate(s, nullptr, true);
         if (rc) return rc;
     }
-    rich::SweepParams p = s->params();
-    for (int k = 0; k < rich::GEOMETRY_STAGES; k++) rich::launch_stage(k, p, nullptr, s->stream);
+    for (int k = 0; k < rich::GEOMETRY_STAGES; k++) s->launch(k, nullptr);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     return RICH_OK;
@@ -490,6 +517,17 @@ static int fetch(rich_sim *s, const void *dev, std::vector<double> &h, size_t co
     return RICH_OK;
 }
 
+// fetch count values stored in the handle's reconstruction precision
+static int fetch_r(rich_sim *s, const void *dev, std::vector<double> &h, size_t count)
+{
+    if (s->rsize() == sizeof(double)) return fetch(s, dev, h, count);
+    std::vector<float> f(count);
+    CUDA_TRY(cudaMemcpyAsync(f.data(), dev, count * 4, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    h.assign(f.begin(), f.end());
+    return RICH_OK;
+}
+
 int rich_get_state(rich_sim *s, int64_t n, double *x, double *y, double *rho, double *vx, double *vy, double *p,
                    double *area)
 {
@@ -502,9 +540,13 @@ int rich_get_state(rich_sim *s, int64_t n, double *x, double *y, double *rho, do
     if (y) { if ((rc = fetch(s, s->y[s->cur].p, h, N))) return rc; unpermute(s, h.data(), y); }
     double *outs[4] = {rho, vx, vy, p};
     if (rho || vx || vy || p) {
-        if ((rc = fetch(s, s->W.p, h, 4 * N))) return rc;
-        for (int v = 0; v < 4; v++)
-            if (outs[v]) unpermute(s, h.data() + v * N, outs[v]);
+        if ((rc = fetch_r(s, s->W.p, h, 4 * N))) return rc;
+        std::vector<double> comp(N);
+        for (int v = 0; v < 4; v++) {
+            if (!outs[v]) continue;
+            for (size_t k = 0; k < N; k++) comp[k] = h[4 * k + v];
+            unpermute(s, comp.data(), outs[v]);
+        }
     }
     if (area) { if ((rc = fetch(s, s->A.p, h, N))) return rc; unpermute(s, h.data(), area); }
     return RICH_OK;
@@ -537,21 +579,24 @@ int rich_get_field(rich_sim *s, int32_t f, int64_t n, double *out)
     int rc;
     // the diagnostics refer to the points before the last completed step
     const int prev = s->geometry_current && !s->tess_current ? 1 - s->cur : s->cur;
+    // gather component c of an array-of-structures field with `stride` values per cell
+    auto comp_of = [&](const DBuf &b, int stride, int c) {
+        int r2 = fetch_r(s, b.p, h2, stride * N);
+        if (r2) return r2;
+        h.resize(N);
+        for (size_t k = 0; k < N; k++) h[k] = h2[stride * k + c];
+        return RICH_OK;
+    };
     if (f == 0) rc = fetch(s, s->A.p, h, N);
     else if (f == 1 || f == 2) {
-        if ((rc = fetch(s, (f == 1 ? s->ox : s->oy).p, h, N))) return rc;
-        rc = fetch(s, (f == 1 ? s->x[prev] : s->y[prev]).p, h2, N);
-        for (size_t k = 0; k < N; k++) h[k] += h2[k];
-    } else if (f >= 3 && f <= 6) {
-        if ((rc = fetch(s, s->W.p, h2, 4 * N))) return rc;
-        h.assign(h2.begin() + (f - 3) * N, h2.begin() + (f - 2) * N);
-    } else if (f == 7) rc = fetch(s, s->cs.p, h, N);
-    else if (f >= 8 && f <= 23) {
-        const DBuf &b = f < 16 ? s->g : s->gl;
-        int c = (f - 8) % 8;
-        if ((rc = fetch(s, b.p, h2, 8 * N))) return rc;
-        h.assign(h2.begin() + c * N, h2.begin() + (c + 1) * N);
-    } else if (f == 24 || f == 25) rc = fetch(s, (f == 24 ? s->wx : s->wy).p, h, N);
+        if ((rc = comp_of(s->o, 2, f - 1))) return rc;
+        std::vector<double> xs;
+        rc = fetch(s, (f == 1 ? s->x[prev] : s->y[prev]).p, xs, N);
+        for (size_t k = 0; k < N; k++) h[k] += xs[k];
+    } else if (f >= 3 && f <= 6) rc = comp_of(s->W, 4, f - 3);
+    else if (f == 7) rc = fetch_r(s, s->cs.p, h, N);
+    else if (f >= 8 && f <= 23) rc = comp_of(f < 16 ? s->g : s->gl, 8, (f - 8) % 8);
+    else if (f == 24 || f == 25) rc = comp_of(s->w, 2, f - 24);
     else if (f == 26) {
         std::vector<int32_t> ti(N);
         CUDA_TRY(cudaMemcpyAsync(ti.data(), s->tess.p, N * 4, cudaMemcpyDeviceToHost, s->stream));
@@ -559,10 +604,8 @@ int rich_get_field(rich_sim *s, int32_t f, int64_t n, double *out)
         h.resize(N);
         for (size_t k = 0; k < N; k++) h[k] = ti[k];
         rc = RICH_OK;
-    } else if (f >= 27 && f <= 30) {
-        if ((rc = fetch(s, s->alpha.p, h2, 4 * N))) return rc;
-        h.assign(h2.begin() + (f - 27) * N, h2.begin() + (f - 26) * N);
-    } else if (f == 31) {
+    } else if (f >= 27 && f <= 30) rc = comp_of(s->alpha, 4, f - 27);
+    else if (f == 31) {
         h.assign(N, s->last_dt);
         rc = RICH_OK;
     } else

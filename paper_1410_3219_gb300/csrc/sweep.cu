@@ -1,0 +1,546 @@
+// Sweep kernels: steps a1-a9 of one extrapolated-fluxes time step of the
+// moving Voronoi mesh scheme (paper Section 2), templated on the
+// reconstruction precision R (double: all FP64; float: split precision).
+//
+// FP64 throughput on GB300 is ~1.2 TFLOP/s (2 FP64 lanes per clock per SM),
+// so every FP64 quantity is computed once and kept in HBM for the next
+// kernel (Voronoi vertices per triangle, edge geometry per edge, one HLLC
+// flux per edge), divisions and square roots are not repeated, and the
+// fluxes are gathered per cell in a fixed order (deterministic, no atomics).
+// In the split instantiation only the geometry (positions, vertices, areas,
+// centres of mass, coordinate differences) and the conserved variables with
+// their flux accumulation are FP64; everything else runs on the FP32 pipe.
+#include <cfloat>
+#include <cmath>
+
+#include "sweep.cuh"
+
+namespace rich {
+namespace {
+
+constexpr int kBlock = 256;
+
+template <class R> __device__ __forceinline__ double px_of(const SweepParams<R> &p, int32_t q)
+{
+    return q < p.n ? p.x[q] : p.gx[q - p.n];
+}
+template <class R> __device__ __forceinline__ double py_of(const SweepParams<R> &p, int32_t q)
+{
+    return q < p.n ? p.y[q] : p.gy[q - p.n];
+}
+
+template <class R> __device__ __forceinline__ int32_t inst_of(const SweepParams<R> &p, int32_t i)
+{
+    return p.cell_inst ? p.cell_inst[i] : 0;
+}
+
+// real cell behind point q and its mirror flags
+template <class R> __device__ __forceinline__ int32_t src_of(const SweepParams<R> &p, int32_t q, int32_t &xf)
+{
+    if (q < p.n) { xf = 0; return q; }
+    xf = p.ghost_xf[q - p.n];
+    return p.ghost_src[q - p.n];
+}
+
+// primitives of point q (a ghost mirrors the velocity of its source)
+template <class R> __device__ __forceinline__ Vec4<R> load_W(const SweepParams<R> &p, int32_t q)
+{
+    int32_t xf;
+    int32_t k = src_of(p, q, xf);
+    Vec4<R> W = p.W[k];
+    if (xf & 1) W.y = -W.y;
+    if (xf & 2) W.z = -W.z;
+    return W;
+}
+
+// ---------------------------------------------------------------------------
+// a1: circumcentre of every triangle touching a real cell (Voronoi vertices), FP64
+template <class R> __global__ void k_circumcentre(SweepParams<R> p)
+{
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.T) return;
+    int32_t a = p.tri[3 * t], b = p.tri[3 * t + 1], c = p.tri[3 * t + 2];
+    double ax = px_of(p, a), ay = py_of(p, a);
+    double bx = px_of(p, b) - ax, by = py_of(p, b) - ay;
+    double cx = px_of(p, c) - ax, cy = py_of(p, c) - ay;
+    double b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+    double inv = 0.5 / (bx * cy - by * cx);
+    p.ccx[t] = ax + (cy * b2 - by * c2) * inv;
+    p.ccy[t] = ay + (bx * c2 - cx * b2) * inv;
+}
+
+// a1: per-edge geometry relative to the edge's left generator.  The
+// coordinate differences are taken in FP64; the rest in R.
+template <class R> __global__ void k_edge_geometry(SweepParams<R> p)
+{
+    int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.E) return;
+    int32_t l = p.edge_l[e], r = p.edge_r[e];
+    double xl = p.x[l], yl = p.y[l];
+    const double ax64 = p.ccx[p.edge_ta[e]] - xl, ay64 = p.ccy[p.edge_ta[e]] - yl;
+    const double bx64 = p.ccx[p.edge_tb[e]] - xl, by64 = p.ccy[p.edge_tb[e]] - yl;
+    R ax = (R)ax64, ay = (R)ay64, bx = (R)bx64, by = (R)by64;
+    R dx = (R)(px_of(p, r) - xl), dy = (R)(py_of(p, r) - yl);
+    // the edge vector from the FP64 endpoints: a zero-length edge stays ~0
+    // instead of inheriting the rounding of two separately rounded endpoints
+    R ex = (R)(bx64 - ax64), ey = (R)(by64 - ay64);
+    R L = sqrt(ex * ex + ey * ey);
+    R mx = R(0.5) * (ax + bx), my = R(0.5) * (ay + by);
+    R rinv = R(1) / sqrt(dx * dx + dy * dy);
+    p.eL[e] = L;
+    p.emlx[e] = mx;
+    p.emly[e] = my;
+    p.emrx[e] = mx - dx;
+    p.emry[e] = my - dy;
+    p.enx[e] = dx * rinv;
+    p.eny[e] = dy * rinv;
+    p.eqx[e] = (mx - R(0.5) * dx) * rinv;
+    p.eqy[e] = (my - R(0.5) * dy) * rinv;
+}
+
+// a1 + a2: area and centre of mass (shoelace about the generator, FP64),
+// then the primitive variables.  With init_W the conserved variables are set.
+template <class R> __global__ void k_cell_geometry(SweepParams<R> p, const double *__restrict__ init_W)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
+    const double xi = p.x[i], yi = p.y[i];
+    int32_t tl = p.slot_tri[hi - 1];
+    double ax = p.ccx[tl] - xi, ay = p.ccy[tl] - yi;
+    double A2 = 0.0, sx = 0.0, sy = 0.0;
+    for (int32_t s = lo; s < hi; s++) {
+        int32_t t = p.slot_tri[s];
+        double bx = p.ccx[t] - xi, by = p.ccy[t] - yi;
+        double cr = ax * by - ay * bx;
+        A2 += cr;
+        sx += (ax + bx) * cr;
+        sy += (ay + by) * cr;
+        ax = bx;
+        ay = by;
+    }
+    const double A = 0.5 * A2;
+    const double inv3 = 1.0 / (3.0 * A2);
+    const double ox = sx * inv3, oy = sy * inv3;
+    p.A[i] = A;
+    p.o[i] = Vec2<R>{(R)ox, (R)oy};
+    // Section 6 trigger: the generator is more than eta R_i from its centre of
+    // mass.  Rounded cells settle at that distance, so the decision is taken
+    // in FP64 in every precision.
+    {
+        const double d = sqrt(ox * ox + oy * oy);
+        const double Rad = sqrt(A * (1.0 / M_PI));
+        p.rounding[i] = d > p.inst[inst_of(p, i)].eta * Rad ? 1 : 0;
+    }
+    const int32_t n = p.n;
+    const InstParams &ip = p.inst[inst_of(p, i)];
+    const double gamma = ip.gamma;
+    const double gm1 = gamma - 1.0;
+    if (init_W) {
+        if (!ip.init) return;
+        double rho = init_W[i], vx = init_W[n + i], vy = init_W[2 * n + i], pr = init_W[3 * n + i];
+        double m = rho * A;
+        p.Un[i] = m;
+        p.Un[n + i] = m * vx;
+        p.Un[2 * n + i] = m * vy;
+        p.Un[3 * n + i] = (pr / gm1 + 0.5 * rho * (vx * vx + vy * vy)) * A;
+        return;
+    }
+    double m = p.U[i], Px = p.U[n + i], Py = p.U[2 * n + i], E = p.U[3 * n + i];
+    Vec4<R> W;
+    if (sizeof(R) == sizeof(double)) {
+        double invA = 1.0 / A, invm = 1.0 / m;
+        double rho = m * invA, vx = Px * invm, vy = Py * invm;
+        double pr = gm1 * (E - 0.5 * (Px * vx + Py * vy)) * invA;
+        W = Vec4<R>{(R)rho, (R)vx, (R)vy, (R)pr};
+    } else {
+        // the thermal energy cancels kinetic against total energy: FP64; the
+        // FP64 pressure also feeds the shock switch's pressure-ratio test
+        double eth = E - 0.5 * (Px * Px + Py * Py) / m;
+        double pr = gm1 * eth / A;
+        p.p64[i] = pr;
+        R Af = (R)A, mf = (R)m;
+        W = Vec4<R>{mf / Af, (R)Px / mf, (R)Py / mf, (R)pr};
+    }
+    p.W[i] = W;
+    p.cs[i] = sqrt((R)gamma * W.w / W.x);
+}
+
+// Smallest non-negative cell time step of each simulation: a warp whose
+// cells all belong to one simulation reduces first and issues one atomic;
+// a mixed warp issues one atomic per lane.
+__device__ __forceinline__ void warp_min_to(double v, int32_t inst, unsigned long long *dst)
+{
+    const int32_t first = __shfl_sync(0xffffffffu, inst, 0);
+    if (__all_sync(0xffffffffu, inst == first)) {
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0 && v >= 0.0 && v < DBL_MAX)
+            atomicMin(dst + first, (unsigned long long)__double_as_longlong(v));
+    } else if (v >= 0.0 && v < DBL_MAX) {
+        atomicMin(dst + inst, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+// a3-a6: Green-Gauss gradient (Eq. 1), limiter with the shock switch
+// (Eqs. 3-8), cell-rounding mesh velocity (Section 6), per-cell time step.
+template <class R> __global__ void __launch_bounds__(kBlock) k_cell_gradient(SweepParams<R> p)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    double dt_cell = DBL_MAX;
+    int32_t my_inst = 0;
+    if (i < p.n) {
+        my_inst = inst_of(p, i);
+        const InstParams &ip = p.inst[my_inst];
+        const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
+        const Vec4<R> W4 = p.W[i];
+        const R Wi[4] = {W4.x, W4.y, W4.z, W4.w};
+        R acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        R fmx[4] = {Wi[0], Wi[1], Wi[2], Wi[3]};
+        R fmn[4] = {Wi[0], Wi[1], Wi[2], Wi[3]};
+        bool shock = false;
+        const R A = (R)p.A[i];
+        const double dp = ip.delta_p;
+        const double pi64 = sizeof(R) == sizeof(double) ? (double)Wi[3] : p.p64[i];
+        // Eqs. 3-8 look at the cells sharing an edge longer than 1e-9 sqrt(A):
+        // shorter edges are point contacts whose presence depends on round-off
+        const R Lmin = R(1e-9) * sqrt(A);
+        for (int32_t s = lo; s < hi; s++) {
+            int32_t es = p.slot_edge[s];
+            int32_t e = es >> 1;
+            R sg = (es & 1) ? R(-1) : R(1);
+            R L = p.eL[e];
+            R nx = sg * p.enx[e], ny = sg * p.eny[e];
+            R qx = p.eqx[e], qy = p.eqy[e];
+            const Vec4<R> Wv = load_W(p, p.slot_nb[s]);
+            const R Wj[4] = {Wv.x, Wv.y, Wv.z, Wv.w};
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                R d = Wj[v] - Wi[v], a = R(0.5) * (Wi[v] + Wj[v]);
+                acc[2 * v] += L * (d * qx + a * nx);
+                acc[2 * v + 1] += L * (d * qy + a * ny);
+            }
+            if (L > Lmin) {
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    fmx[v] = fmax(fmx[v], Wj[v]);
+                    fmn[v] = fmin(fmn[v], Wj[v]);
+                }
+                double pj64;
+                if (sizeof(R) == sizeof(double)) {
+                    pj64 = (double)Wj[3];
+                } else {
+                    int32_t xf;
+                    pj64 = p.p64[src_of(p, p.slot_nb[s], xf)];
+                }
+                if (fmin(pi64, pj64) < dp * fmax(pi64, pj64)) shock = true;
+            }
+        }
+        const R invA = R(1) / A;
+        R g[8];
+#pragma unroll
+        for (int c = 0; c < 8; c++) g[c] = acc[c] * invA;
+        const R cs = p.cs[i];
+        const R Rad = sqrt(A * (R(1) / R(M_PI)));
+        if (-(g[2] + g[5]) * Rad > (R)ip.delta_v * cs) shock = true;
+        const bool use_tess = ip.limiter == 2 || (ip.limiter == 0 && shock);
+        const Vec2<R> oi = p.o[i];
+        const R ox = oi.x, oy = oi.y;
+        // alpha = min(1, min_j psi_ij) without a division per edge.
+        // AREPO (Eqs. 4-5): psi_ij = (phi_max - phi_i)/dphi for dphi > 0, so the
+        // minimum over those edges sits at the largest dphi (likewise for
+        // dphi < 0); one division per sign and variable.
+        // TESS (Eq. 6): psi_ij = max(theta (phi_j - phi_i)/dphi, 0); the
+        // smallest ratio is found by cross-multiplication, divided once.
+        R alpha[4];
+        if (!use_tess) {
+            R dpos[4] = {0, 0, 0, 0}, dneg[4] = {0, 0, 0, 0};
+            for (int32_t s = lo; s < hi; s++) {
+                int32_t es = p.slot_edge[s];
+                int32_t e = es >> 1;
+                if (!(p.eL[e] > Lmin)) continue;
+                R offx = ((es & 1) ? p.emrx[e] : p.emlx[e]) - ox;
+                R offy = ((es & 1) ? p.emry[e] : p.emly[e]) - oy;
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    R dphi = g[2 * v] * offx + g[2 * v + 1] * offy;
+                    dpos[v] = fmax(dpos[v], dphi);
+                    dneg[v] = fmin(dneg[v], dphi);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                R a = R(1);
+                if (dpos[v] > R(0)) a = fmin(a, (fmx[v] - Wi[v]) / dpos[v]);
+                if (dneg[v] < R(0)) a = fmin(a, (fmn[v] - Wi[v]) / dneg[v]);
+                alpha[v] = a;
+            }
+        } else {
+            R bn[4] = {0, 0, 0, 0}, bd[4] = {0, 0, 0, 0};  // smallest |N|/|D| so far (bd == 0: none)
+            bool zero[4] = {false, false, false, false};
+            for (int32_t s = lo; s < hi; s++) {
+                int32_t es = p.slot_edge[s];
+                int32_t e = es >> 1;
+                if (!(p.eL[e] > Lmin)) continue;
+                R offx = ((es & 1) ? p.emrx[e] : p.emlx[e]) - ox;
+                R offy = ((es & 1) ? p.emry[e] : p.emly[e]) - oy;
+                const Vec4<R> Wv = load_W(p, p.slot_nb[s]);
+                const R Wj[4] = {Wv.x, Wv.y, Wv.z, Wv.w};
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    R dphi = g[2 * v] * offx + g[2 * v + 1] * offy;
+                    if (dphi == R(0)) continue;
+                    R num = Wj[v] - Wi[v];
+                    if (!(num * dphi > R(0))) { zero[v] = true; continue; }
+                    R an = fabs(num), ad = fabs(dphi);
+                    if (bd[v] == R(0) || an * bd[v] < bn[v] * ad) { bn[v] = an; bd[v] = ad; }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                R a = R(1);
+                if (zero[v]) a = R(0);
+                else if (bd[v] > R(0)) a = fmin(a, (R)ip.theta * bn[v] / bd[v]);
+                alpha[v] = a;
+            }
+        }
+        p.gl[2 * i] = Vec4<R>{alpha[0] * g[0], alpha[0] * g[1], alpha[1] * g[2], alpha[1] * g[3]};
+        p.gl[2 * i + 1] = Vec4<R>{alpha[2] * g[4], alpha[2] * g[5], alpha[3] * g[6], alpha[3] * g[7]};
+        if (p.diagnostics) {
+            p.g[2 * i] = Vec4<R>{g[0], g[1], g[2], g[3]};
+            p.g[2 * i + 1] = Vec4<R>{g[4], g[5], g[6], g[7]};
+            p.alpha[i] = Vec4<R>{alpha[0], alpha[1], alpha[2], alpha[3]};
+            p.tess[i] = use_tess ? 1 : 0;
+        }
+        // Section 6: mesh-generating point velocity
+        R wx = 0, wy = 0;
+        if (ip.motion == 0) {
+            wx = Wi[1];
+            wy = Wi[2];
+            if (p.rounding[i]) {
+                R d = sqrt(ox * ox + oy * oy);
+                R f = (R)ip.chi * cs / d;
+                wx += f * ox;
+                wy += f * oy;
+            }
+        }
+        p.w[i] = Vec2<R>{wx, wy};
+        R rx = Wi[1] - wx, ry = Wi[2] - wy;
+        dt_cell = (double)(Rad / (cs + sqrt(rx * rx + ry * ry)));
+    }
+    warp_min_to(dt_cell, my_inst, p.dtmin_bits);
+}
+
+template <class R> __device__ __forceinline__ double step_dt(const SweepParams<R> &p, int32_t inst)
+{
+    const InstParams &ip = p.inst[inst];
+    double dt = ip.cfl * __longlong_as_double((long long)p.dtmin_bits[inst]);
+    return dt > ip.remaining ? ip.remaining : dt;
+}
+
+// half-step prediction of one side's edge state in the frame moving with wf
+template <class R>
+__device__ __forceinline__ void predict(R gam, R hdt, const R W[4], const R g[8], R offx, R offy, R wfx, R wfy,
+                                        R out[4])
+{
+    R ux = W[1] - wfx, uy = W[2] - wfy;
+    R div = g[2] + g[5];
+    R irho = R(1) / W[0];
+    out[0] = W[0] + g[0] * offx + g[1] * offy - hdt * (ux * g[0] + uy * g[1] + W[0] * div);
+    out[1] = W[1] + g[2] * offx + g[3] * offy - hdt * (ux * g[2] + uy * g[3] + g[6] * irho);
+    out[2] = W[2] + g[4] * offx + g[5] * offy - hdt * (ux * g[4] + uy * g[5] + g[7] * irho);
+    out[3] = W[3] + g[6] * offx + g[7] * offy - hdt * (ux * g[6] + uy * g[7] + gam * W[3] * div);
+}
+
+// HLLC (Toro) in the edge frame, states (rho, u_n, u_t, p)
+template <class R> __device__ __forceinline__ void hllc(R gam, const R L[4], const R Rs[4], R F[4])
+{
+    const R rL = L[0], uL = L[1], tL = L[2], pL = L[3];
+    const R rR = Rs[0], uR = Rs[1], tR = Rs[2], pR = Rs[3];
+    const R cL = sqrt(gam * pL / rL), cR = sqrt(gam * pR / rR);
+    const R igm1 = R(1) / (gam - R(1));
+    const R EL = pL * igm1 + R(0.5) * rL * (uL * uL + tL * tL);
+    const R ER = pR * igm1 + R(0.5) * rR * (uR * uR + tR * tR);
+    const R SL = fmin(uL - cL, uR - cR);
+    const R SR = fmax(uL + cL, uR + cR);
+    if (SL >= R(0)) {
+        F[0] = rL * uL; F[1] = rL * uL * uL + pL; F[2] = rL * uL * tL; F[3] = uL * (EL + pL);
+        return;
+    }
+    if (SR <= R(0)) {
+        F[0] = rR * uR; F[1] = rR * uR * uR + pR; F[2] = rR * uR * tR; F[3] = uR * (ER + pR);
+        return;
+    }
+    const R mL = rL * (SL - uL), mR = rR * (SR - uR);
+    const R Ss = (pR - pL + uL * mL - uR * mR) / (mL - mR);
+    if (Ss >= R(0)) {
+        const R f = mL / (SL - Ss);
+        const R Es = f * (EL / rL + (Ss - uL) * (Ss + pL / mL));
+        F[0] = rL * uL + SL * (f - rL);
+        F[1] = rL * uL * uL + pL + SL * (f * Ss - rL * uL);
+        F[2] = rL * uL * tL + SL * (f * tL - rL * tL);
+        F[3] = uL * (EL + pL) + SL * (Es - EL);
+    } else {
+        const R f = mR / (SR - Ss);
+        const R Es = f * (ER / rR + (Ss - uR) * (Ss + pR / mR));
+        F[0] = rR * uR + SR * (f - rR);
+        F[1] = rR * uR * uR + pR + SR * (f * Ss - rR * uR);
+        F[2] = rR * uR * tR + SR * (f * tR - rR * tR);
+        F[3] = uR * (ER + pR) + SR * (Es - ER);
+    }
+}
+
+// a7: one flux per edge in the frame of the moving edge
+template <class R> __global__ void __launch_bounds__(kBlock) k_edge_flux(SweepParams<R> p)
+{
+    int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.E) return;
+    const int32_t l = p.edge_l[e];
+    const int32_t li = inst_of(p, l);
+    const R dt = (R)step_dt(p, li);
+    const R hdt = R(0.5) * dt;
+    int32_t xf;
+    const int32_t k = src_of(p, p.edge_r[e], xf);
+    const R sx = (xf & 1) ? R(-1) : R(1), sy = (xf & 2) ? R(-1) : R(1);
+    const Vec4<R> Wl4 = p.W[l], Wr4 = p.W[k];
+    const R Wl[4] = {Wl4.x, Wl4.y, Wl4.z, Wl4.w};
+    const R Wr[4] = {Wr4.x, sx * Wr4.y, sy * Wr4.z, Wr4.w};
+    const Vec4<R> gl0 = p.gl[2 * l], gl1 = p.gl[2 * l + 1];
+    const Vec4<R> gr0 = p.gl[2 * k], gr1 = p.gl[2 * k + 1];
+    const R gL[8] = {gl0.x, gl0.y, gl0.z, gl0.w, gl1.x, gl1.y, gl1.z, gl1.w};
+    // mirrored source: each derivative takes the flip of its axis, velocity
+    // components also the flip of their own axis
+    const R gR[8] = {sx * gr0.x, sy * gr0.y, gr0.z, sx * sy * gr0.w,
+                     sx * sy * gr1.x, gr1.y, sx * gr1.z, sy * gr1.w};
+    const Vec2<R> wl = p.w[l], wk = p.w[k];
+    const Vec2<R> ol = p.o[l], ok = p.o[k];
+    const R wlx = wl.x, wly = wl.y;
+    const R wrx = sx * wk.x, wry = sy * wk.y;
+    const R orx = sx * ok.x, ory = sy * ok.y;
+    const R L = p.eL[e];
+    const R nx = p.enx[e], ny = p.eny[e];
+    const R qx = p.eqx[e], qy = p.eqy[e];
+    // velocity of the perpendicular bisector at the edge midpoint
+    const R dwc = (wrx - wlx) * qx + (wry - wly) * qy;
+    const R wfx = R(0.5) * (wlx + wrx) - dwc * nx;
+    const R wfy = R(0.5) * (wly + wry) - dwc * ny;
+    R Sl[4], Sr[4];
+    const R gam = (R)p.inst[li].gamma;
+    predict(gam, hdt, Wl, gL, p.emlx[e] - ol.x, p.emly[e] - ol.y, wfx, wfy, Sl);
+    predict(gam, hdt, Wr, gR, p.emrx[e] - orx, p.emry[e] - ory, wfx, wfy, Sr);
+    const R tx = -ny, ty = nx;
+    R WL[4] = {Sl[0], (Sl[1] - wfx) * nx + (Sl[2] - wfy) * ny, (Sl[1] - wfx) * tx + (Sl[2] - wfy) * ty, Sl[3]};
+    R WR[4] = {Sr[0], (Sr[1] - wfx) * nx + (Sr[2] - wfy) * ny, (Sr[1] - wfx) * tx + (Sr[2] - wfy) * ty, Sr[3]};
+    R Fe[4];
+    hllc(gam, WL, WR, Fe);
+    const R Fmx = Fe[1] * nx + Fe[2] * tx, Fmy = Fe[1] * ny + Fe[2] * ty;
+    p.F[e] = Vec4<R>{L * Fe[0], L * (Fmx + Fe[0] * wfx), L * (Fmy + Fe[0] * wfy),
+                     L * (Fe[3] + Fmx * wfx + Fmy * wfy + R(0.5) * (wfx * wfx + wfy * wfy) * Fe[0])};
+}
+
+// a8 + a9: conservative update in FP64 (fixed CSR order, no atomics),
+// advance the generating points in FP64
+template <class R> __global__ void __launch_bounds__(kBlock) k_cell_update(SweepParams<R> p)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    const int32_t n = p.n;
+    const int32_t my_inst = inst_of(p, i);
+    const InstParams &ip = p.inst[my_inst];
+    const double dt = step_dt(p, my_inst);
+    if (i == 0 || inst_of(p, i - 1) != my_inst) p.dt_out[my_inst] = dt;
+    const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int32_t s = lo; s < hi; s++) {
+        int32_t es = p.slot_edge[s];
+        const Vec4<R> f = p.F[es >> 1];
+        if (es & 1) { s0 -= (double)f.x; s1 -= (double)f.y; s2 -= (double)f.z; s3 -= (double)f.w; }
+        else { s0 += (double)f.x; s1 += (double)f.y; s2 += (double)f.z; s3 += (double)f.w; }
+    }
+    double m = p.U[i] - dt * s0;
+    double Px = p.U[n + i] - dt * s1;
+    double Py = p.U[2 * n + i] - dt * s2;
+    double E = p.U[3 * n + i] - dt * s3;
+    p.Un[i] = m;
+    p.Un[n + i] = Px;
+    p.Un[2 * n + i] = Py;
+    p.Un[3 * n + i] = E;
+    int32_t st = 0;
+    if (!(isfinite(m) && isfinite(Px) && isfinite(Py) && isfinite(E))) st |= ST_NAN;
+    else if (!(m > 0.0) || !(2.0 * m * E - (Px * Px + Py * Py) > 0.0)) st |= ST_NEGATIVE;
+    const Vec2<R> w = p.w[i];
+    double xn = p.x[i] + dt * (double)w.x, yn = p.y[i] + dt * (double)w.y;
+    if (ip.boundary == 1) {
+        const double Lx = ip.x1 - ip.x0, Ly = ip.y1 - ip.y0;
+        if (xn < ip.x0) xn += Lx;
+        else if (xn >= ip.x1) xn -= Lx;
+        if (yn < ip.y0) yn += Ly;
+        else if (yn >= ip.y1) yn -= Ly;
+    } else if (!(xn > ip.x0 && xn < ip.x1 && yn > ip.y0 && yn < ip.y1)) {
+        st |= ST_LEFT_BOX;
+    }
+    p.xn[i] = xn;
+    p.yn[i] = yn;
+    if (st) atomicOr(p.status + my_inst, st);
+}
+
+__global__ void k_repack(const int32_t *__restrict__ src, int32_t n_new, int32_t n_old,
+                         const double *__restrict__ U_old, double *__restrict__ U_new)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_new) return;
+    int32_t k = src[i];
+    if (k < 0) return;
+#pragma unroll
+    for (int c = 0; c < 4; c++) U_new[(size_t)c * n_new + i] = U_old[(size_t)c * n_old + k];
+}
+
+inline int blocks(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
+
+}  // namespace
+
+const char *stage_name(int k)
+{
+    static const char *names[NUM_STAGES] = {"k_circumcentre", "k_edge_geometry", "k_cell_geometry", "dt_reset",
+                                            "k_cell_gradient", "k_edge_flux", "k_cell_update"};
+    return k >= 0 && k < NUM_STAGES ? names[k] : "";
+}
+
+template <class R> void launch_stage(int k, const SweepParams<R> &p, const double *init_W, cudaStream_t st)
+{
+    switch (k) {
+    case K_CIRCUMCENTRE:
+        if (p.T > 0) k_circumcentre<R><<<blocks(p.T), kBlock, 0, st>>>(p);
+        break;
+    case K_EDGE_GEOMETRY:
+        if (p.E > 0) k_edge_geometry<R><<<blocks(p.E), kBlock, 0, st>>>(p);
+        break;
+    case K_CELL_GEOMETRY:
+        if (p.n > 0) k_cell_geometry<R><<<blocks(p.n), kBlock, 0, st>>>(p, init_W);
+        break;
+    case K_DT_RESET:
+        cudaMemsetAsync(p.dtmin_bits, 0x7f, sizeof(unsigned long long) * p.n_inst, st);
+        break;
+    case K_CELL_GRADIENT:
+        if (p.n > 0) k_cell_gradient<R><<<blocks(p.n), kBlock, 0, st>>>(p);
+        break;
+    case K_EDGE_FLUX:
+        if (p.E > 0) k_edge_flux<R><<<blocks(p.E), kBlock, 0, st>>>(p);
+        break;
+    case K_CELL_UPDATE:
+        if (p.n > 0) k_cell_update<R><<<blocks(p.n), kBlock, 0, st>>>(p);
+        break;
+    default:
+        break;
+    }
+}
+
+void launch_repack(const int32_t *src, int32_t n_new, int32_t n_old, const double *U_old, double *U_new,
+                   cudaStream_t st)
+{
+    if (n_new > 0) k_repack<<<blocks(n_new), kBlock, 0, st>>>(src, n_new, n_old, U_old, U_new);
+}
+
+template void launch_stage<double>(int, const SweepParams<double> &, const double *, cudaStream_t);
+template void launch_stage<float>(int, const SweepParams<float> &, const double *, cudaStream_t);
+
+}  // namespace rich

@@ -1,20 +1,33 @@
 // Device data of one simulation and the launchers of the sweep kernels
 // (steps a1-a9 of one extrapolated-fluxes time step, paper Section 2.3).
 //
-// Layout in HBM (structure of arrays, cells in Hilbert order):
-//   points     x[2][n], y[2][n] ping-pong real generators; gx, gy ghost images
-//   state      U[2][4*n] ping-pong extensive (m, Px, Py, E), component-major
+// The sweep is instantiated for two reconstruction precisions R:
+//   R = double  every step in FP64;
+//   R = float   split precision: primitives, gradients, limiter, mesh
+//               velocity, edge states and HLLC in FP32, while positions,
+//               Voronoi vertices, areas, centres of mass, the coordinate
+//               differences feeding every edge quantity, and the conserved
+//               variables (with the flux accumulation) stay in FP64.
+//
+// Layout in HBM (cells in Hilbert order):
+//   points     x[2][n], y[2][n] ping-pong real generators (FP64); gx, gy ghosts
+//   state      U[2][4*n] ping-pong extensive (m, Px, Py, E), component-major, FP64
 //   mesh       tri[3*T]; cell_ptr[n+1]; slot_nb/slot_tri/slot_edge[S];
 //              edge_l/edge_r/edge_ta/edge_tb[E]; ghost_src/ghost_xf[g]
-//   geometry   ccx, ccy[T]; per edge L, midpoint-minus-left (mlx, mly),
-//              midpoint-minus-right (mrx, mry), unit normal (nx, ny),
-//              q = c_ij/|r_ij| (qx, qy); per cell A, centre of mass minus
-//              generator (ox, oy)
-//   cell       W[4*n] (rho, vx, vy, p), cs[n], g[8*n] unlimited and
-//              gl[8*n] limited gradients (d/dx,d/dy of each primitive,
-//              component-major), alpha[4*n], tess[n], wx, wy[n]
-//   flux       F[4*E] = L_ij * F_ij, outward from the edge's left cell
-//   scalars    dtmin (bits of the smallest positive cell time step), dt, status
+//   geometry   ccx, ccy[T] (FP64); A[n] (FP64); per edge (R): L, unit normal
+//              (nx, ny), q = c_ij/|r_ij| (qx, qy), midpoint minus left
+//              generator (mlx, mly) and minus right generator (mrx, mry)
+//   cell (R)   W[n] = {rho, vx, vy, p}; o[n] = centre of mass - generator;
+//              cs[n]; gl[2n] limited gradient {drho/dx, drho/dy, dvx/dx,
+//              dvx/dy}, {dvy/dx, dvy/dy, dp/dx, dp/dy}; w[n] mesh velocity;
+//              diagnostics g[2n] (unlimited), alpha[n], tess[n];
+//              rounding[n] (uint8) and, in split precision, p64[n] (FP64):
+//              the two discontinuous decisions of the step (rounding trigger,
+//              pressure-ratio switch) are taken on FP64 values
+//   flux (R)   F[E] = L_ij * F_ij (mass, momentum x, y, energy), outward
+//              from the edge's left cell
+//   per sim    inst[] scheme parameters and remaining time; dtmin (bits of the
+//              smallest cell time step), dt, status
 #pragma once
 
 #include <cstdint>
@@ -28,14 +41,27 @@ enum : int32_t {
     ST_LEFT_BOX = 4,  // a generating point crossed a wall
 };
 
-struct SweepParams {
-    // scheme
+template <class R> struct alignas(4 * sizeof(R)) Vec4 { R x, y, z, w; };
+template <class R> struct alignas(2 * sizeof(R)) Vec2 { R x, y; };
+
+// Scheme parameters of one simulation of a batch (device table).
+struct InstParams {
     double gamma, cfl, chi, eta, theta, delta_v, delta_p;
     double x0, x1, y0, y1;
+    double remaining;  // t_end - t: the step is shortened to land on t_end
     int32_t boundary, motion, limiter;
-    // sizes
+    int32_t init;      // the geometry stage with primitives given sets this simulation's U
+};
+
+template <class R> struct SweepParams {
+    // per-simulation parameters; cell_inst[i] names the simulation of real
+    // cell i (nullptr: every cell belongs to simulation 0)
+    const InstParams *inst;
+    const int32_t *cell_inst;
+    int32_t n_inst, diagnostics;
+    // sizes (all simulations together)
     int32_t n, ng, T, E, S;
-    // points (current and next)
+    // points (current and next), FP64
     const double *x, *y;
     double *xn, *yn;
     const double *gx, *gy;
@@ -44,20 +70,25 @@ struct SweepParams {
     const int32_t *edge_l, *edge_r, *edge_ta, *edge_tb;
     const int32_t *ghost_src, *ghost_xf;
     // geometry
-    double *ccx, *ccy;
-    double *eL, *emlx, *emly, *emrx, *emry, *enx, *eny, *eqx, *eqy;
-    double *A, *ox, *oy;
+    double *ccx, *ccy, *A;
+    R *eL, *enx, *eny, *eqx, *eqy, *emlx, *emly, *emrx, *emry;
     // state
     const double *U;
     double *Un;
-    double *W, *cs, *g, *gl, *alpha, *wx, *wy;
+    Vec4<R> *W;
+    Vec2<R> *o;
+    R *cs;
+    uint8_t *rounding;  // 1 where the Section 6 rounding velocity is on (decided in FP64)
+    double *p64;        // FP64 pressure for the shock switch (split precision only)
+    Vec4<R> *gl, *g, *alpha;
+    Vec2<R> *w;
     int32_t *tess;
-    double *F;
-    // scalars
+    Vec4<R> *F;
+    // per simulation: bits of the smallest cell time step, the step taken,
+    // status flags
     unsigned long long *dtmin_bits;
     double *dt_out;
     int32_t *status;
-    double remaining;  // t_end - t
 };
 
 // Stages of one step, in launch order.  GEOMETRY_STAGES = a1 + a2;
@@ -76,8 +107,13 @@ enum Stage : int {
 
 const char *stage_name(int k);
 
-// Launch one stage.  For K_CELL_GEOMETRY a non-null init_W (4*n primitives,
-// component-major) sets the conserved variables from it instead.
-void launch_stage(int k, const SweepParams &p, const double *init_W, cudaStream_t st);
+// Launch one stage.  For K_CELL_GEOMETRY a non-null init_W (4*n FP64
+// primitives, component-major) sets the conserved variables from it instead.
+template <class R> void launch_stage(int k, const SweepParams<R> &p, const double *init_W, cudaStream_t st);
+
+// U_new[c][i] = U_old[c][src[i]] for the 4 components (component-major
+// arrays of n_old and n_new cells); cells with src[i] < 0 are left alone.
+void launch_repack(const int32_t *src, int32_t n_new, int32_t n_old, const double *U_old, double *U_new,
+                   cudaStream_t st);
 
 }  // namespace rich

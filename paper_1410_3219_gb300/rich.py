@@ -27,7 +27,11 @@ EXPORTS = ["rich_default_config", "rich_init_mesh", "rich_step", "rich_get_state
            "rich_destroy", "rich_strerror", "rich_last_error", "rich_set_stream", "rich_tessellate",
            "rich_sweep", "rich_sync", "rich_get_field", "rich_num_cells", "rich_delaunay_host",
            "rich_rings_host", "rich_set_profiling", "rich_kernel_times", "rich_kernel_name",
-           "rich_courant_dt_noalloc"]
+           "rich_courant_dt_noalloc", "rich_set_diagnostics", "rich_batch_create", "rich_batch_add",
+           "rich_batch_step", "rich_batch_query", "rich_batch_get_conserved", "rich_batch_remove",
+           "rich_batch_set_diagnostics", "rich_batch_cells", "rich_batch_destroy"]
+
+SIM_STATES = {0: "pending", 1: "running", 2: "done", 3: "failed"}
 
 
 class RichError(RuntimeError):
@@ -96,6 +100,18 @@ def _lib():
         L.rich_rings_host.argtypes = [C.POINTER(rich_config), I64, _D, _D, I64, C.POINTER(I64), _D, _D,
                                       C.POINTER(I64), C.POINTER(I64)]
         L.rich_set_profiling.argtypes = [P, I32]
+        L.rich_set_diagnostics.argtypes = [P, I32]
+        L.rich_batch_create.argtypes = [I32, I64, I32, C.POINTER(P)]
+        L.rich_batch_add.argtypes = [P, C.POINTER(rich_config), I64] + [_D] * 6 + [d, I64, C.POINTER(I32)]
+        L.rich_batch_step.argtypes = [P, C.POINTER(rich_step_info)]
+        L.rich_batch_query.argtypes = [P, I32, C.POINTER(I32), C.POINTER(I32), _D, C.POINTER(I64), _D]
+        L.rich_batch_get_conserved.argtypes = [P, I32, I64] + [_D] * 6
+        L.rich_batch_remove.argtypes = [P, I32]
+        L.rich_batch_set_diagnostics.argtypes = [P, I32]
+        L.rich_batch_cells.argtypes = [P]
+        L.rich_batch_cells.restype = I64
+        L.rich_batch_destroy.argtypes = [P]
+        L.rich_batch_destroy.restype = None
         L.rich_kernel_times.argtypes = [P, I32, _D, C.POINTER(I32)]
         L.rich_kernel_name.argtypes = [I32]
         L.rich_kernel_name.restype = C.c_char_p
@@ -184,6 +200,10 @@ def rich_get_field(h, n, name, comp=0):
     return out
 
 
+def rich_set_diagnostics(h, on=True):
+    _check(_lib().rich_set_diagnostics(h, 1 if on else 0))
+
+
 def rich_set_profiling(h, on=True):
     _check(_lib().rich_set_profiling(h, 1 if on else 0))
 
@@ -230,6 +250,93 @@ def rich_rings_host(cfg, x, y):
                                   src.ctypes.data_as(I64P), C.byref(ns)))
     k = ns.value
     return ptr, nbx[:k], nby[:k], src[:k]
+
+
+def rich_batch_create(precision=0, max_cells=1 << 24, host_threads=0):
+    h = C.c_void_p()
+    _check(_lib().rich_batch_create(precision, max_cells, host_threads, C.byref(h)))
+    return h
+
+
+def rich_batch_add(b, cfg, x, y, rho, vx, vy, p, t_end=float("inf"), max_steps=1 << 62):
+    c = cfg if isinstance(cfg, rich_config) else rich_config.from_dict(cfg)
+    n = len(x)
+    arrs = [_f64(a, n) for a in (x, y, rho, vx, vy, p)]
+    sid = C.c_int32()
+    _check(_lib().rich_batch_add(b, C.byref(c), n, *[_p(a) for a in arrs], t_end, max_steps, C.byref(sid)))
+    return sid.value
+
+
+def rich_batch_step(b):
+    info = rich_step_info()
+    _check(_lib().rich_batch_step(b, C.byref(info)))
+    return info.as_dict()
+
+
+def rich_batch_query(b, sid):
+    st, err, t, steps, lat = C.c_int32(), C.c_int32(), C.c_double(), C.c_int64(), C.c_double()
+    _check(_lib().rich_batch_query(b, sid, C.byref(st), C.byref(err), C.byref(t), C.byref(steps), C.byref(lat)))
+    return {"state": SIM_STATES.get(st.value, st.value), "error": err.value, "t": t.value, "steps": steps.value,
+            "latency_ms": lat.value}
+
+
+def rich_batch_get_conserved(b, sid, n):
+    out = [np.zeros(n) for _ in range(6)]
+    _check(_lib().rich_batch_get_conserved(b, sid, n, *[_p(a) for a in out]))
+    return dict(zip(("x", "y", "m", "px", "py", "E"), out))
+
+
+def rich_batch_remove(b, sid):
+    _check(_lib().rich_batch_remove(b, sid))
+
+
+def rich_batch_set_diagnostics(b, on=True):
+    _check(_lib().rich_batch_set_diagnostics(b, 1 if on else 0))
+
+
+def rich_batch_cells(b):
+    return _lib().rich_batch_cells(b)
+
+
+def rich_batch_destroy(b):
+    _lib().rich_batch_destroy(b)
+
+
+class Batch:
+    """Many independent simulations stepped together (device-resident)."""
+
+    def __init__(self, precision=0, max_cells=1 << 24, host_threads=0):
+        self.h = rich_batch_create(precision, max_cells, host_threads)
+        self.sizes = {}
+
+    def add(self, wl, t_end=float("inf"), max_steps=1 << 62):
+        sid = rich_batch_add(self.h, wl["cfg"], wl["x"], wl["y"], wl["rho"], wl["vx"], wl["vy"], wl["p"],
+                             t_end, max_steps)
+        self.sizes[sid] = len(wl["x"])
+        return sid
+
+    def step(self):
+        return rich_batch_step(self.h)
+
+    def query(self, sid):
+        return rich_batch_query(self.h, sid)
+
+    def conserved(self, sid):
+        return rich_batch_get_conserved(self.h, sid, self.sizes[sid])
+
+    def remove(self, sid):
+        rich_batch_remove(self.h, sid)
+
+    def close(self):
+        if self.h:
+            rich_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- convenience wrapper ------------------------------------------------------

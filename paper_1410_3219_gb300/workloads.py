@@ -29,6 +29,8 @@ MESH_EULERIAN = 1
 LIM_SWITCHED = 0
 LIM_AREPO = 1
 LIM_TESS = 2
+FP64 = 0
+FP32_SPLIT = 1
 
 
 def default_cfg(**over):
