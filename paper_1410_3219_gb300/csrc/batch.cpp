@@ -237,8 +237,8 @@ int ensure_device(rich_batch *b)
     for (int k = 0; k < 2; k++) {
         CUDA_TRY(b->x[k].ensure(N * d + 8));
         CUDA_TRY(b->y[k].ensure(N * d + 8));
-        CUDA_TRY(b->U[k].ensure(4 * N * d + 8));
     }
+    // U is grown by the caller: one of its two buffers may hold the live state
     CUDA_TRY(b->A.ensure(N * d + 8)); CUDA_TRY(b->o.ensure(2 * N * r + 16));
     CUDA_TRY(b->W.ensure(4 * N * r + 32)); CUDA_TRY(b->cs.ensure(N * r + 8));
     CUDA_TRY(b->g.ensure(8 * N * r + 64)); CUDA_TRY(b->gl.ensure(8 * N * r + 64));
@@ -433,13 +433,20 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     if (rc) return rc;
     const int nxt = 1 - b->cur;
     if (!same_layout && n_old > 0) {
-        // regather the conserved state of continuing simulations into the other buffer
+        // regather the conserved state of continuing simulations into the other
+        // buffer (grown first: U[cur] holds the live state and is not touched)
+        CUDA_TRY(b->U[nxt].ensure(4 * N * sizeof(double) + 8));
         CUDA_TRY(upload(b->src, b->h_src, b->stream));
         rich::launch_repack(b->src.as<int32_t>(), (int32_t)N, (int32_t)n_old, b->U[b->cur].as<double>(),
                             b->U[nxt].as<double>(), b->stream);
         CUDA_TRY(cudaGetLastError());
         b->cur = nxt;
+    } else if (n_old == 0) {
+        CUDA_TRY(b->U[b->cur].ensure(4 * N * sizeof(double) + 8));  // nothing live yet
     }
+    // the buffer the sweep writes; its old contents are dead
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    CUDA_TRY(b->U[1 - b->cur].ensure(4 * N * sizeof(double) + 8));
     CUDA_TRY(upload(b->x[b->cur], b->h_x, b->stream));
     CUDA_TRY(upload(b->y[b->cur], b->h_y, b->stream));
     CUDA_TRY(upload(b->cell_inst, b->h_cell_inst, b->stream));
