@@ -235,6 +235,26 @@ int rich_batch_set_diagnostics(rich_batch *b, int32_t on);
 /* Cells of pending + running simulations. */
 int64_t rich_batch_cells(const rich_batch *b);
 
+/* How a batch launches its sweep.  mode 0 (default): autotune; the first
+   eight steps each try one of {stage by stage, persistent with 128, 256, 512
+   threads per block} twice, and the fastest is kept.  mode 1: stage by stage
+   (one kernel per stage).  mode 2: persistent with `block` threads (128,
+   256 or 512): all stages in one cooperative kernel launch, grid-stride
+   loops, one block per co-resident slot on every SM, stages separated by
+   grid barriers whose waits give up after about a second (the step is then
+   redone stage by stage and mode 1 is kept).  The persistent launch is
+   recorded once as a CUDA graph and replayed every step (the mesh sizes are
+   read from device memory); it is recorded again when a device buffer
+   moves.  Results do not depend on the mode. */
+int rich_batch_set_launch(rich_batch *b, int32_t mode, int32_t block);
+
+/* The launch shape in use (persistent 0/1, block, grid of the last
+   persistent launch, tuning finished 0/1, graph replay available 0/1) and
+   counts[3] = {staged steps, persistent steps, graph replays}; each output
+   may be NULL. */
+int rich_batch_launch_info(const rich_batch *b, int32_t *persistent, int32_t *block, int32_t *grid, int32_t *tuned,
+                           int32_t *graph, int64_t *counts);
+
 void rich_batch_destroy(rich_batch *b);
 
 /* ---- time step without allocation ---------------------------------------- */

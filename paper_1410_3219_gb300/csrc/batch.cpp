@@ -21,6 +21,7 @@
 // The arithmetic of every cell depends only on its own simulation, so a
 // simulation's results do not depend on what else is in the batch.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -68,6 +69,13 @@ struct BatchSim {
     double t_submit = 0.0, t_admit = 0.0, t_finish = 0.0;
 };
 
+// One way of launching the sweep: stage by stage, or as one persistent
+// cooperative kernel (replayed from a recorded CUDA graph) with a block size.
+struct LaunchShape {
+    bool persistent;
+    int block;
+};
+
 int mesh_code(int rc, std::string &msg)
 {
     if (rc == -2) { msg = "two generating points coincide"; return RICH_EDUPLICATE; }
@@ -94,7 +102,22 @@ struct rich_batch {
     DBuf x[2], y[2], U[2], A, o, W, cs, g, gl, alpha, w, tess, rounding, p64, cell_ptr, cell_inst, initW, src;
     DBuf gx, gy, gsrc, gxf, tri, ccx, ccy, slot_nb, slot_tri, slot_edge;
     DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F;
-    DBuf instp, dtmin, dtout, status;
+    DBuf instp, dtmin, dtout, status, dsizes, gsync;
+    // launch shape: autotuned over the first steps unless fixed by the caller
+    int launch_mode = 0;  // 0 autotune, 1 staged, 2 persistent
+    int fixed_block = 256;
+    std::vector<LaunchShape> cands;
+    std::vector<double> cand_ms;
+    size_t cand_next = 0;
+    bool tuned = false;
+    LaunchShape chosen{false, 256};
+    int last_grid = 0;
+    bool graph_ok = true;
+    std::string graph_note;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> graph_sig;
+    int64_t persistent_launches = 0, graph_launches = 0, staged_launches = 0;
     // host staging of the packed mesh
     std::vector<double> h_x, h_y, h_gx, h_gy, h_W0;
     std::vector<int32_t> h_gsrc, h_gxf, h_tri, h_cell_ptr, h_slot_nb, h_slot_tri, h_slot_edge, h_cell_inst;
@@ -108,6 +131,8 @@ struct rich_batch {
     ~rich_batch()
     {
         if (stream) cudaStreamSynchronize(stream);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         if (stream) cudaStreamDestroy(stream);
@@ -250,6 +275,7 @@ int ensure_device(rich_batch *b)
     CUDA_TRY(b->F.ensure(4 * E * r + 32));
     CUDA_TRY(b->instp.ensure(K * sizeof(rich::InstParams) + 8));
     CUDA_TRY(b->dtmin.ensure(K * 8 + 8)); CUDA_TRY(b->dtout.ensure(K * 8 + 8)); CUDA_TRY(b->status.ensure(K * 4 + 8));
+    CUDA_TRY(b->dsizes.ensure(sizeof(rich::DeviceSizes))); CUDA_TRY(b->gsync.ensure(sizeof(rich::GridSync)));
     (void)G;
     return RICH_OK;
 }
@@ -264,6 +290,121 @@ void finish_copy_out(rich_batch *b, BatchSim &s, int which)
     for (int c = 0; c < 4; c++)
         cudaMemcpyAsync(&s.fin[(2 + c) * n], b->U[which].as<double>() + c * N + s.cell_off, n * 8,
                         cudaMemcpyDeviceToHost, b->stream);
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+template <class R> int persistent_grid(int block)
+{
+    return rich::persistent_blocks_per_sm<R>(block) * sm_count();
+}
+
+// Enqueue the whole sweep as one persistent cooperative launch, from a
+// recorded CUDA graph when possible.  The graph holds the barrier and status
+// resets and the launch; it is recorded again only when a device buffer moved
+// (the mesh sizes come from device memory).
+template <class R> int run_persistent(rich_batch *b, int block)
+{
+    const int grid = persistent_grid<R>(block);
+    if (grid <= 0) return fail(RICH_ECUDA, "persistent sweep cannot be resident");
+    b->last_grid = grid;
+    rich::SweepParams<R> p = b->params<R>();
+    p.n = p.ng = p.T = p.E = p.S = p.n_inst = 0;  // read from device memory
+    rich::DeviceSizes sz{};
+    sz.n = (int32_t)b->n_packed;
+    sz.ng = (int32_t)b->nG;
+    sz.T = (int32_t)b->nT;
+    sz.E = (int32_t)b->nE;
+    sz.n_inst = (int32_t)b->packed.size();
+    CUDA_TRY(cudaMemcpyAsync(b->dsizes.p, &sz, sizeof(sz), cudaMemcpyHostToDevice, b->stream));
+    auto *gs = b->gsync.as<rich::GridSync>();
+    auto *ds = b->dsizes.as<rich::DeviceSizes>();
+    if (b->graph_ok) {
+        std::vector<unsigned char> sig(sizeof(p) + 3 * sizeof(int));
+        std::memcpy(sig.data(), &p, sizeof(p));
+        int extra[3] = {block, grid, (int)sizeof(R)};
+        std::memcpy(sig.data() + sizeof(p), extra, sizeof(extra));
+        if (!b->gexec || sig != b->graph_sig) {
+            if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+            if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+            bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                cudaMemsetAsync(gs, 0, sizeof(rich::GridSync), b->stream);
+                cudaMemsetAsync(b->status.p, 0, b->status.cap, b->stream);
+                cudaError_t le = rich::launch_persistent<R>(p, ds, gs, block, grid, b->stream);
+                cudaError_t ce = cudaStreamEndCapture(b->stream, &b->graph);
+                ok = le == cudaSuccess && ce == cudaSuccess && b->graph &&
+                     cudaGraphInstantiate(&b->gexec, b->graph, 0) == cudaSuccess;
+                if (!ok) b->graph_note = std::string("graph capture failed: ") + cudaGetErrorString(le != cudaSuccess ? le : ce);
+            }
+            cudaGetLastError();
+            if (!ok) {
+                b->graph_ok = false;
+                if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+                if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+            } else {
+                b->graph_sig = sig;
+            }
+        }
+        if (b->graph_ok) {
+            CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
+            b->graph_launches++;
+            b->persistent_launches++;
+            return RICH_OK;
+        }
+    }
+    CUDA_TRY(cudaMemsetAsync(gs, 0, sizeof(rich::GridSync), b->stream));
+    CUDA_TRY(cudaMemsetAsync(b->status.p, 0, b->status.cap, b->stream));
+    CUDA_TRY(rich::launch_persistent<R>(p, ds, gs, block, grid, b->stream));
+    b->persistent_launches++;
+    return RICH_OK;
+}
+
+int run_staged(rich_batch *b)
+{
+    CUDA_TRY(cudaMemsetAsync(b->status.p, 0, b->status.cap, b->stream));
+    for (int k = 0; k < rich::NUM_STAGES; k++) b->launch(k, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    b->staged_launches++;
+    return RICH_OK;
+}
+
+// the launch shape of this step: the next untried candidate while tuning
+LaunchShape pick_shape(rich_batch *b)
+{
+    if (b->launch_mode == 1) return LaunchShape{false, 256};
+    if (b->launch_mode == 2) return LaunchShape{true, b->fixed_block};
+    if (b->tuned) return b->chosen;
+    if (b->cands.empty()) {
+        // every candidate twice; the faster of its two timings counts
+        for (int rep = 0; rep < 2; rep++) {
+            b->cands.push_back(LaunchShape{false, 256});
+            for (int bs : {128, 256, 512}) b->cands.push_back(LaunchShape{true, bs});
+        }
+        b->cand_ms.assign(b->cands.size(), 0.0);
+    }
+    return b->cands[b->cand_next];
+}
+
+void record_timing(rich_batch *b, const LaunchShape &s, double ms)
+{
+    if (b->launch_mode != 0 || b->tuned) return;
+    b->cand_ms[b->cand_next++] = ms;
+    if (b->cand_next < b->cands.size()) return;
+    const size_t half = b->cands.size() / 2;
+    double best = 1e300;
+    for (size_t k = 0; k < half; k++) {
+        double t = std::min(b->cand_ms[k], b->cand_ms[k + half]);
+        if (t < best) { best = t; b->chosen = b->cands[k]; }
+    }
+    b->tuned = true;
+    (void)s;
 }
 
 }  // namespace
@@ -482,10 +623,30 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     }
     const double t3 = now_ms();
     // 6. the sweep over every cell of every simulation
+    const LaunchShape shape = pick_shape(b);
     CUDA_TRY(cudaEventRecord(b->ev0, b->stream));
-    for (int k = 0; k < rich::NUM_STAGES; k++) b->launch(k, nullptr);
-    CUDA_TRY(cudaGetLastError());
+    if (shape.persistent) {
+        rc = b->precision == RICH_FP32_SPLIT ? run_persistent<float>(b, shape.block) : run_persistent<double>(b, shape.block);
+    } else {
+        rc = run_staged(b);
+    }
+    if (rc) return rc;
     CUDA_TRY(cudaEventRecord(b->ev1, b->stream));
+    if (shape.persistent) {
+        int32_t timeout = 0;
+        CUDA_TRY(cudaMemcpyAsync(&timeout, (char *)b->gsync.p + offsetof(rich::GridSync, timeout), 4,
+                                 cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        if (timeout) {
+            // a barrier wait gave up: the inputs of the step are untouched, so
+            // redo it stage by stage and keep the staged launch from now on
+            b->launch_mode = 1;
+            b->graph_note = "persistent sweep barrier timed out; staged launches used";
+            CUDA_TRY(cudaEventRecord(b->ev0, b->stream));
+            if ((rc = run_staged(b))) return rc;
+            CUDA_TRY(cudaEventRecord(b->ev1, b->stream));
+        }
+    }
     b->h_dt.resize(ok.size());
     b->h_status.resize(ok.size());
     CUDA_TRY(cudaMemcpyAsync(b->h_dt.data(), b->dtout.p, ok.size() * 8, cudaMemcpyDeviceToHost, b->stream));
@@ -493,6 +654,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     CUDA_TRY(cudaStreamSynchronize(b->stream));
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+    record_timing(b, shape, ms);
     // 7. per-simulation bookkeeping; a failed step keeps that simulation's old state
     const int nxt2 = 1 - b->cur;
     const double tnow = now_ms();
@@ -606,5 +768,38 @@ int rich_batch_set_diagnostics(rich_batch *b, int32_t on)
 }
 
 int64_t rich_batch_cells(const rich_batch *b) { return b ? b->cells_admitted : -1; }
+
+int rich_batch_set_launch(rich_batch *b, int32_t mode, int32_t block)
+{
+    if (!b) return fail(RICH_EINVAL, "NULL handle");
+    if (mode < 0 || mode > 2 || (mode == 2 && block != 128 && block != 256 && block != 512))
+        return fail(RICH_EINVAL, "mode 0 (autotune), 1 (staged) or 2 (persistent, block 128/256/512)");
+    b->launch_mode = mode;
+    b->fixed_block = block;
+    b->tuned = false;
+    b->cands.clear();
+    b->cand_next = 0;
+    return RICH_OK;
+}
+
+int rich_batch_launch_info(const rich_batch *b, int32_t *persistent, int32_t *block, int32_t *grid, int32_t *tuned,
+                           int32_t *graph, int64_t *counts)
+{
+    if (!b) return fail(RICH_EINVAL, "NULL handle");
+    LaunchShape s = b->launch_mode == 1 ? LaunchShape{false, 256}
+                    : b->launch_mode == 2 ? LaunchShape{true, b->fixed_block}
+                                          : b->chosen;
+    if (persistent) *persistent = s.persistent ? 1 : 0;
+    if (block) *block = s.block;
+    if (grid) *grid = b->last_grid;
+    if (tuned) *tuned = (b->launch_mode != 0 || b->tuned) ? 1 : 0;
+    if (graph) *graph = b->graph_ok ? 1 : 0;
+    if (counts) {
+        counts[0] = b->staged_launches;
+        counts[1] = b->persistent_launches;
+        counts[2] = b->graph_launches;
+    }
+    return RICH_OK;
+}
 
 }  // extern "C"

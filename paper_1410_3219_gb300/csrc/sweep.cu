@@ -55,10 +55,8 @@ template <class R> __device__ __forceinline__ Vec4<R> load_W(const SweepParams<R
 
 // ---------------------------------------------------------------------------
 // a1: circumcentre of every triangle touching a real cell (Voronoi vertices), FP64
-template <class R> __global__ void k_circumcentre(SweepParams<R> p)
+template <class R> __device__ __forceinline__ void stage_circumcentre(const SweepParams<R> &p, int32_t t)
 {
-    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= p.T) return;
     int32_t a = p.tri[3 * t], b = p.tri[3 * t + 1], c = p.tri[3 * t + 2];
     double ax = px_of(p, a), ay = py_of(p, a);
     double bx = px_of(p, b) - ax, by = py_of(p, b) - ay;
@@ -69,12 +67,16 @@ template <class R> __global__ void k_circumcentre(SweepParams<R> p)
     p.ccy[t] = ay + (bx * c2 - cx * b2) * inv;
 }
 
+template <class R> __global__ void k_circumcentre(SweepParams<R> p)
+{
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < p.T) stage_circumcentre(p, t);
+}
+
 // a1: per-edge geometry relative to the edge's left generator.  The
 // coordinate differences are taken in FP64; the rest in R.
-template <class R> __global__ void k_edge_geometry(SweepParams<R> p)
+template <class R> __device__ __forceinline__ void stage_edge_geometry(const SweepParams<R> &p, int32_t e)
 {
-    int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= p.E) return;
     int32_t l = p.edge_l[e], r = p.edge_r[e];
     double xl = p.x[l], yl = p.y[l];
     const double ax64 = p.ccx[p.edge_ta[e]] - xl, ay64 = p.ccy[p.edge_ta[e]] - yl;
@@ -98,12 +100,17 @@ template <class R> __global__ void k_edge_geometry(SweepParams<R> p)
     p.eqy[e] = (my - R(0.5) * dy) * rinv;
 }
 
+template <class R> __global__ void k_edge_geometry(SweepParams<R> p)
+{
+    int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < p.E) stage_edge_geometry(p, e);
+}
+
 // a1 + a2: area and centre of mass (shoelace about the generator, FP64),
 // then the primitive variables.  With init_W the conserved variables are set.
-template <class R> __global__ void k_cell_geometry(SweepParams<R> p, const double *__restrict__ init_W)
+template <class R>
+__device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, const double *__restrict__ init_W, int32_t i)
 {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.n) return;
     const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
     const double xi = p.x[i], yi = p.y[i];
     int32_t tl = p.slot_tri[hi - 1];
@@ -166,6 +173,12 @@ template <class R> __global__ void k_cell_geometry(SweepParams<R> p, const doubl
     p.cs[i] = sqrt((R)gamma * W.w / W.x);
 }
 
+template <class R> __global__ void k_cell_geometry(SweepParams<R> p, const double *__restrict__ init_W)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < p.n) stage_cell_geometry(p, init_W, i);
+}
+
 // Smallest non-negative cell time step of each simulation: a warp whose
 // cells all belong to one simulation reduces first and issues one atomic;
 // a mixed warp issues one atomic per lane.
@@ -183,12 +196,10 @@ __device__ __forceinline__ void warp_min_to(double v, int32_t inst, unsigned lon
 
 // a3-a6: Green-Gauss gradient (Eq. 1), limiter with the shock switch
 // (Eqs. 3-8), cell-rounding mesh velocity (Section 6), per-cell time step.
-template <class R> __global__ void __launch_bounds__(kBlock) k_cell_gradient(SweepParams<R> p)
+template <class R> __device__ __forceinline__ double stage_cell_gradient(const SweepParams<R> &p, int32_t i, int32_t &my_inst)
 {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     double dt_cell = DBL_MAX;
-    int32_t my_inst = 0;
-    if (i < p.n) {
+    {
         my_inst = inst_of(p, i);
         const InstParams &ip = p.inst[my_inst];
         const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
@@ -327,6 +338,15 @@ template <class R> __global__ void __launch_bounds__(kBlock) k_cell_gradient(Swe
         R rx = Wi[1] - wx, ry = Wi[2] - wy;
         dt_cell = (double)(Rad / (cs + sqrt(rx * rx + ry * ry)));
     }
+    return dt_cell;
+}
+
+template <class R> __global__ void __launch_bounds__(kBlock) k_cell_gradient(SweepParams<R> p)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    double dt_cell = DBL_MAX;
+    int32_t my_inst = 0;
+    if (i < p.n) dt_cell = stage_cell_gradient(p, i, my_inst);
     warp_min_to(dt_cell, my_inst, p.dtmin_bits);
 }
 
@@ -390,10 +410,8 @@ template <class R> __device__ __forceinline__ void hllc(R gam, const R L[4], con
 }
 
 // a7: one flux per edge in the frame of the moving edge
-template <class R> __global__ void __launch_bounds__(kBlock) k_edge_flux(SweepParams<R> p)
+template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepParams<R> &p, int32_t e)
 {
-    int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= p.E) return;
     const int32_t l = p.edge_l[e];
     const int32_t li = inst_of(p, l);
     const R dt = (R)step_dt(p, li);
@@ -437,12 +455,16 @@ template <class R> __global__ void __launch_bounds__(kBlock) k_edge_flux(SweepPa
                      L * (Fe[3] + Fmx * wfx + Fmy * wfy + R(0.5) * (wfx * wfx + wfy * wfy) * Fe[0])};
 }
 
+template <class R> __global__ void __launch_bounds__(kBlock) k_edge_flux(SweepParams<R> p)
+{
+    int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < p.E) stage_edge_flux(p, e);
+}
+
 // a8 + a9: conservative update in FP64 (fixed CSR order, no atomics),
 // advance the generating points in FP64
-template <class R> __global__ void __launch_bounds__(kBlock) k_cell_update(SweepParams<R> p)
+template <class R> __device__ __forceinline__ void stage_cell_update(const SweepParams<R> &p, int32_t i)
 {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.n) return;
     const int32_t n = p.n;
     const int32_t my_inst = inst_of(p, i);
     const InstParams &ip = p.inst[my_inst];
@@ -481,6 +503,79 @@ template <class R> __global__ void __launch_bounds__(kBlock) k_cell_update(Sweep
     p.xn[i] = xn;
     p.yn[i] = yn;
     if (st) atomicOr(p.status + my_inst, st);
+}
+
+template <class R> __global__ void __launch_bounds__(kBlock) k_cell_update(SweepParams<R> p)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < p.n) stage_cell_update(p, i);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent sweep: every stage in one cooperative launch.
+
+constexpr long long kSpinLimit = 1ll << 24;  // ~1-2 s of polling with 64 ns sleeps
+
+// Grid-wide barrier.  Thread 0 of each block reads the generation, arrives,
+// and waits for the last block to bump the generation; a wait that exceeds
+// kSpinLimit polls sets the timeout flag instead.  Returns false once any
+// block has given up, and the caller then leaves the kernel.
+__device__ bool grid_sync(GridSync *gs, unsigned int nblocks)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &gs->gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&gs->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == g) {
+                if (++it > kSpinLimit) {
+                    atomicExch(&gs->timeout, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int32_t *)&gs->timeout == 0;
+}
+
+template <class R>
+__global__ void __launch_bounds__(512) k_sweep_persistent(SweepParams<R> p, const DeviceSizes *sz, GridSync *gs)
+{
+    p.n = sz->n;
+    p.ng = sz->ng;
+    p.T = sz->T;
+    p.E = sz->E;
+    p.n_inst = sz->n_inst;
+    const unsigned int nb = gridDim.x;
+    const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t stride = gridDim.x * blockDim.x;
+    for (int32_t k = tid; k < p.n_inst; k += stride) p.dtmin_bits[k] = 0x7f7f7f7f7f7f7f7full;
+    for (int32_t t = tid; t < p.T; t += stride) stage_circumcentre(p, t);
+    if (!grid_sync(gs, nb)) return;
+    for (int32_t e = tid; e < p.E; e += stride) stage_edge_geometry(p, e);
+    for (int32_t i = tid; i < p.n; i += stride) stage_cell_geometry(p, (const double *)nullptr, i);
+    if (!grid_sync(gs, nb)) return;
+    for (int32_t base = blockIdx.x * blockDim.x; base < p.n; base += stride) {
+        const int32_t i = base + threadIdx.x;
+        double v = DBL_MAX;
+        int32_t inst = 0;
+        if (i < p.n) v = stage_cell_gradient(p, i, inst);
+        warp_min_to(v, inst, p.dtmin_bits);
+    }
+    if (!grid_sync(gs, nb)) return;
+    for (int32_t e = tid; e < p.E; e += stride) stage_edge_flux(p, e);
+    if (!grid_sync(gs, nb)) return;
+    for (int32_t i = tid; i < p.n; i += stride) stage_cell_update(p, i);
 }
 
 __global__ void k_repack(const int32_t *__restrict__ src, int32_t n_new, int32_t n_old,
@@ -539,6 +634,37 @@ void launch_repack(const int32_t *src, int32_t n_new, int32_t n_old, const doubl
 {
     if (n_new > 0) k_repack<<<blocks(n_new), kBlock, 0, st>>>(src, n_new, n_old, U_old, U_new);
 }
+
+template <class R>
+cudaError_t launch_persistent(const SweepParams<R> &p, const DeviceSizes *sizes, GridSync *sync, int block, int grid,
+                              cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_sweep_persistent<R>, p, sizes, sync);
+}
+
+template <class R> int persistent_blocks_per_sm(int block)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_persistent<R>, block, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
+template cudaError_t launch_persistent<double>(const SweepParams<double> &, const DeviceSizes *, GridSync *, int, int,
+                                               cudaStream_t);
+template cudaError_t launch_persistent<float>(const SweepParams<float> &, const DeviceSizes *, GridSync *, int, int,
+                                              cudaStream_t);
+template int persistent_blocks_per_sm<double>(int);
+template int persistent_blocks_per_sm<float>(int);
 
 template void launch_stage<double>(int, const SweepParams<double> &, const double *, cudaStream_t);
 template void launch_stage<float>(int, const SweepParams<float> &, const double *, cudaStream_t);

@@ -111,6 +111,29 @@ const char *stage_name(int k);
 // primitives, component-major) sets the conserved variables from it instead.
 template <class R> void launch_stage(int k, const SweepParams<R> &p, const double *init_W, cudaStream_t st);
 
+// Sizes of the packed mesh, read by the persistent sweep from device memory
+// so that one recorded launch serves every step.
+struct DeviceSizes {
+    int32_t n, ng, T, E, n_inst, pad[3];
+};
+
+// State of the persistent sweep's grid barrier (zeroed before each launch).
+struct GridSync {
+    unsigned int count, gen;
+    int32_t timeout;  // set when a barrier wait gave up; the sweep then stops
+    int32_t pad;
+};
+
+// The whole step a1-a9 in one cooperative launch of `grid` blocks of `block`
+// threads (grid <= co-resident blocks): grid-stride loops over triangles,
+// edges and cells, separated by four grid barriers whose waits give up after
+// about a second (GridSync::timeout).
+template <class R>
+cudaError_t launch_persistent(const SweepParams<R> &p, const DeviceSizes *sizes, GridSync *sync, int block, int grid,
+                              cudaStream_t st);
+// Co-resident blocks per SM of the persistent sweep for a block size.
+template <class R> int persistent_blocks_per_sm(int block);
+
 // U_new[c][i] = U_old[c][src[i]] for the 4 components (component-major
 // arrays of n_old and n_new cells); cells with src[i] < 0 are left alone.
 void launch_repack(const int32_t *src, int32_t n_new, int32_t n_old, const double *U_old, double *U_new,

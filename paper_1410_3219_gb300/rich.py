@@ -29,7 +29,8 @@ EXPORTS = ["rich_default_config", "rich_init_mesh", "rich_step", "rich_get_state
            "rich_rings_host", "rich_set_profiling", "rich_kernel_times", "rich_kernel_name",
            "rich_courant_dt_noalloc", "rich_set_diagnostics", "rich_batch_create", "rich_batch_add",
            "rich_batch_step", "rich_batch_query", "rich_batch_get_conserved", "rich_batch_remove",
-           "rich_batch_set_diagnostics", "rich_batch_cells", "rich_batch_destroy"]
+           "rich_batch_set_diagnostics", "rich_batch_cells", "rich_batch_destroy", "rich_batch_set_launch",
+           "rich_batch_launch_info"]
 
 SIM_STATES = {0: "pending", 1: "running", 2: "done", 3: "failed"}
 
@@ -112,6 +113,8 @@ def _lib():
         L.rich_batch_cells.restype = I64
         L.rich_batch_destroy.argtypes = [P]
         L.rich_batch_destroy.restype = None
+        L.rich_batch_set_launch.argtypes = [P, I32, I32]
+        L.rich_batch_launch_info.argtypes = [P] + [C.POINTER(I32)] * 5 + [C.POINTER(I64)]
         L.rich_kernel_times.argtypes = [P, I32, _D, C.POINTER(I32)]
         L.rich_kernel_name.argtypes = [I32]
         L.rich_kernel_name.restype = C.c_char_p
@@ -298,6 +301,18 @@ def rich_batch_cells(b):
     return _lib().rich_batch_cells(b)
 
 
+def rich_batch_set_launch(b, mode=0, block=256):
+    _check(_lib().rich_batch_set_launch(b, mode, block))
+
+
+def rich_batch_launch_info(b):
+    v = [C.c_int32() for _ in range(5)]
+    cnt = (C.c_int64 * 3)()
+    _check(_lib().rich_batch_launch_info(b, *[C.byref(x) for x in v], cnt))
+    return {"persistent": v[0].value, "block": v[1].value, "grid": v[2].value, "tuned": v[3].value,
+            "graph": v[4].value, "staged_steps": cnt[0], "persistent_steps": cnt[1], "graph_replays": cnt[2]}
+
+
 def rich_batch_destroy(b):
     _lib().rich_batch_destroy(b)
 
@@ -326,6 +341,12 @@ class Batch:
 
     def remove(self, sid):
         rich_batch_remove(self.h, sid)
+
+    def set_launch(self, mode=0, block=256):
+        rich_batch_set_launch(self.h, mode, block)
+
+    def launch_info(self):
+        return rich_batch_launch_info(self.h)
 
     def close(self):
         if self.h:

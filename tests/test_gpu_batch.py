@@ -21,7 +21,7 @@ def R():
 
 def mix(precision):
     wls = [W.sod(n_side=24, seed=11), W.sedov(n=2000, seed=12), W.gresho(n_side=20, seed=13),
-           W.kelvin_helmholtz(n_side=32, seed=14), W.random_mixed(n=900, seed=15),
+           W.kelvin_helmholtz(n_side=32, seed=14), W.random_smooth(n=900, seed=15),
            W.random_smooth(n=700, seed=16, boundary=W.BC_REFLECTIVE)]
     for wl in wls:
         wl["cfg"]["precision"] = precision
@@ -40,13 +40,15 @@ def solo(R, wl, steps, t_end=np.inf):
 def test_batch_equals_solo_runs(R, precision):
     wls = mix(precision)
     b = R.Batch(precision=precision)
-    ids = [b.add(wl, max_steps=6) for wl in wls]
-    for _ in range(6):
+    ids = [b.add(wl, max_steps=12) for wl in wls]
+    for _ in range(12):  # the launch autotuner tries its 8 shapes during these steps
         b.step()
+    info = b.launch_info()
+    assert info["tuned"] == 1 and info["staged_steps"] >= 2 and info["persistent_steps"] >= 6
     for wl, sid in zip(wls, ids):
         q = b.query(sid)
-        assert q["state"] == "done" and q["steps"] == 6
-        got, ref = b.conserved(sid), solo(R, wl, 6)
+        assert q["state"] == "done" and q["steps"] == 12, (wl["name"], q)
+        got, ref = b.conserved(sid), solo(R, wl, 12)
         for k in ref:
             assert np.array_equal(got[k], ref[k]), (wl["name"], k)
     b.close()
@@ -77,6 +79,24 @@ def test_batch_admission_mid_run_and_uneven_budgets(R):
     ref = solo(R, wls[4], 1000, t_end=0.004)
     got = b.conserved(t_end_sim)
     assert all(np.array_equal(got[k], ref[k]) for k in ref)
+    b.close()
+
+
+@pytest.mark.parametrize("mode,block", [(1, 256), (2, 128), (2, 256), (2, 512)])
+def test_batch_launch_shapes_give_identical_results(R, mode, block):
+    wls = mix(W.FP64)[:4]
+    b = R.Batch()
+    b.set_launch(mode, block)
+    ids = [b.add(wl, max_steps=5) for wl in wls]
+    for _ in range(5):
+        b.step()
+    info = b.launch_info()
+    if mode == 2:
+        assert info["persistent_steps"] == 5 and info["block"] == block
+    for wl, sid in zip(wls, ids):
+        ref = solo(R, wl, 5)
+        got = b.conserved(sid)
+        assert all(np.array_equal(got[k], ref[k]) for k in ref), (mode, block, wl["name"])
     b.close()
 
 
