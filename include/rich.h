@@ -257,6 +257,51 @@ int rich_batch_launch_info(const rich_batch *b, int32_t *persistent, int32_t *bl
 
 void rich_batch_destroy(rich_batch *b);
 
+/* ---- continuous-batching server -------------------------------------------- */
+
+/* A request loop over a batch: submitted simulations wait in arrival order
+   and are admitted at the next tick at which their cells fit in the device
+   budget; each tick advances every admitted simulation by one step in one
+   batched sweep, and finished ones free their cells at once.  State stays on
+   the device between ticks.  Per request the server records queueing time
+   (submission to admission) and latency (submission to the end of its last
+   step), host wall clock in milliseconds. */
+typedef struct rich_server rich_server;
+
+#define RICH_REQ_QUEUED 0
+#define RICH_REQ_RUNNING 1
+#define RICH_REQ_DONE 2
+#define RICH_REQ_FAILED 3
+
+/* As rich_batch_create; max_cells is the admission budget. */
+int rich_server_create(int32_t precision, int64_t max_cells, int32_t host_threads, rich_server **out);
+
+/* Queue a simulation (inputs are copied; arguments as rich_batch_add).
+   *req receives the request id.  Errors: RICH_EINVAL (also for n above the
+   budget); invalid simulation parameters surface as a failed request. */
+int rich_server_submit(rich_server *s, const rich_config *cfg, int64_t n, const double *x, const double *y,
+                       const double *rho, const double *vx, const double *vy, const double *p, double t_end,
+                       int64_t max_steps, int64_t *req);
+
+/* Admit what fits, then one batched step.  info as rich_batch_step; the
+   counts of requests admitted this tick, still running, and still queued
+   (each output may be NULL). */
+int rich_server_tick(rich_server *s, rich_step_info *info, int32_t *admitted, int32_t *running, int32_t *queued);
+
+/* State (RICH_REQ_*), error code of a failed request, steps taken, queueing
+   time (-1 while queued) and latency (-1 until finished). */
+int rich_server_query(rich_server *s, int64_t req, int32_t *state, int32_t *error, int64_t *steps, double *queue_ms,
+                      double *latency_ms);
+
+/* Results of a finished request (as rich_batch_get_conserved), then forget it. */
+int rich_server_fetch(rich_server *s, int64_t req, int64_t n, double *x, double *y, double *m, double *px,
+                      double *py, double *E);
+
+/* The batch the server steps (for rich_batch_set_launch / launch_info). */
+rich_batch *rich_server_batch(rich_server *s);
+
+void rich_server_destroy(rich_server *s);
+
 /* ---- time step without allocation ---------------------------------------- */
 
 /* Largest n accepted by rich_courant_dt_noalloc. */

@@ -15,7 +15,7 @@ OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librich.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["sweep.cu", "courant_noalloc.cu"]
-HOST_SOURCES = ["predicates.cpp", "mesh.cpp", "rich_api.cpp", "batch.cpp"]
+HOST_SOURCES = ["predicates.cpp", "mesh.cpp", "rich_api.cpp", "batch.cpp", "server.cpp"]
 
 
 def _nvcc():

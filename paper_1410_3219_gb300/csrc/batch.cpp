@@ -191,9 +191,9 @@ struct rich_batch {
 
     BatchSim *find(int32_t id) const
     {
-        for (auto &s : sims)
-            if (s->id == id && s->state != REMOVED) return s.get();
-        return nullptr;
+        if (id < 0 || (size_t)id >= sims.size()) return nullptr;
+        BatchSim *s = sims[id].get();
+        return s->state == REMOVED ? nullptr : s;
     }
 };
 
@@ -471,9 +471,7 @@ int rich_batch_add(rich_batch *b, const rich_config *cfg, int64_t n, const doubl
     s->t_end = t_end;
     s->max_steps = max_steps;
     s->t_submit = now_ms();
-    int32_t next = 0;
-    for (auto &o : b->sims) next = std::max(next, o->id + 1);
-    s->id = next;
+    s->id = (int32_t)b->sims.size();  // ids index the simulation list
     *id = s->id;
     b->cells_admitted += n;
     b->sims.push_back(std::move(s));
@@ -757,6 +755,10 @@ int rich_batch_remove(rich_batch *b, int32_t id)
     s->fin.shrink_to_fit();
     s->hm = rich::HostMesh();
     s->dt = rich::Delaunay();
+    s->hx = std::vector<double>();
+    s->hy = std::vector<double>();
+    s->perm = std::vector<int32_t>();
+    s->W0 = std::vector<double>();
     return RICH_OK;
 }
 

@@ -353,7 +353,10 @@ template <class R> __global__ void __launch_bounds__(kBlock) k_cell_gradient(Swe
 template <class R> __device__ __forceinline__ double step_dt(const SweepParams<R> &p, int32_t inst)
 {
     const InstParams &ip = p.inst[inst];
-    double dt = ip.cfl * __longlong_as_double((long long)p.dtmin_bits[inst]);
+    // read through L2: in the persistent sweep the minimum was reset and then
+    // reduced with atomics earlier in the same launch, and a line of it may
+    // still sit stale in this SM's L1
+    double dt = ip.cfl * __longlong_as_double((long long)__ldcg(p.dtmin_bits + inst));
     return dt > ip.remaining ? ip.remaining : dt;
 }
 
@@ -450,6 +453,14 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
     R WR[4] = {Sr[0], (Sr[1] - wfx) * nx + (Sr[2] - wfy) * ny, (Sr[1] - wfx) * tx + (Sr[2] - wfy) * ty, Sr[3]};
     R Fe[4];
     hllc(gam, WL, WR, Fe);
+    if (xf && k == l) {
+        // a wall: the cell faces its own mirror image.  The mirrored Riemann
+        // problem has u* = 0 and the wall does not move normal to itself, so
+        // mass, tangential momentum and energy fluxes vanish exactly; only
+        // the normal pressure flux remains (round-off would otherwise leak).
+        p.F[e] = Vec4<R>{R(0), L * Fe[1] * nx, L * Fe[1] * ny, R(0)};
+        return;
+    }
     const R Fmx = Fe[1] * nx + Fe[2] * tx, Fmy = Fe[1] * ny + Fe[2] * ty;
     p.F[e] = Vec4<R>{L * Fe[0], L * (Fmx + Fe[0] * wfx), L * (Fmy + Fe[0] * wfy),
                      L * (Fe[3] + Fmx * wfx + Fmy * wfy + R(0.5) * (wfx * wfx + wfy * wfy) * Fe[0])};
@@ -559,7 +570,7 @@ __global__ void __launch_bounds__(512) k_sweep_persistent(SweepParams<R> p, cons
     const unsigned int nb = gridDim.x;
     const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t stride = gridDim.x * blockDim.x;
-    for (int32_t k = tid; k < p.n_inst; k += stride) p.dtmin_bits[k] = 0x7f7f7f7f7f7f7f7full;
+    for (int32_t k = tid; k < p.n_inst; k += stride) atomicExch(p.dtmin_bits + k, 0x7f7f7f7f7f7f7f7full);
     for (int32_t t = tid; t < p.T; t += stride) stage_circumcentre(p, t);
     if (!grid_sync(gs, nb)) return;
     for (int32_t e = tid; e < p.E; e += stride) stage_edge_geometry(p, e);

@@ -30,7 +30,10 @@ EXPORTS = ["rich_default_config", "rich_init_mesh", "rich_step", "rich_get_state
            "rich_courant_dt_noalloc", "rich_set_diagnostics", "rich_batch_create", "rich_batch_add",
            "rich_batch_step", "rich_batch_query", "rich_batch_get_conserved", "rich_batch_remove",
            "rich_batch_set_diagnostics", "rich_batch_cells", "rich_batch_destroy", "rich_batch_set_launch",
-           "rich_batch_launch_info"]
+           "rich_batch_launch_info", "rich_server_create", "rich_server_submit", "rich_server_tick",
+           "rich_server_query", "rich_server_fetch", "rich_server_batch", "rich_server_destroy"]
+
+REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
 SIM_STATES = {0: "pending", 1: "running", 2: "done", 3: "failed"}
 
@@ -115,6 +118,15 @@ def _lib():
         L.rich_batch_destroy.restype = None
         L.rich_batch_set_launch.argtypes = [P, I32, I32]
         L.rich_batch_launch_info.argtypes = [P] + [C.POINTER(I32)] * 5 + [C.POINTER(I64)]
+        L.rich_server_create.argtypes = [I32, I64, I32, C.POINTER(P)]
+        L.rich_server_submit.argtypes = [P, C.POINTER(rich_config), I64] + [_D] * 6 + [d, I64, C.POINTER(I64)]
+        L.rich_server_tick.argtypes = [P, C.POINTER(rich_step_info)] + [C.POINTER(I32)] * 3
+        L.rich_server_query.argtypes = [P, I64, C.POINTER(I32), C.POINTER(I32), C.POINTER(I64), _D, _D]
+        L.rich_server_fetch.argtypes = [P, I64, I64] + [_D] * 6
+        L.rich_server_batch.argtypes = [P]
+        L.rich_server_batch.restype = P
+        L.rich_server_destroy.argtypes = [P]
+        L.rich_server_destroy.restype = None
         L.rich_kernel_times.argtypes = [P, I32, _D, C.POINTER(I32)]
         L.rich_kernel_name.argtypes = [I32]
         L.rich_kernel_name.restype = C.c_char_p
@@ -351,6 +363,61 @@ class Batch:
     def close(self):
         if self.h:
             rich_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (native scheduler in librich.so)."""
+
+    def __init__(self, precision=0, max_cells=1 << 24, host_threads=0):
+        h = C.c_void_p()
+        _check(_lib().rich_server_create(precision, max_cells, host_threads, C.byref(h)))
+        self.h = h
+        self.sizes = {}
+
+    def submit(self, wl, t_end=float("inf"), max_steps=1 << 62):
+        c = rich_config.from_dict(wl["cfg"])
+        n = len(wl["x"])
+        arrs = [_f64(wl[k], n) for k in ("x", "y", "rho", "vx", "vy", "p")]
+        rid = C.c_int64()
+        _check(_lib().rich_server_submit(self.h, C.byref(c), n, *[_p(a) for a in arrs], t_end, max_steps,
+                                         C.byref(rid)))
+        self.sizes[rid.value] = n
+        return rid.value
+
+    def tick(self):
+        info = rich_step_info()
+        a, r, q = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(_lib().rich_server_tick(self.h, C.byref(info), C.byref(a), C.byref(r), C.byref(q)))
+        out = info.as_dict()
+        out.update(admitted=a.value, running=r.value, queued=q.value)
+        return out
+
+    def query(self, rid):
+        st, err, steps, qm, lm = C.c_int32(), C.c_int32(), C.c_int64(), C.c_double(), C.c_double()
+        _check(_lib().rich_server_query(self.h, rid, C.byref(st), C.byref(err), C.byref(steps), C.byref(qm),
+                                        C.byref(lm)))
+        return {"state": REQ_STATES.get(st.value, st.value), "error": err.value, "steps": steps.value,
+                "queue_ms": qm.value, "latency_ms": lm.value}
+
+    def fetch(self, rid):
+        n = self.sizes.pop(rid)
+        out = [np.zeros(n) for _ in range(6)]
+        _check(_lib().rich_server_fetch(self.h, rid, n, *[_p(a) for a in out]))
+        return dict(zip(("x", "y", "m", "px", "py", "E"), out))
+
+    def launch_info(self):
+        return rich_batch_launch_info(_lib().rich_server_batch(self.h))
+
+    def close(self):
+        if self.h:
+            _lib().rich_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,94 @@
+"""GPU tests of the continuous-batching server (rich_server_*): requests
+arriving while others run are admitted as the cell budget frees up, their
+work shares one batched sweep per tick, and each result is the same alone
+and in the mix (bit for bit)."""
+import numpy as np
+import pytest
+
+from paper_1410_3219_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1410_3219_gb300 import rich
+    return rich
+
+
+def requests():
+    out = []
+    for k in range(9):
+        kind = k % 3
+        if kind == 0:
+            wl = W.sod(n_side=16 + 2 * k, seed=100 + k)
+        elif kind == 1:
+            wl = W.sedov(n=600 + 150 * k, seed=100 + k)
+        else:
+            wl = W.gresho(n_side=14 + k, seed=100 + k, eta=0.01 + 0.01 * k, chi=0.5 + 0.1 * k)
+        out.append((wl, 3 + (k % 4)))
+    return out
+
+
+def solo(R, wl, steps):
+    s = R.Sim(wl)
+    s.step(steps)
+    c = s.conserved()
+    s.close()
+    return c
+
+
+def test_server_results_equal_solo_runs(R):
+    reqs = requests()
+    budget = 3500  # forces queueing: the requests hold 256..1800 cells each
+    srv = R.Server(max_cells=budget)
+    ids, arrival_tick, finished = [], {}, {}
+    tick = 0
+    pending = list(enumerate(reqs))
+    max_cells_seen = 0
+    while pending or any(srv.query(r)["state"] in ("queued", "running") for r in ids):
+        # two new requests arrive every tick while others are on the GPU
+        for _ in range(2):
+            if pending:
+                k, (wl, steps) = pending.pop(0)
+                rid = srv.submit(wl, max_steps=steps)
+                ids.append(rid)
+                arrival_tick[rid] = (k, tick)
+        t = srv.tick()
+        max_cells_seen = max(max_cells_seen, sum(len(reqs[arrival_tick[r][0]][0]["x"]) for r in ids
+                                                 if srv.query(r)["state"] == "running"))
+        tick += 1
+        assert tick < 200
+    assert max_cells_seen <= budget
+    for rid in ids:
+        q = srv.query(rid)
+        k, _ = arrival_tick[rid]
+        wl, steps = reqs[k]
+        assert q["state"] == "done" and q["steps"] == steps
+        assert q["latency_ms"] >= q["queue_ms"] >= 0
+        got = srv.fetch(rid)
+        ref = solo(R, wl, steps)
+        for f in ref:
+            assert np.array_equal(got[f], ref[f]), (k, f)
+    srv.close()
+
+
+def test_server_fifo_admission_and_oversize_reject(R):
+    srv = R.Server(max_cells=1000)
+    big = W.sod(n_side=30, seed=1)  # 900 cells
+    small = W.sod(n_side=10, seed=2)  # 100 cells
+    a = srv.submit(big, max_steps=2)
+    b = srv.submit(big, max_steps=2)
+    c = srv.submit(small, max_steps=1)
+    srv.tick()
+    assert srv.query(a)["state"] == "running"
+    # strict arrival order: the small request waits behind the second big one
+    assert srv.query(b)["state"] == "queued" and srv.query(c)["state"] == "queued"
+    for _ in range(6):
+        srv.tick()
+    assert all(srv.query(r)["state"] == "done" for r in (a, b, c))
+    with pytest.raises(R.RichError):
+        srv.submit(W.sod(n_side=40, seed=3), max_steps=1)  # 1600 cells > budget
+    srv.close()
