@@ -298,11 +298,112 @@ def run_ours(args):
                        "ms_per_step": float(np.mean(res32["sweep_ms"])),
                        "p99_ms": float(np.percentile(res32["sweep_ms"], 99)), "roofline": roof32},
     }
+    if not args.no_batched:
+        line["batched"] = {"fp64": run_batched(rich, 0, args.batch_instances, args.batch_steps),
+                           "fp32_split": run_batched(rich, 1, args.batch_instances, args.batch_steps)}
+    if not args.no_serving:
+        line["serving"] = run_serving(rich, 1, args.serve_requests, args.serve_steps, 4000, 64000, 0.8)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_batched(rich, precision, n_inst, steps, seed=4):
+    """256 independent simulations (sizes log-uniform in 1k-64k, Sod / Sedov /
+    Gresho) advanced as one batch: one device sweep per step over all cells.
+    The autotuner's 8 trial steps run first (untimed)."""
+    from paper_1410_3219_gb300 import workloads as W
+    wls = W.batch_mix(n_inst=n_inst, seed=seed)
+    b = rich.Batch(precision=precision, max_cells=1 << 26)
+    for wl in wls:
+        wl["cfg"]["precision"] = precision
+        b.add(wl, max_steps=1 << 40)
+    cells = sum(len(wl["x"]) for wl in wls)
+    for _ in range(8):
+        b.step()
+    sweep_ms, tess_ms, wall = [], [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        info = b.step()
+        wall.append(1e3 * (time.perf_counter() - t0))
+        sweep_ms.append(info["sweep_ms"])
+        tess_ms.append(info["tess_ms"])
+    li = b.launch_info()
+    b.close()
+    return {"value": cells * steps / (sum(sweep_ms) / 1e3), "unit": UNIT, "instances": n_inst, "cells": cells,
+            "ms_per_step": float(np.mean(sweep_ms)), "p99_ms": float(np.percentile(sweep_ms, 99)),
+            "host_tess_ms_per_step": float(np.mean(tess_ms)),
+            "e2e": {"value": cells * steps / (sum(wall) / 1e3), "unit": UNIT,
+                    "wall_ms_per_step": float(np.mean(wall))},
+            "launch": {"persistent": li["persistent"], "block": li["block"], "grid": li["grid"],
+                       "graph_replay": li["graph"]},
+            "gpu_launches_per_step": 1 if li["persistent"] else 6}
+
+
+def run_serving(rich, precision, n_req, steps_per_req, n_min, n_max, load, seed=5):
+    """Poisson stream of requests (Sod / Sedov / Gresho, sizes log-uniform in
+    [n_min, n_max], Lloyd eta in [0.01, 0.1], chi in [0.5, 1.5]) through the
+    continuous-batching server, against the same requests run one at a time
+    through rich_step.  The arrival rate is `load` times the measured
+    one-at-a-time service rate."""
+    import math
+    from paper_1410_3219_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n_req):
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        side = max(4, int(round(math.sqrt(n))))
+        kind = k % 3
+        eta, chi = float(rng.uniform(0.01, 0.1)), float(rng.uniform(0.5, 1.5))
+        if kind == 0:
+            wl = W.sod(n_side=side, seed=2000 + k)
+        elif kind == 1:
+            wl = W.sedov(n=n, seed=2000 + k)
+        else:
+            wl = W.gresho(n_side=side, seed=2000 + k)
+        wl["cfg"].update(eta=eta, chi=chi, precision=precision)
+        reqs.append(wl)
+    cells = [len(w["x"]) for w in reqs]
+    # one request at a time (each its own rich_step loop, one launch set per step)
+    solo_lat, t_solo0 = [], time.perf_counter()
+    for wl in reqs:
+        t0 = time.perf_counter()
+        sim = rich.Sim(wl)
+        sim.step(steps_per_req)
+        sim.conserved()
+        sim.close()
+        solo_lat.append(1e3 * (time.perf_counter() - t0))
+    t_solo = time.perf_counter() - t_solo0
+    rate = load * n_req / t_solo  # requests per second offered
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    srv = rich.Server(precision=precision, max_cells=1 << 24)
+    ids, k = [], 0
+    t0 = time.perf_counter()
+    sweep_ms = 0.0
+    while k < n_req or any(srv.query(r)["state"] in ("queued", "running") for r in ids):
+        now = time.perf_counter() - t0
+        while k < n_req and arrivals[k] <= now:
+            ids.append(srv.submit(reqs[k], max_steps=steps_per_req))
+            k += 1
+        if not ids or all(srv.query(r)["state"] in ("done", "failed") for r in ids):
+            if k < n_req:
+                time.sleep(max(0.0, arrivals[k] - (time.perf_counter() - t0)))
+            continue
+        sweep_ms += srv.tick()["sweep_ms"]
+    t_srv = time.perf_counter() - t0
+    lat = [srv.query(r)["latency_ms"] for r in ids]
+    for r in ids:
+        srv.fetch(r)
+    srv.close()
+    total = sum(cells) * steps_per_req
+    return {"requests": n_req, "steps_per_request": steps_per_req, "cells_range": [n_min, n_max],
+            "offered_load": load, "unit": UNIT,
+            "served": {"value": total / t_srv, "device_value": total / (sweep_ms / 1e3),
+                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
+            "one_at_a_time": {"value": total / t_solo, "p50_ms": float(np.percentile(solo_lat, 50)),
+                              "p99_ms": float(np.percentile(solo_lat, 99))}}
 
 
 def cpu_baseline(wl, budget_s):
@@ -364,6 +465,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-steps", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

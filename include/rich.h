@@ -46,8 +46,9 @@ extern "C" {
 #define RICH_EDUPLICATE -2 /* two generating points coincide */
 #define RICH_ETESS -3      /* tessellation failed (inconsistent connectivity) */
 #define RICH_ETOOFEW -4    /* too few points for the ghost band to close every cell */
-#define RICH_ENEGATIVE -5  /* a step produced m <= 0, thermal energy <= 0, or a point left a walled box;
-                              the state stays at the last good step */
+#define RICH_ENEGATIVE -5  /* a step produced m <= 0 or thermal energy <= 0, or moved a point so far
+                              that reflecting it at a rigid wall leaves it outside; the state stays
+                              at the last good step */
 #define RICH_ENAN -6       /* a step produced a non-finite value; state kept as for RICH_ENEGATIVE */
 #define RICH_ENOMEM -7     /* device or host allocation failed */
 #define RICH_ECUDA -8      /* CUDA runtime error (see rich_last_error) */

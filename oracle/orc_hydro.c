@@ -38,7 +38,8 @@
  *     midpoint: w_f = (w_i+w_j)/2 - ((w_j-w_i).c_ij/|r_ij|) n_ij;
  *   - HLLC wave speeds are the direct (Davis) estimates;
  *   - dt = cfl * min_i R_i/(c_i + |v_i - w_i|), clipped to reach t_end;
- *   - the rounding velocity switches on as a step at d = eta*R_i.
+ *   - the rounding velocity switches on as a step at d = eta*R_i;
+ *   - a generating point that crosses a rigid wall is reflected back across it.
  * Every edge flux is evaluated from each of its two cells separately, which
  * is the literal per-cell sum above; the two evaluations agree to round-off.
  */
@@ -620,7 +621,8 @@ int orc_sweep(orc_sim *s, double t_end, double *dt_out)
         s->py[i] += dU[4 * i + 2];
         s->E[i] += dU[4 * i + 3];
         if (!(s->m[i] > 0) || !(s->E[i] - 0.5 * (s->px[i] * s->px[i] + s->py[i] * s->py[i]) / s->m[i] > 0)) bad = 1;
-        /* move the generating points; wrap into a periodic box */
+        /* move the generating points; wrap into a periodic box, and reflect a
+           point that crossed a rigid wall back across it (as its mirror image) */
         double nx = s->x[i] + dt * s->wx[i], ny = s->y[i] + dt * s->wy[i];
         if (c->boundary == 1) {
             double Lx = c->x1 - c->x0, Ly = c->y1 - c->y0;
@@ -628,8 +630,12 @@ int orc_sweep(orc_sim *s, double t_end, double *dt_out)
             else if (nx >= c->x1) nx -= Lx;
             if (ny < c->y0) ny += Ly;
             else if (ny >= c->y1) ny -= Ly;
-        } else if (!(nx > c->x0 && nx < c->x1 && ny > c->y0 && ny < c->y1)) {
-            bad = 1;
+        } else {
+            if (nx <= c->x0) nx = (c->x0 + c->x0) - nx;
+            else if (nx >= c->x1) nx = (c->x1 + c->x1) - nx;
+            if (ny <= c->y0) ny = (c->y0 + c->y0) - ny;
+            else if (ny >= c->y1) ny = (c->y1 + c->y1) - ny;
+            if (!(nx > c->x0 && nx < c->x1 && ny > c->y0 && ny < c->y1)) bad = 1;
         }
         s->x[i] = nx;
         s->y[i] = ny;

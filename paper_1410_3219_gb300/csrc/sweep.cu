@@ -508,8 +508,13 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
         else if (xn >= ip.x1) xn -= Lx;
         if (yn < ip.y0) yn += Ly;
         else if (yn >= ip.y1) yn -= Ly;
-    } else if (!(xn > ip.x0 && xn < ip.x1 && yn > ip.y0 && yn < ip.y1)) {
-        st |= ST_LEFT_BOX;
+    } else {
+        // a point that crossed a rigid wall comes back as its mirror image
+        if (xn <= ip.x0) xn = (ip.x0 + ip.x0) - xn;
+        else if (xn >= ip.x1) xn = (ip.x1 + ip.x1) - xn;
+        if (yn <= ip.y0) yn = (ip.y0 + ip.y0) - yn;
+        else if (yn >= ip.y1) yn = (ip.y1 + ip.y1) - yn;
+        if (!(xn > ip.x0 && xn < ip.x1 && yn > ip.y0 && yn < ip.y1)) st |= ST_LEFT_BOX;
     }
     p.xn[i] = xn;
     p.yn[i] = yn;

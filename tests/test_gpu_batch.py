@@ -22,7 +22,7 @@ def R():
 def mix(precision):
     wls = [W.sod(n_side=24, seed=11), W.sedov(n=2000, seed=12), W.gresho(n_side=20, seed=13),
            W.kelvin_helmholtz(n_side=32, seed=14), W.random_smooth(n=900, seed=15),
-           W.random_smooth(n=700, seed=16, boundary=W.BC_REFLECTIVE)]
+           W.random_smooth(n=700, seed=16, boundary=W.BC_REFLECTIVE)]  # a point reaches a wall at step 9
     for wl in wls:
         wl["cfg"]["precision"] = precision
     return wls
