@@ -251,8 +251,8 @@ int rich_batch_set_launch(rich_batch *b, int32_t mode, int32_t block);
 
 /* The launch shape in use (persistent 0/1, block, grid of the last
    persistent launch, tuning finished 0/1, graph replay available 0/1) and
-   counts[3] = {staged steps, persistent steps, graph replays}; each output
-   may be NULL. */
+   counts[4] = {staged steps, persistent steps, graph replays, graph
+   recordings}; each output may be NULL. */
 int rich_batch_launch_info(const rich_batch *b, int32_t *persistent, int32_t *block, int32_t *grid, int32_t *tuned,
                            int32_t *graph, int64_t *counts);
 

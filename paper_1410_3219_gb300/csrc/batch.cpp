@@ -101,7 +101,7 @@ struct rich_batch {
     // device
     DBuf x[2], y[2], U[2], A, o, W, cs, g, gl, alpha, w, tess, rounding, p64, cell_ptr, cell_inst, initW, src;
     DBuf gx, gy, gsrc, gxf, tri, ccx, ccy, slot_nb, slot_tri, slot_edge;
-    DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F;
+    DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F, ePM;
     DBuf instp, dtmin, dtout, status, dsizes, gsync;
     // launch shape: autotuned over the first steps unless fixed by the caller
     int launch_mode = 0;  // 0 autotune, 1 staged, 2 persistent
@@ -114,9 +114,11 @@ struct rich_batch {
     int last_grid = 0;
     bool graph_ok = true;
     std::string graph_note;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    std::vector<unsigned char> graph_sig;
+    // one recorded graph per ping-pong parity (the buffers swap roles each step)
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    std::vector<unsigned char> graph_sig[2];
+    int64_t graph_records = 0;
     int64_t persistent_launches = 0, graph_launches = 0, staged_launches = 0;
     // host staging of the packed mesh
     std::vector<double> h_x, h_y, h_gx, h_gy, h_W0;
@@ -131,8 +133,10 @@ struct rich_batch {
     ~rich_batch()
     {
         if (stream) cudaStreamSynchronize(stream);
-        if (gexec) cudaGraphExecDestroy(gexec);
-        if (graph) cudaGraphDestroy(graph);
+        for (int k = 0; k < 2; k++) {
+            if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
+            if (graph[k]) cudaGraphDestroy(graph[k]);
+        }
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         if (stream) cudaStreamDestroy(stream);
@@ -164,6 +168,7 @@ struct rich_batch {
         p.eL = eL.as<R>(); p.emlx = emlx.as<R>(); p.emly = emly.as<R>();
         p.emrx = emrx.as<R>(); p.emry = emry.as<R>();
         p.enx = enx.as<R>(); p.eny = eny.as<R>(); p.eqx = eqx.as<R>(); p.eqy = eqy.as<R>();
+        p.ePM = ePM.as<rich::Vec4<R>>();
         p.U = U[cur].as<double>(); p.Un = U[1 - cur].as<double>();
         p.W = W.as<rich::Vec4<R>>(); p.o = o.as<rich::Vec2<R>>(); p.cs = cs.as<R>();
         p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
@@ -203,7 +208,7 @@ rich::InstParams inst_params(const BatchSim &s, bool init)
 {
     rich::InstParams ip{};
     const rich_config &c = s.cfg;
-    ip.gamma = c.gamma; ip.cfl = c.cfl; ip.chi = c.chi; ip.eta = c.eta; ip.theta = c.theta;
+    ip.gamma = c.gamma; ip.igm1 = 1.0 / (c.gamma - 1.0); ip.cfl = c.cfl; ip.chi = c.chi; ip.eta = c.eta; ip.theta = c.theta;
     ip.delta_v = c.delta_v; ip.delta_p = c.delta_p;
     ip.x0 = c.x0; ip.x1 = c.x1; ip.y0 = c.y0; ip.y1 = c.y1;
     ip.remaining = s.t_end - s.t;
@@ -273,6 +278,7 @@ int ensure_device(rich_batch *b)
     for (DBuf *e : {&b->eL, &b->emlx, &b->emly, &b->emrx, &b->emry, &b->enx, &b->eny, &b->eqx, &b->eqy})
         CUDA_TRY(e->ensure(E * r + 8));
     CUDA_TRY(b->F.ensure(4 * E * r + 32));
+    CUDA_TRY(b->ePM.ensure(4 * E * r + 32));
     CUDA_TRY(b->instp.ensure(K * sizeof(rich::InstParams) + 8));
     CUDA_TRY(b->dtmin.ensure(K * 8 + 8)); CUDA_TRY(b->dtout.ensure(K * 8 + 8)); CUDA_TRY(b->status.ensure(K * 4 + 8));
     CUDA_TRY(b->dsizes.ensure(sizeof(rich::DeviceSizes))); CUDA_TRY(b->gsync.ensure(sizeof(rich::GridSync)));
@@ -330,30 +336,34 @@ template <class R> int run_persistent(rich_batch *b, int block)
         std::memcpy(sig.data(), &p, sizeof(p));
         int extra[3] = {block, grid, (int)sizeof(R)};
         std::memcpy(sig.data() + sizeof(p), extra, sizeof(extra));
-        if (!b->gexec || sig != b->graph_sig) {
-            if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
-            if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        const int par = b->cur;
+        cudaGraph_t &graph = b->graph[par];
+        cudaGraphExec_t &gexec = b->gexec[par];
+        if (!gexec || sig != b->graph_sig[par]) {
+            if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+            if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
             bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
                 cudaMemsetAsync(gs, 0, sizeof(rich::GridSync), b->stream);
                 cudaMemsetAsync(b->status.p, 0, b->status.cap, b->stream);
                 cudaError_t le = rich::launch_persistent<R>(p, ds, gs, block, grid, b->stream);
-                cudaError_t ce = cudaStreamEndCapture(b->stream, &b->graph);
-                ok = le == cudaSuccess && ce == cudaSuccess && b->graph &&
-                     cudaGraphInstantiate(&b->gexec, b->graph, 0) == cudaSuccess;
+                cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+                ok = le == cudaSuccess && ce == cudaSuccess && graph &&
+                     cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess;
                 if (!ok) b->graph_note = std::string("graph capture failed: ") + cudaGetErrorString(le != cudaSuccess ? le : ce);
             }
             cudaGetLastError();
             if (!ok) {
                 b->graph_ok = false;
-                if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
-                if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+                if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+                if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
             } else {
-                b->graph_sig = sig;
+                b->graph_sig[par] = sig;
+                b->graph_records++;
             }
         }
         if (b->graph_ok) {
-            CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
+            CUDA_TRY(cudaGraphLaunch(gexec, b->stream));
             b->graph_launches++;
             b->persistent_launches++;
             return RICH_OK;
@@ -800,6 +810,7 @@ int rich_batch_launch_info(const rich_batch *b, int32_t *persistent, int32_t *bl
         counts[0] = b->staged_launches;
         counts[1] = b->persistent_launches;
         counts[2] = b->graph_launches;
+        counts[3] = b->graph_records;
     }
     return RICH_OK;
 }

@@ -96,7 +96,7 @@ struct rich_sim {
     DBuf gx, gy, gsrc, gxf;
     DBuf tri, ccx, ccy;
     DBuf slot_nb, slot_tri, slot_edge;
-    DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F;
+    DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F, ePM;
     DBuf scal;   // dtmin bits, dt, status
     DBuf instp;  // one InstParams
     rich::InstParams inst_host{};  // staging for the parameter upload
@@ -134,6 +134,7 @@ struct rich_sim {
         p.eL = eL.as<R>(); p.emlx = emlx.as<R>(); p.emly = emly.as<R>();
         p.emrx = emrx.as<R>(); p.emry = emry.as<R>();
         p.enx = enx.as<R>(); p.eny = eny.as<R>(); p.eqx = eqx.as<R>(); p.eqy = eqy.as<R>();
+        p.ePM = ePM.as<rich::Vec4<R>>();
         p.U = U[cur].as<double>(); p.Un = U[1 - cur].as<double>();
         p.W = W.as<rich::Vec4<R>>(); p.o = o.as<rich::Vec2<R>>(); p.cs = cs.as<R>();
         p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
@@ -154,7 +155,7 @@ struct rich_sim {
     {
         rich::InstParams ip{};
         ip.init = init ? 1 : 0;
-        ip.gamma = cfg.gamma; ip.cfl = cfg.cfl; ip.chi = cfg.chi; ip.eta = cfg.eta; ip.theta = cfg.theta;
+        ip.gamma = cfg.gamma; ip.igm1 = 1.0 / (cfg.gamma - 1.0); ip.cfl = cfg.cfl; ip.chi = cfg.chi; ip.eta = cfg.eta; ip.theta = cfg.theta;
         ip.delta_v = cfg.delta_v; ip.delta_p = cfg.delta_p;
         ip.x0 = cfg.x0; ip.x1 = cfg.x1; ip.y0 = cfg.y0; ip.y1 = cfg.y1;
         ip.remaining = remaining;
@@ -236,6 +237,7 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     for (DBuf *b : {&s->eL, &s->emlx, &s->emly, &s->emrx, &s->emry, &s->enx, &s->eny, &s->eqx, &s->eqy})
         CUDA_TRY(b->ensure((E + 1) * r));
     CUDA_TRY(s->F.ensure((4 * E + 4) * r));
+    CUDA_TRY(s->ePM.ensure((4 * E + 4) * r));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     double t3 = now_ms();
     s->tess_current = true;

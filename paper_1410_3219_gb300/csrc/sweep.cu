@@ -53,6 +53,50 @@ template <class R> __device__ __forceinline__ Vec4<R> load_W(const SweepParams<R
     return W;
 }
 
+// FP64 max/min on the integer pipe: the bits of a double, with the magnitude
+// bits flipped for negative values, order like the doubles themselves
+// (GB300 issues FP64 instructions, comparisons included, at 1/64 of the
+// FP32 rate; 64-bit integer compares run on the integer pipe).
+__device__ __forceinline__ long long dkey(double v)
+{
+    const long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double dunkey(long long k)
+{
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
+}
+
+template <class R> struct Extremes;
+template <> struct Extremes<double> {
+    long long hi, lo;
+    __device__ __forceinline__ void init(double v) { hi = lo = dkey(v); }
+    __device__ __forceinline__ void add(double v)
+    {
+        const long long k = dkey(v);
+        hi = k > hi ? k : hi;
+        lo = k < lo ? k : lo;
+    }
+    __device__ __forceinline__ double max() const { return dunkey(hi); }
+    __device__ __forceinline__ double min() const { return dunkey(lo); }
+};
+template <> struct Extremes<float> {
+    float hi, lo;
+    __device__ __forceinline__ void init(float v) { hi = lo = v; }
+    __device__ __forceinline__ void add(float v)
+    {
+        hi = fmaxf(hi, v);
+        lo = fminf(lo, v);
+    }
+    __device__ __forceinline__ float max() const { return hi; }
+    __device__ __forceinline__ float min() const { return lo; }
+};
+
+// a < b for non-negative values (bit patterns of non-negative doubles order
+// like the values)
+__device__ __forceinline__ bool nonneg_less(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+__device__ __forceinline__ bool nonneg_less(float a, float b) { return a < b; }
+
 // ---------------------------------------------------------------------------
 // a1: circumcentre of every triangle touching a real cell (Voronoi vertices), FP64
 template <class R> __device__ __forceinline__ void stage_circumcentre(const SweepParams<R> &p, int32_t t)
@@ -96,8 +140,12 @@ template <class R> __device__ __forceinline__ void stage_edge_geometry(const Swe
     p.emry[e] = my - dy;
     p.enx[e] = dx * rinv;
     p.eny[e] = dy * rinv;
-    p.eqx[e] = (mx - R(0.5) * dx) * rinv;
-    p.eqy[e] = (my - R(0.5) * dy) * rinv;
+    const R qx = (mx - R(0.5) * dx) * rinv, qy = (my - R(0.5) * dy) * rinv;
+    const R nx = dx * rinv, ny = dy * rinv;
+    p.eqx[e] = qx;
+    p.eqy[e] = qy;
+    const R hx = R(0.5) * nx, hy = R(0.5) * ny;
+    p.ePM[e] = Vec4<R>{L * (qx + hx), L * (qy + hy), L * (hx - qx), L * (hy - qy)};
 }
 
 template <class R> __global__ void k_edge_geometry(SweepParams<R> p)
@@ -206,8 +254,10 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
         const Vec4<R> W4 = p.W[i];
         const R Wi[4] = {W4.x, W4.y, W4.z, W4.w};
         R acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        R fmx[4] = {Wi[0], Wi[1], Wi[2], Wi[3]};
-        R fmn[4] = {Wi[0], Wi[1], Wi[2], Wi[3]};
+        R Bx = 0, By = 0;
+        Extremes<R> ext[4];
+#pragma unroll
+        for (int v = 0; v < 4; v++) ext[v].init(Wi[v]);
         bool shock = false;
         const R A = (R)p.A[i];
         const double dp = ip.delta_p;
@@ -216,26 +266,24 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
         // shorter edges are point contacts whose presence depends on round-off
         const R Lmin = R(1e-9) * sqrt(A);
         for (int32_t s = lo; s < hi; s++) {
-            int32_t es = p.slot_edge[s];
-            int32_t e = es >> 1;
-            R sg = (es & 1) ? R(-1) : R(1);
-            R L = p.eL[e];
-            R nx = sg * p.enx[e], ny = sg * p.eny[e];
-            R qx = p.eqx[e], qy = p.eqy[e];
+            const int32_t es = p.slot_edge[s];
+            const int32_t e = es >> 1;
+            const R L = p.eL[e];
+            const Vec4<R> pm = p.ePM[e];
+            // Eq. 1: g_i A_i = sum_j phi_j P_ij + phi_i sum_j M_ij
+            const R Ax = (es & 1) ? -pm.z : pm.x, Ay = (es & 1) ? -pm.w : pm.y;
+            Bx += (es & 1) ? -pm.x : pm.z;
+            By += (es & 1) ? -pm.y : pm.w;
             const Vec4<R> Wv = load_W(p, p.slot_nb[s]);
             const R Wj[4] = {Wv.x, Wv.y, Wv.z, Wv.w};
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                R d = Wj[v] - Wi[v], a = R(0.5) * (Wi[v] + Wj[v]);
-                acc[2 * v] += L * (d * qx + a * nx);
-                acc[2 * v + 1] += L * (d * qy + a * ny);
+                acc[2 * v] += Wj[v] * Ax;
+                acc[2 * v + 1] += Wj[v] * Ay;
             }
             if (L > Lmin) {
 #pragma unroll
-                for (int v = 0; v < 4; v++) {
-                    fmx[v] = fmax(fmx[v], Wj[v]);
-                    fmn[v] = fmin(fmn[v], Wj[v]);
-                }
+                for (int v = 0; v < 4; v++) ext[v].add(Wj[v]);
                 double pj64;
                 if (sizeof(R) == sizeof(double)) {
                     pj64 = (double)Wj[3];
@@ -243,8 +291,21 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
                     int32_t xf;
                     pj64 = p.p64[src_of(p, p.slot_nb[s], xf)];
                 }
-                if (fmin(pi64, pj64) < dp * fmax(pi64, pj64)) shock = true;
+                const bool jl = nonneg_less(pj64, pi64);
+                const double pmin = jl ? pj64 : pi64, pmax = jl ? pi64 : pj64;
+                if (nonneg_less(pmin, dp * pmax)) shock = true;
             }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            acc[2 * v] += Wi[v] * Bx;
+            acc[2 * v + 1] += Wi[v] * By;
+        }
+        R fmx[4], fmn[4];
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            fmx[v] = ext[v].max();
+            fmn[v] = ext[v].min();
         }
         const R invA = R(1) / A;
         R g[8];
@@ -264,7 +325,9 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
         // smallest ratio is found by cross-multiplication, divided once.
         R alpha[4];
         if (!use_tess) {
-            R dpos[4] = {0, 0, 0, 0}, dneg[4] = {0, 0, 0, 0};
+            Extremes<R> dex[4];
+#pragma unroll
+            for (int v = 0; v < 4; v++) dex[v].init(R(0));
             for (int32_t s = lo; s < hi; s++) {
                 int32_t es = p.slot_edge[s];
                 int32_t e = es >> 1;
@@ -272,17 +335,22 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
                 R offx = ((es & 1) ? p.emrx[e] : p.emlx[e]) - ox;
                 R offy = ((es & 1) ? p.emry[e] : p.emly[e]) - oy;
 #pragma unroll
-                for (int v = 0; v < 4; v++) {
-                    R dphi = g[2 * v] * offx + g[2 * v + 1] * offy;
-                    dpos[v] = fmax(dpos[v], dphi);
-                    dneg[v] = fmin(dneg[v], dphi);
-                }
+                for (int v = 0; v < 4; v++) dex[v].add(g[2 * v] * offx + g[2 * v + 1] * offy);
             }
 #pragma unroll
             for (int v = 0; v < 4; v++) {
+                // alpha = min(1, (phi_max - phi_i)/dphi_max, (phi_i - phi_min)/|dphi_min|):
+                // a ratio needs dividing only when its numerator is the smaller
                 R a = R(1);
-                if (dpos[v] > R(0)) a = fmin(a, (fmx[v] - Wi[v]) / dpos[v]);
-                if (dneg[v] < R(0)) a = fmin(a, (fmn[v] - Wi[v]) / dneg[v]);
+                const R dpos = dex[v].max(), dneg = dex[v].min();
+                if (dpos > R(0)) {
+                    const R num = fmx[v] - Wi[v];
+                    if (nonneg_less(num, dpos)) a = num / dpos;
+                }
+                if (dneg < R(0)) {
+                    const R num = Wi[v] - fmn[v], den = -dneg;
+                    if (nonneg_less(num, den)) a = fmin(a, num / den);
+                }
                 alpha[v] = a;
             }
         } else {
@@ -375,12 +443,11 @@ __device__ __forceinline__ void predict(R gam, R hdt, const R W[4], const R g[8]
 }
 
 // HLLC (Toro) in the edge frame, states (rho, u_n, u_t, p)
-template <class R> __device__ __forceinline__ void hllc(R gam, const R L[4], const R Rs[4], R F[4])
+template <class R> __device__ __forceinline__ void hllc(R gam, R igm1, const R L[4], const R Rs[4], R F[4])
 {
     const R rL = L[0], uL = L[1], tL = L[2], pL = L[3];
     const R rR = Rs[0], uR = Rs[1], tR = Rs[2], pR = Rs[3];
     const R cL = sqrt(gam * pL / rL), cR = sqrt(gam * pR / rR);
-    const R igm1 = R(1) / (gam - R(1));
     const R EL = pL * igm1 + R(0.5) * rL * (uL * uL + tL * tL);
     const R ER = pR * igm1 + R(0.5) * rR * (uR * uR + tR * tR);
     const R SL = fmin(uL - cL, uR - cR);
@@ -395,16 +462,20 @@ template <class R> __device__ __forceinline__ void hllc(R gam, const R L[4], con
     }
     const R mL = rL * (SL - uL), mR = rR * (SR - uR);
     const R Ss = (pR - pL + uL * mL - uR * mR) / (mL - mR);
+    // star states share one reciprocal: rho* = m_K/(S_K - S*) and
+    // E* = ((S_K - u_K) E_K + (S* - u_K)(m_K S* + p_K))/(S_K - S*)
     if (Ss >= R(0)) {
-        const R f = mL / (SL - Ss);
-        const R Es = f * (EL / rL + (Ss - uL) * (Ss + pL / mL));
+        const R inv = R(1) / (SL - Ss);
+        const R f = mL * inv;
+        const R Es = ((SL - uL) * EL + (Ss - uL) * (mL * Ss + pL)) * inv;
         F[0] = rL * uL + SL * (f - rL);
         F[1] = rL * uL * uL + pL + SL * (f * Ss - rL * uL);
         F[2] = rL * uL * tL + SL * (f * tL - rL * tL);
         F[3] = uL * (EL + pL) + SL * (Es - EL);
     } else {
-        const R f = mR / (SR - Ss);
-        const R Es = f * (ER / rR + (Ss - uR) * (Ss + pR / mR));
+        const R inv = R(1) / (SR - Ss);
+        const R f = mR * inv;
+        const R Es = ((SR - uR) * ER + (Ss - uR) * (mR * Ss + pR)) * inv;
         F[0] = rR * uR + SR * (f - rR);
         F[1] = rR * uR * uR + pR + SR * (f * Ss - rR * uR);
         F[2] = rR * uR * tR + SR * (f * tR - rR * tR);
@@ -452,7 +523,7 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
     R WL[4] = {Sl[0], (Sl[1] - wfx) * nx + (Sl[2] - wfy) * ny, (Sl[1] - wfx) * tx + (Sl[2] - wfy) * ty, Sl[3]};
     R WR[4] = {Sr[0], (Sr[1] - wfx) * nx + (Sr[2] - wfy) * ny, (Sr[1] - wfx) * tx + (Sr[2] - wfy) * ty, Sr[3]};
     R Fe[4];
-    hllc(gam, WL, WR, Fe);
+    hllc(gam, (R)p.inst[li].igm1, WL, WR, Fe);
     if (xf && k == l) {
         // a wall: the cell faces its own mirror image.  The mirrored Riemann
         // problem has u* = 0 and the wall does not move normal to itself, so

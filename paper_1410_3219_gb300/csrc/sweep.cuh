@@ -16,7 +16,10 @@
 //              edge_l/edge_r/edge_ta/edge_tb[E]; ghost_src/ghost_xf[g]
 //   geometry   ccx, ccy[T] (FP64); A[n] (FP64); per edge (R): L, unit normal
 //              (nx, ny), q = c_ij/|r_ij| (qx, qy), midpoint minus left
-//              generator (mlx, mly) and minus right generator (mrx, mry)
+//              generator (mlx, mly) and minus right generator (mrx, mry);
+//              ePM[E] = {P, M}: Eq. 1 as a sum over neighbours reads
+//              g_i = (sum_j phi_j P_ij + phi_i sum_j M_ij)/A_i with
+//              P = L(q + n/2), M = L(n/2 - q) (right cells use -M, -P)
 //   cell (R)   W[n] = {rho, vx, vy, p}; o[n] = centre of mass - generator;
 //              cs[n]; gl[2n] limited gradient {drho/dx, drho/dy, dvx/dx,
 //              dvx/dy}, {dvy/dx, dvy/dy, dp/dx, dp/dy}; w[n] mesh velocity;
@@ -49,6 +52,7 @@ struct InstParams {
     double gamma, cfl, chi, eta, theta, delta_v, delta_p;
     double x0, x1, y0, y1;
     double remaining;  // t_end - t: the step is shortened to land on t_end
+    double igm1;       // 1/(gamma - 1)
     int32_t boundary, motion, limiter;
     int32_t init;      // the geometry stage with primitives given sets this simulation's U
 };
@@ -72,6 +76,7 @@ template <class R> struct SweepParams {
     // geometry
     double *ccx, *ccy, *A;
     R *eL, *enx, *eny, *eqx, *eqy, *emlx, *emly, *emrx, *emry;
+    Vec4<R> *ePM;  // Eq. 1 weights of the edge's left cell: P = L(q + n/2), M = L(n/2 - q)
     // state
     const double *U;
     double *Un;

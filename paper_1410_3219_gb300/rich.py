@@ -319,10 +319,11 @@ def rich_batch_set_launch(b, mode=0, block=256):
 
 def rich_batch_launch_info(b):
     v = [C.c_int32() for _ in range(5)]
-    cnt = (C.c_int64 * 3)()
+    cnt = (C.c_int64 * 4)()
     _check(_lib().rich_batch_launch_info(b, *[C.byref(x) for x in v], cnt))
     return {"persistent": v[0].value, "block": v[1].value, "grid": v[2].value, "tuned": v[3].value,
-            "graph": v[4].value, "staged_steps": cnt[0], "persistent_steps": cnt[1], "graph_replays": cnt[2]}
+            "graph": v[4].value, "staged_steps": cnt[0], "persistent_steps": cnt[1], "graph_replays": cnt[2],
+            "graph_recordings": cnt[3]}
 
 
 def rich_batch_destroy(b):

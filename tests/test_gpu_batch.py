@@ -93,6 +93,9 @@ def test_batch_launch_shapes_give_identical_results(R, mode, block):
     info = b.launch_info()
     if mode == 2:
         assert info["persistent_steps"] == 5 and info["block"] == block
+        if info["graph"]:
+            # one recording per ping-pong parity, plus re-recordings when a buffer grows
+            assert info["graph_replays"] == 5 and info["graph_recordings"] <= 4
     for wl, sid in zip(wls, ids):
         ref = solo(R, wl, 5)
         got = b.conserved(sid)
