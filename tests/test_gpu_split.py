@@ -3,9 +3,16 @@ gradients, limiter, mesh velocity, edge states and HLLC in FP32; geometry,
 positions and conserved variables in FP64.  Against the FP64 oracle:
   - one step: every conserved field within 2e-6 of its scale (FP32
     reconstruction: ~6e-8 relative per value, amplified by the flux sums);
-  - whole runs: L1(rho) relative to the oracle's L1 norm <= 1e-5;
+  - whole runs: L1(rho) relative to the oracle's L1 norm <= 1e-5, except on
+    the Sod tube, where the FP64 scheme itself moves by up to a few 1e-4 under
+    FP32-size per-step noise (its limiter and shock switch, Eqs. 4-8, are
+    discontinuous in the state; tests/golden/sod_fp32_envelope.txt records
+    the spread, written by the oracle alone), and the bound is twice the
+    largest L1 seen there;
   - conservation: total mass, momentum (periodic) and energy drift <= 1e-10.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -56,17 +63,25 @@ def test_split_one_step(R, oracle, name):
     gpu.close()
 
 
+def sod_envelope():
+    """Largest L1(rho) between the FP64 oracle and its noisy re-runs."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "sod_fp32_envelope.txt")
+    vals = [float(ln.split()[-1]) for ln in open(path) if ln.startswith("eps")]
+    assert len(vals) >= 8
+    return max(vals)
+
+
 RUNS = {
-    "sod_64_t0.2": (lambda: W.sod(n_side=64), 0.2, 10000),
-    "gresho_32_t0.2": (lambda: W.gresho(n_side=32), 0.2, 10000),
-    "kh_64_200steps": (lambda: W.kelvin_helmholtz(n_side=64), np.inf, 200),
-    "sedov_4096_t0.01": (lambda: W.sedov(n=4096), 0.01, 10000),
+    "sod_64_t0.2": (lambda: W.sod(n_side=64), 0.2, 10000, lambda: 2.0 * sod_envelope()),
+    "gresho_32_t0.2": (lambda: W.gresho(n_side=32), 0.2, 10000, lambda: 1e-5),
+    "kh_64_200steps": (lambda: W.kelvin_helmholtz(n_side=64), np.inf, 200, lambda: 1e-5),
+    "sedov_4096_t0.01": (lambda: W.sedov(n=4096), 0.01, 10000, lambda: 1e-5),
 }
 
 
 @pytest.mark.parametrize("name", list(RUNS))
 def test_split_run_l1_density(R, oracle, name):
-    make, t_end, steps = RUNS[name]
+    make, t_end, steps, bound = RUNS[name]
     wl = make()
     ref = oracle.Sim(wl)
     gpu = R.Sim(split(wl))
@@ -80,7 +95,7 @@ def test_split_run_l1_density(R, oracle, name):
     l1 = float(np.sum(np.abs(a["rho"] - b["rho"])) / np.sum(np.abs(b["rho"])))
     print(f"{name}: steps gpu={info['steps_done']} oracle={k} L1(rho) rel = {l1:.3e}")
     assert info["steps_done"] == k
-    assert l1 <= 1e-5, l1
+    assert l1 <= bound(), (l1, bound())
     c1 = gpu.conserved()
     for q in ("m", "E") + (("px", "py") if wl["cfg"]["boundary"] == W.BC_PERIODIC else ()):
         drift = abs(c1[q].sum() - c0[q].sum()) / np.abs(c0[q]).sum()
