@@ -41,13 +41,13 @@ class Config(C.Structure):
                 ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
                 ("motion", C.c_int), ("chi", C.c_double), ("eta", C.c_double),
                 ("theta", C.c_double), ("delta_v", C.c_double), ("delta_p", C.c_double),
-                ("limiter", C.c_int)]
+                ("limiter", C.c_int), ("scheme", C.c_int)]
 
     @classmethod
     def from_dict(cls, d):
         c = cls()
         for name, _ in cls._fields_:
-            setattr(c, name, d[name])
+            setattr(c, name, d.get(name, 0) if name == "scheme" else d[name])
         return c
 
 

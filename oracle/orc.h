@@ -21,6 +21,7 @@ typedef struct {
     double chi, eta;
     double theta, delta_v, delta_p;
     int limiter; /* 0: AREPO with switch to TESS near shocks, 1: AREPO, 2: TESS */
+    int scheme;  /* Section 2.3: 0 extrapolated fluxes, 1 time-centred fluxes */
 } orc_config;
 
 typedef struct orc_sim orc_sim;

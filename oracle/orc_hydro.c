@@ -23,6 +23,17 @@
  *                 frame of the moving edge (Section 1); Galilean transform back.
  *   update        U_i <- U_i - dt sum_j L_ij F_ij (conservative, Section 5).
  *
+ * The second time advancement of Section 2.3, "time centred fluxes" (the
+ * paper's own), runs the same sweep twice per step with no time prediction
+ * of the edge states (spatial extrapolation only):
+ *   half step     on the mesh of r^n: dt from the Courant condition;
+ *                 U^{n+1/2} = U^n - (dt/2) sum L F(W^n),
+ *                 r^{n+1/2} = r^n + (dt/2) w^n;
+ *   full step     mesh rebuilt at r^{n+1/2}, W^{n+1/2} from U^{n+1/2} and the
+ *                 new areas, w^{n+1/2} from them; the same dt;
+ *                 U^{n+1} = U^n - dt sum L F(W^{n+1/2}) over the edges of the
+ *                 half-step mesh, r^{n+1} = r^n + dt w^{n+1/2}.
+ *
  * Points the paper leaves open and the reading taken here:
  *   - the limiter's max/min include the cell's own value (so alpha is in [0,1])
  *     and alpha is the minimum over all edges of the cell; the neighbours of
@@ -82,6 +93,8 @@ struct orc_sim {
     int *tess;
     double dt;
     double *x_prev, *y_prev;    /* generating points at the start of the last sweep */
+    /* time-centred scheme: state and points at the start of the step */
+    double *m0, *px0, *py0, *E0, *x0, *y0;
 };
 
 static void *xmalloc(size_t n) { void *p = calloc(1, n > 0 ? n : 1); if (!p) abort(); return p; }
@@ -378,6 +391,7 @@ int orc_create(const orc_config *cfg, int n, const double *x, const double *y, c
 {
     *out = NULL;
     if (n < 3 || !(cfg->gamma > 1.0) || !(cfg->x1 > cfg->x0) || !(cfg->y1 > cfg->y0)) return ORC_EINVAL;
+    if (cfg->scheme != 0 && cfg->scheme != 1) return ORC_EINVAL;
     for (int i = 0; i < n; i++) {
         if (!(x[i] > cfg->x0 && x[i] < cfg->x1 && y[i] > cfg->y0 && y[i] < cfg->y1)) {
             if (!(cfg->boundary == 1 && x[i] >= cfg->x0 && x[i] < cfg->x1 && y[i] >= cfg->y0 && y[i] < cfg->y1))
@@ -400,6 +414,9 @@ int orc_create(const orc_config *cfg, int n, const double *x, const double *y, c
     s->tess = xmalloc(sizeof(int) * n);
     s->x_prev = xmalloc(sizeof(double) * n); s->y_prev = xmalloc(sizeof(double) * n);
     memcpy(s->x_prev, x, sizeof(double) * n); memcpy(s->y_prev, y, sizeof(double) * n);
+    s->m0 = xmalloc(sizeof(double) * n); s->px0 = xmalloc(sizeof(double) * n);
+    s->py0 = xmalloc(sizeof(double) * n); s->E0 = xmalloc(sizeof(double) * n);
+    s->x0 = xmalloc(sizeof(double) * n); s->y0 = xmalloc(sizeof(double) * n);
     int rc = orc_tessellate(s);
     if (rc != ORC_OK) { orc_destroy(s); return rc; }
     /* areas of the initial cells turn the primitive fields into extensive ones */
@@ -430,6 +447,7 @@ void orc_destroy(orc_sim *s)
     free(s->A); free(s->ox); free(s->oy); free(s->W); free(s->cs); free(s->g); free(s->gl);
     free(s->alpha); free(s->wx); free(s->wy); free(s->tess);
     free(s->x_prev); free(s->y_prev);
+    free(s->m0); free(s->px0); free(s->py0); free(s->E0); free(s->x0); free(s->y0);
     free(s);
 }
 
@@ -467,7 +485,11 @@ static int geometry_and_primitives(orc_sim *s)
     return ORC_OK;
 }
 
-int orc_sweep(orc_sim *s, double t_end, double *dt_out)
+/* One sweep over the current tessellation.  pass 0: the extrapolated-fluxes
+   step; pass 1: the half step of the time-centred scheme (saves U^n and r^n
+   first); pass 2: its full step with the half step's dt, from the saved
+   U^n and r^n. */
+static int sweep_pass(orc_sim *s, double t_end, int pass, double *dt_out)
 {
     if (!s->tess_ok) return ORC_ETESS;
     const orc_config *c = &s->c;
@@ -558,18 +580,31 @@ int orc_sweep(orc_sim *s, double t_end, double *dt_out)
             s->wy[i] = vy;
         }
     }
-    /* Courant condition */
+    /* Courant condition (the full step of the time-centred scheme keeps the
+       half step's dt) */
     double dt = INFINITY;
-    for (int i = 0; i < n; i++) {
-        double R = sqrt(s->A[i] / M_PI);
-        double rel = hypot(s->W[4 * i + 1] - s->wx[i], s->W[4 * i + 2] - s->wy[i]);
-        double d = R / (s->cs[i] + rel);
-        if (d < dt) dt = d;
+    if (pass == 2) {
+        dt = s->dt;
+    } else {
+        for (int i = 0; i < n; i++) {
+            double R = sqrt(s->A[i] / M_PI);
+            double rel = hypot(s->W[4 * i + 1] - s->wx[i], s->W[4 * i + 2] - s->wy[i]);
+            double d = R / (s->cs[i] + rel);
+            if (d < dt) dt = d;
+        }
+        dt *= c->cfl;
+        if (s->t + dt > t_end) dt = t_end - s->t;
+        if (!(dt >= 0)) return ORC_EBAD;
+        s->dt = dt;
     }
-    dt *= c->cfl;
-    if (s->t + dt > t_end) dt = t_end - s->t;
-    if (!(dt >= 0)) return ORC_EBAD;
-    s->dt = dt;
+    /* edge states: advanced half a step in time by the extrapolated-fluxes
+       scheme, spatial extrapolation only in the time-centred one */
+    const double hdt = pass == 0 ? 0.5 * dt : 0.0;
+    if (pass == 1) {
+        memcpy(s->m0, s->m, sizeof(double) * n); memcpy(s->px0, s->px, sizeof(double) * n);
+        memcpy(s->py0, s->py, sizeof(double) * n); memcpy(s->E0, s->E, sizeof(double) * n);
+        memcpy(s->x0, s->x, sizeof(double) * n); memcpy(s->y0, s->y, sizeof(double) * n);
+    }
     /* fluxes through every edge of every cell, and the conservative update */
     double *dU = xmalloc(sizeof(double) * 4 * n);
     for (int i = 0; i < n; i++) {
@@ -592,8 +627,8 @@ int orc_sweep(orc_sim *s, double t_end, double *dt_out)
             double offi_x = G.mx - oi[0], offi_y = G.my - oi[1];
             double offj_x = G.mx - (G.rx + oj[0]), offj_y = G.my - (G.ry + oj[1]);
             double Si[4], Sj[4];
-            predict(gam, 0.5 * dt, Wi, gi, offi_x, offi_y, wf, Si);
-            predict(gam, 0.5 * dt, Wj, gj, offj_x, offj_y, wf, Sj);
+            predict(gam, hdt, Wi, gi, offi_x, offi_y, wf, Si);
+            predict(gam, hdt, Wj, gj, offj_x, offj_y, wf, Sj);
             /* boost into the edge frame and rotate to (normal, tangential) */
             double tx = -G.ny, ty = G.nx;
             double WL[4] = {Si[0], (Si[1] - wf[0]) * G.nx + (Si[2] - wf[1]) * G.ny,
@@ -614,16 +649,22 @@ int orc_sweep(orc_sim *s, double t_end, double *dt_out)
             dU[4 * i + 3] -= dt * G.L * F3;
         }
     }
+    /* new state and points from those at the start of the step: half the
+       change in the half step of the time-centred scheme */
+    const double f = pass == 1 ? 0.5 : 1.0;
+    const double *bm = pass == 0 ? s->m : s->m0, *bpx = pass == 0 ? s->px : s->px0;
+    const double *bpy = pass == 0 ? s->py : s->py0, *bE = pass == 0 ? s->E : s->E0;
+    const double *bx = pass == 0 ? s->x : s->x0, *by = pass == 0 ? s->y : s->y0;
     int bad = 0;
     for (int i = 0; i < n; i++) {
-        s->m[i] += dU[4 * i];
-        s->px[i] += dU[4 * i + 1];
-        s->py[i] += dU[4 * i + 2];
-        s->E[i] += dU[4 * i + 3];
+        s->m[i] = bm[i] + f * dU[4 * i];
+        s->px[i] = bpx[i] + f * dU[4 * i + 1];
+        s->py[i] = bpy[i] + f * dU[4 * i + 2];
+        s->E[i] = bE[i] + f * dU[4 * i + 3];
         if (!(s->m[i] > 0) || !(s->E[i] - 0.5 * (s->px[i] * s->px[i] + s->py[i] * s->py[i]) / s->m[i] > 0)) bad = 1;
         /* move the generating points; wrap into a periodic box, and reflect a
            point that crossed a rigid wall back across it (as its mirror image) */
-        double nx = s->x[i] + dt * s->wx[i], ny = s->y[i] + dt * s->wy[i];
+        double nx = bx[i] + f * dt * s->wx[i], ny = by[i] + f * dt * s->wy[i];
         if (c->boundary == 1) {
             double Lx = c->x1 - c->x0, Ly = c->y1 - c->y0;
             if (nx < c->x0) nx += Lx;
@@ -641,7 +682,7 @@ int orc_sweep(orc_sim *s, double t_end, double *dt_out)
         s->y[i] = ny;
     }
     free(dU);
-    s->t += dt;
+    if (pass != 1) s->t += dt;
     s->tess_ok = 0;
     if (dt_out) *dt_out = dt;
     return bad ? ORC_EBAD : ORC_OK;
@@ -666,6 +707,18 @@ int orc_get_primitives(orc_sim *s, double *rho, double *vx, double *vy, double *
         if (area) area[i] = s->A[i];
     }
     return ORC_OK;
+}
+
+/* one step over the current tessellation: one sweep (extrapolated fluxes),
+   or half step, re-tessellation and full step (time-centred fluxes) */
+int orc_sweep(orc_sim *s, double t_end, double *dt_out)
+{
+    if (s->c.scheme == 0) return sweep_pass(s, t_end, 0, dt_out);
+    int rc = sweep_pass(s, t_end, 1, NULL);
+    if (rc) return rc;
+    rc = orc_tessellate(s);
+    if (rc) return rc;
+    return sweep_pass(s, t_end, 2, dt_out);
 }
 
 int orc_step(orc_sim *s, double t_end, double *dt_out)

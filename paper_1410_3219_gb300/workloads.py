@@ -31,13 +31,16 @@ LIM_AREPO = 1
 LIM_TESS = 2
 FP64 = 0
 FP32_SPLIT = 1
+SCHEME_EXTRAPOLATED = 0
+SCHEME_TIME_CENTRED = 1
 
 
 def default_cfg(**over):
     cfg = dict(gamma=5.0 / 3.0, cfl=0.3, boundary=BC_PERIODIC,
                x0=0.0, x1=1.0, y0=0.0, y1=1.0,
                motion=MESH_LAGRANGIAN, chi=0.15, eta=0.02,
-               theta=0.5, delta_v=0.2, delta_p=0.7, limiter=LIM_SWITCHED)
+               theta=0.5, delta_v=0.2, delta_p=0.7, limiter=LIM_SWITCHED,
+               scheme=SCHEME_EXTRAPOLATED)
     cfg.update(over)
     return cfg
 
@@ -144,6 +147,20 @@ def advection(n_side=32, seed=0, jitter=0.0, motion=MESH_LAGRANGIAN):
     x, y = jittered_lattice(n_side, n_side, -0.5, 0.5, -0.5, 0.5, jitter, rng)
     rho = np.where(np.hypot(x, y) < 0.2, 100.0, 1.0)
     return _pack("advection", seed, cfg, x, y, rho, 1.0, 1.0, 1.0)
+
+
+def sound_wave(n_side=32, seed=9, jitter=0.1, amp=1e-3, motion=MESH_LAGRANGIAN, scheme=SCHEME_EXTRAPOLATED):
+    """Right-moving linear sound wave along x in the periodic unit box:
+    gamma = 5/3, rho = 1 + a sin(2 pi x), p = 1 + gamma a sin(2 pi x),
+    vx = c a sin(2 pi x) with c = sqrt(gamma); a smooth solution for
+    convergence checks."""
+    rng = np.random.default_rng(seed)
+    g = 5.0 / 3.0
+    cfg = default_cfg(gamma=g, boundary=BC_PERIODIC, motion=motion, scheme=scheme)
+    x, y = jittered_lattice(n_side, n_side, 0.0, 1.0, 0.0, 1.0, jitter, rng)
+    s = np.sin(2.0 * math.pi * x)
+    return _pack("sound_wave", seed, cfg, x, y, 1.0 + amp * s, math.sqrt(g) * amp * s, 0.0,
+                 1.0 + g * amp * s)
 
 
 def uniform(n_side=16, seed=5, jitter=0.25, boundary=BC_PERIODIC, rho=1.3, vx=0.4,
