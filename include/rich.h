@@ -65,7 +65,14 @@ extern "C" {
 #define RICH_LIM_AREPO 1
 #define RICH_LIM_TESS 2
 
-#define RICH_SCHEME_EXTRAPOLATED 0 /* Section 2.3 "extrapolated fluxes" */
+#define RICH_SCHEME_EXTRAPOLATED 0 /* Section 2.3 "extrapolated fluxes": one sweep per step, edge
+                                      states advanced half a step in time */
+#define RICH_SCHEME_TIME_CENTRED 1 /* Section 2.3 "time centred fluxes" (the paper's own): a half
+                                      step with spatially extrapolated edge states, the mesh rebuilt
+                                      at the half-step points, then the full step from the
+                                      start-of-step state with the half-step fluxes and mesh
+                                      velocities; two tessellations and two sweeps per step.
+                                      Single simulations only (batches and the server reject it). */
 
 #define RICH_FP64 0       /* every step in FP64 */
 #define RICH_FP32_SPLIT 1 /* primitives, gradients, limiter, mesh velocity, edge states and HLLC in
@@ -116,7 +123,8 @@ int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const dou
 
 /* Advance up to max_steps steps, stopping early once the time reaches t_end
    (the last step is shortened to land on t_end).  Each step: a0 on the host
-   for the current points, then a1-a9 on the device.  info may be NULL.
+   for the current points, then a1-a9 on the device (twice, with a0 for the
+   half-step points in between, in the time-centred scheme).  info may be NULL.
    Errors: RICH_ENEGATIVE / RICH_ENAN (state left at the last good step),
    RICH_ETESS, RICH_EDUPLICATE, RICH_ECUDA. */
 int rich_step(rich_sim *s, int32_t max_steps, double t_end, rich_step_info *info);
@@ -124,7 +132,9 @@ int rich_step(rich_sim *s, int32_t max_steps, double t_end, rich_step_info *info
 /* Primitive fields and cell areas on the current generating points (each
    output may be NULL; n must equal the simulation's size).  If the points
    moved since the last tessellation this tessellates and recomputes the
-   geometry first. */
+   geometry first.  Between the two sweeps of a time-centred step (pieces
+   API below) the current points and state are the half-step ones; the same
+   holds for rich_get_conserved. */
 int rich_get_state(rich_sim *s, int64_t n, double *x, double *y, double *rho, double *vx, double *vy,
                    double *p, double *area);
 
@@ -149,7 +159,10 @@ int rich_set_stream(rich_sim *s, void *cuda_stream);
 int rich_tessellate(rich_sim *s, rich_step_info *info);
 
 /* Enqueue a1-a9 for one step on the current connectivity (asynchronous; no
-   host synchronisation).  Requires a current tessellation. */
+   host synchronisation).  Requires a current tessellation.  In the
+   time-centred scheme a step takes two rounds of rich_tessellate /
+   rich_sweep / rich_sync: the first sweep (half step) leaves the half-step
+   points current, the second completes the step. */
 int rich_sweep(rich_sim *s, double t_end);
 
 /* Wait for the enqueued sweep, read time step, time and status flags.

@@ -170,6 +170,7 @@ struct rich_batch {
         p.enx = enx.as<R>(); p.eny = eny.as<R>(); p.eqx = eqx.as<R>(); p.eqy = eqy.as<R>();
         p.ePM = ePM.as<rich::Vec4<R>>();
         p.U = U[cur].as<double>(); p.Un = U[1 - cur].as<double>();
+        p.U0 = p.U; p.x0 = p.x; p.y0 = p.y;
         p.W = W.as<rich::Vec4<R>>(); p.o = o.as<rich::Vec2<R>>(); p.cs = cs.as<R>();
         p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
         p.w = w.as<rich::Vec2<R>>();
@@ -450,6 +451,8 @@ int rich_batch_add(rich_batch *b, const rich_config *cfg, int64_t n, const doubl
                    int64_t max_steps, int32_t *id)
 {
     if (!b || !id) return fail(RICH_EINVAL, "NULL argument");
+    if (cfg && cfg->scheme != RICH_SCHEME_EXTRAPOLATED)
+        return fail(RICH_EINVAL, "batches run the extrapolated-fluxes scheme only");
     if (!rich::valid_config(cfg) || cfg->precision != b->precision)
         return fail(RICH_EINVAL, "invalid configuration or precision differs from the batch");
     if (n < 3 || n > ((int64_t)1 << 30) || !x || !y || !rho || !vx || !vy || !p) return fail(RICH_EINVAL, "bad arrays");

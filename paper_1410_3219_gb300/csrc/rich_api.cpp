@@ -56,7 +56,7 @@ bool valid_config(const rich_config *c)
     return c && c->gamma > 1.0 && std::isfinite(c->gamma) && c->cfl > 0.0 && c->x1 > c->x0 && c->y1 > c->y0 &&
            (c->boundary == RICH_BC_REFLECTIVE || c->boundary == RICH_BC_PERIODIC) &&
            (c->motion == RICH_MESH_LAGRANGIAN || c->motion == RICH_MESH_EULERIAN) && c->limiter >= 0 &&
-           c->limiter <= 2 && c->scheme == RICH_SCHEME_EXTRAPOLATED && (c->precision == RICH_FP64 || c->precision == RICH_FP32_SPLIT) && c->chi >= 0 &&
+           c->limiter <= 2 && (c->scheme == RICH_SCHEME_EXTRAPOLATED || c->scheme == RICH_SCHEME_TIME_CENTRED) && (c->precision == RICH_FP64 || c->precision == RICH_FP32_SPLIT) && c->chi >= 0 &&
            c->eta >= 0 && c->theta >= 0 && c->delta_p >= 0 && c->delta_v >= 0;
 }
 
@@ -79,9 +79,13 @@ struct rich_sim {
     rich::HostMesh hm;
     double t = 0.0;
     int cur = 0;
+    // time-centred scheme: 1 between its two sweeps (buffers [2] then hold
+    // the half-step points and state)
+    int tc_phase = 0;
     bool tess_current = false;
     bool pending = false;
     bool geometry_current = false;
+    int diag_pts = 0;  // points buffer of the last completed sweep
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -90,7 +94,7 @@ struct rich_sim {
     double kms[rich::NUM_STAGES] = {};
     double last_dt = 0.0;
     // device buffers
-    DBuf x[2], y[2], U[2];
+    DBuf x[3], y[3], U[3];
     DBuf A, o, W, cs, g, gl, alpha, w, tess, cell_ptr, initW, rounding, p64;
     bool diagnostics = true;
     DBuf gx, gy, gsrc, gxf;
@@ -122,8 +126,13 @@ struct rich_sim {
         p.T = (int32_t)(hm.tri.size() / 3);
         p.E = (int32_t)hm.edge_l.size();
         p.S = (int32_t)hm.slot_nb.size();
-        p.x = x[cur].as<double>(); p.y = y[cur].as<double>();
-        p.xn = x[1 - cur].as<double>(); p.yn = y[1 - cur].as<double>();
+        // extrapolated fluxes: [cur] -> [1 - cur].  Time-centred: [cur] -> [2]
+        // by half a step, then primitives and mesh of [2], update of [cur]
+        // into [1 - cur]
+        const int src = pts(), dst = time_centred() && tc_phase == 0 ? 2 : 1 - cur;
+        p.x = x[src].as<double>(); p.y = y[src].as<double>();
+        p.xn = x[dst].as<double>(); p.yn = y[dst].as<double>();
+        p.x0 = x[cur].as<double>(); p.y0 = y[cur].as<double>();
         p.gx = gx.as<double>(); p.gy = gy.as<double>();
         p.tri = tri.as<int32_t>(); p.cell_ptr = cell_ptr.as<int32_t>();
         p.slot_nb = slot_nb.as<int32_t>(); p.slot_tri = slot_tri.as<int32_t>(); p.slot_edge = slot_edge.as<int32_t>();
@@ -135,7 +144,7 @@ struct rich_sim {
         p.emrx = emrx.as<R>(); p.emry = emry.as<R>();
         p.enx = enx.as<R>(); p.eny = eny.as<R>(); p.eqx = eqx.as<R>(); p.eqy = eqy.as<R>();
         p.ePM = ePM.as<rich::Vec4<R>>();
-        p.U = U[cur].as<double>(); p.Un = U[1 - cur].as<double>();
+        p.U = U[src].as<double>(); p.Un = U[dst].as<double>(); p.U0 = U[cur].as<double>();
         p.W = W.as<rich::Vec4<R>>(); p.o = o.as<rich::Vec2<R>>(); p.cs = cs.as<R>();
         p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
         p.w = w.as<rich::Vec2<R>>();
@@ -149,6 +158,9 @@ struct rich_sim {
     }
 
     size_t rsize() const { return cfg.precision == RICH_FP32_SPLIT ? sizeof(float) : sizeof(double); }
+    bool time_centred() const { return cfg.scheme == RICH_SCHEME_TIME_CENTRED; }
+    // buffer of the points (and state) that the current mesh and sweep describe
+    int pts() const { return tc_phase == 1 ? 2 : cur; }
 
     // scheme parameters of this simulation with the time left to t_end
     rich::InstParams inst_params(double remaining, bool init = false) const
@@ -160,6 +172,7 @@ struct rich_sim {
         ip.x0 = cfg.x0; ip.x1 = cfg.x1; ip.y0 = cfg.y0; ip.y1 = cfg.y1;
         ip.remaining = remaining;
         ip.boundary = cfg.boundary; ip.motion = cfg.motion; ip.limiter = cfg.limiter;
+        ip.phase = time_centred() ? 1 + tc_phase : 0;
         return ip;
     }
 
@@ -187,7 +200,7 @@ namespace {
 int alloc_cells(rich_sim *s)
 {
     const size_t n = (size_t)s->n, d = sizeof(double), r = s->rsize();
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < (s->time_centred() ? 3 : 2); k++) {
         CUDA_TRY(s->x[k].ensure(n * d));
         CUDA_TRY(s->y[k].ensure(n * d));
         CUDA_TRY(s->U[k].ensure(4 * n * d));
@@ -208,8 +221,9 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
 {
     double t0 = now_ms();
     if (fetch_points) {
-        CUDA_TRY(cudaMemcpyAsync(s->hx.data(), s->x[s->cur].p, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(s->hy.data(), s->y[s->cur].p, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+        const int q = s->pts();
+        CUDA_TRY(cudaMemcpyAsync(s->hx.data(), s->x[q].p, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(s->hy.data(), s->y[q].p, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
     }
     double t1 = now_ms();
@@ -453,17 +467,29 @@ int rich_sync(rich_sim *s, rich_step_info *info)
         info->copy_ms += now_ms() - t0;
     }
     s->geometry_current = true;  // diagnostics describe this sweep
+    s->diag_pts = s->pts();
     if (status) {
         CUDA_TRY(cudaMemsetAsync(sc + 16, 0, 4, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (s->tc_phase == 1) {
+            // the full step failed: start the step again from [cur]
+            s->tc_phase = 0;
+            s->tess_current = false;
+        }
         if (status & rich::ST_NAN) return fail(RICH_ENAN, "non-finite state after the step");
         if (status & rich::ST_LEFT_BOX) return fail(RICH_ENEGATIVE, "a generating point left the box");
         return fail(RICH_ENEGATIVE, "non-positive mass or thermal energy after the step");
     }
-    s->cur = 1 - s->cur;
     s->last_dt = dt;
-    s->t += dt;
     s->tess_current = false;
+    if (s->time_centred() && s->tc_phase == 0) {
+        // half step done: the next sweep is the full step on the half-step mesh
+        s->tc_phase = 1;
+        return RICH_OK;
+    }
+    s->tc_phase = 0;
+    s->cur = 1 - s->cur;
+    s->t += dt;
     if (info) {
         info->steps_done += 1;
         info->t = s->t;
@@ -480,9 +506,15 @@ int rich_step(rich_sim *s, int32_t max_steps, double t_end, rich_step_info *info
         if (!(s->t < t_end)) break;
         int rc;
         if (!s->tess_current && (rc = tessellate(s, info, true)) != RICH_OK) return rc;
-        if ((rc = rich_sweep(s, t_end)) != RICH_OK) return rc;
         double before = s->t;
+        if ((rc = rich_sweep(s, t_end)) != RICH_OK) return rc;
         if ((rc = rich_sync(s, info)) != RICH_OK) return rc;
+        if (s->tc_phase == 1) {
+            // time-centred: the mesh of the half-step points, then the full step
+            if ((rc = tessellate(s, info, true)) != RICH_OK) return rc;
+            if ((rc = rich_sweep(s, t_end)) != RICH_OK) return rc;
+            if ((rc = rich_sync(s, info)) != RICH_OK) return rc;
+        }
         if (s->last_dt >= t_end - before) s->t = t_end;  // landed on t_end
         if (info) info->t = s->t;
     }
@@ -538,8 +570,9 @@ int rich_get_state(rich_sim *s, int64_t n, double *x, double *y, double *rho, do
     if (rc) return rc;
     std::vector<double> h;
     const size_t N = (size_t)s->n;
-    if (x) { if ((rc = fetch(s, s->x[s->cur].p, h, N))) return rc; unpermute(s, h.data(), x); }
-    if (y) { if ((rc = fetch(s, s->y[s->cur].p, h, N))) return rc; unpermute(s, h.data(), y); }
+    const int q = s->pts();
+    if (x) { if ((rc = fetch(s, s->x[q].p, h, N))) return rc; unpermute(s, h.data(), x); }
+    if (y) { if ((rc = fetch(s, s->y[q].p, h, N))) return rc; unpermute(s, h.data(), y); }
     double *outs[4] = {rho, vx, vy, p};
     if (rho || vx || vy || p) {
         if ((rc = fetch_r(s, s->W.p, h, 4 * N))) return rc;
@@ -561,11 +594,12 @@ int rich_get_conserved(rich_sim *s, int64_t n, double *x, double *y, double *m, 
     std::vector<double> h;
     int rc;
     const size_t N = (size_t)s->n;
-    if (x) { if ((rc = fetch(s, s->x[s->cur].p, h, N))) return rc; unpermute(s, h.data(), x); }
-    if (y) { if ((rc = fetch(s, s->y[s->cur].p, h, N))) return rc; unpermute(s, h.data(), y); }
+    const int q = s->pts();
+    if (x) { if ((rc = fetch(s, s->x[q].p, h, N))) return rc; unpermute(s, h.data(), x); }
+    if (y) { if ((rc = fetch(s, s->y[q].p, h, N))) return rc; unpermute(s, h.data(), y); }
     double *outs[4] = {m, px, py, E};
     if (m || px || py || E) {
-        if ((rc = fetch(s, s->U[s->cur].p, h, 4 * N))) return rc;
+        if ((rc = fetch(s, s->U[q].p, h, 4 * N))) return rc;
         for (int v = 0; v < 4; v++)
             if (outs[v]) unpermute(s, h.data() + v * N, outs[v]);
     }
@@ -579,8 +613,8 @@ int rich_get_field(rich_sim *s, int32_t f, int64_t n, double *out)
     const size_t N = (size_t)s->n;
     std::vector<double> h, h2;
     int rc;
-    // the diagnostics refer to the points before the last completed step
-    const int prev = s->geometry_current && !s->tess_current ? 1 - s->cur : s->cur;
+    // the diagnostics refer to the points of the last sweep
+    const int prev = s->geometry_current && !s->tess_current ? s->diag_pts : s->pts();
     // gather component c of an array-of-structures field with `stride` values per cell
     auto comp_of = [&](const DBuf &b, int stride, int c) {
         int r2 = fetch_r(s, b.p, h2, stride * N);

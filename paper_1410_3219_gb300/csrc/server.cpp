@@ -79,6 +79,8 @@ int rich_server_submit(rich_server *s, const rich_config *cfg, int64_t n, const 
     if (!s || !cfg || !req) return fail(RICH_EINVAL, "NULL argument");
     if (n < 3 || n > s->max_cells) return fail(RICH_EINVAL, "n must be in [3, the server's cell budget]");
     if (!x || !y || !rho || !vx || !vy || !p) return fail(RICH_EINVAL, "NULL input array");
+    if (cfg->scheme != RICH_SCHEME_EXTRAPOLATED)
+        return fail(RICH_EINVAL, "the server runs the extrapolated-fluxes scheme only");
     auto r = std::make_unique<Request>();
     r->id = s->next_id++;
     r->cfg = *cfg;

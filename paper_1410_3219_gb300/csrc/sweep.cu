@@ -421,6 +421,8 @@ template <class R> __global__ void __launch_bounds__(kBlock) k_cell_gradient(Swe
 template <class R> __device__ __forceinline__ double step_dt(const SweepParams<R> &p, int32_t inst)
 {
     const InstParams &ip = p.inst[inst];
+    // the second sweep of the time-centred scheme keeps the first one's dt
+    if (ip.phase == 2) return __ldcg(p.dt_out + inst);
     // read through L2: in the persistent sweep the minimum was reset and then
     // reduced with atomics earlier in the same launch, and a line of it may
     // still sit stale in this SM's L1
@@ -488,8 +490,8 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
 {
     const int32_t l = p.edge_l[e];
     const int32_t li = inst_of(p, l);
-    const R dt = (R)step_dt(p, li);
-    const R hdt = R(0.5) * dt;
+    // edge states advance half a step in time only in the extrapolated scheme
+    const R hdt = p.inst[li].phase == 0 ? R(0.5) * (R)step_dt(p, li) : R(0);
     int32_t xf;
     const int32_t k = src_of(p, p.edge_r[e], xf);
     const R sx = (xf & 1) ? R(-1) : R(1), sy = (xf & 2) ? R(-1) : R(1);
@@ -551,7 +553,9 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
     const int32_t my_inst = inst_of(p, i);
     const InstParams &ip = p.inst[my_inst];
     const double dt = step_dt(p, my_inst);
-    if (i == 0 || inst_of(p, i - 1) != my_inst) p.dt_out[my_inst] = dt;
+    if (ip.phase != 2 && (i == 0 || inst_of(p, i - 1) != my_inst)) p.dt_out[my_inst] = dt;
+    // the first sweep of the time-centred scheme moves state and points half a step
+    const double hdt = ip.phase == 1 ? 0.5 * dt : dt;
     const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (int32_t s = lo; s < hi; s++) {
@@ -560,10 +564,10 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
         if (es & 1) { s0 -= (double)f.x; s1 -= (double)f.y; s2 -= (double)f.z; s3 -= (double)f.w; }
         else { s0 += (double)f.x; s1 += (double)f.y; s2 += (double)f.z; s3 += (double)f.w; }
     }
-    double m = p.U[i] - dt * s0;
-    double Px = p.U[n + i] - dt * s1;
-    double Py = p.U[2 * n + i] - dt * s2;
-    double E = p.U[3 * n + i] - dt * s3;
+    double m = p.U0[i] - hdt * s0;
+    double Px = p.U0[n + i] - hdt * s1;
+    double Py = p.U0[2 * n + i] - hdt * s2;
+    double E = p.U0[3 * n + i] - hdt * s3;
     p.Un[i] = m;
     p.Un[n + i] = Px;
     p.Un[2 * n + i] = Py;
@@ -572,7 +576,7 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
     if (!(isfinite(m) && isfinite(Px) && isfinite(Py) && isfinite(E))) st |= ST_NAN;
     else if (!(m > 0.0) || !(2.0 * m * E - (Px * Px + Py * Py) > 0.0)) st |= ST_NEGATIVE;
     const Vec2<R> w = p.w[i];
-    double xn = p.x[i] + dt * (double)w.x, yn = p.y[i] + dt * (double)w.y;
+    double xn = p.x0[i] + hdt * (double)w.x, yn = p.y0[i] + hdt * (double)w.y;
     if (ip.boundary == 1) {
         const double Lx = ip.x1 - ip.x0, Ly = ip.y1 - ip.y0;
         if (xn < ip.x0) xn += Lx;

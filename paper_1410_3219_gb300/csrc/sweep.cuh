@@ -55,6 +55,13 @@ struct InstParams {
     double igm1;       // 1/(gamma - 1)
     int32_t boundary, motion, limiter;
     int32_t init;      // the geometry stage with primitives given sets this simulation's U
+    // Section 2.3 time advancement of this sweep: 0 extrapolated fluxes (edge
+    // states advanced dt/2 in time, full update); 1 first sweep of the
+    // time-centred scheme (spatial extrapolation only, Courant dt, half
+    // update); 2 its second sweep (spatial extrapolation only, the dt of
+    // sweep 1 from dt_out, full update)
+    int32_t phase;
+    int32_t pad;
 };
 
 template <class R> struct SweepParams {
@@ -77,9 +84,12 @@ template <class R> struct SweepParams {
     double *ccx, *ccy, *A;
     R *eL, *enx, *eny, *eqx, *eqy, *emlx, *emly, *emrx, *emry;
     Vec4<R> *ePM;  // Eq. 1 weights of the edge's left cell: P = L(q + n/2), M = L(n/2 - q)
-    // state
+    // state: U gives the primitives, the update writes Un = U0 - dt... and
+    // xn = x0 + dt w (U0 = U and x0 = x except in the time-centred scheme's
+    // second sweep, which starts again from the state at the start of the step)
     const double *U;
     double *Un;
+    const double *U0, *x0, *y0;
     Vec4<R> *W;
     Vec2<R> *o;
     R *cs;
