@@ -53,7 +53,7 @@ struct BatchSim {
     std::vector<int32_t> perm;  // internal (Hilbert) -> caller index
     std::vector<double> hx, hy;  // points, internal order
     std::vector<double> W0;      // initial primitives (4n, component-major) until admitted
-    rich::Delaunay dt;
+    rich::MeshWork mw;
     rich::HostMesh hm;
     int mesh_rc = 0;
     double t = 0.0, t_end = 0.0, last_dt = 0.0;
@@ -100,6 +100,7 @@ struct rich_batch {
     int cur = 0;
     // device
     DBuf x[2], y[2], U[2], A, o, W, cs, g, gl, alpha, w, tess, rounding, p64, cell_ptr, cell_inst, initW, src;
+    DBuf corder, psrc;
     DBuf gx, gy, gsrc, gxf, tri, ccx, ccy, slot_nb, slot_tri, slot_edge;
     DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F, ePM;
     DBuf instp, dtmin, dtout, status, dsizes, gsync;
@@ -123,6 +124,7 @@ struct rich_batch {
     // host staging of the packed mesh
     std::vector<double> h_x, h_y, h_gx, h_gy, h_W0;
     std::vector<int32_t> h_gsrc, h_gxf, h_tri, h_cell_ptr, h_slot_nb, h_slot_tri, h_slot_edge, h_cell_inst;
+    std::vector<int32_t> h_corder;
     std::vector<int32_t> h_edge_l, h_edge_r, h_edge_ta, h_edge_tb, h_src;
     std::vector<rich::InstParams> h_inst;
     std::vector<double> h_dt;
@@ -159,7 +161,7 @@ struct rich_batch {
         p.x = x[cur].as<double>(); p.y = y[cur].as<double>();
         p.xn = x[1 - cur].as<double>(); p.yn = y[1 - cur].as<double>();
         p.gx = gx.as<double>(); p.gy = gy.as<double>();
-        p.tri = tri.as<int32_t>(); p.cell_ptr = cell_ptr.as<int32_t>();
+        p.tri = tri.as<int32_t>(); p.cell_ptr = cell_ptr.as<int32_t>(); p.cell_order = corder.as<int32_t>();
         p.slot_nb = slot_nb.as<int32_t>(); p.slot_tri = slot_tri.as<int32_t>(); p.slot_edge = slot_edge.as<int32_t>();
         p.edge_l = edge_l.as<int32_t>(); p.edge_r = edge_r.as<int32_t>();
         p.edge_ta = edge_ta.as<int32_t>(); p.edge_tb = edge_tb.as<int32_t>();
@@ -175,7 +177,7 @@ struct rich_batch {
         p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
         p.w = w.as<rich::Vec2<R>>();
         p.rounding = rounding.as<uint8_t>(); p.p64 = p64.as<double>();
-        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<R>>();
+        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<R>>(); p.psrc = psrc.as<rich::Vec4<R>>();
         p.dtmin_bits = dtmin.as<unsigned long long>();
         p.dt_out = dtout.as<double>();
         p.status = status.as<int32_t>();
@@ -240,6 +242,7 @@ void pack_one(rich_batch *b, BatchSim &s, int32_t k)
     const size_t T = m.tri.size() / 3;
     for (size_t t = 0; t < 3 * T; t++) b->h_tri[3 * to + t] = pid(m.tri[t]);
     for (int32_t i = 0; i < n; i++) b->h_cell_ptr[co + i] = (int32_t)(so + m.cell_ptr[i]);
+    for (int32_t i = 0; i < n; i++) b->h_corder[co + i] = (int32_t)(co + m.cell_order[i]);
     const size_t S = m.slot_nb.size();
     for (size_t q = 0; q < S; q++) {
         b->h_slot_nb[so + q] = pid(m.slot_nb[q]);
@@ -275,6 +278,7 @@ int ensure_device(rich_batch *b)
     CUDA_TRY(b->g.ensure(8 * N * r + 64)); CUDA_TRY(b->gl.ensure(8 * N * r + 64));
     CUDA_TRY(b->alpha.ensure(4 * N * r + 32)); CUDA_TRY(b->w.ensure(2 * N * r + 16));
     CUDA_TRY(b->tess.ensure(N * 4 + 4)); CUDA_TRY(b->rounding.ensure(N + 8)); CUDA_TRY(b->p64.ensure(N * d + 8));
+    CUDA_TRY(b->psrc.ensure(4 * N * r + 32));
     CUDA_TRY(b->ccx.ensure(T * d + 8)); CUDA_TRY(b->ccy.ensure(T * d + 8));
     for (DBuf *e : {&b->eL, &b->emlx, &b->emly, &b->emrx, &b->emry, &b->enx, &b->eny, &b->eqx, &b->eqy})
         CUDA_TRY(e->ensure(E * r + 8));
@@ -525,7 +529,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     b->pool.parallel_for((int64_t)list.size(), [&](int64_t k) {
         BatchSim *s = list[k];
         rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
-        s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->dt, s->hm);
+        s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm);
     });
     const double t2 = now_ms();
     std::vector<BatchSim *> ok;
@@ -572,7 +576,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     for (BatchSim *s : ok) any_pending |= s->state == PENDING;
     b->h_x.resize(N); b->h_y.resize(N); b->h_cell_inst.resize(N); b->h_src.resize(N);
     b->h_gx.resize(go); b->h_gy.resize(go); b->h_gsrc.resize(go); b->h_gxf.resize(go);
-    b->h_tri.resize(3 * to); b->h_cell_ptr.resize(N + 1);
+    b->h_tri.resize(3 * to); b->h_cell_ptr.resize(N + 1); b->h_corder.resize(N);
     b->h_slot_nb.resize(so); b->h_slot_tri.resize(so); b->h_slot_edge.resize(so);
     b->h_edge_l.resize(eo); b->h_edge_r.resize(eo); b->h_edge_ta.resize(eo); b->h_edge_tb.resize(eo);
     if (any_pending) b->h_W0.assign(4 * N, 0.0);
@@ -608,6 +612,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     CUDA_TRY(upload(b->gxf, b->h_gxf, b->stream));
     CUDA_TRY(upload(b->tri, b->h_tri, b->stream));
     CUDA_TRY(upload(b->cell_ptr, b->h_cell_ptr, b->stream));
+    CUDA_TRY(upload(b->corder, b->h_corder, b->stream));
     CUDA_TRY(upload(b->slot_nb, b->h_slot_nb, b->stream));
     CUDA_TRY(upload(b->slot_tri, b->h_slot_tri, b->stream));
     CUDA_TRY(upload(b->slot_edge, b->h_slot_edge, b->stream));
@@ -767,7 +772,7 @@ int rich_batch_remove(rich_batch *b, int32_t id)
     s->fin.clear();
     s->fin.shrink_to_fit();
     s->hm = rich::HostMesh();
-    s->dt = rich::Delaunay();
+    s->mw = rich::MeshWork();
     s->hx = std::vector<double>();
     s->hy = std::vector<double>();
     s->perm = std::vector<int32_t>();

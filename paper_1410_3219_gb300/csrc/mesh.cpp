@@ -8,6 +8,7 @@
 #include <cstring>
 
 #include "predicates.h"
+#include "threadpool.h"
 
 namespace rich {
 
@@ -250,6 +251,24 @@ int Delaunay::build(const double *x, const double *y, int32_t np)
     return 0;
 }
 
+void degree_order(int32_t n, const int32_t *cell_ptr, int32_t *order)
+{
+    constexpr int32_t kMaxDeg = 64;
+    for (int32_t w0 = 0; w0 < n; w0 += kOrderWindow) {
+        const int32_t w1 = std::min(n, w0 + kOrderWindow);
+        int32_t count[kMaxDeg + 1] = {};
+        for (int32_t i = w0; i < w1; i++) count[std::min(cell_ptr[i + 1] - cell_ptr[i], kMaxDeg)]++;
+        // exclusive offsets, largest degree first
+        int32_t pos[kMaxDeg + 1];
+        int32_t acc = w0;
+        for (int32_t d = kMaxDeg; d >= 0; d--) {
+            pos[d] = acc;
+            acc += count[d];
+        }
+        for (int32_t i = w0; i < w1; i++) order[pos[std::min(cell_ptr[i + 1] - cell_ptr[i], kMaxDeg)]++] = i;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // ghosts + rings + edges
 
@@ -286,16 +305,161 @@ static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const 
     m.g = (int32_t)m.gx.size();
 }
 
-int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const double *y, Delaunay &dt, HostMesh &m)
+namespace {
+
+// Circumdisk of the triangle (a, b, c), radius padded for round-off so that a
+// containment test against it errs on the safe side.
+struct Disk {
+    double ux, uy, R;
+};
+
+inline Disk circumdisk(const double *X, const double *Y, int32_t a, int32_t b, int32_t c, double pad)
+{
+    double ax = X[a], ay = Y[a];
+    double bx = X[b] - ax, by = Y[b] - ay, cx = X[c] - ax, cy = Y[c] - ay;
+    double d = 2.0 * (bx * cy - by * cx);
+    double b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+    double ux = (cy * b2 - by * c2) / d, uy = (bx * c2 - cx * b2) / d;
+    return Disk{ux + ax, uy + ay, std::sqrt(ux * ux + uy * uy) * (1.0 + 1e-9) + pad};
+}
+
+// Outcome of one slab: the rings of its real core cells, the triangles they
+// use (global point ids, smallest id first), and whether the halo and the
+// ghost band were wide enough.
+struct SlabResult {
+    int rc = 0;
+    bool halo_ok = true, band_ok = true;
+    std::vector<int32_t> cells;  // real core cells, increasing id
+    std::vector<int32_t> deg;    // ring length of each
+    std::vector<int32_t> nb;     // concatenated rings: neighbour point ids
+    std::vector<int32_t> tri;    // concatenated rings: slab-local triangle number
+    std::vector<int32_t> tris;   // 3 per slab-local triangle
+};
+
+// Triangulate the points of slab [a, b) (x) plus a halo of width H, and read
+// off the stars of its real core points.  A star is the true one when the
+// circumdisk of each of its triangles lies inside the triangulated strip:
+// every point of the whole set inside such a disk was then triangulated too,
+// and an empty circumdisk among them is empty in the whole set.
+void build_slab(int32_t n, int32_t np, const double *X, const double *Y, double xmin, double xmax, double a, double b,
+                bool first, bool last, double H, const double band[4], double pad, Delaunay &dt,
+                std::vector<int32_t> &loc, std::vector<double> &LX, std::vector<double> &LY, SlabResult &r)
+{
+    r = SlabResult();
+    double lo = first ? -INFINITY : a - H, hi = last ? INFINITY : b + H;
+    // a halo that covers every point makes the slab's triangulation the whole one
+    const bool whole = lo <= xmin && hi > xmax;
+    if (whole) {
+        lo = -INFINITY;
+        hi = INFINITY;
+    }
+    loc.clear();
+    LX.clear();
+    LY.clear();
+    for (int32_t q = 0; q < np; q++)
+        if (X[q] >= lo && X[q] < hi) {
+            loc.push_back(q);
+            LX.push_back(X[q]);
+            LY.push_back(Y[q]);
+        }
+    const int32_t nl = (int32_t)loc.size();
+    if (nl == 0) return;
+    r.rc = dt.build(LX.data(), LY.data(), nl);
+    if (r.rc) return;
+    const std::vector<Tri> &T = dt.tris;
+    auto core_real = [&](int32_t v) { return v < nl && loc[v] < n && (first || X[loc[v]] >= a) && (last || X[loc[v]] < b); };
+    // the stars of the real core points: check, number, and find one
+    // triangle incident to each such point
+    std::vector<int32_t> tnum(T.size(), -1), vtri(nl, -1);
+    int32_t nt = 0;
+    for (size_t t = 0; t < T.size(); t++) {
+        const int32_t *v = T[t].v;
+        if (!core_real(v[0]) && !core_real(v[1]) && !core_real(v[2])) continue;
+        if (v[0] >= nl || v[1] >= nl || v[2] >= nl) {
+            // a real point on the hull of the triangulated points: the ghost
+            // band, or else the halo, is too narrow
+            if (whole) r.band_ok = false;
+            else r.halo_ok = false;
+            return;
+        }
+        const Disk D = circumdisk(LX.data(), LY.data(), v[0], v[1], v[2], pad);
+        if (!(D.ux - D.R >= band[0] && D.ux + D.R <= band[1] && D.uy - D.R >= band[2] && D.uy + D.R <= band[3])) {
+            r.band_ok = false;
+            return;
+        }
+        if (!(D.ux - D.R >= lo && D.ux + D.R <= hi)) {
+            r.halo_ok = false;
+            return;
+        }
+        tnum[t] = nt++;
+        for (int k = 0; k < 3; k++)
+            if (core_real(v[k])) vtri[v[k]] = (int32_t)t;
+    }
+    // triangles with global ids, rotated so that the smallest id comes first
+    // (a shared triangle then gives the same circumcentre in every slab)
+    r.tris.resize(3 * (size_t)nt);
+    for (size_t t = 0; t < T.size(); t++) {
+        if (tnum[t] < 0) continue;
+        int32_t g0 = loc[T[t].v[0]], g1 = loc[T[t].v[1]], g2 = loc[T[t].v[2]];
+        int rot = (g0 < g1 && g0 < g2) ? 0 : (g1 < g2 ? 1 : 2);
+        int32_t gg[3] = {g0, g1, g2};
+        for (int k = 0; k < 3; k++) r.tris[3 * (size_t)tnum[t] + k] = gg[(rot + k) % 3];
+    }
+    // rings, counter-clockwise, starting at the smallest neighbour id
+    std::vector<std::pair<int32_t, int32_t>> ring;
+    for (int32_t v = 0; v < nl; v++) {
+        if (!core_real(v)) continue;
+        if (vtri[v] < 0) {
+            r.rc = -3;
+            return;
+        }
+        ring.clear();
+        int32_t t = vtri[v], t0 = t;
+        int guard = 0;
+        do {
+            const Tri &tr = T[t];
+            int k = tr.v[0] == v ? 0 : (tr.v[1] == v ? 1 : 2);
+            ring.emplace_back(loc[tr.v[(k + 1) % 3]], tnum[t]);
+            t = tr.nb[(k + 1) % 3];
+            if (t < 0 || tnum[t] < 0 || ++guard > 4096) {
+                r.rc = -3;
+                return;
+            }
+        } while (t != t0);
+        size_t k0 = 0;
+        for (size_t k = 1; k < ring.size(); k++)
+            if (ring[k].first < ring[k0].first) k0 = k;
+        r.cells.push_back(loc[v]);
+        r.deg.push_back((int32_t)ring.size());
+        for (size_t k = 0; k < ring.size(); k++) {
+            r.nb.push_back(ring[(k0 + k) % ring.size()].first);
+            r.tri.push_back(ring[(k0 + k) % ring.size()].second);
+        }
+    }
+    // cells were visited in local order, which follows the global order
+}
+
+}  // namespace
+
+int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const double *y, MeshWork &work, HostMesh &m,
+                    ThreadPool *pool)
 {
     const double Lx = box.x1 - box.x0, Ly = box.y1 - box.y0;
     const double h = std::sqrt(Lx * Ly / std::max(n, 1));
     const double wmax = std::min(Lx, Ly);
+    const double pad = 1e-12 * (Lx + Ly);
     double w = std::min(5.0 * h, wmax);
-    std::vector<double> X, Y;
-    std::vector<int32_t> vtri, tmap;
     m.n = n;
     m.attempts = 0;
+    // slabs: enough points each that the halo stays a small fraction
+    const int threads = pool ? pool->size() : 1;
+    const int K = std::max(1, std::min(threads, n / 16384));
+    if ((int)work.dts.size() < K) work.dts.resize(K);
+    work.loc.resize(K);
+    work.lx.resize(K);
+    work.ly.resize(K);
+    std::vector<SlabResult> res(K);
+    std::vector<double> X, Y;
     for (;;) {
         m.attempts++;
         make_ghosts(box, n, x, y, w, m);
@@ -306,122 +470,176 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         std::memcpy(Y.data(), y, sizeof(double) * n);
         std::memcpy(X.data() + n, m.gx.data(), sizeof(double) * m.g);
         std::memcpy(Y.data() + n, m.gy.data(), sizeof(double) * m.g);
-        int rc = dt.build(X.data(), Y.data(), np);
-        if (rc) return rc;
-        const std::vector<Tri> &T = dt.tris;
-        // compact the triangles touching a real point and check the band
-        tmap.assign(T.size(), -1);
-        m.tri.clear();
-        bool ok = true;
-        const double lox = box.x0 - w, hix = box.x1 + w, loy = box.y0 - w, hiy = box.y1 + w;
-        for (size_t t = 0; t < T.size() && ok; t++) {
-            const int32_t *v = T[t].v;
-            if (v[0] >= n && v[1] >= n && v[2] >= n) continue;
-            if (v[0] >= np || v[1] >= np || v[2] >= np) { ok = false; break; }
-            double ax = X[v[0]], ay = Y[v[0]];
-            double bx = X[v[1]] - ax, by = Y[v[1]] - ay, cx = X[v[2]] - ax, cy = Y[v[2]] - ay;
-            double d = 2.0 * (bx * cy - by * cx);
-            double b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
-            double ux = (cy * b2 - by * c2) / d, uy = (bx * c2 - cx * b2) / d;
-            double R = std::sqrt(ux * ux + uy * uy) * (1.0 + 1e-9) + 1e-12 * (Lx + Ly);
-            ux += ax;
-            uy += ay;
-            if (!(ux - R >= lox && ux + R <= hix && uy - R >= loy && uy + R <= hiy)) { ok = false; break; }
-            tmap[t] = (int32_t)(m.tri.size() / 3);
-            m.tri.push_back(v[0]);
-            m.tri.push_back(v[1]);
-            m.tri.push_back(v[2]);
+        const double band[4] = {box.x0 - w, box.x1 + w, box.y0 - w, box.y1 + w};
+        double xmin = X[0], xmax = X[0];
+        for (int32_t q = 1; q < np; q++) {
+            xmin = std::min(xmin, X[q]);
+            xmax = std::max(xmax, X[q]);
         }
-        if (!ok) {
+        // slab cuts at x-quantiles of the real + ghost points
+        std::vector<double> cut(K + 1);
+        if (K > 1) {
+            std::vector<double> sx;
+            sx.reserve(np / 8 + 1);
+            for (int32_t q = 0; q < np; q += 8) sx.push_back(X[q]);
+            std::sort(sx.begin(), sx.end());
+            for (int s = 1; s < K; s++) cut[s] = sx[(size_t)s * sx.size() / K];
+        }
+        // halo: the width that sufficed last time (in mean spacings), else 6 h
+        std::vector<double> H(K, (work.halo > 0 ? work.halo : 6.0) * h);
+        std::vector<int> todo(K);
+        for (int s = 0; s < K; s++) todo[s] = s;
+        bool band_ok = true;
+        while (!todo.empty()) {
+            auto run = [&](int64_t k) {
+                const int s = todo[k];
+                build_slab(n, np, X.data(), Y.data(), xmin, xmax, cut[s], cut[s + 1], s == 0, s == K - 1, H[s], band,
+                           pad, work.dts[s], work.loc[s], work.lx[s], work.ly[s], res[s]);
+            };
+            if (pool && todo.size() > 1) pool->parallel_for((int64_t)todo.size(), run);
+            else
+                for (size_t k = 0; k < todo.size(); k++) run((int64_t)k);
+            std::vector<int> again;
+            for (int s : todo) {
+                if (res[s].rc) return res[s].rc;
+                if (!res[s].band_ok) band_ok = false;
+                else if (!res[s].halo_ok) {
+                    H[s] *= 1.5;
+                    again.push_back(s);
+                }
+            }
+            if (!band_ok) break;
+            todo.swap(again);
+        }
+        if (!band_ok) {
             if (w >= wmax) return -4;
             w = std::min(2.0 * w, wmax);
             continue;
         }
         m.band = w;
-        // one incident triangle per real point
-        vtri.assign(n, -1);
-        for (size_t t = 0; t < T.size(); t++) {
-            if (tmap[t] < 0) continue;
-            for (int k = 0; k < 3; k++)
-                if (T[t].v[k] < n) vtri[T[t].v[k]] = (int32_t)t;
+        work.halo = *std::max_element(H.begin(), H.end()) / h;
+        break;
+    }
+    // triangles: concatenation of the slabs' lists
+    std::vector<int64_t> toff(K + 1, 0);
+    for (int s = 0; s < K; s++) toff[s + 1] = toff[s] + (int64_t)res[s].tris.size() / 3;
+    m.tri.resize(3 * (size_t)toff[K]);
+    // ring offsets
+    m.cell_ptr.assign(n + 1, 0);
+    std::vector<int32_t> owner(n, -1);
+    for (int s = 0; s < K; s++)
+        for (size_t k = 0; k < res[s].cells.size(); k++) {
+            const int32_t i = res[s].cells[k];
+            if (owner[i] >= 0) return -3;
+            owner[i] = s;
+            m.cell_ptr[i + 1] = res[s].deg[k];
         }
-        // rings: rotate counter-clockwise about each real point
-        m.cell_ptr.assign(n + 1, 0);
-        m.slot_nb.clear();
-        m.slot_tri.clear();
-        for (int32_t i = 0; i < n; i++) {
-            m.cell_ptr[i] = (int32_t)m.slot_nb.size();
-            int32_t t0 = vtri[i];
-            if (t0 < 0) return -3;
-            int32_t t = t0;
-            int guard = 0;
-            do {
-                const Tri &tr = T[t];
-                int k = tr.v[0] == i ? 0 : (tr.v[1] == i ? 1 : 2);
-                m.slot_nb.push_back(tr.v[(k + 1) % 3]);
-                m.slot_tri.push_back(tmap[t]);
-                t = tr.nb[(k + 1) % 3];
-                if (t < 0 || tmap[t] < 0 || ++guard > 4096) return -3;
-            } while (t != t0);
-        }
-        m.cell_ptr[n] = (int32_t)m.slot_nb.size();
-        // edges, each physical edge once
-        const size_t S = m.slot_nb.size();
-        m.slot_edge.assign(S, -1);
-        m.edge_l.clear(); m.edge_r.clear(); m.edge_ta.clear(); m.edge_tb.clear();
-        for (int32_t i = 0; i < n; i++) {
-            const int32_t lo = m.cell_ptr[i], deg = m.cell_ptr[i + 1] - lo;
-            for (int32_t k = 0; k < deg; k++) {
-                const int32_t s = lo + k;
-                if (m.slot_edge[s] >= 0) continue;
-                const int32_t j = m.slot_nb[s];
-                int32_t partner_cell = -1, partner_nb = -1;
-                if (j < n) {
-                    if (j < i) return -3;  // should have been assigned from j's ring
-                    partner_cell = j;
-                    partner_nb = i;
-                } else {
-                    const int32_t gq = j - n;
-                    if (box.boundary == 1) {
-                        const int32_t src = m.ghost_src[gq];
-                        const int32_t sh = m.ghost_shift[gq];
-                        const int32_t sx = sh % 3 - 1, sy = sh / 3 - 1;
-                        if (src < i) return -3;
-                        if (src == i && (sy < 0 || (sy == 0 && sx < 0))) continue;  // created by the +shift slot
-                        partner_cell = src;
-                        partner_nb = -((-sx + 1) + 3 * (-sy + 1)) - 1;  // ghost of i with the opposite shift
-                    }
-                }
-                const int32_t e = (int32_t)m.edge_l.size();
-                m.edge_l.push_back(i);
-                m.edge_r.push_back(j);
-                m.edge_ta.push_back(m.slot_tri[lo + (k + deg - 1) % deg]);
-                m.edge_tb.push_back(m.slot_tri[s]);
-                m.slot_edge[s] = 2 * e;
-                if (partner_cell >= 0) {
-                    const int32_t plo = m.cell_ptr[partner_cell], phi = m.cell_ptr[partner_cell + 1];
-                    int32_t found = -1;
-                    for (int32_t q = plo; q < phi; q++) {
-                        const int32_t c = m.slot_nb[q];
-                        if (partner_nb >= 0) {
-                            if (c == partner_nb) { found = q; break; }
-                        } else if (c >= n) {
-                            const int32_t want = -partner_nb - 1;
-                            if (m.ghost_src[c - n] == i && m.ghost_shift[c - n] == want && q != s) {
-                                found = q;
-                                break;
-                            }
-                        }
-                    }
-                    if (found < 0 || m.slot_edge[found] >= 0) return -3;
-                    m.slot_edge[found] = 2 * e + 1;
-                }
+    for (int32_t i = 0; i < n; i++) {
+        if (owner[i] < 0) return -3;
+        m.cell_ptr[i + 1] += m.cell_ptr[i];
+    }
+    const size_t S = (size_t)m.cell_ptr[n];
+    m.slot_nb.resize(S);
+    m.slot_tri.resize(S);
+    auto fill = [&](int64_t s) {
+        const SlabResult &r = res[s];
+        std::copy(r.tris.begin(), r.tris.end(), m.tri.begin() + 3 * toff[s]);
+        size_t q = 0;
+        for (size_t k = 0; k < r.cells.size(); k++) {
+            const int32_t i = r.cells[k];
+            for (int32_t j = 0; j < r.deg[k]; j++, q++) {
+                m.slot_nb[m.cell_ptr[i] + j] = r.nb[q];
+                m.slot_tri[m.cell_ptr[i] + j] = (int32_t)(toff[s] + r.tri[q]);
             }
         }
-        for (size_t s = 0; s < S; s++)
-            if (m.slot_edge[s] < 0) return -3;
-        return 0;
+    };
+    if (pool && K > 1) pool->parallel_for(K, fill);
+    else
+        for (int s = 0; s < K; s++) fill(s);
+    // edges: each physical edge once, owned by its smaller real cell; a
+    // periodic edge between a cell and its own copy by the +shift slot
+    auto owns = [&](int32_t i, int32_t j) -> int {  // 1 own, 0 partner's, -1 inconsistent
+        if (j < n) return j > i ? 1 : (j < i ? 0 : -1);
+        if (box.boundary != 1) return 1;
+        const int32_t gq = j - n;
+        const int32_t src = m.ghost_src[gq];
+        if (src != i) return src > i ? 1 : 0;
+        const int32_t sh = m.ghost_shift[gq];
+        const int32_t sx = sh % 3 - 1, sy = sh / 3 - 1;
+        return (sy < 0 || (sy == 0 && sx < 0)) ? 0 : 1;
+    };
+    const int64_t chunk = 8192;
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    std::vector<int64_t> ecount(nchunks + 1, 0);
+    std::vector<int> bad(nchunks, 0);
+    auto count = [&](int64_t c) {
+        int64_t e = 0;
+        for (int32_t i = (int32_t)(c * chunk); i < std::min<int64_t>(n, (c + 1) * chunk); i++)
+            for (int32_t s = m.cell_ptr[i]; s < m.cell_ptr[i + 1]; s++) {
+                const int o = owns(i, m.slot_nb[s]);
+                if (o < 0) bad[c] = 1;
+                e += o > 0;
+            }
+        ecount[c + 1] = e;
+    };
+    if (pool) pool->parallel_for(nchunks, count);
+    else
+        for (int64_t c = 0; c < nchunks; c++) count(c);
+    for (int64_t c = 0; c < nchunks; c++) {
+        if (bad[c]) return -3;
+        ecount[c + 1] += ecount[c];
     }
+    const size_t E = (size_t)ecount[nchunks];
+    m.slot_edge.assign(S, -1);
+    m.edge_l.resize(E);
+    m.edge_r.resize(E);
+    m.edge_ta.resize(E);
+    m.edge_tb.resize(E);
+    auto place = [&](int64_t c) {
+        int64_t e = ecount[c];
+        for (int32_t i = (int32_t)(c * chunk); i < std::min<int64_t>(n, (c + 1) * chunk); i++) {
+            const int32_t lo = m.cell_ptr[i], deg = m.cell_ptr[i + 1] - lo;
+            for (int32_t k = 0; k < deg; k++) {
+                const int32_t s = lo + k, j = m.slot_nb[s];
+                if (owns(i, j) <= 0) continue;
+                m.edge_l[e] = i;
+                m.edge_r[e] = j;
+                m.edge_ta[e] = m.slot_tri[lo + (k + deg - 1) % deg];
+                m.edge_tb[e] = m.slot_tri[s];
+                m.slot_edge[s] = (int32_t)(2 * e);
+                // the same edge seen from the other cell's ring
+                int32_t pc = -1;
+                if (j < n) pc = j;
+                else if (box.boundary == 1) pc = m.ghost_src[j - n];
+                if (pc >= 0) {
+                    int32_t want_shift = -1;
+                    if (j >= n) {
+                        const int32_t sh = m.ghost_shift[j - n];
+                        want_shift = (-(sh % 3 - 1) + 1) + 3 * (-(sh / 3 - 1) + 1);
+                    }
+                    for (int32_t q = m.cell_ptr[pc]; q < m.cell_ptr[pc + 1]; q++) {
+                        const int32_t c2 = m.slot_nb[q];
+                        const bool hit = j < n ? c2 == i
+                                               : (c2 >= n && m.ghost_src[c2 - n] == i && m.ghost_shift[c2 - n] == want_shift &&
+                                                  q != s);
+                        if (hit) {
+                            m.slot_edge[q] = (int32_t)(2 * e + 1);
+                            break;
+                        }
+                    }
+                }
+                e++;
+            }
+        }
+    };
+    if (pool) pool->parallel_for(nchunks, place);
+    else
+        for (int64_t c = 0; c < nchunks; c++) place(c);
+    for (size_t s = 0; s < S; s++)
+        if (m.slot_edge[s] < 0) return -3;
+    m.cell_order.resize(n);
+    degree_order(n, m.cell_ptr.data(), m.cell_order.data());
+    return 0;
 }
 
 }  // namespace rich

@@ -11,7 +11,8 @@
 //      circumdisk inside the band, so that every real cell's neighbourhood
 //      equals that of the infinite mirrored / periodic point set; otherwise w
 //      doubles and the construction repeats;
-//   4. per real cell, its neighbours in counter-clockwise order; per ring slot
+//   4. per real cell, its neighbours in counter-clockwise order starting at
+//      the smallest neighbour id; per ring slot
 //      the triangle (i, nb[k], nb[k+1]) whose circumcentre is the Voronoi
 //      vertex after that slot; and a list of Voronoi edges in which every
 //      physical edge appears once (periodic copies of one edge are merged).
@@ -47,6 +48,7 @@ struct HostMesh {
     std::vector<int32_t> slot_edge;     // 2*edge + (1 if the cell is the edge's right side)
     std::vector<int32_t> edge_l, edge_r;   // left (real) and right (real or ghost) points
     std::vector<int32_t> edge_ta, edge_tb; // Voronoi edge runs from cc[ta] to cc[tb], ccw about left
+    std::vector<int32_t> cell_order;    // processing order of the per-cell kernels (see degree_order)
     double band = 0.0;
     int attempts = 0;
 };
@@ -80,11 +82,36 @@ private:
     uint32_t rng_ = 12345u;
 };
 
-// Build the whole host mesh for n real points (x, y).  Returns 0, -2 for
-// coincident points, -3 for a failed triangulation, -4 when the box holds too
-// few points for the band check to succeed.
-int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const double *y, Delaunay &dt,
-                    HostMesh &out);
+// Reusable buffers of build_host_mesh (one triangulator per slab).
+struct MeshWork {
+    std::vector<Delaunay> dts;
+    std::vector<std::vector<int32_t>> loc;
+    std::vector<std::vector<double>> lx, ly;
+    double halo = 0.0;  // slab halo of the last build, in mean point spacings
+};
+
+class ThreadPool;
+
+// Build the whole host mesh for n real points (x, y).  With a pool the real
+// + ghost points are cut into vertical slabs at x-quantiles (one per thread,
+// at least 16384 real points each); each slab is triangulated with a halo
+// that doubles until every circumdisk of its real points' stars lies inside
+// it, so the stars equal those of the whole set, and the rings and the edge
+// list are filled in parallel.  Rings start at their smallest neighbour id
+// and triangles at their smallest vertex id, so the mesh seen by the sweep
+// does not depend on the number of slabs (only triangle and edge numbering
+// do).  Returns 0, -2 for coincident points, -3 for a failed triangulation,
+// -4 when the box holds too few points for the band check to succeed.
+int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const double *y, MeshWork &work,
+                    HostMesh &out, ThreadPool *pool = nullptr);
+
+// Processing order for the per-cell device loops over ring slots: within
+// each window of kOrderWindow consecutive cells, cells by decreasing ring
+// degree (stable), so that the 32 cells of a warp have nearly equal degrees
+// and the warp's loop runs close to their mean length rather than to the
+// largest degree among 32 random ones.  Windows keep Hilbert locality.
+constexpr int32_t kOrderWindow = 1024;
+void degree_order(int32_t n, const int32_t *cell_ptr, int32_t *order);
 
 // Order of points along a Hilbert curve over their bounding box.
 void hilbert_order(int32_t n, const double *x, const double *y, std::vector<int32_t> &order);

@@ -6,8 +6,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -16,6 +18,7 @@
 #include "api_internal.h"
 #include "mesh.h"
 #include "sweep.cuh"
+#include "threadpool.h"
 
 namespace rich {
 namespace {
@@ -75,8 +78,9 @@ struct rich_sim {
     int32_t n = 0;
     std::vector<int32_t> perm;  // internal -> caller index
     std::vector<double> hx, hy; // host copy of the points (internal order)
-    rich::Delaunay dt;
+    rich::MeshWork mw;
     rich::HostMesh hm;
+    std::unique_ptr<rich::ThreadPool> pool;  // host threads of the slab-parallel tessellation
     double t = 0.0;
     int cur = 0;
     // time-centred scheme: 1 between its two sweeps (buffers [2] then hold
@@ -95,7 +99,7 @@ struct rich_sim {
     double last_dt = 0.0;
     // device buffers
     DBuf x[3], y[3], U[3];
-    DBuf A, o, W, cs, g, gl, alpha, w, tess, cell_ptr, initW, rounding, p64;
+    DBuf A, o, W, cs, g, gl, alpha, w, tess, cell_ptr, corder, initW, rounding, p64, psrc;
     bool diagnostics = true;
     DBuf gx, gy, gsrc, gxf;
     DBuf tri, ccx, ccy;
@@ -134,7 +138,7 @@ struct rich_sim {
         p.xn = x[dst].as<double>(); p.yn = y[dst].as<double>();
         p.x0 = x[cur].as<double>(); p.y0 = y[cur].as<double>();
         p.gx = gx.as<double>(); p.gy = gy.as<double>();
-        p.tri = tri.as<int32_t>(); p.cell_ptr = cell_ptr.as<int32_t>();
+        p.tri = tri.as<int32_t>(); p.cell_ptr = cell_ptr.as<int32_t>(); p.cell_order = corder.as<int32_t>();
         p.slot_nb = slot_nb.as<int32_t>(); p.slot_tri = slot_tri.as<int32_t>(); p.slot_edge = slot_edge.as<int32_t>();
         p.edge_l = edge_l.as<int32_t>(); p.edge_r = edge_r.as<int32_t>();
         p.edge_ta = edge_ta.as<int32_t>(); p.edge_tb = edge_tb.as<int32_t>();
@@ -149,7 +153,7 @@ struct rich_sim {
         p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
         p.w = w.as<rich::Vec2<R>>();
         p.rounding = rounding.as<uint8_t>(); p.p64 = p64.as<double>();
-        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<R>>();
+        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<R>>(); p.psrc = psrc.as<rich::Vec4<R>>();
         char *sc = scal.as<char>();
         p.dtmin_bits = reinterpret_cast<unsigned long long *>(sc);
         p.dt_out = reinterpret_cast<double *>(sc + 8);
@@ -208,7 +212,7 @@ int alloc_cells(rich_sim *s)
     CUDA_TRY(s->A.ensure(n * d)); CUDA_TRY(s->o.ensure(2 * n * r));
     CUDA_TRY(s->W.ensure(4 * n * r)); CUDA_TRY(s->cs.ensure(n * r));
     CUDA_TRY(s->g.ensure(8 * n * r)); CUDA_TRY(s->gl.ensure(8 * n * r)); CUDA_TRY(s->alpha.ensure(4 * n * r));
-    CUDA_TRY(s->w.ensure(2 * n * r)); CUDA_TRY(s->tess.ensure(n * 4));
+    CUDA_TRY(s->w.ensure(2 * n * r)); CUDA_TRY(s->tess.ensure(n * 4)); CUDA_TRY(s->psrc.ensure(4 * n * r));
     CUDA_TRY(s->rounding.ensure(n)); CUDA_TRY(s->p64.ensure(n * d));
     CUDA_TRY(s->scal.ensure(64));
     CUDA_TRY(cudaMemsetAsync(s->scal.p, 0, 64, s->stream));
@@ -228,7 +232,7 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     }
     double t1 = now_ms();
     rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
-    int rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->dt, s->hm);
+    int rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm, s->pool.get());
     if (rc) return mesh_rc(rc);
     double t2 = now_ms();
     const rich::HostMesh &m = s->hm;
@@ -239,6 +243,7 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     CUDA_TRY(upload(s->gxf, m.ghost_xf, s->stream));
     CUDA_TRY(upload(s->tri, m.tri, s->stream));
     CUDA_TRY(upload(s->cell_ptr, m.cell_ptr, s->stream));
+    CUDA_TRY(upload(s->corder, m.cell_order, s->stream));
     CUDA_TRY(upload(s->slot_nb, m.slot_nb, s->stream));
     CUDA_TRY(upload(s->slot_tri, m.slot_tri, s->stream));
     CUDA_TRY(upload(s->slot_edge, m.slot_edge, s->stream));
@@ -330,6 +335,11 @@ int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const dou
     if (!s) return fail(RICH_ENOMEM, "host allocation");
     s->cfg = *cfg;
     s->n = (int32_t)n;
+    s->pool.reset(new (std::nothrow) rich::ThreadPool((int)std::max(1u, std::thread::hardware_concurrency())));
+    if (!s->pool) {
+        delete s;
+        return fail(RICH_ENOMEM, "host thread pool");
+    }
     // renumber cells along a Hilbert curve for locality
     rich::hilbert_order(s->n, x, y, s->perm);
     s->hx.resize(n);
@@ -671,10 +681,11 @@ int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const do
     if (!valid_config(cfg) || n < 3 || !x || !y || !nslots || !ptr) return fail(RICH_EINVAL, "bad arguments");
     for (int64_t i = 0; i < n; i++)
         if (!point_inside(cfg, x[i], y[i])) return fail(RICH_EINVAL, "point outside the box");
-    rich::Delaunay dt;
+    rich::MeshWork mw;
     rich::HostMesh m;
     rich::BoxConfig box{cfg->boundary, cfg->x0, cfg->x1, cfg->y0, cfg->y1};
-    int rc = rich::build_host_mesh(box, (int32_t)n, x, y, dt, m);
+    rich::ThreadPool pool((int)std::max(1u, std::thread::hardware_concurrency()));
+    int rc = rich::build_host_mesh(box, (int32_t)n, x, y, mw, m, &pool);
     if (rc) return mesh_rc(rc);
     *nslots = (int64_t)m.slot_nb.size();
     for (int64_t i = 0; i <= n; i++) ptr[i] = m.cell_ptr[i];

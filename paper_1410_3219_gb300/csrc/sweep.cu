@@ -35,6 +35,12 @@ template <class R> __device__ __forceinline__ int32_t inst_of(const SweepParams<
 }
 
 // real cell behind point q and its mirror flags
+// cell handled by thread k of a per-cell stage
+template <class R> __device__ __forceinline__ int32_t cell_at(const SweepParams<R> &p, int32_t k)
+{
+    return p.cell_order ? __ldg(p.cell_order + k) : k;
+}
+
 template <class R> __device__ __forceinline__ int32_t src_of(const SweepParams<R> &p, int32_t q, int32_t &xf)
 {
     if (q < p.n) { xf = 0; return q; }
@@ -223,8 +229,8 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
 
 template <class R> __global__ void k_cell_geometry(SweepParams<R> p, const double *__restrict__ init_W)
 {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < p.n) stage_cell_geometry(p, init_W, i);
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < p.n) stage_cell_geometry(p, init_W, cell_at(p, k));
 }
 
 // Smallest non-negative cell time step of each simulation: a warp whose
@@ -382,8 +388,18 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
                 alpha[v] = a;
             }
         }
-        p.gl[2 * i] = Vec4<R>{alpha[0] * g[0], alpha[0] * g[1], alpha[1] * g[2], alpha[1] * g[3]};
-        p.gl[2 * i + 1] = Vec4<R>{alpha[2] * g[4], alpha[2] * g[5], alpha[3] * g[6], alpha[3] * g[7]};
+        R lg[8];
+#pragma unroll
+        for (int c = 0; c < 8; c++) lg[c] = alpha[c >> 1] * g[c];
+        p.gl[2 * i] = Vec4<R>{lg[0], lg[1], lg[2], lg[3]};
+        p.gl[2 * i + 1] = Vec4<R>{lg[4], lg[5], lg[6], lg[7]};
+        {
+            // cell-only terms of the half-step prediction (used by every edge
+            // of the cell): rho div v, grad p / rho, gamma p div v
+            const R ldiv = lg[2] + lg[5];
+            const R irho = R(1) / Wi[0];
+            p.psrc[i] = Vec4<R>{Wi[0] * ldiv, lg[6] * irho, lg[7] * irho, (R)ip.gamma * Wi[3] * ldiv};
+        }
         if (p.diagnostics) {
             p.g[2 * i] = Vec4<R>{g[0], g[1], g[2], g[3]};
             p.g[2 * i + 1] = Vec4<R>{g[4], g[5], g[6], g[7]};
@@ -411,10 +427,10 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
 
 template <class R> __global__ void __launch_bounds__(kBlock) k_cell_gradient(SweepParams<R> p)
 {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     double dt_cell = DBL_MAX;
     int32_t my_inst = 0;
-    if (i < p.n) dt_cell = stage_cell_gradient(p, i, my_inst);
+    if (k < p.n) dt_cell = stage_cell_gradient(p, cell_at(p, k), my_inst);
     warp_min_to(dt_cell, my_inst, p.dtmin_bits);
 }
 
@@ -430,18 +446,18 @@ template <class R> __device__ __forceinline__ double step_dt(const SweepParams<R
     return dt > ip.remaining ? ip.remaining : dt;
 }
 
-// half-step prediction of one side's edge state in the frame moving with wf
+// half-step prediction of one side's edge state in the frame moving with wf:
+// Eq. 2 extrapolation minus hdt times the primitive Euler right-hand side,
+// whose cell-only terms (rho div v, grad p / rho, gamma p div v) come in src
 template <class R>
-__device__ __forceinline__ void predict(R gam, R hdt, const R W[4], const R g[8], R offx, R offy, R wfx, R wfy,
-                                        R out[4])
+__device__ __forceinline__ void predict(R hdt, const R W[4], const R g[8], const R src[4], R offx, R offy, R wfx,
+                                        R wfy, R out[4])
 {
     R ux = W[1] - wfx, uy = W[2] - wfy;
-    R div = g[2] + g[5];
-    R irho = R(1) / W[0];
-    out[0] = W[0] + g[0] * offx + g[1] * offy - hdt * (ux * g[0] + uy * g[1] + W[0] * div);
-    out[1] = W[1] + g[2] * offx + g[3] * offy - hdt * (ux * g[2] + uy * g[3] + g[6] * irho);
-    out[2] = W[2] + g[4] * offx + g[5] * offy - hdt * (ux * g[4] + uy * g[5] + g[7] * irho);
-    out[3] = W[3] + g[6] * offx + g[7] * offy - hdt * (ux * g[6] + uy * g[7] + gam * W[3] * div);
+    out[0] = W[0] + g[0] * offx + g[1] * offy - hdt * (ux * g[0] + uy * g[1] + src[0]);
+    out[1] = W[1] + g[2] * offx + g[3] * offy - hdt * (ux * g[2] + uy * g[3] + src[1]);
+    out[2] = W[2] + g[4] * offx + g[5] * offy - hdt * (ux * g[4] + uy * g[5] + src[2]);
+    out[3] = W[3] + g[6] * offx + g[7] * offy - hdt * (ux * g[6] + uy * g[7] + src[3]);
 }
 
 // HLLC (Toro) in the edge frame, states (rho, u_n, u_t, p)
@@ -454,34 +470,32 @@ template <class R> __device__ __forceinline__ void hllc(R gam, R igm1, const R L
     const R ER = pR * igm1 + R(0.5) * rR * (uR * uR + tR * tR);
     const R SL = fmin(uL - cL, uR - cR);
     const R SR = fmax(uL + cL, uR + cR);
-    if (SL >= R(0)) {
-        F[0] = rL * uL; F[1] = rL * uL * uL + pL; F[2] = rL * uL * tL; F[3] = uL * (EL + pL);
-        return;
-    }
-    if (SR <= R(0)) {
-        F[0] = rR * uR; F[1] = rR * uR * uR + pR; F[2] = rR * uR * tR; F[3] = uR * (ER + pR);
-        return;
-    }
+    // The flux is that of one side K plus, between the outer waves,
+    // S_K (U*_K - U_K).  K is picked by selects rather than branches, so a
+    // warp whose edges take different sides evaluates one star state, not two.
+    const bool supL = SL >= R(0), supR = !supL && SR <= R(0);
+    const bool sub = !(supL || supR);
     const R mL = rL * (SL - uL), mR = rR * (SR - uR);
-    const R Ss = (pR - pL + uL * mL - uR * mR) / (mL - mR);
-    // star states share one reciprocal: rho* = m_K/(S_K - S*) and
-    // E* = ((S_K - u_K) E_K + (S* - u_K)(m_K S* + p_K))/(S_K - S*)
-    if (Ss >= R(0)) {
-        const R inv = R(1) / (SL - Ss);
-        const R f = mL * inv;
-        const R Es = ((SL - uL) * EL + (Ss - uL) * (mL * Ss + pL)) * inv;
-        F[0] = rL * uL + SL * (f - rL);
-        F[1] = rL * uL * uL + pL + SL * (f * Ss - rL * uL);
-        F[2] = rL * uL * tL + SL * (f * tL - rL * tL);
-        F[3] = uL * (EL + pL) + SL * (Es - EL);
-    } else {
-        const R inv = R(1) / (SR - Ss);
-        const R f = mR * inv;
-        const R Es = ((SR - uR) * ER + (Ss - uR) * (mR * Ss + pR)) * inv;
-        F[0] = rR * uR + SR * (f - rR);
-        F[1] = rR * uR * uR + pR + SR * (f * Ss - rR * uR);
-        F[2] = rR * uR * tR + SR * (f * tR - rR * tR);
-        F[3] = uR * (ER + pR) + SR * (Es - ER);
+    R Ss = R(0);
+    if (sub) Ss = (pR - pL + uL * mL - uR * mR) / (mL - mR);
+    const bool useL = supL || (sub && Ss >= R(0));
+    const R rK = useL ? rL : rR, uK = useL ? uL : uR, tK = useL ? tL : tR, pK = useL ? pL : pR;
+    const R EK = useL ? EL : ER;
+    const R ruK = rK * uK;
+    F[0] = ruK;
+    F[1] = ruK * uK + pK;
+    F[2] = ruK * tK;
+    F[3] = uK * (EK + pK);
+    if (sub) {
+        // star state: rho* = m_K/(S_K - S*), E* = ((S_K - u_K) E_K + (S* - u_K)(m_K S* + p_K))/(S_K - S*)
+        const R SK = useL ? SL : SR, mK = useL ? mL : mR;
+        const R inv = R(1) / (SK - Ss);
+        const R f = mK * inv;
+        const R Es = ((SK - uK) * EK + (Ss - uK) * (mK * Ss + pK)) * inv;
+        F[0] += SK * (f - rK);
+        F[1] += SK * (f * Ss - ruK);
+        F[2] += SK * (f * tK - rK * tK);
+        F[3] += SK * (Es - EK);
     }
 }
 
@@ -519,8 +533,11 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
     const R wfy = R(0.5) * (wly + wry) - dwc * ny;
     R Sl[4], Sr[4];
     const R gam = (R)p.inst[li].gamma;
-    predict(gam, hdt, Wl, gL, p.emlx[e] - ol.x, p.emly[e] - ol.y, wfx, wfy, Sl);
-    predict(gam, hdt, Wr, gR, p.emrx[e] - orx, p.emry[e] - ory, wfx, wfy, Sr);
+    const Vec4<R> sl4 = p.psrc[l], sr4 = p.psrc[k];
+    // a mirrored source flips the pressure-gradient term of its axis
+    const R srcL[4] = {sl4.x, sl4.y, sl4.z, sl4.w}, srcR[4] = {sr4.x, sx * sr4.y, sy * sr4.z, sr4.w};
+    predict(hdt, Wl, gL, srcL, p.emlx[e] - ol.x, p.emly[e] - ol.y, wfx, wfy, Sl);
+    predict(hdt, Wr, gR, srcR, p.emrx[e] - orx, p.emry[e] - ory, wfx, wfy, Sr);
     const R tx = -ny, ty = nx;
     R WL[4] = {Sl[0], (Sl[1] - wfx) * nx + (Sl[2] - wfy) * ny, (Sl[1] - wfx) * tx + (Sl[2] - wfy) * ty, Sl[3]};
     R WR[4] = {Sr[0], (Sr[1] - wfx) * nx + (Sr[2] - wfy) * ny, (Sr[1] - wfx) * tx + (Sr[2] - wfy) * ty, Sr[3]};
@@ -561,8 +578,14 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
     for (int32_t s = lo; s < hi; s++) {
         int32_t es = p.slot_edge[s];
         const Vec4<R> f = p.F[es >> 1];
-        if (es & 1) { s0 -= (double)f.x; s1 -= (double)f.y; s2 -= (double)f.z; s3 -= (double)f.w; }
-        else { s0 += (double)f.x; s1 += (double)f.y; s2 += (double)f.z; s3 += (double)f.w; }
+        // the right cell takes the flux with the opposite sign: flip the sign
+        // bit (integer pipe) rather than branch, so each slot costs one add
+        // per component whatever the mix of sides in the warp
+        const unsigned long long sg = (unsigned long long)(es & 1) << 63;
+        s0 += __longlong_as_double(__double_as_longlong((double)f.x) ^ sg);
+        s1 += __longlong_as_double(__double_as_longlong((double)f.y) ^ sg);
+        s2 += __longlong_as_double(__double_as_longlong((double)f.z) ^ sg);
+        s3 += __longlong_as_double(__double_as_longlong((double)f.w) ^ sg);
     }
     double m = p.U0[i] - hdt * s0;
     double Px = p.U0[n + i] - hdt * s1;
@@ -598,8 +621,8 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
 
 template <class R> __global__ void __launch_bounds__(kBlock) k_cell_update(SweepParams<R> p)
 {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < p.n) stage_cell_update(p, i);
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < p.n) stage_cell_update(p, cell_at(p, k));
 }
 
 // ---------------------------------------------------------------------------
@@ -654,19 +677,19 @@ __global__ void __launch_bounds__(512) k_sweep_persistent(SweepParams<R> p, cons
     for (int32_t t = tid; t < p.T; t += stride) stage_circumcentre(p, t);
     if (!grid_sync(gs, nb)) return;
     for (int32_t e = tid; e < p.E; e += stride) stage_edge_geometry(p, e);
-    for (int32_t i = tid; i < p.n; i += stride) stage_cell_geometry(p, (const double *)nullptr, i);
+    for (int32_t k = tid; k < p.n; k += stride) stage_cell_geometry(p, (const double *)nullptr, cell_at(p, k));
     if (!grid_sync(gs, nb)) return;
     for (int32_t base = blockIdx.x * blockDim.x; base < p.n; base += stride) {
-        const int32_t i = base + threadIdx.x;
+        const int32_t k = base + threadIdx.x;
         double v = DBL_MAX;
         int32_t inst = 0;
-        if (i < p.n) v = stage_cell_gradient(p, i, inst);
+        if (k < p.n) v = stage_cell_gradient(p, cell_at(p, k), inst);
         warp_min_to(v, inst, p.dtmin_bits);
     }
     if (!grid_sync(gs, nb)) return;
     for (int32_t e = tid; e < p.E; e += stride) stage_edge_flux(p, e);
     if (!grid_sync(gs, nb)) return;
-    for (int32_t i = tid; i < p.n; i += stride) stage_cell_update(p, i);
+    for (int32_t k = tid; k < p.n; k += stride) stage_cell_update(p, cell_at(p, k));
 }
 
 __global__ void k_repack(const int32_t *__restrict__ src, int32_t n_new, int32_t n_old,

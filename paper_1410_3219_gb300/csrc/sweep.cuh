@@ -20,9 +20,11 @@
 //              ePM[E] = {P, M}: Eq. 1 as a sum over neighbours reads
 //              g_i = (sum_j phi_j P_ij + phi_i sum_j M_ij)/A_i with
 //              P = L(q + n/2), M = L(n/2 - q) (right cells use -M, -P)
+//   order      cell_order[n]: per-cell kernels visit cells in this order
 //   cell (R)   W[n] = {rho, vx, vy, p}; o[n] = centre of mass - generator;
 //              cs[n]; gl[2n] limited gradient {drho/dx, drho/dy, dvx/dx,
 //              dvx/dy}, {dvy/dx, dvy/dy, dp/dx, dp/dy}; w[n] mesh velocity;
+//              psrc[n] cell terms of the half-step prediction;
 //              diagnostics g[2n] (unlimited), alpha[n], tess[n];
 //              rounding[n] (uint8) and, in split precision, p64[n] (FP64):
 //              the two discontinuous decisions of the step (rounding trigger,
@@ -78,6 +80,9 @@ template <class R> struct SweepParams {
     const double *gx, *gy;
     // mesh
     const int32_t *tri, *cell_ptr, *slot_nb, *slot_tri, *slot_edge;
+    // processing order of the per-cell stages: thread k handles cell
+    // cell_order[k] (cells of equal ring degree side by side in a warp)
+    const int32_t *cell_order;
     const int32_t *edge_l, *edge_r, *edge_ta, *edge_tb;
     const int32_t *ghost_src, *ghost_xf;
     // geometry
@@ -96,6 +101,9 @@ template <class R> struct SweepParams {
     uint8_t *rounding;  // 1 where the Section 6 rounding velocity is on (decided in FP64)
     double *p64;        // FP64 pressure for the shock switch (split precision only)
     Vec4<R> *gl, *g, *alpha;
+    // per cell, from the limited gradient: the cell-only terms of the
+    // half-step prediction {rho div v, (dp/dx)/rho, (dp/dy)/rho, gamma p div v}
+    Vec4<R> *psrc;
     Vec2<R> *w;
     int32_t *tess;
     Vec4<R> *F;

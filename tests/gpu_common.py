@@ -30,3 +30,17 @@ def compare_conserved(gpu, ref, cfg, tol=TOL):
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, (bad, errs)
     return errs
+
+
+def grad_scale(ref, c):
+    """Scale of gradient component c (d/dx, d/dy of rho, vx, vy, p) for the
+    parity tolerance.  Eq. 1 sums terms phi_j L_ij / A_i of size |phi| / h,
+    so its round-off, and any round-off already in the field values (on a
+    moved mesh the densities carry the Section 5 area mismatch, whose
+    rounding follows the conditioning of the Voronoi vertices), scales with
+    max |phi| / h rather than with the gradient itself; h is the smallest
+    cell size sqrt(min A)."""
+    import numpy as np
+    phi = ref.field(["rho", "vx", "vy", "p"][c // 2])
+    h = float(np.sqrt(np.min(ref.field("area"))))
+    return max(float(np.max(np.abs(ref.field("grad", c)))), float(np.max(np.abs(phi))) / h)
