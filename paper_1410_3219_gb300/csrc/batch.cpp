@@ -177,7 +177,7 @@ struct rich_batch {
         p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
         p.w = w.as<rich::Vec2<R>>();
         p.rounding = rounding.as<uint8_t>(); p.p64 = p64.as<double>();
-        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<R>>(); p.psrc = psrc.as<rich::Vec4<R>>();
+        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<double>>(); p.psrc = psrc.as<rich::Vec4<R>>();
         p.dtmin_bits = dtmin.as<unsigned long long>();
         p.dt_out = dtout.as<double>();
         p.status = status.as<int32_t>();
@@ -282,7 +282,7 @@ int ensure_device(rich_batch *b)
     CUDA_TRY(b->ccx.ensure(T * d + 8)); CUDA_TRY(b->ccy.ensure(T * d + 8));
     for (DBuf *e : {&b->eL, &b->emlx, &b->emly, &b->emrx, &b->emry, &b->enx, &b->eny, &b->eqx, &b->eqy})
         CUDA_TRY(e->ensure(E * r + 8));
-    CUDA_TRY(b->F.ensure(4 * E * r + 32));
+    CUDA_TRY(b->F.ensure(4 * E * sizeof(double) + 32));
     CUDA_TRY(b->ePM.ensure(4 * E * r + 32));
     CUDA_TRY(b->instp.ensure(K * sizeof(rich::InstParams) + 8));
     CUDA_TRY(b->dtmin.ensure(K * 8 + 8)); CUDA_TRY(b->dtout.ensure(K * 8 + 8)); CUDA_TRY(b->status.ensure(K * 4 + 8));

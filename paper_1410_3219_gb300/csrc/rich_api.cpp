@@ -153,7 +153,7 @@ struct rich_sim {
         p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
         p.w = w.as<rich::Vec2<R>>();
         p.rounding = rounding.as<uint8_t>(); p.p64 = p64.as<double>();
-        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<R>>(); p.psrc = psrc.as<rich::Vec4<R>>();
+        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<double>>(); p.psrc = psrc.as<rich::Vec4<R>>();
         char *sc = scal.as<char>();
         p.dtmin_bits = reinterpret_cast<unsigned long long *>(sc);
         p.dt_out = reinterpret_cast<double *>(sc + 8);
@@ -255,7 +255,7 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     CUDA_TRY(s->ccx.ensure((T + 1) * d)); CUDA_TRY(s->ccy.ensure((T + 1) * d));
     for (DBuf *b : {&s->eL, &s->emlx, &s->emly, &s->emrx, &s->emry, &s->enx, &s->eny, &s->eqx, &s->eqy})
         CUDA_TRY(b->ensure((E + 1) * r));
-    CUDA_TRY(s->F.ensure((4 * E + 4) * r));
+    CUDA_TRY(s->F.ensure((4 * E + 4) * sizeof(double)));
     CUDA_TRY(s->ePM.ensure((4 * E + 4) * r));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     double t3 = now_ms();

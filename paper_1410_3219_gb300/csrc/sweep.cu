@@ -85,6 +85,9 @@ template <> struct Extremes<double> {
     }
     __device__ __forceinline__ double max() const { return dunkey(hi); }
     __device__ __forceinline__ double min() const { return dunkey(lo); }
+    // max() > 0 and min() < 0 on the keys (the key of -0.0 is -1)
+    __device__ __forceinline__ bool max_positive() const { return hi > 0; }
+    __device__ __forceinline__ bool min_negative() const { return lo < -1; }
 };
 template <> struct Extremes<float> {
     float hi, lo;
@@ -96,6 +99,8 @@ template <> struct Extremes<float> {
     }
     __device__ __forceinline__ float max() const { return hi; }
     __device__ __forceinline__ float min() const { return lo; }
+    __device__ __forceinline__ bool max_positive() const { return hi > 0.0f; }
+    __device__ __forceinline__ bool min_negative() const { return lo < 0.0f; }
 };
 
 // a < b for non-negative values (bit patterns of non-negative doubles order
@@ -138,7 +143,9 @@ template <class R> __device__ __forceinline__ void stage_edge_geometry(const Swe
     R ex = (R)(bx64 - ax64), ey = (R)(by64 - ay64);
     R L = sqrt(ex * ex + ey * ey);
     R mx = R(0.5) * (ax + bx), my = R(0.5) * (ay + by);
-    R rinv = R(1) / sqrt(dx * dx + dy * dy);
+    // 1/|r_ij| with one reciprocal square root (a divide and a square root
+    // each cost several FP64 issue slots on this part)
+    R rinv = rsqrt(dx * dx + dy * dy);
     p.eL[e] = L;
     p.emlx[e] = mx;
     p.emly[e] = my;
@@ -287,7 +294,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
                 acc[2 * v] += Wj[v] * Ax;
                 acc[2 * v + 1] += Wj[v] * Ay;
             }
-            if (L > Lmin) {
+            if (nonneg_less(Lmin, L)) {
 #pragma unroll
                 for (int v = 0; v < 4; v++) ext[v].add(Wj[v]);
                 double pj64;
@@ -337,7 +344,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             for (int32_t s = lo; s < hi; s++) {
                 int32_t es = p.slot_edge[s];
                 int32_t e = es >> 1;
-                if (!(p.eL[e] > Lmin)) continue;
+                if (!nonneg_less(Lmin, p.eL[e])) continue;
                 R offx = ((es & 1) ? p.emrx[e] : p.emlx[e]) - ox;
                 R offy = ((es & 1) ? p.emry[e] : p.emly[e]) - oy;
 #pragma unroll
@@ -347,15 +354,16 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             for (int v = 0; v < 4; v++) {
                 // alpha = min(1, (phi_max - phi_i)/dphi_max, (phi_i - phi_min)/|dphi_min|):
                 // a ratio needs dividing only when its numerator is the smaller
+                // the smaller of the two ratios below one is chosen by
+                // cross-multiplication (all terms non-negative) and divided once
                 R a = R(1);
-                const R dpos = dex[v].max(), dneg = dex[v].min();
-                if (dpos > R(0)) {
-                    const R num = fmx[v] - Wi[v];
-                    if (nonneg_less(num, dpos)) a = num / dpos;
-                }
-                if (dneg < R(0)) {
-                    const R num = Wi[v] - fmn[v], den = -dneg;
-                    if (nonneg_less(num, den)) a = fmin(a, num / den);
+                const R n1 = fmx[v] - Wi[v], d1 = dex[v].max();
+                const R n2 = Wi[v] - fmn[v], d2 = -dex[v].min();
+                const bool c1 = dex[v].max_positive() && nonneg_less(n1, d1);
+                const bool c2 = dex[v].min_negative() && nonneg_less(n2, d2);
+                if (c1 || c2) {
+                    const bool use1 = c1 && (!c2 || nonneg_less(n1 * d2, n2 * d1));
+                    a = (use1 ? n1 : n2) / (use1 ? d1 : d2);
                 }
                 alpha[v] = a;
             }
@@ -365,7 +373,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             for (int32_t s = lo; s < hi; s++) {
                 int32_t es = p.slot_edge[s];
                 int32_t e = es >> 1;
-                if (!(p.eL[e] > Lmin)) continue;
+                if (!nonneg_less(Lmin, p.eL[e])) continue;
                 R offx = ((es & 1) ? p.emrx[e] : p.emlx[e]) - ox;
                 R offy = ((es & 1) ? p.emry[e] : p.emly[e]) - oy;
                 const Vec4<R> Wv = load_W(p, p.slot_nb[s]);
@@ -412,8 +420,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             wx = Wi[1];
             wy = Wi[2];
             if (p.rounding[i]) {
-                R d = sqrt(ox * ox + oy * oy);
-                R f = (R)ip.chi * cs / d;
+                R f = (R)ip.chi * cs * rsqrt(ox * ox + oy * oy);
                 wx += f * ox;
                 wy += f * oy;
             }
@@ -548,12 +555,12 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
         // problem has u* = 0 and the wall does not move normal to itself, so
         // mass, tangential momentum and energy fluxes vanish exactly; only
         // the normal pressure flux remains (round-off would otherwise leak).
-        p.F[e] = Vec4<R>{R(0), L * Fe[1] * nx, L * Fe[1] * ny, R(0)};
+        p.F[e] = Vec4<double>{0.0, (double)(L * Fe[1] * nx), (double)(L * Fe[1] * ny), 0.0};
         return;
     }
     const R Fmx = Fe[1] * nx + Fe[2] * tx, Fmy = Fe[1] * ny + Fe[2] * ty;
-    p.F[e] = Vec4<R>{L * Fe[0], L * (Fmx + Fe[0] * wfx), L * (Fmy + Fe[0] * wfy),
-                     L * (Fe[3] + Fmx * wfx + Fmy * wfy + R(0.5) * (wfx * wfx + wfy * wfy) * Fe[0])};
+    p.F[e] = Vec4<double>{(double)(L * Fe[0]), (double)(L * (Fmx + Fe[0] * wfx)), (double)(L * (Fmy + Fe[0] * wfy)),
+                          (double)(L * (Fe[3] + Fmx * wfx + Fmy * wfy + R(0.5) * (wfx * wfx + wfy * wfy) * Fe[0]))};
 }
 
 template <class R> __global__ void __launch_bounds__(kBlock) k_edge_flux(SweepParams<R> p)
@@ -577,7 +584,7 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (int32_t s = lo; s < hi; s++) {
         int32_t es = p.slot_edge[s];
-        const Vec4<R> f = p.F[es >> 1];
+        const Vec4<double> f = p.F[es >> 1];
         // the right cell takes the flux with the opposite sign: flip the sign
         // bit (integer pipe) rather than branch, so each slot costs one add
         // per component whatever the mix of sides in the warp

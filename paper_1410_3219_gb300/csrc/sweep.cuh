@@ -29,8 +29,11 @@
 //              rounding[n] (uint8) and, in split precision, p64[n] (FP64):
 //              the two discontinuous decisions of the step (rounding trigger,
 //              pressure-ratio switch) are taken on FP64 values
-//   flux (R)   F[E] = L_ij * F_ij (mass, momentum x, y, energy), outward
-//              from the edge's left cell
+//   flux       F[E] = L_ij * F_ij (mass, momentum x, y, energy), outward
+//              from the edge's left cell, FP64: in split precision the
+//              edge kernel widens its FP32 flux once per edge (exactly) on
+//              the otherwise idle FP64 pipe, instead of the gather widening
+//              it once per ring slot
 //   per sim    inst[] scheme parameters and remaining time; dtmin (bits of the
 //              smallest cell time step), dt, status
 #pragma once
@@ -106,7 +109,7 @@ template <class R> struct SweepParams {
     Vec4<R> *psrc;
     Vec2<R> *w;
     int32_t *tess;
-    Vec4<R> *F;
+    Vec4<double> *F;  // stored in FP64 in both precisions (see the flux layout)
     // per simulation: bits of the smallest cell time step, the step taken,
     // status flags
     unsigned long long *dtmin_bits;

@@ -1,0 +1,78 @@
+"""GPU tests at the benchmark's full sizes (Sedov 262,144 cells, Kelvin-
+Helmholtz 1024^2), in the launch configuration bench.py times:
+
+  - one FP64 step against the oracle, every cell (the oracle finishes one
+    full-size step in seconds), at the per-step parity tolerance;
+  - the split-precision runs of the two configurations that ask for it,
+    against the FP64 path over the whole run (Sedov to t = 0.05, KH for
+    200 steps).  The FP64 GPU path stands in for the oracle there: it
+    matches the oracle within 1e-12 per step and within 5e-15 in L1(rho)
+    over a 158-step Sod run, while a 200-step oracle run at 1M cells would
+    take most of an hour of host time.  Also checked: mass and energy drift
+    of the split run (momentum too on the periodic box).
+"""
+import numpy as np
+import pytest
+
+from paper_1410_3219_gb300 import workloads as W
+from tests.gpu_common import TOL, compare_conserved, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1410_3219_gb300 import rich
+    return rich
+
+
+FULL = {
+    "sedov_262144": lambda: W.sedov(n=262144, seed=2),
+    "kh_1048576": lambda: W.kelvin_helmholtz(n_side=1024, seed=3),
+}
+
+
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_step_matches_oracle(R, oracle, name):
+    wl = FULL[name]()
+    gpu, ref = R.Sim(wl), oracle.Sim(wl)
+    info = gpu.step(1)
+    dt = ref.step()
+    assert abs(info["dt_last"] - dt) <= TOL * dt
+    for f in ("area", "rho", "vx", "vy", "p"):
+        assert rel_err(gpu.field(f), ref.field(f)) <= TOL, f
+    compare_conserved(gpu, ref, wl["cfg"])
+    gpu.close()
+    ref.close()
+
+
+RUNS = {
+    "sedov_262144_t0.05": (FULL["sedov_262144"], 0.05, 1 << 30),
+    "kh_1048576_200steps": (FULL["kh_1048576"], np.inf, 200),
+}
+
+
+@pytest.mark.parametrize("name", list(RUNS))
+def test_full_size_split_run(R, name):
+    make, t_end, steps = RUNS[name]
+    a = R.Sim(make())
+    ws = make()
+    ws["cfg"]["precision"] = W.FP32_SPLIT
+    b = R.Sim(ws)
+    c0 = b.conserved()
+    ia = a.step(steps, t_end)
+    ib = b.step(steps, t_end)
+    assert ia["steps_done"] == ib["steps_done"]
+    ra, rb = a.state()["rho"], b.state()["rho"]
+    l1 = float(np.sum(np.abs(ra - rb)) / np.sum(np.abs(ra)))
+    print(f"{name}: {ia['steps_done']} steps, L1(rho) split vs FP64 = {l1:.3e}")
+    assert l1 <= 1e-5, l1
+    c1 = b.conserved()
+    qs = ("m", "E") + (("px", "py") if ws["cfg"]["boundary"] == W.BC_PERIODIC else ())
+    for q in qs:
+        drift = abs(c1[q].sum() - c0[q].sum()) / np.abs(c0[q]).sum()
+        assert drift <= 1e-10, (q, drift)
+    a.close()
+    b.close()
