@@ -68,6 +68,16 @@ FLOPS = {
 }
 
 
+# DRAM bytes (read + write) per unit of the dominant kernel from one ncu
+# capture of the kernel version in this tree (profiles/*_sedov262k.md give
+# the command and the raw counters), scaled to a launch by its units.  Set
+# to None whenever the kernel changes after the capture.
+TRAFFIC_PER_UNIT = {
+    "fp64": {"k_edge_flux": 146.1},      # profiles/k_edge_flux_fp64_sedov262k.md
+    "split": {"k_cell_geometry": 114.2},  # profiles/k_cell_geometry_split_sedov262k.md
+}
+
+
 def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -161,8 +171,10 @@ def roofline_of(prec, kern_means, units, sweep_ms):
         tot["fp32"] += f["fp32"]
     hbm, src = hbm_peak()
     cells_per_s = units["cell"] / (sweep_ms / 1e3)
+    per_unit = TRAFFIC_PER_UNIT.get(prec, {}).get(dom)
+    traffic = per_unit * units[FLOPS[prec][dom][1]] if per_unit is not None else None
     return {"bound": "alu", "pipe": pipe, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu DRAM read + write)",
             "peak_source": ("derived: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz" if pipe == "fp64"
                             else "derived: 152 SMs x 128 FP32 FMA lanes/clk x 2 flop x 2.07 GHz"),
             "sweep_fp64_tflops": tot["fp64"] / (sweep_ms / 1e3) / 1e12,
@@ -277,8 +289,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2d = d2h = 0
+    parts = {"tess_ms": 0.0, "copy_ms": 0.0, "sweep_ms": 0.0}
     for _ in range(e2e_steps):
         info = sim2.step(1)
+        for k in parts:
+            parts[k] += info[k] / e2e_steps
         rc = L.rich_get_conserved(sim2.h, n, *[b.ctypes.data_as(Dp) for b in bufs])
         assert rc == 0
         h2d = (16 * info["n_ghost"] + 8 * info["n_ghost"] + 12 * info["n_tri"] + 4 * (n + 1)
@@ -307,7 +322,8 @@ def run_ours(args):
                    "wall_ms_per_step": 1e3 * wall / args.steps, "parallelism": f"replicas x{ws}"},
         "roofline": roof,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "steps": e2e_steps},
+                "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps,
+                "host_tess_ms": parts["tess_ms"], "copy_ms": parts["copy_ms"], "sweep_ms": parts["sweep_ms"]},
         "gpu_launches": 6 * args.steps,
         "clocks": clk,
         "fp32_split": {"value": res32["value"], "unit": UNIT, "dtype": "f32 reconstruction + f64 geometry/state",

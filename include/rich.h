@@ -142,6 +142,23 @@ int rich_get_state(rich_sim *s, int64_t n, double *x, double *y, double *rho, do
 int rich_get_conserved(rich_sim *s, int64_t n, double *x, double *y, double *m, double *px, double *py,
                        double *E);
 
+/* ---- checkpoint and restart (no counterpart in the paper) ---------------
+   A checkpoint taken between steps is the configuration, rich_time, the
+   points and conserved variables of rich_get_conserved, and the cell order
+   of rich_get_order.  rich_init_conserved restarts from it; the restarted
+   simulation then repeats the uninterrupted one bit for bit (same precision,
+   scheme and device).  order may be NULL: cells are then renumbered along a
+   Hilbert curve of the given points (a valid restart, not bit-identical).
+   Errors as rich_init_mesh; RICH_EINVAL also for a non-positive mass or
+   thermal energy, or an order that is not a permutation of 0..n-1. */
+int rich_init_conserved(const rich_config *cfg, int64_t n, const double *x, const double *y, const double *m,
+                        const double *px, const double *py, const double *E, double t, const int64_t *order,
+                        rich_sim **out);
+/* order[k] = the caller's index of the simulation's k-th internal cell. */
+int rich_get_order(const rich_sim *s, int64_t n, int64_t *order);
+/* Simulation time (-1 for a NULL handle). */
+double rich_time(const rich_sim *s);
+
 /* Release the handle and all its device memory.  NULL is ignored. */
 void rich_destroy(rich_sim *s);
 

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/rich.h"
 
@@ -53,6 +54,16 @@ template <class T> cudaError_t upload(DBuf &b, const std::vector<T> &v, cudaStre
     if (e != cudaSuccess || v.empty()) return e;
     return cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
 }
+
+// NVTX range for the host phases of a step (tessellation, uploads, sweep
+// launch, synchronisation), visible to profilers that record NVTX; the calls
+// do nothing when no profiler is attached.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 inline double now_ms()
 {

@@ -497,6 +497,7 @@ int rich_batch_add(rich_batch *b, const rich_config *cfg, int64_t n, const doubl
 
 int rich_batch_step(rich_batch *b, rich_step_info *info)
 {
+    rich::Range range("rich batch step");
     if (!b) return fail(RICH_EINVAL, "NULL handle");
     if (info) std::memset(info, 0, sizeof(*info));
     const double t0 = now_ms();
@@ -526,11 +527,20 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     }
     // 2. tessellations in parallel
     const double t1 = now_ms();
-    b->pool.parallel_for((int64_t)list.size(), [&](int64_t k) {
-        BatchSim *s = list[k];
-        rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
-        s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm);
-    });
+    // largest first: the pool hands out tasks in order, so the longest
+    // tessellations start first and the step's makespan stays near the
+    // largest one (or the mean load per thread)
+    std::vector<int32_t> by_size(list.size());
+    for (size_t k = 0; k < list.size(); k++) by_size[k] = (int32_t)k;
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t c) { return list[a]->n > list[c]->n; });
+    {
+        rich::Range range("rich batch tessellate (a0)");
+        b->pool.parallel_for((int64_t)list.size(), [&](int64_t k) {
+            BatchSim *s = list[by_size[k]];
+            rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
+            s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm);
+        });
+    }
     const double t2 = now_ms();
     std::vector<BatchSim *> ok;
     for (BatchSim *s : list) {

@@ -281,11 +281,18 @@ static inline double image_coord(double v, double lo, double hi, int flip, int s
     return v;
 }
 
-static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const double *y, double w, HostMesh &m)
+// Ghost images of the points in chunks of kChunk (in parallel with a pool):
+// count per chunk, then fill at the prefix offsets, so the ghost order is
+// the same as one pass over the points.
+static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const double *y, double w, HostMesh &m,
+                        ThreadPool *pool)
 {
-    m.gx.clear(); m.gy.clear(); m.ghost_src.clear(); m.ghost_xf.clear(); m.ghost_shift.clear();
     const double lox = box.x0 - w, hix = box.x1 + w, loy = box.y0 - w, hiy = box.y1 + w;
-    for (int32_t i = 0; i < n; i++) {
+    constexpr int32_t kChunk = 16384;
+    const int64_t nc = (n + kChunk - 1) / kChunk;
+    std::vector<int64_t> off(nc + 1, 0);
+    // visit(i, emit): every image of point i inside the band
+    auto visit = [&](int32_t i, auto &&emit) {
         for (int a = -1; a <= 1; a++)
             for (int b = -1; b <= 1; b++) {
                 if (a == 0 && b == 0) continue;
@@ -295,14 +302,33 @@ static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const 
                 double X = image_coord(x[i], box.x0, box.x1, fx, sx);
                 double Y = image_coord(y[i], box.y0, box.y1, fy, sy);
                 if (X < lox || X > hix || Y < loy || Y > hiy) continue;
-                m.gx.push_back(X);
-                m.gy.push_back(Y);
-                m.ghost_src.push_back(i);
-                m.ghost_xf.push_back((fx ? XF_MIRROR_X : 0) | (fy ? XF_MIRROR_Y : 0));
-                m.ghost_shift.push_back((sx + 1) + 3 * (sy + 1));
+                emit(X, Y, (fx ? XF_MIRROR_X : 0) | (fy ? XF_MIRROR_Y : 0), (sx + 1) + 3 * (sy + 1));
             }
-    }
-    m.g = (int32_t)m.gx.size();
+    };
+    auto count = [&](int64_t c) {
+        int64_t k = 0;
+        for (int32_t i = (int32_t)(c * kChunk); i < std::min<int64_t>(n, (c + 1) * kChunk); i++)
+            visit(i, [&](double, double, int32_t, int32_t) { k++; });
+        off[c + 1] = k;
+    };
+    if (pool && nc > 1) pool->parallel_for(nc, count);
+    else
+        for (int64_t c = 0; c < nc; c++) count(c);
+    for (int64_t c = 0; c < nc; c++) off[c + 1] += off[c];
+    const size_t g = (size_t)off[nc];
+    m.gx.resize(g); m.gy.resize(g); m.ghost_src.resize(g); m.ghost_xf.resize(g); m.ghost_shift.resize(g);
+    auto fill = [&](int64_t c) {
+        int64_t k = off[c];
+        for (int32_t i = (int32_t)(c * kChunk); i < std::min<int64_t>(n, (c + 1) * kChunk); i++)
+            visit(i, [&](double X, double Y, int32_t xf, int32_t sh) {
+                m.gx[k] = X; m.gy[k] = Y; m.ghost_src[k] = i; m.ghost_xf[k] = xf; m.ghost_shift[k] = sh;
+                k++;
+            });
+    };
+    if (pool && nc > 1) pool->parallel_for(nc, fill);
+    else
+        for (int64_t c = 0; c < nc; c++) fill(c);
+    m.g = (int32_t)g;
 }
 
 namespace {
@@ -323,12 +349,20 @@ inline Disk circumdisk(const double *X, const double *Y, int32_t a, int32_t b, i
     return Disk{ux + ax, uy + ay, std::sqrt(ux * ux + uy * uy) * (1.0 + 1e-9) + pad};
 }
 
-// Outcome of one slab: the rings of its real core cells, the triangles they
-// use (global point ids, smallest id first), and whether the halo and the
-// ghost band were wide enough.
+// A tile of the point set: x in [x0, x1), y in [y0, y1); open sides (the
+// first / last along an axis) extend to infinity.
+struct Tile {
+    double x0, x1, y0, y1;
+    bool fx, lx, fy, ly;
+};
+
+// Outcome of one tile: the rings of its real core cells, the triangles they
+// use (global point ids, smallest id first), whether the halo and the ghost
+// band were wide enough, and the halo its stars actually needed.
 struct SlabResult {
     int rc = 0;
     bool halo_ok = true, band_ok = true;
+    double needed = 0.0;
     std::vector<int32_t> cells;  // real core cells, increasing id
     std::vector<int32_t> deg;    // ring length of each
     std::vector<int32_t> nb;     // concatenated rings: neighbour point ids
@@ -336,28 +370,27 @@ struct SlabResult {
     std::vector<int32_t> tris;   // 3 per slab-local triangle
 };
 
-// Triangulate the points of slab [a, b) (x) plus a halo of width H, and read
-// off the stars of its real core points.  A star is the true one when the
-// circumdisk of each of its triangles lies inside the triangulated strip:
-// every point of the whole set inside such a disk was then triangulated too,
-// and an empty circumdisk among them is empty in the whole set.
-void build_slab(int32_t n, int32_t np, const double *X, const double *Y, double xmin, double xmax, double a, double b,
-                bool first, bool last, double H, const double band[4], double pad, Delaunay &dt,
-                std::vector<int32_t> &loc, std::vector<double> &LX, std::vector<double> &LY, SlabResult &r)
+// Triangulate the points of a tile plus a halo of width H, and read off the
+// stars of its real core points.  A star is the true one when the
+// circumdisk of each of its triangles lies inside the triangulated
+// rectangle: every point of the whole set inside such a disk was then
+// triangulated too, and an empty circumdisk among them is empty in the
+// whole set.
+void build_slab(int32_t n, int32_t np, const double *X, const double *Y, const double ext[4], const Tile &tile,
+                double H, const double band[4], double pad, Delaunay &dt, std::vector<int32_t> &loc,
+                std::vector<double> &LX, std::vector<double> &LY, SlabResult &r)
 {
     r = SlabResult();
-    double lo = first ? -INFINITY : a - H, hi = last ? INFINITY : b + H;
-    // a halo that covers every point makes the slab's triangulation the whole one
-    const bool whole = lo <= xmin && hi > xmax;
-    if (whole) {
-        lo = -INFINITY;
-        hi = INFINITY;
-    }
+    double xlo = tile.fx ? -INFINITY : tile.x0 - H, xhi = tile.lx ? INFINITY : tile.x1 + H;
+    double ylo = tile.fy ? -INFINITY : tile.y0 - H, yhi = tile.ly ? INFINITY : tile.y1 + H;
+    // a halo that covers every point makes the tile's triangulation the whole one
+    const bool whole = xlo <= ext[0] && xhi > ext[1] && ylo <= ext[2] && yhi > ext[3];
+    if (whole) xlo = ylo = -INFINITY, xhi = yhi = INFINITY;
     loc.clear();
     LX.clear();
     LY.clear();
     for (int32_t q = 0; q < np; q++)
-        if (X[q] >= lo && X[q] < hi) {
+        if (X[q] >= xlo && X[q] < xhi && Y[q] >= ylo && Y[q] < yhi) {
             loc.push_back(q);
             LX.push_back(X[q]);
             LY.push_back(Y[q]);
@@ -367,7 +400,12 @@ void build_slab(int32_t n, int32_t np, const double *X, const double *Y, double 
     r.rc = dt.build(LX.data(), LY.data(), nl);
     if (r.rc) return;
     const std::vector<Tri> &T = dt.tris;
-    auto core_real = [&](int32_t v) { return v < nl && loc[v] < n && (first || X[loc[v]] >= a) && (last || X[loc[v]] < b); };
+    auto core_real = [&](int32_t v) {
+        if (v >= nl || loc[v] >= n) return false;
+        const double px = X[loc[v]], py = Y[loc[v]];
+        return (tile.fx || px >= tile.x0) && (tile.lx || px < tile.x1) && (tile.fy || py >= tile.y0) &&
+               (tile.ly || py < tile.y1);
+    };
     // the stars of the real core points: check, number, and find one
     // triangle incident to each such point
     std::vector<int32_t> tnum(T.size(), -1), vtri(nl, -1);
@@ -387,10 +425,15 @@ void build_slab(int32_t n, int32_t np, const double *X, const double *Y, double 
             r.band_ok = false;
             return;
         }
-        if (!(D.ux - D.R >= lo && D.ux + D.R <= hi)) {
+        if (!(D.ux - D.R >= xlo && D.ux + D.R <= xhi && D.uy - D.R >= ylo && D.uy + D.R <= yhi)) {
             r.halo_ok = false;
             return;
         }
+        // how far this disk reaches past the tile: the halo it needs
+        if (!tile.fx) r.needed = std::max(r.needed, tile.x0 - (D.ux - D.R));
+        if (!tile.lx) r.needed = std::max(r.needed, D.ux + D.R - tile.x1);
+        if (!tile.fy) r.needed = std::max(r.needed, tile.y0 - (D.uy - D.R));
+        if (!tile.ly) r.needed = std::max(r.needed, D.uy + D.R - tile.y1);
         tnum[t] = nt++;
         for (int k = 0; k < 3; k++)
             if (core_real(v[k])) vtri[v[k]] = (int32_t)t;
@@ -451,9 +494,13 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     double w = std::min(5.0 * h, wmax);
     m.n = n;
     m.attempts = 0;
-    // slabs: enough points each that the halo stays a small fraction
+    // tiles: enough points each that the halo stays a small fraction; Kx
+    // columns of Ky rows, as square as K allows
     const int threads = pool ? pool->size() : 1;
     const int K = std::max(1, std::min(threads, n / 16384));
+    int Ky = (int)std::sqrt((double)K);
+    while (K % Ky) Ky--;
+    const int Kx = K / Ky;
     if ((int)work.dts.size() < K) work.dts.resize(K);
     work.loc.resize(K);
     work.lx.resize(K);
@@ -462,7 +509,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     std::vector<double> X, Y;
     for (;;) {
         m.attempts++;
-        make_ghosts(box, n, x, y, w, m);
+        make_ghosts(box, n, x, y, w, m, pool);
         const int32_t np = n + m.g;
         X.resize(np);
         Y.resize(np);
@@ -471,21 +518,47 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         std::memcpy(X.data() + n, m.gx.data(), sizeof(double) * m.g);
         std::memcpy(Y.data() + n, m.gy.data(), sizeof(double) * m.g);
         const double band[4] = {box.x0 - w, box.x1 + w, box.y0 - w, box.y1 + w};
-        double xmin = X[0], xmax = X[0];
+        double ext[4] = {X[0], X[0], Y[0], Y[0]};
         for (int32_t q = 1; q < np; q++) {
-            xmin = std::min(xmin, X[q]);
-            xmax = std::max(xmax, X[q]);
+            ext[0] = std::min(ext[0], X[q]);
+            ext[1] = std::max(ext[1], X[q]);
+            ext[2] = std::min(ext[2], Y[q]);
+            ext[3] = std::max(ext[3], Y[q]);
         }
-        // slab cuts at x-quantiles of the real + ghost points
-        std::vector<double> cut(K + 1);
-        if (K > 1) {
-            std::vector<double> sx;
-            sx.reserve(np / 8 + 1);
-            for (int32_t q = 0; q < np; q += 8) sx.push_back(X[q]);
-            std::sort(sx.begin(), sx.end());
-            for (int s = 1; s < K; s++) cut[s] = sx[(size_t)s * sx.size() / K];
+        // column cuts at x-quantiles of (a sample of) the real + ghost
+        // points, then row cuts at y-quantiles within each column
+        std::vector<Tile> tiles(K);
+        {
+            std::vector<int32_t> smp;
+            smp.reserve(np / 8 + 1);
+            for (int32_t q = 0; q < np; q += 8) smp.push_back(q);
+            auto byx = [&](int32_t a, int32_t c) { return X[a] < X[c]; };
+            auto byy = [&](int32_t a, int32_t c) { return Y[a] < Y[c]; };
+            std::vector<size_t> cb(Kx + 1);
+            for (int i = 0; i <= Kx; i++) cb[i] = (size_t)i * smp.size() / Kx;
+            for (int i = 1; i < Kx; i++)
+                std::nth_element(smp.begin() + cb[i - 1], smp.begin() + cb[i], smp.end(), byx);
+            for (int i = 0; i < Kx; i++) {
+                const double x0 = i ? X[smp[cb[i]]] : 0.0, x1 = i + 1 < Kx ? X[smp[cb[i + 1]]] : 0.0;
+                const size_t m0 = cb[i], m1 = cb[i + 1];
+                std::vector<size_t> rb(Ky + 1);
+                for (int j = 0; j <= Ky; j++) rb[j] = m0 + (size_t)j * (m1 - m0) / Ky;
+                for (int j = 1; j < Ky; j++)
+                    std::nth_element(smp.begin() + rb[j - 1], smp.begin() + rb[j], smp.begin() + m1, byy);
+                for (int j = 0; j < Ky; j++) {
+                    Tile &t = tiles[i * Ky + j];
+                    t.x0 = x0;
+                    t.x1 = x1;
+                    t.y0 = j ? Y[smp[rb[j]]] : 0.0;
+                    t.y1 = j + 1 < Ky ? Y[smp[rb[j + 1]]] : 0.0;
+                    t.fx = i == 0;
+                    t.lx = i + 1 == Kx;
+                    t.fy = j == 0;
+                    t.ly = j + 1 == Ky;
+                }
+            }
         }
-        // halo: the width that sufficed last time (in mean spacings), else 6 h
+        // halo: what the stars needed last time (in mean spacings), else 6 h
         std::vector<double> H(K, (work.halo > 0 ? work.halo : 6.0) * h);
         std::vector<int> todo(K);
         for (int s = 0; s < K; s++) todo[s] = s;
@@ -493,8 +566,8 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         while (!todo.empty()) {
             auto run = [&](int64_t k) {
                 const int s = todo[k];
-                build_slab(n, np, X.data(), Y.data(), xmin, xmax, cut[s], cut[s + 1], s == 0, s == K - 1, H[s], band,
-                           pad, work.dts[s], work.loc[s], work.lx[s], work.ly[s], res[s]);
+                build_slab(n, np, X.data(), Y.data(), ext, tiles[s], H[s], band, pad, work.dts[s], work.loc[s],
+                           work.lx[s], work.ly[s], res[s]);
             };
             if (pool && todo.size() > 1) pool->parallel_for((int64_t)todo.size(), run);
             else
@@ -517,7 +590,11 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
             continue;
         }
         m.band = w;
-        work.halo = *std::max_element(H.begin(), H.end()) / h;
+        // next time: the widest reach seen, with a margin for the points'
+        // motion in one step
+        double need = 0.0;
+        for (int s = 0; s < K; s++) need = std::max(need, res[s].needed);
+        work.halo = std::max(2.0, 1.25 * need / h + 0.5);
         break;
     }
     // triangles: concatenation of the slabs' lists

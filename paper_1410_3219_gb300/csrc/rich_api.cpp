@@ -223,6 +223,7 @@ int alloc_cells(rich_sim *s)
 // host tessellation of the current points + upload of the connectivity
 int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
 {
+    rich::Range range("rich tessellate (a0)");
     double t0 = now_ms();
     if (fetch_points) {
         const int q = s->pts();
@@ -314,20 +315,25 @@ const char *rich_last_error(void) { return rich::last_error(); }
 
 int64_t rich_num_cells(const rich_sim *s) { return s ? s->n : -1; }
 
-int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const double *y, const double *rho,
-                   const double *vx, const double *vy, const double *p, rich_sim **out)
+// Shared by rich_init_mesh (f = primitives rho, vx, vy, p) and
+// rich_init_conserved (f = extensive m, px, py, E at time t0, cells in the
+// internal order `order` when given).
+static int create_sim(const rich_config *cfg, int64_t n, const double *x, const double *y, const double *const f[4],
+                      bool conserved, double t0, const int64_t *order, rich_sim **out)
 {
     if (!out) return fail(RICH_EINVAL, "out is NULL");
     *out = nullptr;
     if (!valid_config(cfg)) return fail(RICH_EINVAL, "invalid configuration");
     if (n < 3 || n > (int64_t)1 << 30) return fail(RICH_EINVAL, "n must be in [3, 2^30]");
-    if (!x || !y || !rho || !vx || !vy || !p) return fail(RICH_EINVAL, "NULL input array");
+    if (!x || !y || !f[0] || !f[1] || !f[2] || !f[3]) return fail(RICH_EINVAL, "NULL input array");
+    if (!std::isfinite(t0)) return fail(RICH_EINVAL, "bad start time");
     for (int64_t i = 0; i < n; i++) {
         if (!std::isfinite(x[i]) || !std::isfinite(y[i]) || !point_inside(cfg, x[i], y[i]))
             return fail(RICH_EINVAL, "point " + std::to_string(i) + " outside the box");
-        if (!(rho[i] > 0) || !(p[i] > 0) || !std::isfinite(rho[i]) || !std::isfinite(p[i]) || !std::isfinite(vx[i]) ||
-            !std::isfinite(vy[i]))
-            return fail(RICH_EINVAL, "bad primitive values at point " + std::to_string(i));
+        bool good = std::isfinite(f[0][i]) && std::isfinite(f[1][i]) && std::isfinite(f[2][i]) && std::isfinite(f[3][i]);
+        if (conserved) good = good && f[0][i] > 0 && 2.0 * f[0][i] * f[3][i] - (f[1][i] * f[1][i] + f[2][i] * f[2][i]) > 0;
+        else good = good && f[0][i] > 0 && f[3][i] > 0;
+        if (!good) return fail(RICH_EINVAL, "bad field values at point " + std::to_string(i));
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(RICH_ENODEV, "no CUDA device");
@@ -335,24 +341,36 @@ int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const dou
     if (!s) return fail(RICH_ENOMEM, "host allocation");
     s->cfg = *cfg;
     s->n = (int32_t)n;
+    s->t = t0;
     s->pool.reset(new (std::nothrow) rich::ThreadPool((int)std::max(1u, std::thread::hardware_concurrency())));
     if (!s->pool) {
         delete s;
         return fail(RICH_ENOMEM, "host thread pool");
     }
-    // renumber cells along a Hilbert curve for locality
-    rich::hilbert_order(s->n, x, y, s->perm);
+    if (order) {
+        // the caller's internal order (a checkpoint's): must be a permutation
+        s->perm.resize(n);
+        std::vector<char> seen(n, 0);
+        for (int64_t k = 0; k < n; k++) {
+            if (order[k] < 0 || order[k] >= n || seen[order[k]]) {
+                delete s;
+                return fail(RICH_EINVAL, "order is not a permutation");
+            }
+            seen[order[k]] = 1;
+            s->perm[k] = (int32_t)order[k];
+        }
+    } else {
+        // renumber cells along a Hilbert curve for locality
+        rich::hilbert_order(s->n, x, y, s->perm);
+    }
     s->hx.resize(n);
     s->hy.resize(n);
-    std::vector<double> Wh(4 * (size_t)n);
+    std::vector<double> Fh(4 * (size_t)n);
     for (int32_t k = 0; k < s->n; k++) {
         int32_t u = s->perm[k];
         s->hx[k] = x[u];
         s->hy[k] = y[u];
-        Wh[k] = rho[u];
-        Wh[n + k] = vx[u];
-        Wh[2 * n + k] = vy[u];
-        Wh[3 * n + k] = p[u];
+        for (int c = 0; c < 4; c++) Fh[(size_t)c * n + k] = f[c][u];
     }
     int rc = RICH_OK;
     auto bail = [&](int code) { delete s; return code; };
@@ -366,13 +384,18 @@ int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const dou
     cudaMemcpyAsync(s->x[0].p, s->hx.data(), n * 8, cudaMemcpyHostToDevice, s->stream);
     cudaMemcpyAsync(s->y[0].p, s->hy.data(), n * 8, cudaMemcpyHostToDevice, s->stream);
     if ((rc = tessellate(s, nullptr, false)) != RICH_OK) return bail(rc);
-    if (s->initW.ensure(4 * n * 8) != cudaSuccess) return bail(fail(RICH_ENOMEM, "device primitives"));
-    cudaMemcpyAsync(s->initW.p, Wh.data(), 4 * n * 8, cudaMemcpyHostToDevice, s->stream);
-    s->inst_host = s->inst_params(0.0, true);
-    if (cudaMemcpyAsync(s->instp.p, &s->inst_host, sizeof(rich::InstParams), cudaMemcpyHostToDevice, s->stream) !=
-        cudaSuccess)
-        return bail(fail(RICH_ECUDA, "parameter upload"));
-    for (int k = 0; k < rich::GEOMETRY_STAGES; k++) s->launch(k, s->initW.as<double>(), s->U[0].as<double>());
+    if (conserved) {
+        if (cudaMemcpyAsync(s->U[0].p, Fh.data(), 4 * n * 8, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+            return bail(fail(RICH_ECUDA, "state upload"));
+    } else {
+        if (s->initW.ensure(4 * n * 8) != cudaSuccess) return bail(fail(RICH_ENOMEM, "device primitives"));
+        cudaMemcpyAsync(s->initW.p, Fh.data(), 4 * n * 8, cudaMemcpyHostToDevice, s->stream);
+        s->inst_host = s->inst_params(0.0, true);
+        if (cudaMemcpyAsync(s->instp.p, &s->inst_host, sizeof(rich::InstParams), cudaMemcpyHostToDevice,
+                            s->stream) != cudaSuccess)
+            return bail(fail(RICH_ECUDA, "parameter upload"));
+        for (int k = 0; k < rich::GEOMETRY_STAGES; k++) s->launch(k, s->initW.as<double>(), s->U[0].as<double>());
+    }
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return bail(fail(RICH_ECUDA, std::string("init: ") + cudaGetErrorString(e)));
@@ -380,6 +403,30 @@ int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const dou
     *out = s;
     return RICH_OK;
 }
+
+int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const double *y, const double *rho,
+                   const double *vx, const double *vy, const double *p, rich_sim **out)
+{
+    const double *f[4] = {rho, vx, vy, p};
+    return create_sim(cfg, n, x, y, f, false, 0.0, nullptr, out);
+}
+
+int rich_init_conserved(const rich_config *cfg, int64_t n, const double *x, const double *y, const double *m,
+                        const double *px, const double *py, const double *E, double t, const int64_t *order,
+                        rich_sim **out)
+{
+    const double *f[4] = {m, px, py, E};
+    return create_sim(cfg, n, x, y, f, true, t, order, out);
+}
+
+int rich_get_order(const rich_sim *s, int64_t n, int64_t *order)
+{
+    if (!s || n != s->n || !order) return fail(RICH_EINVAL, "bad arguments");
+    for (int32_t k = 0; k < s->n; k++) order[k] = s->perm[k];
+    return RICH_OK;
+}
+
+double rich_time(const rich_sim *s) { return s ? s->t : -1.0; }
 
 void rich_destroy(rich_sim *s)
 {
@@ -433,6 +480,7 @@ int rich_tessellate(rich_sim *s, rich_step_info *info)
 
 int rich_sweep(rich_sim *s, double t_end)
 {
+    rich::Range range("rich sweep launch (a1-a9)");
     if (!s) return fail(RICH_EINVAL, "NULL handle");
     if (!s->tess_current) return fail(RICH_ESTATE, "no current tessellation");
     if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
@@ -454,6 +502,7 @@ int rich_sweep(rich_sim *s, double t_end)
 
 int rich_sync(rich_sim *s, rich_step_info *info)
 {
+    rich::Range range("rich sync");
     if (!s) return fail(RICH_EINVAL, "NULL handle");
     if (!s->pending) return fail(RICH_ESTATE, "no sweep pending");
     double t0 = now_ms();
@@ -510,6 +559,7 @@ int rich_sync(rich_sim *s, rich_step_info *info)
 
 int rich_step(rich_sim *s, int32_t max_steps, double t_end, rich_step_info *info)
 {
+    rich::Range range("rich step");
     if (!s) return fail(RICH_EINVAL, "NULL handle");
     if (info) std::memset(info, 0, sizeof(*info));
     for (int32_t k = 0; k < max_steps; k++) {

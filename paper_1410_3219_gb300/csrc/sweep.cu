@@ -472,7 +472,10 @@ template <class R> __device__ __forceinline__ void hllc(R gam, R igm1, const R L
 {
     const R rL = L[0], uL = L[1], tL = L[2], pL = L[3];
     const R rR = Rs[0], uR = Rs[1], tR = Rs[2], pR = Rs[3];
-    const R cL = sqrt(gam * pL / rL), cR = sqrt(gam * pR / rR);
+    // c = sqrt(gamma p / rho) = gamma p / sqrt(gamma p rho): one reciprocal
+    // square root instead of a divide and a square root
+    const R gpL = gam * pL, gpR = gam * pR;
+    const R cL = gpL * rsqrt(gpL * rL), cR = gpR * rsqrt(gpR * rR);
     const R EL = pL * igm1 + R(0.5) * rL * (uL * uL + tL * tL);
     const R ER = pR * igm1 + R(0.5) * rR * (uR * uR + tR * tR);
     const R SL = fmin(uL - cL, uR - cR);

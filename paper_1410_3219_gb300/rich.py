@@ -16,6 +16,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librich.so")
 
 RICH_OK = 0
+RICH_EINVAL, RICH_EDUPLICATE, RICH_ETESS, RICH_ETOOFEW = -1, -2, -3, -4
+RICH_ENEGATIVE, RICH_ENAN, RICH_ENOMEM, RICH_ECUDA, RICH_ENODEV, RICH_ESTATE = -5, -6, -7, -8, -9, -10
 ERRORS = {-1: "EINVAL", -2: "EDUPLICATE", -3: "ETESS", -4: "ETOOFEW", -5: "ENEGATIVE", -6: "ENAN",
           -7: "ENOMEM", -8: "ECUDA", -9: "ENODEV", -10: "ESTATE"}
 
@@ -31,7 +33,8 @@ EXPORTS = ["rich_default_config", "rich_init_mesh", "rich_step", "rich_get_state
            "rich_batch_step", "rich_batch_query", "rich_batch_get_conserved", "rich_batch_remove",
            "rich_batch_set_diagnostics", "rich_batch_cells", "rich_batch_destroy", "rich_batch_set_launch",
            "rich_batch_launch_info", "rich_server_create", "rich_server_submit", "rich_server_tick",
-           "rich_server_query", "rich_server_fetch", "rich_server_batch", "rich_server_destroy"]
+           "rich_server_query", "rich_server_fetch", "rich_server_batch", "rich_server_destroy",
+           "rich_init_conserved", "rich_get_order", "rich_time"]
 
 REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
@@ -131,6 +134,11 @@ def _lib():
         L.rich_kernel_name.argtypes = [I32]
         L.rich_kernel_name.restype = C.c_char_p
         L.rich_courant_dt_noalloc.argtypes = [C.POINTER(rich_config), I64] + [P] * 8 + [P]
+        L.rich_init_conserved.argtypes = [C.POINTER(rich_config), I64] + [_D] * 6 + [d, C.POINTER(I64),
+                                                                                     C.POINTER(P)]
+        L.rich_get_order.argtypes = [P, I64, C.POINTER(I64)]
+        L.rich_time.argtypes = [P]
+        L.rich_time.restype = d
         _handle = L
     return _handle
 
@@ -165,6 +173,32 @@ def rich_init_mesh(cfg, x, y, rho, vx, vy, p):
     h = C.c_void_p()
     _check(_lib().rich_init_mesh(C.byref(c), n, *[_p(a) for a in arrs], C.byref(h)))
     return h
+
+
+def rich_init_conserved(cfg, x, y, m, px, py, E, t=0.0, order=None):
+    c = cfg if isinstance(cfg, rich_config) else rich_config.from_dict(cfg)
+    n = len(x)
+    arrs = [_f64(a, n) for a in (x, y, m, px, py, E)]
+    o = None
+    if order is not None:
+        o = np.ascontiguousarray(order, dtype=np.int64)
+        if o.shape != (n,):
+            raise ValueError("order must have one entry per point")
+    h = C.c_void_p()
+    _check(_lib().rich_init_conserved(C.byref(c), n, *[_p(a) for a in arrs], float(t),
+                                      o.ctypes.data_as(C.POINTER(C.c_int64)) if o is not None else None,
+                                      C.byref(h)))
+    return h
+
+
+def rich_get_order(h, n):
+    o = np.empty(n, np.int64)
+    _check(_lib().rich_get_order(h, n, o.ctypes.data_as(C.POINTER(C.c_int64))))
+    return o
+
+
+def rich_time(h):
+    return _lib().rich_time(h)
 
 
 def rich_step(h, max_steps=1, t_end=float("inf")):
@@ -468,6 +502,22 @@ class Sim:
 
     def conserved(self):
         return rich_get_conserved(self.h, self.n)
+
+    def checkpoint(self):
+        """Everything a bit-identical restart needs (take it between steps)."""
+        c = rich_get_conserved(self.h, self.n)
+        c["t"] = rich_time(self.h)
+        c["order"] = rich_get_order(self.h, self.n)
+        return c
+
+    @classmethod
+    def restart(cls, cfg, ck):
+        """A simulation continuing from checkpoint() output."""
+        self = cls.__new__(cls)
+        self.n = len(ck["x"])
+        self.h = rich_init_conserved(cfg, ck["x"], ck["y"], ck["m"], ck["px"], ck["py"], ck["E"], ck["t"],
+                                     ck.get("order"))
+        return self
 
     def field(self, name, comp=0):
         return rich_get_field(self.h, self.n, name, comp)

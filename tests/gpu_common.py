@@ -18,10 +18,17 @@ def periodic_delta(a, b, L):
 
 
 def compare_conserved(gpu, ref, cfg, tol=TOL):
+    """Conserved variables and points of the library against the oracle.
+    Mass and energy are measured against their own scale; momentum against
+    the larger of its own and mass times sound speed: its net value can be
+    far below the pressure and advection terms that update it (a shear flow
+    with a small transverse seed), whose round-off sets the agreement."""
     a, b = gpu.conserved(), ref.conserved()
     errs = {}
+    mscale = float(np.max(np.abs(b["m"])) * np.max(ref.field("cs")))
     for k in ("m", "px", "py", "E"):
-        errs[k] = rel_err(a[k], b[k])
+        sc = max(float(np.max(np.abs(b[k]))), mscale) if k in ("px", "py") else None
+        errs[k] = rel_err(a[k], b[k], sc)
     Lx, Ly = cfg["x1"] - cfg["x0"], cfg["y1"] - cfg["y0"]
     dx = periodic_delta(a["x"], b["x"], Lx) if cfg["boundary"] == 1 else a["x"] - b["x"]
     dy = periodic_delta(a["y"], b["y"], Ly) if cfg["boundary"] == 1 else a["y"] - b["y"]
