@@ -104,6 +104,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device="cuda"):
+    """The largest of the ranks' values of x (the job's time is its slowest
+    rank's).  Replicas exchange nothing else."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws, units_per_rank, seconds):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return ws * units_per_rank / seconds
+
+
 class Clocks:
     """nvidia-smi samples during the timed region."""
 
@@ -261,13 +278,9 @@ def run_ours(args):
             dist.barrier()
         clk = clocks.stop(local) if clocks else None
         sim.close()
-        total_s = sum(sweep_ms) / 1e3
-        if ws > 1:
-            t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_s = float(t.item())
+        total_s = max_over_ranks(sum(sweep_ms) / 1e3, ws)
         means = {k: float(np.mean(v)) for k, v in kern.items() if k != "dt_reset"}
-        return {"value": ws * n * args.steps / total_s, "sweep_ms": sweep_ms, "tess_ms": tess_ms, "wall": wall,
+        return {"value": job_value(ws, n * args.steps, total_s), "sweep_ms": sweep_ms, "tess_ms": tess_ms, "wall": wall,
                 "units": units, "kernel_means": means, "clocks": clk}
 
     res64 = time_precision("fp64", True)
@@ -300,7 +313,8 @@ def run_ours(args):
                + 12 * info["n_slots"] + 16 * info["n_edges"])
         d2h = 16 * n + 12 + 48 * n
     e2e_s = time.perf_counter() - t0
-    e2e_val = ws * n * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, ws)
+    e2e_val = job_value(ws, n * e2e_steps, e2e_s)
     sim2.close()
 
     if rank != 0:
