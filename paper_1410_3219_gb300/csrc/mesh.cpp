@@ -15,42 +15,42 @@ namespace rich {
 // ---------------------------------------------------------------------------
 // Hilbert order
 
-static uint32_t hilbert_index(uint32_t x, uint32_t y)
+static uint32_t hilbert_index(uint32_t x, uint32_t y, int levels)
 {
-    // position along the Hilbert curve of a 2^16 x 2^16 grid: at each level the
-    // quadrant contributes (3*rx)^ry and the remaining coordinates are rotated
-    // into that quadrant's frame
-    const uint32_t n = 1u << 16;
+    // position along the Hilbert curve of a 2^levels x 2^levels grid: at each
+    // level the quadrant contributes (3*rx)^ry and the remaining coordinates
+    // are rotated into that quadrant's frame
+    // (branch-free: the reflection n-1-v is v ^ (n-1) for v < n)
+    const uint32_t top = (1u << levels) - 1u;
     uint32_t d = 0;
-    for (uint32_t s = n >> 1; s > 0; s >>= 1) {
-        uint32_t rx = (x & s) ? 1u : 0u;
-        uint32_t ry = (y & s) ? 1u : 0u;
-        d += s * s * ((3u * rx) ^ ry);
-        if (ry == 0) {
-            if (rx == 1) {
-                x = n - 1 - x;
-                y = n - 1 - y;
-            }
-            std::swap(x, y);
-        }
+    for (int k = levels - 1; k >= 0; k--) {
+        const uint32_t rx = (x >> k) & 1u, ry = (y >> k) & 1u;
+        d += ((3u * rx) ^ ry) << (2 * k);
+        const uint32_t flip = 0u - (rx & (ry ^ 1u));
+        x ^= flip & top;
+        y ^= flip & top;
+        const uint32_t sw = (x ^ y) & (0u - (ry ^ 1u));
+        x ^= sw;
+        y ^= sw;
     }
     return d;
 }
 
-static void radix_sort(std::vector<uint32_t> &keys, std::vector<int32_t> &idx, std::vector<uint32_t> &tk,
-                       std::vector<int32_t> &ti)
+// LSD radix sort of (key, index) pairs on the low `bits` bits, 11 bits a pass
+static void radix_sort(std::vector<uint32_t> &keys, std::vector<int32_t> &idx, int bits)
 {
-    size_t n = keys.size();
-    tk.resize(n);
-    ti.resize(n);
-    for (int pass = 0; pass < 2; pass++) {
-        int shift = 16 * pass;
-        std::vector<uint32_t> cnt(65537, 0);
-        for (size_t i = 0; i < n; i++) cnt[((keys[i] >> shift) & 0xffffu) + 1]++;
-        for (int b = 0; b < 65536; b++) cnt[b + 1] += cnt[b];
+    const size_t n = keys.size();
+    std::vector<uint32_t> tk(n);
+    std::vector<int32_t> ti(n);
+    constexpr int kDigit = 11;
+    std::vector<uint32_t> cnt((1u << kDigit) + 1);
+    for (int shift = 0; shift < bits; shift += kDigit) {
+        std::fill(cnt.begin(), cnt.end(), 0u);
+        const uint32_t mask = (1u << kDigit) - 1u;
+        for (size_t i = 0; i < n; i++) cnt[((keys[i] >> shift) & mask) + 1]++;
+        for (uint32_t b = 0; b < mask + 1; b++) cnt[b + 1] += cnt[b];
         for (size_t i = 0; i < n; i++) {
-            uint32_t b = (keys[i] >> shift) & 0xffffu;
-            uint32_t pos = cnt[b]++;
+            const uint32_t pos = cnt[(keys[i] >> shift) & mask]++;
             tk[pos] = keys[i];
             ti[pos] = idx[i];
         }
@@ -61,24 +61,28 @@ static void radix_sort(std::vector<uint32_t> &keys, std::vector<int32_t> &idx, s
 
 void hilbert_order(int32_t n, const double *x, const double *y, std::vector<int32_t> &order)
 {
-    std::vector<uint32_t> keys(n), tk;
-    std::vector<int32_t> ti;
     order.resize(n);
     if (n == 0) return;
+    // resolution: about 2^3 grid cells per point along each axis is plenty
+    // for locality; the curve index then needs 2 * levels bits
+    int levels = 4;
+    while (levels < 16 && (int64_t)1 << (2 * (levels - 3)) < (int64_t)n) levels++;
+    std::vector<uint32_t> keys(n);
     double xmin = x[0], xmax = x[0], ymin = y[0], ymax = y[0];
     for (int32_t i = 1; i < n; i++) {
         xmin = std::min(xmin, x[i]); xmax = std::max(xmax, x[i]);
         ymin = std::min(ymin, y[i]); ymax = std::max(ymax, y[i]);
     }
-    double sx = xmax > xmin ? 65535.0 / (xmax - xmin) : 0.0;
-    double sy = ymax > ymin ? 65535.0 / (ymax - ymin) : 0.0;
+    const double top = (double)((1u << levels) - 1u);
+    double sx = xmax > xmin ? top / (xmax - xmin) : 0.0;
+    double sy = ymax > ymin ? top / (ymax - ymin) : 0.0;
     for (int32_t i = 0; i < n; i++) {
-        uint32_t gx = (uint32_t)std::min(65535.0, std::max(0.0, (x[i] - xmin) * sx));
-        uint32_t gy = (uint32_t)std::min(65535.0, std::max(0.0, (y[i] - ymin) * sy));
-        keys[i] = hilbert_index(gx, gy);
+        uint32_t gx = (uint32_t)std::min(top, std::max(0.0, (x[i] - xmin) * sx));
+        uint32_t gy = (uint32_t)std::min(top, std::max(0.0, (y[i] - ymin) * sy));
+        keys[i] = hilbert_index(gx, gy, levels);
         order[i] = i;
     }
-    radix_sort(keys, order, tk, ti);
+    radix_sort(keys, order, 2 * levels);
 }
 
 // ---------------------------------------------------------------------------
@@ -534,23 +538,31 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
             for (int32_t q = 0; q < np; q += 8) smp.push_back(q);
             auto byx = [&](int32_t a, int32_t c) { return X[a] < X[c]; };
             auto byy = [&](int32_t a, int32_t c) { return Y[a] < Y[c]; };
+            // (each cut value is read right after its selection: a later
+            // selection on the remaining range moves the elements)
             std::vector<size_t> cb(Kx + 1);
+            std::vector<double> xc(Kx + 1, 0.0);
             for (int i = 0; i <= Kx; i++) cb[i] = (size_t)i * smp.size() / Kx;
-            for (int i = 1; i < Kx; i++)
+            for (int i = 1; i < Kx; i++) {
                 std::nth_element(smp.begin() + cb[i - 1], smp.begin() + cb[i], smp.end(), byx);
+                xc[i] = X[smp[cb[i]]];
+            }
             for (int i = 0; i < Kx; i++) {
-                const double x0 = i ? X[smp[cb[i]]] : 0.0, x1 = i + 1 < Kx ? X[smp[cb[i + 1]]] : 0.0;
+                const double x0 = xc[i], x1 = xc[i + 1];
                 const size_t m0 = cb[i], m1 = cb[i + 1];
                 std::vector<size_t> rb(Ky + 1);
+                std::vector<double> yc(Ky + 1, 0.0);
                 for (int j = 0; j <= Ky; j++) rb[j] = m0 + (size_t)j * (m1 - m0) / Ky;
-                for (int j = 1; j < Ky; j++)
+                for (int j = 1; j < Ky; j++) {
                     std::nth_element(smp.begin() + rb[j - 1], smp.begin() + rb[j], smp.begin() + m1, byy);
+                    yc[j] = Y[smp[rb[j]]];
+                }
                 for (int j = 0; j < Ky; j++) {
                     Tile &t = tiles[i * Ky + j];
                     t.x0 = x0;
                     t.x1 = x1;
-                    t.y0 = j ? Y[smp[rb[j]]] : 0.0;
-                    t.y1 = j + 1 < Ky ? Y[smp[rb[j + 1]]] : 0.0;
+                    t.y0 = yc[j];
+                    t.y1 = yc[j + 1];
                     t.fx = i == 0;
                     t.lx = i + 1 == Kx;
                     t.fy = j == 0;

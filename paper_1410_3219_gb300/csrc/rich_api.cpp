@@ -109,8 +109,23 @@ struct rich_sim {
     DBuf instp;  // one InstParams
     rich::InstParams inst_host{};  // staging for the parameter upload
 
+    // pinned host staging for reads of the state (grown as needed)
+    double *pinned = nullptr;
+    size_t pinned_cap = 0;
+    cudaError_t pinned_ensure(size_t count)
+    {
+        if (count <= pinned_cap) return cudaSuccess;
+        if (pinned) cudaFreeHost(pinned);
+        pinned = nullptr;
+        pinned_cap = 0;
+        cudaError_t e = cudaMallocHost(&pinned, count * sizeof(double));
+        if (e == cudaSuccess) pinned_cap = count;
+        return e;
+    }
+
     ~rich_sim()
     {
+        if (pinned) cudaFreeHost(pinned);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         for (cudaEvent_t e : kev)
@@ -651,18 +666,26 @@ int rich_get_conserved(rich_sim *s, int64_t n, double *x, double *y, double *m, 
 {
     if (!s || n != s->n) return fail(RICH_EINVAL, "bad handle or size");
     if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
-    std::vector<double> h;
-    int rc;
     const size_t N = (size_t)s->n;
     const int q = s->pts();
-    if (x) { if ((rc = fetch(s, s->x[q].p, h, N))) return rc; unpermute(s, h.data(), x); }
-    if (y) { if ((rc = fetch(s, s->y[q].p, h, N))) return rc; unpermute(s, h.data(), y); }
-    double *outs[4] = {m, px, py, E};
-    if (m || px || py || E) {
-        if ((rc = fetch(s, s->U[q].p, h, 4 * N))) return rc;
-        for (int v = 0; v < 4; v++)
-            if (outs[v]) unpermute(s, h.data() + v * N, outs[v]);
-    }
+    // points and state into pinned staging with one wait, then put back in
+    // the caller's order on the host threads
+    CUDA_TRY(s->pinned_ensure(6 * N));
+    double *st = s->pinned;
+    CUDA_TRY(cudaMemcpyAsync(st, s->x[q].p, N * 8, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(st + N, s->y[q].p, N * 8, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(st + 2 * N, s->U[q].p, 4 * N * 8, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    double *outs[6] = {x, y, m, px, py, E};
+    const int64_t chunk = 65536, nch = ((int64_t)N + chunk - 1) / chunk;
+    s->pool->parallel_for(6 * nch, [&](int64_t t) {
+        const int f = (int)(t / nch);
+        if (!outs[f]) return;
+        const int64_t k0 = (t % nch) * chunk, k1 = std::min<int64_t>((int64_t)N, k0 + chunk);
+        const double *src = st + (size_t)f * N;
+        double *dst = outs[f];
+        for (int64_t k = k0; k < k1; k++) dst[s->perm[k]] = src[k];
+    });
     return RICH_OK;
 }
 

@@ -188,17 +188,19 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
         ay = by;
     }
     const double A = 0.5 * A2;
-    const double inv3 = 1.0 / (3.0 * A2);
+    // one division serves both the centre of mass and 1/A
+    const double rA2 = 1.0 / A2;
+    const double inv3 = rA2 * (1.0 / 3.0);
     const double ox = sx * inv3, oy = sy * inv3;
     p.A[i] = A;
     p.o[i] = Vec2<R>{(R)ox, (R)oy};
     // Section 6 trigger: the generator is more than eta R_i from its centre of
-    // mass.  Rounded cells settle at that distance, so the decision is taken
-    // in FP64 in every precision.
+    // mass, d^2 > eta^2 A / pi (both sides non-negative, so no square roots).
+    // Rounded cells settle at that distance, so the decision is taken in
+    // FP64 in every precision.
     {
-        const double d = sqrt(ox * ox + oy * oy);
-        const double Rad = sqrt(A * (1.0 / M_PI));
-        p.rounding[i] = d > p.inst[inst_of(p, i)].eta * Rad ? 1 : 0;
+        const double eta = p.inst[inst_of(p, i)].eta;
+        p.rounding[i] = ox * ox + oy * oy > (eta * eta) * (A * (1.0 / M_PI)) ? 1 : 0;
     }
     const int32_t n = p.n;
     const InstParams &ip = p.inst[inst_of(p, i)];
@@ -217,7 +219,7 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
     double m = p.U[i], Px = p.U[n + i], Py = p.U[2 * n + i], E = p.U[3 * n + i];
     Vec4<R> W;
     if (sizeof(R) == sizeof(double)) {
-        double invA = 1.0 / A, invm = 1.0 / m;
+        double invA = 2.0 * rA2, invm = 1.0 / m;
         double rho = m * invA, vx = Px * invm, vy = Py * invm;
         double pr = gm1 * (E - 0.5 * (Px * vx + Py * vy)) * invA;
         W = Vec4<R>{(R)rho, (R)vx, (R)vy, (R)pr};
@@ -231,7 +233,9 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
         W = Vec4<R>{mf / Af, (R)Px / mf, (R)Py / mf, (R)pr};
     }
     p.W[i] = W;
-    p.cs[i] = sqrt((R)gamma * W.w / W.x);
+    // c_s = sqrt(gamma p / rho) = gamma p / sqrt(gamma p rho): one reciprocal square root
+    const R gp = (R)gamma * W.w;
+    p.cs[i] = gp * rsqrt(gp * W.x);
 }
 
 template <class R> __global__ void k_cell_geometry(SweepParams<R> p, const double *__restrict__ init_W)
@@ -320,12 +324,16 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             fmx[v] = ext[v].max();
             fmn[v] = ext[v].min();
         }
-        const R invA = R(1) / A;
+        // R_i = sqrt(A/pi) and 1/A from one reciprocal square root:
+        // rR = 1/R_i, so 1/A = rR^2 / pi and R_i = (A/pi) rR
+        const R Api = A * (R(1) / R(M_PI));
+        const R rR = rsqrt(Api);
+        const R invA = rR * rR * (R(1) / R(M_PI));
         R g[8];
 #pragma unroll
         for (int c = 0; c < 8; c++) g[c] = acc[c] * invA;
         const R cs = p.cs[i];
-        const R Rad = sqrt(A * (R(1) / R(M_PI)));
+        const R Rad = Api * rR;
         if (-(g[2] + g[5]) * Rad > (R)ip.delta_v * cs) shock = true;
         const bool use_tess = ip.limiter == 2 || (ip.limiter == 0 && shock);
         const Vec2<R> oi = p.o[i];
@@ -485,28 +493,34 @@ template <class R> __device__ __forceinline__ void hllc(R gam, R igm1, const R L
     // warp whose edges take different sides evaluates one star state, not two.
     const bool supL = SL >= R(0), supR = !supL && SR <= R(0);
     const bool sub = !(supL || supR);
+    // m_K = rho_K (S_K - u_K): m_L < 0 < m_R, so the contact speed
+    // S* = num / den has den = m_L - m_R < 0 and S* >= 0 exactly when num <= 0
     const R mL = rL * (SL - uL), mR = rR * (SR - uR);
-    R Ss = R(0);
-    if (sub) Ss = (pR - pL + uL * mL - uR * mR) / (mL - mR);
-    const bool useL = supL || (sub && Ss >= R(0));
+    const R num = pR - pL + uL * mL - uR * mR, den = mL - mR;
+    const bool useL = supL || (sub && num <= R(0));
     const R rK = useL ? rL : rR, uK = useL ? uL : uR, tK = useL ? tL : tR, pK = useL ? pL : pR;
     const R EK = useL ? EL : ER;
     const R ruK = rK * uK;
     F[0] = ruK;
     F[1] = ruK * uK + pK;
-    F[2] = ruK * tK;
     F[3] = uK * (EK + pK);
     if (sub) {
-        // star state: rho* = m_K/(S_K - S*), E* = ((S_K - u_K) E_K + (S* - u_K)(m_K S* + p_K))/(S_K - S*)
+        // star state: rho* = m_K/(S_K - S*), E* = ((S_K - u_K) E_K + (S* - u_K)(m_K S* + p_K))/(S_K - S*).
+        // With D = S_K den - num, S_K - S* = D / den; one reciprocal
+        // r = 1/(den D) gives S* = num D r and 1/(S_K - S*) = den^2 r.
         const R SK = useL ? SL : SR, mK = useL ? mL : mR;
-        const R inv = R(1) / (SK - Ss);
+        const R D = SK * den - num;
+        const R r = R(1) / (den * D);
+        const R Ss = num * D * r;
+        const R inv = den * den * r;
         const R f = mK * inv;
         const R Es = ((SK - uK) * EK + (Ss - uK) * (mK * Ss + pK)) * inv;
         F[0] += SK * (f - rK);
         F[1] += SK * (f * Ss - ruK);
-        F[2] += SK * (f * tK - rK * tK);
         F[3] += SK * (Es - EK);
     }
+    // the tangential momentum flux is the mass flux times u_t of side K
+    F[2] = F[0] * tK;
 }
 
 // a7: one flux per edge in the frame of the moving edge
