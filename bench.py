@@ -218,7 +218,8 @@ def run_ours(args):
     n = len(wl["x"])
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    import tempfile
+    clock_dir = tempfile.mkdtemp(prefix="rich_bench_clocks_")
 
     def time_precision(prec, with_clocks, scheme=0):
         w = dict(wl)
@@ -256,7 +257,7 @@ def run_ours(args):
 
         for _ in range(args.warmup):
             one_step()
-        clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_{prec}_r{rank}.csv")) \
+        clocks = Clocks(os.path.join(clock_dir, f"clocks_{prec}_r{rank}.csv")) \
             if (rank == 0 and with_clocks) else None
         if ws > 1:
             dist.barrier()
