@@ -344,7 +344,9 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
         // dphi < 0); one division per sign and variable.
         // TESS (Eq. 6): psi_ij = max(theta (phi_j - phi_i)/dphi, 0); the
         // smallest ratio is found by cross-multiplication, divided once.
-        R alpha[4];
+        // alpha_v = an[v] / ad[v] (1/1 where the variable is not limited)
+        R an[4] = {1, 1, 1, 1}, ad[4] = {1, 1, 1, 1};
+        bool lim[4] = {false, false, false, false};
         if (!use_tess) {
             Extremes<R> dex[4];
 #pragma unroll
@@ -361,19 +363,19 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 // alpha = min(1, (phi_max - phi_i)/dphi_max, (phi_i - phi_min)/|dphi_min|):
-                // a ratio needs dividing only when its numerator is the smaller
-                // the smaller of the two ratios below one is chosen by
-                // cross-multiplication (all terms non-negative) and divided once
-                R a = R(1);
+                // a ratio below one needs its numerator to be the smaller, and
+                // the smaller of two such ratios is found by cross-multiplication
+                // (all terms non-negative)
                 const R n1 = fmx[v] - Wi[v], d1 = dex[v].max();
                 const R n2 = Wi[v] - fmn[v], d2 = -dex[v].min();
                 const bool c1 = dex[v].max_positive() && nonneg_less(n1, d1);
                 const bool c2 = dex[v].min_negative() && nonneg_less(n2, d2);
                 if (c1 || c2) {
                     const bool use1 = c1 && (!c2 || nonneg_less(n1 * d2, n2 * d1));
-                    a = (use1 ? n1 : n2) / (use1 ? d1 : d2);
+                    an[v] = use1 ? n1 : n2;
+                    ad[v] = use1 ? d1 : d2;
+                    lim[v] = true;
                 }
-                alpha[v] = a;
             }
         } else {
             R bn[4] = {0, 0, 0, 0}, bd[4] = {0, 0, 0, 0};  // smallest |N|/|D| so far (bd == 0: none)
@@ -392,35 +394,17 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
                     if (dphi == R(0)) continue;
                     R num = Wj[v] - Wi[v];
                     if (!(num * dphi > R(0))) { zero[v] = true; continue; }
-                    R an = fabs(num), ad = fabs(dphi);
-                    if (bd[v] == R(0) || an * bd[v] < bn[v] * ad) { bn[v] = an; bd[v] = ad; }
+                    R a_n = fabs(num), a_d = fabs(dphi);
+                    if (bd[v] == R(0) || a_n * bd[v] < bn[v] * a_d) { bn[v] = a_n; bd[v] = a_d; }
                 }
             }
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                R a = R(1);
-                if (zero[v]) a = R(0);
-                else if (bd[v] > R(0)) a = fmin(a, (R)ip.theta * bn[v] / bd[v]);
-                alpha[v] = a;
+                // alpha = 0, or min(1, theta bn / bd)
+                const R tn = (R)ip.theta * bn[v];
+                if (zero[v]) { an[v] = R(0); lim[v] = true; }
+                else if (bd[v] > R(0) && tn < bd[v]) { an[v] = tn; ad[v] = bd[v]; lim[v] = true; }
             }
-        }
-        R lg[8];
-#pragma unroll
-        for (int c = 0; c < 8; c++) lg[c] = alpha[c >> 1] * g[c];
-        p.gl[2 * i] = Vec4<R>{lg[0], lg[1], lg[2], lg[3]};
-        p.gl[2 * i + 1] = Vec4<R>{lg[4], lg[5], lg[6], lg[7]};
-        {
-            // cell-only terms of the half-step prediction (used by every edge
-            // of the cell): rho div v, grad p / rho, gamma p div v
-            const R ldiv = lg[2] + lg[5];
-            const R irho = R(1) / Wi[0];
-            p.psrc[i] = Vec4<R>{Wi[0] * ldiv, lg[6] * irho, lg[7] * irho, (R)ip.gamma * Wi[3] * ldiv};
-        }
-        if (p.diagnostics) {
-            p.g[2 * i] = Vec4<R>{g[0], g[1], g[2], g[3]};
-            p.g[2 * i + 1] = Vec4<R>{g[4], g[5], g[6], g[7]};
-            p.alpha[i] = Vec4<R>{alpha[0], alpha[1], alpha[2], alpha[3]};
-            p.tess[i] = use_tess ? 1 : 0;
         }
         // Section 6: mesh-generating point velocity
         R wx = 0, wy = 0;
@@ -434,8 +418,55 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             }
         }
         p.w[i] = Vec2<R>{wx, wy};
-        R rx = Wi[1] - wx, ry = Wi[2] - wy;
-        dt_cell = (double)(Rad / (cs + sqrt(rx * rx + ry * ry)));
+        const R rx = Wi[1] - wx, ry = Wi[2] - wy;
+        const R speed = cs + sqrt(rx * rx + ry * ry);
+        // the cell's six quotients (alpha of each variable, 1/rho for the
+        // prediction terms, R_i over the Courant speed)
+        R alpha[4], irho, cdt;
+        R prod = R(1), pre[6], suf[6];
+        const R q[6] = {ad[0], ad[1], ad[2], ad[3], Wi[0], speed};
+        if (sizeof(R) == sizeof(double)) {
+            pre[0] = R(1);
+#pragma unroll
+            for (int k = 1; k < 6; k++) pre[k] = pre[k - 1] * q[k - 1];
+            prod = pre[5] * q[5];
+        }
+        // the product must stay well inside the FP64 exponent range
+        const int pexp = sizeof(R) == sizeof(double) ? (int)((__double_as_longlong((double)prod) >> 52) & 0x7ff) : 0;
+        if (sizeof(R) == sizeof(double) && pexp > 64 && pexp < 1983) {
+            // in FP64 from one reciprocal: 1/q_k = (prod of the others) / (prod of all)
+            suf[5] = R(1);
+#pragma unroll
+            for (int k = 4; k >= 0; k--) suf[k] = suf[k + 1] * q[k + 1];
+            const R r = R(1) / prod;
+#pragma unroll
+            for (int v = 0; v < 4; v++) alpha[v] = lim[v] ? an[v] * (pre[v] * suf[v] * r) : R(1);
+            irho = pre[4] * suf[4] * r;
+            cdt = Rad * (pre[5] * r);
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; v++) alpha[v] = lim[v] ? an[v] / ad[v] : R(1);
+            irho = R(1) / Wi[0];
+            cdt = Rad / speed;
+        }
+        R lg[8];
+#pragma unroll
+        for (int c = 0; c < 8; c++) lg[c] = alpha[c >> 1] * g[c];
+        p.gl[2 * i] = Vec4<R>{lg[0], lg[1], lg[2], lg[3]};
+        p.gl[2 * i + 1] = Vec4<R>{lg[4], lg[5], lg[6], lg[7]};
+        {
+            // cell-only terms of the half-step prediction (used by every edge
+            // of the cell): rho div v, grad p / rho, gamma p div v
+            const R ldiv = lg[2] + lg[5];
+            p.psrc[i] = Vec4<R>{Wi[0] * ldiv, lg[6] * irho, lg[7] * irho, (R)ip.gamma * Wi[3] * ldiv};
+        }
+        if (p.diagnostics) {
+            p.g[2 * i] = Vec4<R>{g[0], g[1], g[2], g[3]};
+            p.g[2 * i + 1] = Vec4<R>{g[4], g[5], g[6], g[7]};
+            p.alpha[i] = Vec4<R>{alpha[0], alpha[1], alpha[2], alpha[3]};
+            p.tess[i] = use_tess ? 1 : 0;
+        }
+        dt_cell = (double)cdt;
     }
     return dt_cell;
 }
