@@ -141,7 +141,10 @@ template <class R> __device__ __forceinline__ void stage_edge_geometry(const Swe
     // the edge vector from the FP64 endpoints: a zero-length edge stays ~0
     // instead of inheriting the rounding of two separately rounded endpoints
     R ex = (R)(bx64 - ax64), ey = (R)(by64 - ay64);
-    R L = sqrt(ex * ex + ey * ey);
+    // |e| = e^2 / sqrt(e^2) with one reciprocal square root (zero-length
+    // edges, from co-circular generators, stay exactly zero)
+    const R e2 = ex * ex + ey * ey;
+    R L = nonneg_less(R(0), e2) ? e2 * rsqrt(e2) : R(0);
     R mx = R(0.5) * (ax + bx), my = R(0.5) * (ay + by);
     // 1/|r_ij| with one reciprocal square root (a divide and a square root
     // each cost several FP64 issue slots on this part)
@@ -499,11 +502,11 @@ template <class R>
 __device__ __forceinline__ void predict(R hdt, const R W[4], const R g[8], const R src[4], R offx, R offy, R wfx,
                                         R wfy, R out[4])
 {
-    R ux = W[1] - wfx, uy = W[2] - wfy;
-    out[0] = W[0] + g[0] * offx + g[1] * offy - hdt * (ux * g[0] + uy * g[1] + src[0]);
-    out[1] = W[1] + g[2] * offx + g[3] * offy - hdt * (ux * g[2] + uy * g[3] + src[1]);
-    out[2] = W[2] + g[4] * offx + g[5] * offy - hdt * (ux * g[4] + uy * g[5] + src[2]);
-    out[3] = W[3] + g[6] * offx + g[7] * offy - hdt * (ux * g[6] + uy * g[7] + src[3]);
+    // phi + g.off - hdt (u.g + src) = phi + g.(off - hdt u) - hdt src: the
+    // advective part of the prediction moves the extrapolation point
+    const R ax = offx - hdt * (W[1] - wfx), ay = offy - hdt * (W[2] - wfy);
+#pragma unroll
+    for (int c = 0; c < 4; c++) out[c] = W[c] + g[2 * c] * ax + g[2 * c + 1] * ay - hdt * src[c];
 }
 
 // HLLC (Toro) in the edge frame, states (rho, u_n, u_t, p)
