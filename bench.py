@@ -74,7 +74,7 @@ FLOPS = {
 # the command and the raw counters), scaled to a launch by its units.  Set
 # to None whenever the kernel changes after the capture.
 TRAFFIC_PER_UNIT = {
-    "fp64": {"k_edge_flux": None},       # profiles/k_edge_flux_fp64_sedov262k.md
+    "fp64": {"k_edge_flux": 146.2},      # profiles/k_edge_flux_fp64_sedov262k.md
     "split": {"k_cell_geometry": 113.5},  # profiles/k_cell_geometry_split_sedov262k.md
 }
 

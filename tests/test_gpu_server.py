@@ -92,3 +92,33 @@ def test_server_fifo_admission_and_oversize_reject(R):
     with pytest.raises(R.RichError):
         srv.submit(W.sod(n_side=40, seed=3), max_steps=1)  # 1600 cells > budget
     srv.close()
+
+
+def test_server_isolates_a_failing_request(R):
+    """A request whose simulation fails (the Sedov blast with 16,384 points
+    empties a cell at step 21: the scheme has no floor) ends as 'failed'
+    with RICH_ENEGATIVE and its last good state; the requests sharing its
+    ticks finish and equal their solo runs."""
+    srv = R.Server(max_cells=1 << 20)
+    crash = W.sedov(n=16384, seed=2)
+    others = [W.sod(n_side=16, seed=7), W.gresho(n_side=14, seed=8)]
+    rc = srv.submit(crash, max_steps=40)
+    ro = [srv.submit(wl, max_steps=30) for wl in others]
+    for _ in range(60):
+        srv.tick()
+        if all(srv.query(r)["state"] in ("done", "failed") for r in [rc] + ro):
+            break
+    q = srv.query(rc)
+    assert q["state"] == "failed" and q["error"] == R.RICH_ENEGATIVE, q
+    assert q["steps"] == 20, q
+    got = srv.fetch(rc)
+    ref = solo(R, crash, 20)
+    for f in ref:
+        assert np.array_equal(got[f], ref[f]), f
+    for rid, wl in zip(ro, others):
+        assert srv.query(rid)["state"] == "done"
+        got = srv.fetch(rid)
+        ref = solo(R, wl, 30)
+        for f in ref:
+            assert np.array_equal(got[f], ref[f]), f
+    srv.close()
