@@ -68,6 +68,13 @@ __device__ __forceinline__ long long dkey(double v)
     const long long b = __double_as_longlong(v);
     return b ^ ((b >> 63) & 0x7fffffffffffffffll);
 }
+// dkey with -0.0 taken as +0.0 (the only key of -1), so that the integer
+// order matches the comparisons of doubles exactly
+__device__ __forceinline__ long long dkey0(double v)
+{
+    const long long k = dkey(v);
+    return k == -1 ? 0 : k;
+}
 __device__ __forceinline__ double dunkey(long long k)
 {
     return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
@@ -653,24 +660,36 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
     p.Un[n + i] = Px;
     p.Un[2 * n + i] = Py;
     p.Un[3 * n + i] = E;
+    // the checks and the box tests compare bit patterns on the integer pipe:
+    // a double is not finite when its exponent bits are all set, positive
+    // when its bits are positive as an integer, and dkey orders doubles
     int32_t st = 0;
-    if (!(isfinite(m) && isfinite(Px) && isfinite(Py) && isfinite(E))) st |= ST_NAN;
-    else if (!(m > 0.0) || !(2.0 * m * E - (Px * Px + Py * Py) > 0.0)) st |= ST_NEGATIVE;
+    {
+        const long long bm = __double_as_longlong(m), bx = __double_as_longlong(Px);
+        const long long by = __double_as_longlong(Py), be = __double_as_longlong(E);
+        const long long ex = 0x7ff0000000000000ll;
+        if ((bm & ex) == ex || (bx & ex) == ex || (by & ex) == ex || (be & ex) == ex) st |= ST_NAN;
+        else if (!(bm > 0) || !(__double_as_longlong(2.0 * m * E - (Px * Px + Py * Py)) > 0)) st |= ST_NEGATIVE;
+    }
     const Vec2<R> w = p.w[i];
     double xn = p.x0[i] + hdt * (double)w.x, yn = p.y0[i] + hdt * (double)w.y;
+    const long long kx0 = dkey0(ip.x0), kx1 = dkey0(ip.x1), ky0 = dkey0(ip.y0), ky1 = dkey0(ip.y1);
+    long long kx = dkey0(xn), ky = dkey0(yn);
     if (ip.boundary == 1) {
         const double Lx = ip.x1 - ip.x0, Ly = ip.y1 - ip.y0;
-        if (xn < ip.x0) xn += Lx;
-        else if (xn >= ip.x1) xn -= Lx;
-        if (yn < ip.y0) yn += Ly;
-        else if (yn >= ip.y1) yn -= Ly;
+        if (kx < kx0) xn += Lx;
+        else if (kx >= kx1) xn -= Lx;
+        if (ky < ky0) yn += Ly;
+        else if (ky >= ky1) yn -= Ly;
     } else {
         // a point that crossed a rigid wall comes back as its mirror image
-        if (xn <= ip.x0) xn = (ip.x0 + ip.x0) - xn;
-        else if (xn >= ip.x1) xn = (ip.x1 + ip.x1) - xn;
-        if (yn <= ip.y0) yn = (ip.y0 + ip.y0) - yn;
-        else if (yn >= ip.y1) yn = (ip.y1 + ip.y1) - yn;
-        if (!(xn > ip.x0 && xn < ip.x1 && yn > ip.y0 && yn < ip.y1)) st |= ST_LEFT_BOX;
+        if (kx <= kx0) xn = (ip.x0 + ip.x0) - xn;
+        else if (kx >= kx1) xn = (ip.x1 + ip.x1) - xn;
+        if (ky <= ky0) yn = (ip.y0 + ip.y0) - yn;
+        else if (ky >= ky1) yn = (ip.y1 + ip.y1) - yn;
+        kx = dkey0(xn);
+        ky = dkey0(yn);
+        if (!(kx > kx0 && kx < kx1 && ky > ky0 && ky < ky1)) st |= ST_LEFT_BOX;
     }
     p.xn[i] = xn;
     p.yn[i] = yn;
