@@ -4,6 +4,7 @@
 #include "mesh.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 
@@ -404,15 +405,20 @@ void build_slab(int32_t n, int32_t np, const double *X, const double *Y, const d
     r.rc = dt.build(LX.data(), LY.data(), nl);
     if (r.rc) return;
     const std::vector<Tri> &T = dt.tris;
-    auto core_real = [&](int32_t v) {
-        if (v >= nl || loc[v] >= n) return false;
-        const double px = X[loc[v]], py = Y[loc[v]];
-        return (tile.fx || px >= tile.x0) && (tile.lx || px < tile.x1) && (tile.fy || py >= tile.y0) &&
-               (tile.ly || py < tile.y1);
-    };
+    // real points of the tile itself (the corners of the enclosing triangle,
+    // nl..nl+2, are not)
+    std::vector<uint8_t> core(nl + 3, 0);
+    int32_t ncore = 0;
+    for (int32_t v = 0; v < nl; v++) {
+        const double px = LX[v], py = LY[v];
+        core[v] = loc[v] < n && (tile.fx || px >= tile.x0) && (tile.lx || px < tile.x1) &&
+                  (tile.fy || py >= tile.y0) && (tile.ly || py < tile.y1);
+        ncore += core[v];
+    }
+    auto core_real = [&](int32_t v) { return core[v] != 0; };
     // the stars of the real core points: check, number, and find one
     // triangle incident to each such point
-    std::vector<int32_t> tnum(T.size(), -1), vtri(nl, -1);
+    std::vector<int32_t> tnum(T.size(), -1);
     int32_t nt = 0;
     for (size_t t = 0; t < T.size(); t++) {
         const int32_t *v = T[t].v;
@@ -439,8 +445,6 @@ void build_slab(int32_t n, int32_t np, const double *X, const double *Y, const d
         if (!tile.fy) r.needed = std::max(r.needed, tile.y0 - (D.uy - D.R));
         if (!tile.ly) r.needed = std::max(r.needed, D.uy + D.R - tile.y1);
         tnum[t] = nt++;
-        for (int k = 0; k < 3; k++)
-            if (core_real(v[k])) vtri[v[k]] = (int32_t)t;
     }
     // triangles with global ids, rotated so that the smallest id comes first
     // (a shared triangle then gives the same circumcentre in every slab)
@@ -452,35 +456,67 @@ void build_slab(int32_t n, int32_t np, const double *X, const double *Y, const d
         int32_t gg[3] = {g0, g1, g2};
         for (int k = 0; k < 3; k++) r.tris[3 * (size_t)tnum[t] + k] = gg[(rot + k) % 3];
     }
-    // rings, counter-clockwise, starting at the smallest neighbour id
-    std::vector<std::pair<int32_t, int32_t>> ring;
+    // rings, counter-clockwise, starting at the smallest neighbour id.  The
+    // triangles are bucketed by core vertex in one pass over the triangle
+    // array (walking each star through the neighbour links jumps across the
+    // whole array); in the bucket of v, triangle (v, a, b) is followed by the
+    // one whose a is this b.
+    std::vector<int32_t> cnt(nl + 1, 0);
+    for (size_t t = 0; t < T.size(); t++) {
+        if (tnum[t] < 0) continue;
+        for (int k = 0; k < 3; k++)
+            if (core_real(T[t].v[k])) cnt[T[t].v[k] + 1]++;
+    }
+    for (int32_t v = 0; v < nl; v++) cnt[v + 1] += cnt[v];
+    std::vector<int32_t> ba(cnt[nl]), bb(cnt[nl]), bt(cnt[nl]), fillp(cnt.begin(), cnt.end() - 1);
+    for (size_t t = 0; t < T.size(); t++) {
+        if (tnum[t] < 0) continue;
+        const int32_t *tv = T[t].v;
+        for (int k = 0; k < 3; k++) {
+            if (!core_real(tv[k])) continue;
+            const int32_t q = fillp[tv[k]]++;
+            ba[q] = tv[(k + 1) % 3];
+            bb[q] = tv[(k + 2) % 3];
+            bt[q] = tnum[t];
+        }
+    }
+    r.cells.reserve(ncore);
+    r.deg.reserve(ncore);
+    r.nb.reserve(cnt[nl]);
+    r.tri.reserve(cnt[nl]);
     for (int32_t v = 0; v < nl; v++) {
         if (!core_real(v)) continue;
-        if (vtri[v] < 0) {
+        const int32_t lo = cnt[v], deg = cnt[v + 1] - lo;
+        if (deg < 3) {
             r.rc = -3;
             return;
         }
-        ring.clear();
-        int32_t t = vtri[v], t0 = t;
-        int guard = 0;
-        do {
-            const Tri &tr = T[t];
-            int k = tr.v[0] == v ? 0 : (tr.v[1] == v ? 1 : 2);
-            ring.emplace_back(loc[tr.v[(k + 1) % 3]], tnum[t]);
-            t = tr.nb[(k + 1) % 3];
-            if (t < 0 || tnum[t] < 0 || ++guard > 4096) {
-                r.rc = -3;
+        // start at the smallest neighbour id, then follow b -> a
+        int32_t k = lo;
+        for (int32_t q = lo + 1; q < lo + deg; q++)
+            if (loc[ba[q]] < loc[ba[k]]) k = q;
+        const int32_t start = k;
+        r.cells.push_back(loc[v]);
+        r.deg.push_back(deg);
+        for (int32_t j = 0; j < deg; j++) {
+            r.nb.push_back(loc[ba[k]]);
+            r.tri.push_back(bt[k]);
+            const int32_t want = bb[k];
+            int32_t nxt = -1;
+            for (int32_t q = lo; q < lo + deg; q++)
+                if (ba[q] == want) {
+                    nxt = q;
+                    break;
+                }
+            if (nxt < 0) {
+                r.rc = -3;  // the star is not closed
                 return;
             }
-        } while (t != t0);
-        size_t k0 = 0;
-        for (size_t k = 1; k < ring.size(); k++)
-            if (ring[k].first < ring[k0].first) k0 = k;
-        r.cells.push_back(loc[v]);
-        r.deg.push_back((int32_t)ring.size());
-        for (size_t k = 0; k < ring.size(); k++) {
-            r.nb.push_back(ring[(k0 + k) % ring.size()].first);
-            r.tri.push_back(ring[(k0 + k) % ring.size()].second);
+            k = nxt;
+        }
+        if (k != start) {
+            r.rc = -3;  // the star is not one cycle
+            return;
         }
     }
     // cells were visited in local order, which follows the global order
@@ -522,12 +558,31 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         std::memcpy(X.data() + n, m.gx.data(), sizeof(double) * m.g);
         std::memcpy(Y.data() + n, m.gy.data(), sizeof(double) * m.g);
         const double band[4] = {box.x0 - w, box.x1 + w, box.y0 - w, box.y1 + w};
+        // bounding box of all points, in chunks
         double ext[4] = {X[0], X[0], Y[0], Y[0]};
-        for (int32_t q = 1; q < np; q++) {
-            ext[0] = std::min(ext[0], X[q]);
-            ext[1] = std::max(ext[1], X[q]);
-            ext[2] = std::min(ext[2], Y[q]);
-            ext[3] = std::max(ext[3], Y[q]);
+        {
+            const int64_t ec = 65536, nec = (np + ec - 1) / ec;
+            std::vector<std::array<double, 4>> part(nec);
+            auto bbox = [&](int64_t c) {
+                const int32_t q0 = (int32_t)(c * ec), q1 = (int32_t)std::min<int64_t>(np, (c + 1) * ec);
+                std::array<double, 4> b = {X[q0], X[q0], Y[q0], Y[q0]};
+                for (int32_t q = q0 + 1; q < q1; q++) {
+                    b[0] = std::min(b[0], X[q]);
+                    b[1] = std::max(b[1], X[q]);
+                    b[2] = std::min(b[2], Y[q]);
+                    b[3] = std::max(b[3], Y[q]);
+                }
+                part[c] = b;
+            };
+            if (pool && nec > 1) pool->parallel_for(nec, bbox);
+            else
+                for (int64_t c = 0; c < nec; c++) bbox(c);
+            for (const auto &b : part) {
+                ext[0] = std::min(ext[0], b[0]);
+                ext[1] = std::max(ext[1], b[1]);
+                ext[2] = std::min(ext[2], b[2]);
+                ext[3] = std::max(ext[3], b[3]);
+            }
         }
         // column cuts at x-quantiles of (a sample of) the real + ghost
         // points, then row cuts at y-quantiles within each column
@@ -614,17 +669,20 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     for (int s = 0; s < K; s++) toff[s + 1] = toff[s] + (int64_t)res[s].tris.size() / 3;
     m.tri.resize(3 * (size_t)toff[K]);
     // ring offsets
+    // (tiles own disjoint cells: each writes its own cells' degrees; a cell
+    // no tile wrote keeps degree 0 and fails the check)
     m.cell_ptr.assign(n + 1, 0);
-    std::vector<int32_t> owner(n, -1);
-    for (int s = 0; s < K; s++)
-        for (size_t k = 0; k < res[s].cells.size(); k++) {
-            const int32_t i = res[s].cells[k];
-            if (owner[i] >= 0) return -3;
-            owner[i] = s;
-            m.cell_ptr[i + 1] = res[s].deg[k];
-        }
+    auto degs = [&](int64_t s) {
+        for (size_t k = 0; k < res[s].cells.size(); k++) m.cell_ptr[res[s].cells[k] + 1] = res[s].deg[k];
+    };
+    if (pool && K > 1) pool->parallel_for(K, degs);
+    else
+        for (int s = 0; s < K; s++) degs(s);
+    size_t owned = 0;
+    for (int s = 0; s < K; s++) owned += res[s].cells.size();
+    if (owned != (size_t)n) return -3;
     for (int32_t i = 0; i < n; i++) {
-        if (owner[i] < 0) return -3;
+        if (m.cell_ptr[i + 1] < 3) return -3;
         m.cell_ptr[i + 1] += m.cell_ptr[i];
     }
     const size_t S = (size_t)m.cell_ptr[n];
@@ -658,6 +716,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         return (sy < 0 || (sy == 0 && sx < 0)) ? 0 : 1;
     };
     const int64_t chunk = 8192;
+    static_assert(8192 % kOrderWindow == 0, "ordering windows must not straddle chunks");
     const int64_t nchunks = (n + chunk - 1) / chunk;
     std::vector<int64_t> ecount(nchunks + 1, 0);
     std::vector<int> bad(nchunks, 0);
@@ -724,10 +783,22 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     if (pool) pool->parallel_for(nchunks, place);
     else
         for (int64_t c = 0; c < nchunks; c++) place(c);
-    for (size_t s = 0; s < S; s++)
-        if (m.slot_edge[s] < 0) return -3;
+    // every slot has its edge; the processing order, one window per task
+    std::vector<int> missing(nchunks, 0);
     m.cell_order.resize(n);
-    degree_order(n, m.cell_ptr.data(), m.cell_order.data());
+    auto finish = [&](int64_t c) {
+        const int32_t i0 = (int32_t)(c * chunk), i1 = (int32_t)std::min<int64_t>(n, (c + 1) * chunk);
+        for (int32_t s = m.cell_ptr[i0]; s < m.cell_ptr[i1]; s++)
+            if (m.slot_edge[s] < 0) missing[c] = 1;
+        // chunk is a multiple of kOrderWindow: windows never straddle chunks
+        degree_order(i1 - i0, m.cell_ptr.data() + i0, m.cell_order.data() + i0);
+        for (int32_t i = i0; i < i1; i++) m.cell_order[i] += i0;
+    };
+    if (pool) pool->parallel_for(nchunks, finish);
+    else
+        for (int64_t c = 0; c < nchunks; c++) finish(c);
+    for (int64_t c = 0; c < nchunks; c++)
+        if (missing[c]) return -3;
     return 0;
 }
 

@@ -75,8 +75,7 @@ private:
     void set_nb(int32_t t, int32_t old_nb, int32_t new_nb);
 
     std::vector<double> px_, py_;
-    std::vector<uint32_t> keys_, tmpk_;
-    std::vector<int32_t> order_, tmpo_;
+    std::vector<int32_t> order_;
     std::vector<int32_t> stack_;
     int32_t hint_ = 0;
     uint32_t rng_ = 12345u;
