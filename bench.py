@@ -77,6 +77,12 @@ TRAFFIC_PER_UNIT = {
     "fp64": {"k_edge_flux": 146.2},      # profiles/k_edge_flux_fp64_sedov262k.md
     "split": {"k_cell_geometry": 113.5},  # profiles/k_cell_geometry_split_sedov262k.md
 }
+# The same captures' sm__pipe_fp64_cycles_active (fraction of peak while the
+# SMs are active): how busy the bounding pipe is, whatever the op mix.
+PIPE_ACTIVE = {
+    "fp64": {"k_edge_flux": 0.887},
+    "split": {"k_cell_geometry": 0.809},
+}
 
 
 def hbm_peak():
@@ -191,8 +197,10 @@ def roofline_of(prec, kern_means, units, sweep_ms):
     cells_per_s = units["cell"] / (sweep_ms / 1e3)
     per_unit = TRAFFIC_PER_UNIT.get(prec, {}).get(dom)
     traffic = per_unit * units[FLOPS[prec][dom][1]] if per_unit is not None else None
+    pipe_active = PIPE_ACTIVE.get(prec, {}).get(dom)
     return {"bound": "alu", "pipe": pipe, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+            "pipe_active_ncu": pipe_active,
             "peak_source": ("derived: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz" if pipe == "fp64"
                             else "derived: 152 SMs x 128 FP32 FMA lanes/clk x 2 flop x 2.07 GHz"),
             "sweep_fp64_tflops": tot["fp64"] / (sweep_ms / 1e3) / 1e12,
