@@ -151,3 +151,57 @@ def test_init_without_gpu_fails_loudly(R):
     with pytest.raises(R.RichError) as e:
         R.Sim(wl)
     assert e.value.code in (-9, -8)
+
+
+def _init(R, wl, **over):
+    """rich_init_mesh on a workload with fields replaced; returns the code."""
+    d = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in wl.items()}
+    d["cfg"] = dict(wl["cfg"])
+    cfg_fields = {name for name, _ in R.rich_config._fields_}
+    for k, v in over.items():
+        if k in cfg_fields:
+            d["cfg"][k] = v
+        else:
+            d[k] = v
+    try:
+        R.Sim(d).close()
+        return 0
+    except R.RichError as e:
+        return e.code
+
+
+@pytest.mark.parametrize("case", ["too_few", "nan_point", "outside_box", "on_wall", "zero_density",
+                                  "negative_pressure", "nan_velocity", "gamma_one", "bad_scheme",
+                                  "bad_precision", "bad_limiter", "negative_eta"])
+def test_init_rejects_bad_input_before_any_device_call(R, case):
+    """Argument checks come first (RICH_EINVAL), so they hold with or without
+    a GPU; a valid input then reaches the device check."""
+    wl = W.sod(n_side=8)
+    x, y = wl["x"].copy(), wl["y"].copy()
+    over = {
+        "too_few": dict(x=x[:2], y=y[:2], rho=wl["rho"][:2], vx=wl["vx"][:2], vy=wl["vy"][:2], p=wl["p"][:2]),
+        "nan_point": dict(x=np.where(np.arange(len(x)) == 5, np.nan, x)),
+        "outside_box": dict(x=np.where(np.arange(len(x)) == 5, 1.5, x)),
+        "on_wall": dict(x=np.where(np.arange(len(x)) == 5, 0.0, x)),  # rigid walls: strictly inside
+        "zero_density": dict(rho=np.where(np.arange(len(x)) == 3, 0.0, wl["rho"])),
+        "negative_pressure": dict(p=np.where(np.arange(len(x)) == 3, -1.0, wl["p"])),
+        "nan_velocity": dict(vx=np.where(np.arange(len(x)) == 3, np.nan, wl["vx"])),
+        "gamma_one": dict(gamma=1.0),
+        "bad_scheme": dict(scheme=7),
+        "bad_precision": dict(precision=5),
+        "bad_limiter": dict(limiter=9),
+        "negative_eta": dict(eta=-0.1),
+    }[case]
+    assert _init(R, wl, **over) == R.RICH_EINVAL
+
+
+def test_restart_rejects_a_non_permutation_order_on_the_host(R):
+    wl = W.sod(n_side=8)
+    n = len(wl["x"])
+    m = np.full(n, 1.0 / n)
+    E = np.full(n, 2.5 / n)
+    z = np.zeros(n)
+    with pytest.raises(R.RichError) as e:
+        R.rich_init_conserved(wl["cfg"], wl["x"], wl["y"], m, z, z, E, 0.0, np.zeros(n, np.int64))
+    # the order is checked once a device exists; without one the device check fails first
+    assert e.value.code in (R.RICH_EINVAL, R.RICH_ENODEV)
