@@ -49,13 +49,24 @@ template <class R> __device__ __forceinline__ int32_t src_of(const SweepParams<R
 }
 
 // primitives of point q (a ghost mirrors the velocity of its source)
+// v with its sign flipped where the mask has the sign bit (a mirror image's
+// component), on the integer pipe instead of a multiply by -1 or 1
+__device__ __forceinline__ double flip(double v, unsigned long long m)
+{
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)m);
+}
+__device__ __forceinline__ float flip(float v, unsigned long long m)
+{
+    return __int_as_float(__float_as_int(v) ^ (int)(unsigned)(m >> 32));
+}
+
 template <class R> __device__ __forceinline__ Vec4<R> load_W(const SweepParams<R> &p, int32_t q)
 {
     int32_t xf;
     int32_t k = src_of(p, q, xf);
     Vec4<R> W = p.W[k];
-    if (xf & 1) W.y = -W.y;
-    if (xf & 2) W.z = -W.z;
+    W.y = flip(W.y, (xf & 1) ? 0x8000000000000000ull : 0ull);
+    W.z = flip(W.z, (xf & 2) ? 0x8000000000000000ull : 0ull);
     return W;
 }
 
@@ -298,9 +309,11 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             const R L = p.eL[e];
             const Vec4<R> pm = p.ePM[e];
             // Eq. 1: g_i A_i = sum_j phi_j P_ij + phi_i sum_j M_ij
-            const R Ax = (es & 1) ? -pm.z : pm.x, Ay = (es & 1) ? -pm.w : pm.y;
-            Bx += (es & 1) ? -pm.x : pm.z;
-            By += (es & 1) ? -pm.y : pm.w;
+            // the right cell of an edge takes -M, -P (sign flips on the integer pipe)
+            const unsigned long long ms = (es & 1) ? 0x8000000000000000ull : 0ull;
+            const R Ax = flip((es & 1) ? pm.z : pm.x, ms), Ay = flip((es & 1) ? pm.w : pm.y, ms);
+            Bx += flip((es & 1) ? pm.x : pm.z, ms);
+            By += flip((es & 1) ? pm.y : pm.w, ms);
             const Vec4<R> Wv = load_W(p, p.slot_nb[s]);
             const R Wj[4] = {Wv.x, Wv.y, Wv.z, Wv.w};
 #pragma unroll
@@ -573,22 +586,25 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
     const R hdt = p.inst[li].phase == 0 ? R(0.5) * (R)step_dt(p, li) : R(0);
     int32_t xf;
     const int32_t k = src_of(p, p.edge_r[e], xf);
-    const R sx = (xf & 1) ? R(-1) : R(1), sy = (xf & 2) ? R(-1) : R(1);
+    // sign masks of a mirror image across an x wall, a y wall, and both
+    const unsigned long long mx = (xf & 1) ? 0x8000000000000000ull : 0ull;
+    const unsigned long long my = (xf & 2) ? 0x8000000000000000ull : 0ull;
+    const unsigned long long mxy = mx ^ my;
     const Vec4<R> Wl4 = p.W[l], Wr4 = p.W[k];
     const R Wl[4] = {Wl4.x, Wl4.y, Wl4.z, Wl4.w};
-    const R Wr[4] = {Wr4.x, sx * Wr4.y, sy * Wr4.z, Wr4.w};
+    const R Wr[4] = {Wr4.x, flip(Wr4.y, mx), flip(Wr4.z, my), Wr4.w};
     const Vec4<R> gl0 = p.gl[2 * l], gl1 = p.gl[2 * l + 1];
     const Vec4<R> gr0 = p.gl[2 * k], gr1 = p.gl[2 * k + 1];
     const R gL[8] = {gl0.x, gl0.y, gl0.z, gl0.w, gl1.x, gl1.y, gl1.z, gl1.w};
     // mirrored source: each derivative takes the flip of its axis, velocity
     // components also the flip of their own axis
-    const R gR[8] = {sx * gr0.x, sy * gr0.y, gr0.z, sx * sy * gr0.w,
-                     sx * sy * gr1.x, gr1.y, sx * gr1.z, sy * gr1.w};
+    const R gR[8] = {flip(gr0.x, mx), flip(gr0.y, my), gr0.z, flip(gr0.w, mxy),
+                     flip(gr1.x, mxy), gr1.y, flip(gr1.z, mx), flip(gr1.w, my)};
     const Vec2<R> wl = p.w[l], wk = p.w[k];
     const Vec2<R> ol = p.o[l], ok = p.o[k];
     const R wlx = wl.x, wly = wl.y;
-    const R wrx = sx * wk.x, wry = sy * wk.y;
-    const R orx = sx * ok.x, ory = sy * ok.y;
+    const R wrx = flip(wk.x, mx), wry = flip(wk.y, my);
+    const R orx = flip(ok.x, mx), ory = flip(ok.y, my);
     const R L = p.eL[e];
     const R nx = p.enx[e], ny = p.eny[e];
     const R qx = p.eqx[e], qy = p.eqy[e];
@@ -600,7 +616,8 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
     const R gam = (R)p.inst[li].gamma;
     const Vec4<R> sl4 = p.psrc[l], sr4 = p.psrc[k];
     // a mirrored source flips the pressure-gradient term of its axis
-    const R srcL[4] = {sl4.x, sl4.y, sl4.z, sl4.w}, srcR[4] = {sr4.x, sx * sr4.y, sy * sr4.z, sr4.w};
+    const R srcL[4] = {sl4.x, sl4.y, sl4.z, sl4.w};
+    const R srcR[4] = {sr4.x, flip(sr4.y, mx), flip(sr4.z, my), sr4.w};
     predict(hdt, Wl, gL, srcL, p.emlx[e] - ol.x, p.emly[e] - ol.y, wfx, wfy, Sl);
     predict(hdt, Wr, gR, srcR, p.emrx[e] - orx, p.emry[e] - ory, wfx, wfy, Sr);
     const R tx = -ny, ty = nx;
