@@ -124,6 +124,16 @@ template <> struct Extremes<float> {
 // a < b for non-negative values (bit patterns of non-negative doubles order
 // like the values)
 __device__ __forceinline__ bool nonneg_less(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+// a < b for any non-NaN values, through order-preserving integer keys (-0.0
+// and +0.0 equal), and the sign tests x >= 0 and x <= 0 likewise
+__device__ __forceinline__ long long okey(double v) { return dkey0(v); }
+__device__ __forceinline__ bool key_less(double a, double b) { return okey(a) < okey(b); }
+__device__ __forceinline__ bool key_nonneg(double a) { return okey(a) >= 0; }
+__device__ __forceinline__ bool key_nonpos(double a) { return okey(a) <= 0; }
+// FP32 compares are cheap on their own pipe and give the same answers
+__device__ __forceinline__ bool key_less(float a, float b) { return a < b; }
+__device__ __forceinline__ bool key_nonneg(float a) { return a >= 0.0f; }
+__device__ __forceinline__ bool key_nonpos(float a) { return a <= 0.0f; }
 __device__ __forceinline__ bool nonneg_less(float a, float b) { return a < b; }
 
 // ---------------------------------------------------------------------------
@@ -221,7 +231,7 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
     // FP64 in every precision.
     {
         const double eta = p.inst[inst_of(p, i)].eta;
-        p.rounding[i] = ox * ox + oy * oy > (eta * eta) * (A * (1.0 / M_PI)) ? 1 : 0;
+        p.rounding[i] = nonneg_less((eta * eta) * (A * (1.0 / M_PI)), ox * ox + oy * oy) ? 1 : 0;
     }
     const int32_t n = p.n;
     const InstParams &ip = p.inst[inst_of(p, i)];
@@ -357,7 +367,8 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
         for (int c = 0; c < 8; c++) g[c] = acc[c] * invA;
         const R cs = p.cs[i];
         const R Rad = Api * rR;
-        if (-(g[2] + g[5]) * Rad > (R)ip.delta_v * cs) shock = true;
+        // Eq. 7: -div v > delta_v c_s / R_i, as (delta_v c_s) < -(div v) R_i
+        if (key_less((R)ip.delta_v * cs, flip((g[2] + g[5]) * Rad, 0x8000000000000000ull))) shock = true;
         const bool use_tess = ip.limiter == 2 || (ip.limiter == 0 && shock);
         const Vec2<R> oi = p.o[i];
         const R ox = oi.x, oy = oi.y;
@@ -538,22 +549,23 @@ template <class R> __device__ __forceinline__ void hllc(R gam, R igm1, const R L
     // square root instead of a divide and a square root
     const R gpL = gam * pL, gpR = gam * pR;
     const R cL = gpL * rsqrt(gpL * rL), cR = gpR * rsqrt(gpR * rR);
-    const R EL = pL * igm1 + R(0.5) * rL * (uL * uL + tL * tL);
-    const R ER = pR * igm1 + R(0.5) * rR * (uR * uR + tR * tR);
-    const R SL = fmin(uL - cL, uR - cR);
-    const R SR = fmax(uL + cL, uR + cR);
+    // Davis speeds, min / max chosen through integer keys
+    const R aL = uL - cL, aR = uR - cR, bL = uL + cL, bR = uR + cR;
+    const R SL = key_less(aR, aL) ? aR : aL;
+    const R SR = key_less(bL, bR) ? bR : bL;
     // The flux is that of one side K plus, between the outer waves,
     // S_K (U*_K - U_K).  K is picked by selects rather than branches, so a
     // warp whose edges take different sides evaluates one star state, not two.
-    const bool supL = SL >= R(0), supR = !supL && SR <= R(0);
+    const bool supL = key_nonneg(SL), supR = !supL && key_nonpos(SR);
     const bool sub = !(supL || supR);
     // m_K = rho_K (S_K - u_K): m_L < 0 < m_R, so the contact speed
     // S* = num / den has den = m_L - m_R < 0 and S* >= 0 exactly when num <= 0
     const R mL = rL * (SL - uL), mR = rR * (SR - uR);
     const R num = pR - pL + uL * mL - uR * mR, den = mL - mR;
-    const bool useL = supL || (sub && num <= R(0));
+    const bool useL = supL || (sub && key_nonpos(num));
     const R rK = useL ? rL : rR, uK = useL ? uL : uR, tK = useL ? tL : tR, pK = useL ? pL : pR;
-    const R EK = useL ? EL : ER;
+    // only side K's total energy enters the flux
+    const R EK = pK * igm1 + R(0.5) * rK * (uK * uK + tK * tK);
     const R ruK = rK * uK;
     F[0] = ruK;
     F[1] = ruK * uK + pK;
