@@ -75,13 +75,13 @@ FLOPS = {
 # the command and the raw counters), scaled to a launch by its units.  Set
 # to None whenever the kernel changes after the capture.
 TRAFFIC_PER_UNIT = {
-    "fp64": {"k_edge_flux": 146.2},      # profiles/k_edge_flux_fp64_sedov262k.md
+    "fp64": {"k_edge_flux": 145.9},      # profiles/k_edge_flux_fp64_sedov262k.md
     "split": {"k_cell_geometry": None},   # profiles/k_cell_geometry_split_sedov262k.md
 }
 # The same captures' sm__pipe_fp64_cycles_active (fraction of peak while the
 # SMs are active): how busy the bounding pipe is, whatever the op mix.
 PIPE_ACTIVE = {
-    "fp64": {"k_edge_flux": 0.891},
+    "fp64": {"k_edge_flux": 0.889},
     "split": {"k_cell_geometry": None},
 }
 

@@ -34,13 +34,13 @@ template <class R> __device__ __forceinline__ int32_t inst_of(const SweepParams<
     return p.cell_inst ? p.cell_inst[i] : 0;
 }
 
-// real cell behind point q and its mirror flags
 // cell handled by thread k of a per-cell stage
 template <class R> __device__ __forceinline__ int32_t cell_at(const SweepParams<R> &p, int32_t k)
 {
     return p.cell_order ? __ldg(p.cell_order + k) : k;
 }
 
+// real cell behind point q and its mirror flags
 template <class R> __device__ __forceinline__ int32_t src_of(const SweepParams<R> &p, int32_t q, int32_t &xf)
 {
     if (q < p.n) { xf = 0; return q; }
@@ -48,7 +48,6 @@ template <class R> __device__ __forceinline__ int32_t src_of(const SweepParams<R
     return p.ghost_src[q - p.n];
 }
 
-// primitives of point q (a ghost mirrors the velocity of its source)
 // v with its sign flipped where the mask has the sign bit (a mirror image's
 // component), on the integer pipe instead of a multiply by -1 or 1
 __device__ __forceinline__ double flip(double v, unsigned long long m)
@@ -59,6 +58,31 @@ __device__ __forceinline__ float flip(float v, unsigned long long m)
 {
     return __int_as_float(__float_as_int(v) ^ (int)(unsigned)(m >> 32));
 }
+
+// 1/x for a normal x with |x| in [2^-1021, 2^1020): the hardware's
+// approximate reciprocal y (about 20 correct bits, issued outside the FP64
+// pipe) refined by the geometric series 1/x = y / (1 - e) ~ y (1 + e + e^2),
+// e = 1 - x y: three FMAs, relative error O(e^3) plus rounding, so within
+// one ulp of the correctly rounded quotient, where IEEE division costs
+// about 4.5 FP64 issue slots.  Other arguments take the IEEE division.
+__device__ __forceinline__ double recip(double x)
+{
+    const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+    if (ex - 2u > 2040u) return 1.0 / x;
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = fma(-x, y, 1.0);
+    return fma(fma(e, e, e), y, y);
+}
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+
+// sqrt(x) for x >= 0 as x / sqrt(x) through one reciprocal square root
+// (about 5.8 FP64 issue slots against 7.4 for the rounded square root)
+__device__ __forceinline__ double sqrt_nonneg(double x)
+{
+    return __double_as_longlong(x) > 0 ? x * rsqrt(x) : 0.0;
+}
+__device__ __forceinline__ float sqrt_nonneg(float x) { return sqrtf(x); }
 
 template <class R> __device__ __forceinline__ Vec4<R> load_W(const SweepParams<R> &p, int32_t q)
 {
@@ -145,7 +169,7 @@ template <class R> __device__ __forceinline__ void stage_circumcentre(const Swee
     double bx = px_of(p, b) - ax, by = py_of(p, b) - ay;
     double cx = px_of(p, c) - ax, cy = py_of(p, c) - ay;
     double b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
-    double inv = 0.5 / (bx * cy - by * cx);
+    double inv = 0.5 * recip(bx * cy - by * cx);
     p.ccx[t] = ax + (cy * b2 - by * c2) * inv;
     p.ccy[t] = ay + (bx * c2 - cx * b2) * inv;
 }
@@ -220,7 +244,7 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
     }
     const double A = 0.5 * A2;
     // one division serves both the centre of mass and 1/A
-    const double rA2 = 1.0 / A2;
+    const double rA2 = recip(A2);
     const double inv3 = rA2 * (1.0 / 3.0);
     const double ox = sx * inv3, oy = sy * inv3;
     p.A[i] = A;
@@ -250,15 +274,15 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
     double m = p.U[i], Px = p.U[n + i], Py = p.U[2 * n + i], E = p.U[3 * n + i];
     Vec4<R> W;
     if (sizeof(R) == sizeof(double)) {
-        double invA = 2.0 * rA2, invm = 1.0 / m;
+        double invA = 2.0 * rA2, invm = recip(m);
         double rho = m * invA, vx = Px * invm, vy = Py * invm;
         double pr = gm1 * (E - 0.5 * (Px * vx + Py * vy)) * invA;
         W = Vec4<R>{(R)rho, (R)vx, (R)vy, (R)pr};
     } else {
         // the thermal energy cancels kinetic against total energy: FP64; the
         // FP64 pressure also feeds the shock switch's pressure-ratio test
-        double eth = E - 0.5 * (Px * Px + Py * Py) / m;
-        double pr = gm1 * eth / A;
+        double eth = E - 0.5 * (Px * Px + Py * Py) * recip(m);
+        double pr = gm1 * eth * (2.0 * rA2);
         p.p64[i] = pr;
         R Af = (R)A, mf = (R)m;
         W = Vec4<R>{mf / Af, (R)Px / mf, (R)Py / mf, (R)pr};
@@ -278,15 +302,24 @@ template <class R> __global__ void k_cell_geometry(SweepParams<R> p, const doubl
 // Smallest non-negative cell time step of each simulation: a warp whose
 // cells all belong to one simulation reduces first and issues one atomic;
 // a mixed warp issues one atomic per lane.
+// The minimum is taken on the bits: non-negative doubles order like their
+// bit patterns, and a negative value, -0.0 or a negative NaN (negative as
+// an integer) is mapped past every candidate, as are +inf and positive NaNs
+// (above DBL_MAX's bits).
 __device__ __forceinline__ void warp_min_to(double v, int32_t inst, unsigned long long *dst)
 {
+    const long long kmax = __double_as_longlong(DBL_MAX);
+    long long k = __double_as_longlong(v);
+    if (k < 0) k = kmax;
     const int32_t first = __shfl_sync(0xffffffffu, inst, 0);
     if (__all_sync(0xffffffffu, inst == first)) {
-        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
-        if ((threadIdx.x & 31) == 0 && v >= 0.0 && v < DBL_MAX)
-            atomicMin(dst + first, (unsigned long long)__double_as_longlong(v));
-    } else if (v >= 0.0 && v < DBL_MAX) {
-        atomicMin(dst + inst, (unsigned long long)__double_as_longlong(v));
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long q = __shfl_down_sync(0xffffffffu, k, o);
+            k = q < k ? q : k;
+        }
+        if ((threadIdx.x & 31) == 0 && k < kmax) atomicMin(dst + first, (unsigned long long)k);
+    } else if (k < kmax) {
+        atomicMin(dst + inst, (unsigned long long)k);
     }
 }
 
@@ -310,9 +343,15 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
         const R A = (R)p.A[i];
         const double dp = ip.delta_p;
         const double pi64 = sizeof(R) == sizeof(double) ? (double)Wi[3] : p.p64[i];
-        // Eqs. 3-8 look at the cells sharing an edge longer than 1e-9 sqrt(A):
-        // shorter edges are point contacts whose presence depends on round-off
-        const R Lmin = R(1e-9) * sqrt(A);
+        // R_i = sqrt(A/pi) and 1/A from one reciprocal square root:
+        // rR = 1/R_i, so 1/A = rR^2 / pi and R_i = (A/pi) rR
+        const R Api = A * (R(1) / R(M_PI));
+        const R rR = rsqrt(Api);
+        const R Rad = Api * rR;
+        // Eqs. 3-8 look at the cells sharing an edge longer than 1e-9 sqrt(A)
+        // = 1e-9 sqrt(pi) R_i: shorter edges are point contacts whose
+        // presence depends on round-off
+        const R Lmin = R(1.7724538509055160273e-9) * Rad;
         for (int32_t s = lo; s < hi; s++) {
             const int32_t es = p.slot_edge[s];
             const int32_t e = es >> 1;
@@ -357,16 +396,11 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             fmx[v] = ext[v].max();
             fmn[v] = ext[v].min();
         }
-        // R_i = sqrt(A/pi) and 1/A from one reciprocal square root:
-        // rR = 1/R_i, so 1/A = rR^2 / pi and R_i = (A/pi) rR
-        const R Api = A * (R(1) / R(M_PI));
-        const R rR = rsqrt(Api);
         const R invA = rR * rR * (R(1) / R(M_PI));
         R g[8];
 #pragma unroll
         for (int c = 0; c < 8; c++) g[c] = acc[c] * invA;
         const R cs = p.cs[i];
-        const R Rad = Api * rR;
         // Eq. 7: -div v > delta_v c_s / R_i, as (delta_v c_s) < -(div v) R_i
         if (key_less((R)ip.delta_v * cs, flip((g[2] + g[5]) * Rad, 0x8000000000000000ull))) shock = true;
         const bool use_tess = ip.limiter == 2 || (ip.limiter == 0 && shock);
@@ -453,7 +487,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
         }
         p.w[i] = Vec2<R>{wx, wy};
         const R rx = Wi[1] - wx, ry = Wi[2] - wy;
-        const R speed = cs + sqrt(rx * rx + ry * ry);
+        const R speed = cs + sqrt_nonneg(rx * rx + ry * ry);
         // the cell's six quotients (alpha of each variable, 1/rho for the
         // prediction terms, R_i over the Courant speed)
         R alpha[4], irho, cdt;
@@ -472,7 +506,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             suf[5] = R(1);
 #pragma unroll
             for (int k = 4; k >= 0; k--) suf[k] = suf[k + 1] * q[k + 1];
-            const R r = R(1) / prod;
+            const R r = recip(prod);
 #pragma unroll
             for (int v = 0; v < 4; v++) alpha[v] = lim[v] ? an[v] * (pre[v] * suf[v] * r) : R(1);
             irho = pre[4] * suf[4] * r;
@@ -523,7 +557,7 @@ template <class R> __device__ __forceinline__ double step_dt(const SweepParams<R
     // reduced with atomics earlier in the same launch, and a line of it may
     // still sit stale in this SM's L1
     double dt = ip.cfl * __longlong_as_double((long long)__ldcg(p.dtmin_bits + inst));
-    return dt > ip.remaining ? ip.remaining : dt;
+    return nonneg_less(ip.remaining, dt) ? ip.remaining : dt;
 }
 
 // half-step prediction of one side's edge state in the frame moving with wf:
@@ -576,7 +610,7 @@ template <class R> __device__ __forceinline__ void hllc(R gam, R igm1, const R L
         // r = 1/(den D) gives S* = num D r and 1/(S_K - S*) = den^2 r.
         const R SK = useL ? SL : SR, mK = useL ? mL : mR;
         const R D = SK * den - num;
-        const R r = R(1) / (den * D);
+        const R r = recip(den * D);
         const R Ss = num * D * r;
         const R inv = den * den * r;
         const R f = mK * inv;
@@ -810,6 +844,16 @@ __global__ void k_repack(const int32_t *__restrict__ src, int32_t n_new, int32_t
 }
 
 inline int blocks(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
+// Threads per block of each stage.  Small blocks let the block scheduler
+// balance the SMs at a fine grain: with 256 threads a per-cell stage over
+// 262,144 cells ran 1.1-3.4 waves of 8-warp blocks, and SMs idled for up
+// to 17 % of the launch waiting for the last blocks (per-SM active cycles
+// from 0.77x to 1.17x of the mean).  Chosen by timing 32, 64, 128 and 256 on
+// GB300 (Sedov, 262,144 cells): the gradient and flux stages, whose register
+// counts cap an SM at 16-21 warps, run best at 128, the others at 32.
+constexpr int kStageBlock[NUM_STAGES] = {32, 32, 32, 0, 128, 128, 32};
+inline int stage_block(int k) { return kStageBlock[k]; }
+inline int nblk(int64_t n, int k) { return (int)((n + stage_block(k) - 1) / stage_block(k)); }
 
 }  // namespace
 
@@ -824,25 +868,25 @@ template <class R> void launch_stage(int k, const SweepParams<R> &p, const doubl
 {
     switch (k) {
     case K_CIRCUMCENTRE:
-        if (p.T > 0) k_circumcentre<R><<<blocks(p.T), kBlock, 0, st>>>(p);
+        if (p.T > 0) k_circumcentre<R><<<nblk(p.T, K_CIRCUMCENTRE), stage_block(K_CIRCUMCENTRE), 0, st>>>(p);
         break;
     case K_EDGE_GEOMETRY:
-        if (p.E > 0) k_edge_geometry<R><<<blocks(p.E), kBlock, 0, st>>>(p);
+        if (p.E > 0) k_edge_geometry<R><<<nblk(p.E, K_EDGE_GEOMETRY), stage_block(K_EDGE_GEOMETRY), 0, st>>>(p);
         break;
     case K_CELL_GEOMETRY:
-        if (p.n > 0) k_cell_geometry<R><<<blocks(p.n), kBlock, 0, st>>>(p, init_W);
+        if (p.n > 0) k_cell_geometry<R><<<nblk(p.n, K_CELL_GEOMETRY), stage_block(K_CELL_GEOMETRY), 0, st>>>(p, init_W);
         break;
     case K_DT_RESET:
         cudaMemsetAsync(p.dtmin_bits, 0x7f, sizeof(unsigned long long) * p.n_inst, st);
         break;
     case K_CELL_GRADIENT:
-        if (p.n > 0) k_cell_gradient<R><<<blocks(p.n), kBlock, 0, st>>>(p);
+        if (p.n > 0) k_cell_gradient<R><<<nblk(p.n, K_CELL_GRADIENT), stage_block(K_CELL_GRADIENT), 0, st>>>(p);
         break;
     case K_EDGE_FLUX:
-        if (p.E > 0) k_edge_flux<R><<<blocks(p.E), kBlock, 0, st>>>(p);
+        if (p.E > 0) k_edge_flux<R><<<nblk(p.E, K_EDGE_FLUX), stage_block(K_EDGE_FLUX), 0, st>>>(p);
         break;
     case K_CELL_UPDATE:
-        if (p.n > 0) k_cell_update<R><<<blocks(p.n), kBlock, 0, st>>>(p);
+        if (p.n > 0) k_cell_update<R><<<nblk(p.n, K_CELL_UPDATE), stage_block(K_CELL_UPDATE), 0, st>>>(p);
         break;
     default:
         break;
