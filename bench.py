@@ -47,24 +47,25 @@ COMPULSORY_BYTES_PER_CELL = 124
 # The cell-only terms of the half-step prediction (rho div v, grad p / rho,
 # gamma p div v: 7 operations) are counted once per cell in k_cell_gradient,
 # where they are computed, not once per edge side; the prediction of each
-# side is phi + g.(off - hdt u) - hdt src (30 operations per side), and
-# HLLC forms the total energy of the upwind side only.
+# side is phi + g.(off - hdt u) - hdt src with u = v - wf formed once for
+# the shift and the boost (30 operations per side), and HLLC forms the total
+# energy of the upwind side only.
 # (per unit, unit kind, extra per ring slot)
 FLOPS = {
     "fp64": {
         "k_circumcentre": ({"fp64": 24}, "tri", {}),
-        "k_edge_geometry": ({"fp64": 31}, "edge", {}),
-        "k_cell_geometry": ({"fp64": 22}, "cell", {"fp64": 12}),
+        "k_edge_geometry": ({"fp64": 32}, "edge", {}),
+        "k_cell_geometry": ({"fp64": 27}, "cell", {"fp64": 11}),
         "k_cell_gradient": ({"fp64": 47}, "cell", {"fp64": 83}),
-        "k_edge_flux": ({"fp64": 179}, "edge", {}),
+        "k_edge_flux": ({"fp64": 175}, "edge", {}),
         "k_cell_update": ({"fp64": 20}, "cell", {"fp64": 4}),
     },
     "split": {
         "k_circumcentre": ({"fp64": 24}, "tri", {}),
-        "k_edge_geometry": ({"fp64": 6, "fp32": 25}, "edge", {}),
-        "k_cell_geometry": ({"fp64": 12, "fp32": 10}, "cell", {"fp64": 12}),
+        "k_edge_geometry": ({"fp64": 6, "fp32": 26}, "edge", {}),
+        "k_cell_geometry": ({"fp64": 17, "fp32": 10}, "cell", {"fp64": 11}),
         "k_cell_gradient": ({"fp32": 47}, "cell", {"fp32": 83}),
-        "k_edge_flux": ({"fp32": 179}, "edge", {}),
+        "k_edge_flux": ({"fp32": 175}, "edge", {}),
         "k_cell_update": ({"fp64": 20}, "cell", {"fp64": 4}),
     },
 }
@@ -75,14 +76,14 @@ FLOPS = {
 # the command and the raw counters), scaled to a launch by its units.  Set
 # to None whenever the kernel changes after the capture.
 TRAFFIC_PER_UNIT = {
-    "fp64": {"k_edge_flux": 145.9},      # profiles/k_edge_flux_fp64_sedov262k.md
-    "split": {"k_cell_geometry": None},   # profiles/k_cell_geometry_split_sedov262k.md
+    "fp64": {"k_edge_flux": 145.8},     # profiles/k_edge_flux_fp64_sedov262k.md
+    "split": {"k_cell_geometry": 113.6},  # profiles/k_cell_geometry_split_sedov262k.md
 }
 # The same captures' sm__pipe_fp64_cycles_active (fraction of peak while the
 # SMs are active): how busy the bounding pipe is, whatever the op mix.
 PIPE_ACTIVE = {
-    "fp64": {"k_edge_flux": 0.889},
-    "split": {"k_cell_geometry": None},
+    "fp64": {"k_edge_flux": 0.891},
+    "split": {"k_cell_geometry": 0.790},
 }
 
 

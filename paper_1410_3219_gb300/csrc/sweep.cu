@@ -13,6 +13,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "fp64ops.cuh"
 #include "sweep.cuh"
 
 namespace rich {
@@ -59,30 +60,6 @@ __device__ __forceinline__ float flip(float v, unsigned long long m)
     return __int_as_float(__float_as_int(v) ^ (int)(unsigned)(m >> 32));
 }
 
-// 1/x for a normal x with |x| in [2^-1021, 2^1020): the hardware's
-// approximate reciprocal y (about 20 correct bits, issued outside the FP64
-// pipe) refined by the geometric series 1/x = y / (1 - e) ~ y (1 + e + e^2),
-// e = 1 - x y: three FMAs, relative error O(e^3) plus rounding, so within
-// one ulp of the correctly rounded quotient, where IEEE division costs
-// about 4.5 FP64 issue slots.  Other arguments take the IEEE division.
-__device__ __forceinline__ double recip(double x)
-{
-    const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
-    if (ex - 2u > 2040u) return 1.0 / x;
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    const double e = fma(-x, y, 1.0);
-    return fma(fma(e, e, e), y, y);
-}
-__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
-
-// sqrt(x) for x >= 0 as x / sqrt(x) through one reciprocal square root
-// (about 5.8 FP64 issue slots against 7.4 for the rounded square root)
-__device__ __forceinline__ double sqrt_nonneg(double x)
-{
-    return __double_as_longlong(x) > 0 ? x * rsqrt(x) : 0.0;
-}
-__device__ __forceinline__ float sqrt_nonneg(float x) { return sqrtf(x); }
 
 template <class R> __device__ __forceinline__ Vec4<R> load_W(const SweepParams<R> &p, int32_t q)
 {
@@ -188,7 +165,7 @@ template <class R> __device__ __forceinline__ void stage_edge_geometry(const Swe
     double xl = p.x[l], yl = p.y[l];
     const double ax64 = p.ccx[p.edge_ta[e]] - xl, ay64 = p.ccy[p.edge_ta[e]] - yl;
     const double bx64 = p.ccx[p.edge_tb[e]] - xl, by64 = p.ccy[p.edge_tb[e]] - yl;
-    R ax = (R)ax64, ay = (R)ay64, bx = (R)bx64, by = (R)by64;
+    R ax = (R)ax64, ay = (R)ay64;
     R dx = (R)(px_of(p, r) - xl), dy = (R)(py_of(p, r) - yl);
     // the edge vector from the FP64 endpoints: a zero-length edge stays ~0
     // instead of inheriting the rounding of two separately rounded endpoints
@@ -197,7 +174,7 @@ template <class R> __device__ __forceinline__ void stage_edge_geometry(const Swe
     // edges, from co-circular generators, stay exactly zero)
     const R e2 = ex * ex + ey * ey;
     R L = nonneg_less(R(0), e2) ? e2 * rsqrt(e2) : R(0);
-    R mx = R(0.5) * (ax + bx), my = R(0.5) * (ay + by);
+    R mx = ax + R(0.5) * ex, my = ay + R(0.5) * ey;
     // 1/|r_ij| with one reciprocal square root (a divide and a square root
     // each cost several FP64 issue slots on this part)
     R rinv = rsqrt(dx * dx + dy * dy);
@@ -212,8 +189,9 @@ template <class R> __device__ __forceinline__ void stage_edge_geometry(const Swe
     const R nx = dx * rinv, ny = dy * rinv;
     p.eqx[e] = qx;
     p.eqy[e] = qy;
-    const R hx = R(0.5) * nx, hy = R(0.5) * ny;
-    p.ePM[e] = Vec4<R>{L * (qx + hx), L * (qy + hy), L * (hx - qx), L * (hy - qy)};
+    // P = L q + L n / 2, M = L n / 2 - L q: one product L n / 2 and four FMAs
+    const R hL = R(0.5) * L, Lhx = hL * nx, Lhy = hL * ny;
+    p.ePM[e] = Vec4<R>{L * qx + Lhx, L * qy + Lhy, Lhx - L * qx, Lhy - L * qy};
 }
 
 template <class R> __global__ void k_edge_geometry(SweepParams<R> p)
@@ -229,18 +207,34 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
 {
     const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
     const double xi = p.x[i], yi = p.y[i];
+    // Shoelace over the ring v_0 .. v_{m-1} (v_{-1} = v_{m-1}), with
+    // c_s = v_{s-1} x v_s: 2A = sum c_s and 6A s = sum (v_{s-1} + v_s) c_s
+    // = sum v_s (c_s + c_{s+1}), so each vertex enters once with the sum of
+    // its two crosses (v_{m-1} last, when c_{m-1} + c_0 is known).
     int32_t tl = p.slot_tri[hi - 1];
-    double ax = p.ccx[tl] - xi, ay = p.ccy[tl] - yi;
+    const double zx = p.ccx[tl] - xi, zy = p.ccy[tl] - yi;
+    double ax = zx, ay = zy, c0 = 0.0, cp = 0.0;
     double A2 = 0.0, sx = 0.0, sy = 0.0;
     for (int32_t s = lo; s < hi; s++) {
         int32_t t = p.slot_tri[s];
         double bx = p.ccx[t] - xi, by = p.ccy[t] - yi;
         double cr = ax * by - ay * bx;
         A2 += cr;
-        sx += (ax + bx) * cr;
-        sy += (ay + by) * cr;
+        if (s == lo) {
+            c0 = cr;
+        } else {
+            const double wv = cp + cr;
+            sx += ax * wv;
+            sy += ay * wv;
+        }
+        cp = cr;
         ax = bx;
         ay = by;
+    }
+    {
+        const double wv = cp + c0;
+        sx += zx * wv;
+        sy += zy * wv;
     }
     const double A = 0.5 * A2;
     // one division serves both the centre of mass and 1/A
@@ -489,34 +483,13 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
         const R rx = Wi[1] - wx, ry = Wi[2] - wy;
         const R speed = cs + sqrt_nonneg(rx * rx + ry * ry);
         // the cell's six quotients (alpha of each variable, 1/rho for the
-        // prediction terms, R_i over the Courant speed)
-        R alpha[4], irho, cdt;
-        R prod = R(1), pre[6], suf[6];
-        const R q[6] = {ad[0], ad[1], ad[2], ad[3], Wi[0], speed};
-        if (sizeof(R) == sizeof(double)) {
-            pre[0] = R(1);
+        // prediction terms, R_i over the Courant speed), each through one
+        // refined reciprocal
+        R alpha[4];
 #pragma unroll
-            for (int k = 1; k < 6; k++) pre[k] = pre[k - 1] * q[k - 1];
-            prod = pre[5] * q[5];
-        }
-        // the product must stay well inside the FP64 exponent range
-        const int pexp = sizeof(R) == sizeof(double) ? (int)((__double_as_longlong((double)prod) >> 52) & 0x7ff) : 0;
-        if (sizeof(R) == sizeof(double) && pexp > 64 && pexp < 1983) {
-            // in FP64 from one reciprocal: 1/q_k = (prod of the others) / (prod of all)
-            suf[5] = R(1);
-#pragma unroll
-            for (int k = 4; k >= 0; k--) suf[k] = suf[k + 1] * q[k + 1];
-            const R r = recip(prod);
-#pragma unroll
-            for (int v = 0; v < 4; v++) alpha[v] = lim[v] ? an[v] * (pre[v] * suf[v] * r) : R(1);
-            irho = pre[4] * suf[4] * r;
-            cdt = Rad * (pre[5] * r);
-        } else {
-#pragma unroll
-            for (int v = 0; v < 4; v++) alpha[v] = lim[v] ? an[v] / ad[v] : R(1);
-            irho = R(1) / Wi[0];
-            cdt = Rad / speed;
-        }
+        for (int v = 0; v < 4; v++) alpha[v] = lim[v] ? an[v] * recip(ad[v]) : R(1);
+        const R irho = recip(Wi[0]);
+        const R cdt = Rad * recip(speed);
         R lg[8];
 #pragma unroll
         for (int c = 0; c < 8; c++) lg[c] = alpha[c >> 1] * g[c];
@@ -562,16 +535,20 @@ template <class R> __device__ __forceinline__ double step_dt(const SweepParams<R
 
 // half-step prediction of one side's edge state in the frame moving with wf:
 // Eq. 2 extrapolation minus hdt times the primitive Euler right-hand side,
-// whose cell-only terms (rho div v, grad p / rho, gamma p div v) come in src
+// whose cell-only terms (rho div v, grad p / rho, gamma p div v) come in src.
+// The velocity comes out relative to the edge (v - wf), ready for the
+// rotation into the edge frame.
 template <class R>
 __device__ __forceinline__ void predict(R hdt, const R W[4], const R g[8], const R src[4], R offx, R offy, R wfx,
                                         R wfy, R out[4])
 {
-    // phi + g.off - hdt (u.g + src) = phi + g.(off - hdt u) - hdt src: the
-    // advective part of the prediction moves the extrapolation point
-    const R ax = offx - hdt * (W[1] - wfx), ay = offy - hdt * (W[2] - wfy);
+    // phi + g.off - hdt (u.g + src) = phi + g.(off - hdt u) - hdt src, u = v - wf:
+    // the advective part of the prediction moves the extrapolation point
+    const R ux = W[1] - wfx, uy = W[2] - wfy;
+    const R ax = offx - hdt * ux, ay = offy - hdt * uy;
+    const R base[4] = {W[0], ux, uy, W[3]};
 #pragma unroll
-    for (int c = 0; c < 4; c++) out[c] = W[c] + g[2 * c] * ax + g[2 * c + 1] * ay - hdt * src[c];
+    for (int c = 0; c < 4; c++) out[c] = base[c] + g[2 * c] * ax + g[2 * c + 1] * ay - hdt * src[c];
 }
 
 // HLLC (Toro) in the edge frame, states (rho, u_n, u_t, p)
@@ -667,8 +644,8 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
     predict(hdt, Wl, gL, srcL, p.emlx[e] - ol.x, p.emly[e] - ol.y, wfx, wfy, Sl);
     predict(hdt, Wr, gR, srcR, p.emrx[e] - orx, p.emry[e] - ory, wfx, wfy, Sr);
     const R tx = -ny, ty = nx;
-    R WL[4] = {Sl[0], (Sl[1] - wfx) * nx + (Sl[2] - wfy) * ny, (Sl[1] - wfx) * tx + (Sl[2] - wfy) * ty, Sl[3]};
-    R WR[4] = {Sr[0], (Sr[1] - wfx) * nx + (Sr[2] - wfy) * ny, (Sr[1] - wfx) * tx + (Sr[2] - wfy) * ty, Sr[3]};
+    R WL[4] = {Sl[0], Sl[1] * nx + Sl[2] * ny, Sl[1] * tx + Sl[2] * ty, Sl[3]};
+    R WR[4] = {Sr[0], Sr[1] * nx + Sr[2] * ny, Sr[1] * tx + Sr[2] * ty, Sr[3]};
     R Fe[4];
     hllc(gam, (R)p.inst[li].igm1, WL, WR, Fe);
     if (xf && k == l) {
