@@ -77,13 +77,13 @@ FLOPS = {
 # to None whenever the kernel changes after the capture.
 TRAFFIC_PER_UNIT = {
     "fp64": {"k_edge_flux": 145.8},     # profiles/k_edge_flux_fp64_sedov262k.md
-    "split": {"k_cell_geometry": 113.6},  # profiles/k_cell_geometry_split_sedov262k.md
+    "split": {"k_cell_geometry": 114.1},  # profiles/k_cell_geometry_split_sedov262k.md
 }
 # The same captures' sm__pipe_fp64_cycles_active (fraction of peak while the
 # SMs are active): how busy the bounding pipe is, whatever the op mix.
 PIPE_ACTIVE = {
     "fp64": {"k_edge_flux": 0.891},
-    "split": {"k_cell_geometry": 0.790},
+    "split": {"k_cell_geometry": 0.781},
 }
 
 

@@ -165,11 +165,11 @@ template <class R> __device__ __forceinline__ void stage_edge_geometry(const Swe
     double xl = p.x[l], yl = p.y[l];
     const double ax64 = p.ccx[p.edge_ta[e]] - xl, ay64 = p.ccy[p.edge_ta[e]] - yl;
     const double bx64 = p.ccx[p.edge_tb[e]] - xl, by64 = p.ccy[p.edge_tb[e]] - yl;
-    R ax = (R)ax64, ay = (R)ay64;
-    R dx = (R)(px_of(p, r) - xl), dy = (R)(py_of(p, r) - yl);
+    R ax = to_R<R>(ax64), ay = to_R<R>(ay64);
+    R dx = to_R<R>(px_of(p, r) - xl), dy = to_R<R>(py_of(p, r) - yl);
     // the edge vector from the FP64 endpoints: a zero-length edge stays ~0
     // instead of inheriting the rounding of two separately rounded endpoints
-    R ex = (R)(bx64 - ax64), ey = (R)(by64 - ay64);
+    R ex = to_R<R>(bx64 - ax64), ey = to_R<R>(by64 - ay64);
     // |e| = e^2 / sqrt(e^2) with one reciprocal square root (zero-length
     // edges, from co-circular generators, stay exactly zero)
     const R e2 = ex * ex + ey * ey;
@@ -242,7 +242,7 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
     const double inv3 = rA2 * (1.0 / 3.0);
     const double ox = sx * inv3, oy = sy * inv3;
     p.A[i] = A;
-    p.o[i] = Vec2<R>{(R)ox, (R)oy};
+    p.o[i] = Vec2<R>{to_R<R>(ox), to_R<R>(oy)};
     // Section 6 trigger: the generator is more than eta R_i from its centre of
     // mass, d^2 > eta^2 A / pi (both sides non-negative, so no square roots).
     // Rounded cells settle at that distance, so the decision is taken in
@@ -271,19 +271,19 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
         double invA = 2.0 * rA2, invm = recip(m);
         double rho = m * invA, vx = Px * invm, vy = Py * invm;
         double pr = gm1 * (E - 0.5 * (Px * vx + Py * vy)) * invA;
-        W = Vec4<R>{(R)rho, (R)vx, (R)vy, (R)pr};
+        W = Vec4<R>{to_R<R>(rho), to_R<R>(vx), to_R<R>(vy), to_R<R>(pr)};
     } else {
         // the thermal energy cancels kinetic against total energy: FP64; the
         // FP64 pressure also feeds the shock switch's pressure-ratio test
         double eth = E - 0.5 * (Px * Px + Py * Py) * recip(m);
         double pr = gm1 * eth * (2.0 * rA2);
         p.p64[i] = pr;
-        R Af = (R)A, mf = (R)m;
-        W = Vec4<R>{mf / Af, (R)Px / mf, (R)Py / mf, (R)pr};
+        R Af = to_R<R>(A), mf = to_R<R>(m);
+        W = Vec4<R>{mf / Af, to_R<R>(Px) / mf, to_R<R>(Py) / mf, to_R<R>(pr)};
     }
     p.W[i] = W;
     // c_s = sqrt(gamma p / rho) = gamma p / sqrt(gamma p rho): one reciprocal square root
-    const R gp = (R)gamma * W.w;
+    const R gp = to_R<R>(gamma) * W.w;
     p.cs[i] = gp * rsqrt(gp * W.x);
 }
 
@@ -334,7 +334,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
 #pragma unroll
         for (int v = 0; v < 4; v++) ext[v].init(Wi[v]);
         bool shock = false;
-        const R A = (R)p.A[i];
+        const R A = to_R<R>(p.A[i]);
         const double dp = ip.delta_p;
         const double pi64 = sizeof(R) == sizeof(double) ? (double)Wi[3] : p.p64[i];
         // R_i = sqrt(A/pi) and 1/A from one reciprocal square root:
@@ -396,7 +396,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
         for (int c = 0; c < 8; c++) g[c] = acc[c] * invA;
         const R cs = p.cs[i];
         // Eq. 7: -div v > delta_v c_s / R_i, as (delta_v c_s) < -(div v) R_i
-        if (key_less((R)ip.delta_v * cs, flip((g[2] + g[5]) * Rad, 0x8000000000000000ull))) shock = true;
+        if (key_less(to_R<R>(ip.delta_v) * cs, flip((g[2] + g[5]) * Rad, 0x8000000000000000ull))) shock = true;
         const bool use_tess = ip.limiter == 2 || (ip.limiter == 0 && shock);
         const Vec2<R> oi = p.o[i];
         const R ox = oi.x, oy = oi.y;
@@ -463,7 +463,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 // alpha = 0, or min(1, theta bn / bd)
-                const R tn = (R)ip.theta * bn[v];
+                const R tn = to_R<R>(ip.theta) * bn[v];
                 if (zero[v]) { an[v] = R(0); lim[v] = true; }
                 else if (bd[v] > R(0) && tn < bd[v]) { an[v] = tn; ad[v] = bd[v]; lim[v] = true; }
             }
@@ -474,7 +474,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             wx = Wi[1];
             wy = Wi[2];
             if (p.rounding[i]) {
-                R f = (R)ip.chi * cs * rsqrt(ox * ox + oy * oy);
+                R f = to_R<R>(ip.chi) * cs * rsqrt(ox * ox + oy * oy);
                 wx += f * ox;
                 wy += f * oy;
             }
@@ -499,7 +499,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             // cell-only terms of the half-step prediction (used by every edge
             // of the cell): rho div v, grad p / rho, gamma p div v
             const R ldiv = lg[2] + lg[5];
-            p.psrc[i] = Vec4<R>{Wi[0] * ldiv, lg[6] * irho, lg[7] * irho, (R)ip.gamma * Wi[3] * ldiv};
+            p.psrc[i] = Vec4<R>{Wi[0] * ldiv, lg[6] * irho, lg[7] * irho, to_R<R>(ip.gamma) * Wi[3] * ldiv};
         }
         if (p.diagnostics) {
             p.g[2 * i] = Vec4<R>{g[0], g[1], g[2], g[3]};
@@ -507,7 +507,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             p.alpha[i] = Vec4<R>{alpha[0], alpha[1], alpha[2], alpha[3]};
             p.tess[i] = use_tess ? 1 : 0;
         }
-        dt_cell = (double)cdt;
+        dt_cell = to_d(cdt);
     }
     return dt_cell;
 }
@@ -657,6 +657,9 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
         return;
     }
     const R Fmx = Fe[1] * nx + Fe[2] * tx, Fmy = Fe[1] * ny + Fe[2] * ty;
+    // (the hardware converts in this stage: it waits on its gathers, and the
+    // integer-pipe conversions' extra registers cost it more than the FP64
+    // issue slots they save)
     p.F[e] = Vec4<double>{(double)(L * Fe[0]), (double)(L * (Fmx + Fe[0] * wfx)), (double)(L * (Fmy + Fe[0] * wfy)),
                           (double)(L * (Fe[3] + Fmx * wfx + Fmy * wfy + R(0.5) * (wfx * wfx + wfy * wfy) * Fe[0]))};
 }
@@ -712,7 +715,7 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
         else if (!(bm > 0) || !(__double_as_longlong(2.0 * m * E - (Px * Px + Py * Py)) > 0)) st |= ST_NEGATIVE;
     }
     const Vec2<R> w = p.w[i];
-    double xn = p.x0[i] + hdt * (double)w.x, yn = p.y0[i] + hdt * (double)w.y;
+    double xn = p.x0[i] + hdt * to_d(w.x), yn = p.y0[i] + hdt * to_d(w.y);
     const long long kx0 = dkey0(ip.x0), kx1 = dkey0(ip.x1), ky0 = dkey0(ip.y0), ky1 = dkey0(ip.y1);
     long long kx = dkey0(xn), ky = dkey0(yn);
     if (ip.boundary == 1) {

@@ -2,7 +2,9 @@
 approximate reciprocal) and its x / sqrt(x) square root, against the
 IEEE-rounded 1/x and sqrt on the GPU: within one and two ulps over normal
 arguments of every exponent, and the IEEE division itself outside the
-refined range (zero, subnormals, the largest exponents, inf, NaN)."""
+refined range (zero, subnormals, the largest exponents, inf, NaN).  The
+integer-pipe FP64 -> FP32 (round to nearest even) and FP32 -> FP64
+conversions must equal the hardware's bit for bit."""
 import os
 import shutil
 import subprocess
@@ -32,7 +34,8 @@ def test_fp64ops_within_ulps(tmp_path):
     out = subprocess.run([exe, str(1 << 22)], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, out.stderr
     f = out.stdout.split()
-    assert f[0] == "recip" and f[3] == "sqrt", out.stdout
+    assert f[0] == "recip" and f[3] == "sqrt" and f[6] == "d2f" and f[8] == "f2d", out.stdout
+    assert int(f[7]) == 0 and int(f[9]) == 0, out.stdout
     r_ulp, r_bad, s_ulp, s_bad = float(f[1]), int(f[2]), float(f[4]), int(f[5])
     assert r_ulp <= 1.0, out.stdout
     assert r_bad == 0, out.stdout
