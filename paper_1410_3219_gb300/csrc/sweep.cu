@@ -512,7 +512,9 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
     return dt_cell;
 }
 
-template <class R> __global__ void __launch_bounds__(kBlock) k_cell_gradient(SweepParams<R> p)
+// launched in blocks of 128 threads; six blocks per SM cap the FP64 build at
+// 80 registers (from 94, with a few spilled to L1), 24 warps instead of 20
+template <class R> __global__ void __launch_bounds__(128, 6) k_cell_gradient(SweepParams<R> p)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     double dt_cell = DBL_MAX;
@@ -832,6 +834,7 @@ inline int blocks(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 // GB300 (Sedov, 262,144 cells): the gradient and flux stages, whose register
 // counts cap an SM at 16-21 warps, run best at 128, the others at 32.
 constexpr int kStageBlock[NUM_STAGES] = {32, 32, 32, 0, 128, 128, 32};
+static_assert(kStageBlock[K_CELL_GRADIENT] == 128, "k_cell_gradient's launch bounds assume 128 threads");
 inline int stage_block(int k) { return kStageBlock[k]; }
 inline int nblk(int64_t n, int k) { return (int)((n + stage_block(k) - 1) / stage_block(k)); }
 
