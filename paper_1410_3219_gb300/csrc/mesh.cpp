@@ -354,6 +354,71 @@ inline Disk circumdisk(const double *X, const double *Y, int32_t a, int32_t b, i
     return Disk{ux + ax, uy + ay, std::sqrt(ux * ux + uy * uy) * (1.0 + 1e-9) + pad};
 }
 
+// The points bucketed on a G x G grid over their bounding box.
+struct PointGrid {
+    int G = 1;
+    double x0 = 0.0, y0 = 0.0, sx = 0.0, sy = 0.0;
+    const int32_t *start = nullptr, *ids = nullptr;
+    // bucket column / row of a coordinate, clamped to the grid (infinite
+    // and NaN coordinates included)
+    int col(double x) const { return clampi((x - x0) * sx); }
+    int row(double y) const { return clampi((y - y0) * sy); }
+    int clampi(double f) const { return !(f > 0.0) ? 0 : (f >= G ? G - 1 : (int)f); }
+};
+
+// Counting sort of the point ids by bucket, in chunks on the pool: a
+// histogram per chunk, offsets per (bucket, chunk), then each chunk scatters
+// its ids in increasing order.
+void build_grid(int32_t np, const double *X, const double *Y, const double ext[4], MeshWork &w, ThreadPool *pool,
+                PointGrid &g)
+{
+    g.G = std::max(1, std::min(1024, (int)std::sqrt(np / 32.0)));
+    const int G = g.G;
+    const int64_t GG = (int64_t)G * G;
+    g.x0 = ext[0];
+    g.y0 = ext[2];
+    g.sx = ext[1] > ext[0] ? G / (ext[1] - ext[0]) : 0.0;
+    g.sy = ext[3] > ext[2] ? G / (ext[3] - ext[2]) : 0.0;
+    const int64_t C = pool ? std::max(1, std::min(pool->size(), (int)(np / 8192) + 1)) : 1;
+    const int64_t chunk = (np + C - 1) / C;
+    w.grid_cell.resize(np);
+    w.grid_hist.assign(C * GG, 0);
+    w.grid_start.assign(GG + 1, 0);
+    w.grid_ids.resize(np);
+    auto count = [&](int64_t c) {
+        int32_t *h = w.grid_hist.data() + c * GG;
+        for (int64_t q = c * chunk; q < std::min<int64_t>(np, (c + 1) * chunk); q++) {
+            const int32_t b = g.row(Y[q]) * G + g.col(X[q]);
+            w.grid_cell[q] = b;
+            h[b]++;
+        }
+    };
+    if (pool && C > 1) pool->parallel_for(C, count);
+    else
+        for (int64_t c = 0; c < C; c++) count(c);
+    // offsets: bucket-major, chunk-minor, so ids stay increasing in a bucket
+    int32_t run = 0;
+    for (int64_t b = 0; b < GG; b++) {
+        w.grid_start[b] = run;
+        for (int64_t c = 0; c < C; c++) {
+            const int32_t k = w.grid_hist[c * GG + b];
+            w.grid_hist[c * GG + b] = run;
+            run += k;
+        }
+    }
+    w.grid_start[GG] = run;
+    auto scatter = [&](int64_t c) {
+        int32_t *off = w.grid_hist.data() + c * GG;
+        for (int64_t q = c * chunk; q < std::min<int64_t>(np, (c + 1) * chunk); q++)
+            w.grid_ids[off[w.grid_cell[q]]++] = (int32_t)q;
+    };
+    if (pool && C > 1) pool->parallel_for(C, scatter);
+    else
+        for (int64_t c = 0; c < C; c++) scatter(c);
+    g.start = w.grid_start.data();
+    g.ids = w.grid_ids.data();
+}
+
 // A tile of the point set: x in [x0, x1), y in [y0, y1); open sides (the
 // first / last along an axis) extend to infinity.
 struct Tile {
@@ -368,7 +433,7 @@ struct SlabResult {
     int rc = 0;
     bool halo_ok = true, band_ok = true;
     double needed = 0.0;
-    std::vector<int32_t> cells;  // real core cells, increasing id
+    std::vector<int32_t> cells;  // real core cells
     std::vector<int32_t> deg;    // ring length of each
     std::vector<int32_t> nb;     // concatenated rings: neighbour point ids
     std::vector<int32_t> tri;    // concatenated rings: slab-local triangle number
@@ -381,9 +446,9 @@ struct SlabResult {
 // rectangle: every point of the whole set inside such a disk was then
 // triangulated too, and an empty circumdisk among them is empty in the
 // whole set.
-void build_slab(int32_t n, int32_t np, const double *X, const double *Y, const double ext[4], const Tile &tile,
-                double H, const double band[4], double pad, Delaunay &dt, std::vector<int32_t> &loc,
-                std::vector<double> &LX, std::vector<double> &LY, SlabResult &r)
+void build_slab(int32_t n, const double *X, const double *Y, const double ext[4], const PointGrid &grid,
+                const Tile &tile, double H, const double band[4], double pad, Delaunay &dt,
+                std::vector<int32_t> &loc, std::vector<double> &LX, std::vector<double> &LY, SlabResult &r)
 {
     r = SlabResult();
     double xlo = tile.fx ? -INFINITY : tile.x0 - H, xhi = tile.lx ? INFINITY : tile.x1 + H;
@@ -394,11 +459,18 @@ void build_slab(int32_t n, int32_t np, const double *X, const double *Y, const d
     loc.clear();
     LX.clear();
     LY.clear();
-    for (int32_t q = 0; q < np; q++)
-        if (X[q] >= xlo && X[q] < xhi && Y[q] >= ylo && Y[q] < yhi) {
-            loc.push_back(q);
-            LX.push_back(X[q]);
-            LY.push_back(Y[q]);
+    // the points of the rectangle, from the grid buckets it overlaps (the
+    // local order is bucket by bucket; the triangulation does not depend on
+    // it, and the rings and triangles are put in canonical order below)
+    const int c0 = grid.col(xlo), c1 = grid.col(xhi), r0 = grid.row(ylo), r1 = grid.row(yhi);
+    for (int rw = r0; rw <= r1; rw++)
+        for (int32_t k = grid.start[rw * grid.G + c0]; k < grid.start[rw * grid.G + c1 + 1]; k++) {
+            const int32_t q = grid.ids[k];
+            if (X[q] >= xlo && X[q] < xhi && Y[q] >= ylo && Y[q] < yhi) {
+                loc.push_back(q);
+                LX.push_back(X[q]);
+                LY.push_back(Y[q]);
+            }
         }
     const int32_t nl = (int32_t)loc.size();
     if (nl == 0) return;
@@ -519,7 +591,6 @@ void build_slab(int32_t n, int32_t np, const double *X, const double *Y, const d
             return;
         }
     }
-    // cells were visited in local order, which follows the global order
 }
 
 }  // namespace
@@ -584,6 +655,8 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
                 ext[3] = std::max(ext[3], b[3]);
             }
         }
+        PointGrid grid;
+        build_grid(np, X.data(), Y.data(), ext, work, pool, grid);
         // column cuts at x-quantiles of (a sample of) the real + ghost
         // points, then row cuts at y-quantiles within each column
         std::vector<Tile> tiles(K);
@@ -633,7 +706,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         while (!todo.empty()) {
             auto run = [&](int64_t k) {
                 const int s = todo[k];
-                build_slab(n, np, X.data(), Y.data(), ext, tiles[s], H[s], band, pad, work.dts[s], work.loc[s],
+                build_slab(n, X.data(), Y.data(), ext, grid, tiles[s], H[s], band, pad, work.dts[s], work.loc[s],
                            work.lx[s], work.ly[s], res[s]);
             };
             if (pool && todo.size() > 1) pool->parallel_for((int64_t)todo.size(), run);

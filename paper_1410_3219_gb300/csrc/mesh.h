@@ -86,20 +86,24 @@ struct MeshWork {
     std::vector<Delaunay> dts;
     std::vector<std::vector<int32_t>> loc;
     std::vector<std::vector<double>> lx, ly;
+    // the points bucketed on a uniform grid over their bounding box (ids in
+    // increasing order within a bucket), so that a tile gathers its points
+    // from the buckets it overlaps instead of testing every point
+    std::vector<int32_t> grid_start, grid_ids, grid_cell, grid_hist;
     double halo = 0.0;  // slab halo of the last build, in mean point spacings
 };
 
 class ThreadPool;
 
 // Build the whole host mesh for n real points (x, y).  With a pool the real
-// + ghost points are cut into vertical slabs at x-quantiles (one per thread,
-// at least 16384 real points each); each slab is triangulated with a halo
-// that doubles until every circumdisk of its real points' stars lies inside
-// it, so the stars equal those of the whole set, and the rings and the edge
-// list are filled in parallel.  Rings start at their smallest neighbour id
-// and triangles at their smallest vertex id, so the mesh seen by the sweep
-// does not depend on the number of slabs (only triangle and edge numbering
-// do).  Returns 0, -2 for coincident points, -3 for a failed triangulation,
+// + ghost points are cut into tiles (columns at x-quantiles, rows at
+// y-quantiles; one per thread, at least 16384 real points each); each tile
+// is triangulated with a halo that widens by 1.5x until every circumdisk of
+// its real points' stars lies inside it, so the stars equal those of the
+// whole set, and the rings and the edge list are filled in parallel.
+// Rings start at their smallest neighbour id and triangles at their
+// smallest vertex id, so the mesh seen by the sweep does not depend on the
+// number of tiles (only the triangle numbering does).  Returns 0, -2 for coincident points, -3 for a failed triangulation,
 // -4 when the box holds too few points for the band check to succeed.
 int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const double *y, MeshWork &work,
                     HostMesh &out, ThreadPool *pool = nullptr);
