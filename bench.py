@@ -268,22 +268,24 @@ def run_ours(args):
                     kt[k] = kt.get(k, 0.0) + v
             return ms, dict(info, tess_ms=tms), kt
 
-        # W warm-up steps; before the first timed run, also up to
-        # warmup_seconds of steps of a throwaway copy of the run (the steps
-        # are mostly host tessellation, an idle GPU's clocks take a moment
-        # to rise, and the Sedov run itself fails after 66 steps)
+        # W warm-up steps; before the first timed run, also warmup_seconds
+        # of steps of throwaway copies of the run (the steps are mostly host
+        # tessellation; on a fresh box the first seconds of FP64 kernels ran
+        # ~4 % slow; the Sedov run itself fails after 66 steps, so a copy
+        # takes at most 40)
         if not warm_state["done"] and args.warmup_seconds > 0:
-            spare = rich.Sim(w)
-            spare.set_stream(stream.cuda_stream)
             t_warm = time.perf_counter()
-            for _ in range(40):
-                if time.perf_counter() - t_warm >= args.warmup_seconds:
-                    break
-                spare.tessellate()
-                with torch.cuda.stream(stream):
-                    spare.sweep()
-                spare.sync()
-            spare.close()
+            while time.perf_counter() - t_warm < args.warmup_seconds:
+                spare = rich.Sim(w)
+                spare.set_stream(stream.cuda_stream)
+                for _ in range(40):
+                    if time.perf_counter() - t_warm >= args.warmup_seconds:
+                        break
+                    spare.tessellate()
+                    with torch.cuda.stream(stream):
+                        spare.sweep()
+                    spare.sync()
+                spare.close()
             warm_state["done"] = True
         for _ in range(args.warmup):
             one_step()
@@ -372,7 +374,7 @@ def run_ours(args):
         "data": "synthetic (seeded)",
         "config": {"workload": args.workload, "cells": n, "precision": "fp64", "scheme": "extrapolated fluxes",
                    "l2": "flushed (256 MB write) before every timed sweep",
-                   "warmup": f"{args.warmup} steps, after up to {args.warmup_seconds:g} s of steps of a throwaway copy",
+                   "warmup": f"{args.warmup} steps, after {args.warmup_seconds:g} s of steps of throwaway copies",
                    "host_tess_ms_per_step": float(np.mean(tess_ms)),
                    "wall_ms_per_step": 1e3 * wall / args.steps, "parallelism": f"replicas x{ws}"},
         "roofline": roof,
@@ -573,7 +575,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--warmup-seconds", type=float, default=1.0)
+    ap.add_argument("--warmup-seconds", type=float, default=3.0)
     ap.add_argument("--workload", default="sedov_262144")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
