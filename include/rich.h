@@ -379,6 +379,19 @@ int rich_delaunay_host(int64_t n, const double *x, const double *y, int64_t cap,
 int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const double *y, int64_t cap,
                     int64_t *ptr, double *nbx, double *nby, int64_t *nbsrc, int64_t *nslots);
 
+/* Check of the host builder's in-place update (a0 keeps each tile's last
+   triangulation, moves its vertices, flips to Delaunay and inserts new
+   points, rebuilding a tile only when a triangle turned over): builds the
+   meshes of `steps` successive point sets (xs, ys: steps x n, row-major,
+   the same cells in each) once with one reused workspace and once afresh
+   each, with `threads` host threads, and counts the steps whose sweep
+   inputs differ (rings, their neighbours and triangles, the edge list,
+   ghosts).  *updated and *rebuilt receive the tile counts of the reused
+   workspace over all steps.  Returns RICH_EINVAL for bad arguments or
+   the builder's error. */
+int rich_mesh_update_check(const rich_config *cfg, int64_t n, int32_t steps, const double *xs, const double *ys,
+                           int32_t threads, int32_t *mismatched, int64_t *updated, int64_t *rebuilt);
+
 #ifdef __cplusplus
 }
 #endif

@@ -236,6 +236,7 @@ int Delaunay::build(const double *x, const double *y, int32_t np)
     double M = std::max(xmax - xmin, ymax - ymin);
     if (!(M > 0)) M = 1.0;
     // enclosing triangle far outside the bounding box
+    corner_ = np;
     px_.push_back(cx - 64.0 * M); py_.push_back(cy - 32.0 * M);
     px_.push_back(cx + 64.0 * M); py_.push_back(cy - 32.0 * M);
     px_.push_back(cx);            py_.push_back(cy + 64.0 * M);
@@ -254,6 +255,66 @@ int Delaunay::build(const double *x, const double *y, int32_t np)
         else insert_on_edge(t, edge, p);
     }
     return 0;
+}
+
+bool Delaunay::all_ccw() const
+{
+    for (const Tri &T : tris)
+        if (orient2d(px_[T.v[0]], py_[T.v[0]], px_[T.v[1]], py_[T.v[1]], px_[T.v[2]], py_[T.v[2]]) <= 0) return false;
+    return true;
+}
+
+// Lawson: test every edge once, flip the ones whose opposite vertex lies
+// inside the circumcircle, and test again the four outer edges of each
+// flipped quadrilateral.  An entry is (triangle, k): the edge opposite
+// vertex k; entries left stale by later flips test whatever edge is there.
+void Delaunay::make_delaunay()
+{
+    edges_.clear();
+    for (int32_t t = 0; t < (int32_t)tris.size(); t++)
+        for (int k = 0; k < 3; k++)
+            if (tris[t].nb[k] > t) edges_.push_back(((int64_t)t << 2) | k);
+    while (!edges_.empty()) {
+        const int64_t ek = edges_.back();
+        edges_.pop_back();
+        const int32_t t = (int32_t)(ek >> 2);
+        const int k = (int)(ek & 3);
+        const Tri T = tris[t];
+        const int32_t u = T.nb[k];
+        if (u < 0) continue;
+        const Tri U = tris[u];
+        int m = 0;
+        while (m < 3 && U.nb[m] != t) m++;
+        if (m == 3) continue;
+        const int32_t a = T.v[k], b = T.v[(k + 1) % 3], c = T.v[(k + 2) % 3], d = U.v[m];
+        if (incircle_sos(px_[a], py_[a], px_[b], py_[b], px_[c], py_[c], px_[d], py_[d]) <= 0) continue;
+        // flip edge (b, c) of (a, b, c) and (d, c, b) into (a, d)
+        const int32_t t_ca = T.nb[(k + 1) % 3], t_ab = T.nb[(k + 2) % 3];
+        const int32_t u_bd = U.nb[(m + 1) % 3], u_dc = U.nb[(m + 2) % 3];
+        tris[t] = Tri{{a, b, d}, {u_bd, u, t_ab}};
+        tris[u] = Tri{{a, d, c}, {u_dc, t_ca, t}};
+        set_nb(u_bd, u, t);
+        set_nb(t_ca, t, u);
+        edges_.push_back(((int64_t)t << 2) | 0);
+        edges_.push_back(((int64_t)t << 2) | 2);
+        edges_.push_back(((int64_t)u << 2) | 0);
+        edges_.push_back(((int64_t)u << 2) | 1);
+    }
+}
+
+int32_t Delaunay::insert_point(double x, double y)
+{
+    const int32_t p = (int32_t)px_.size();
+    px_.push_back(x);
+    py_.push_back(y);
+    int32_t t = -1;
+    int edge = -1;
+    const int r = locate(p, t, edge);
+    if (r == -2) return -2;
+    if (r < 0) return -3;
+    if (r == 0) insert_inside(t, p);
+    else insert_on_edge(t, edge, p);
+    return p;
 }
 
 void degree_order(int32_t n, const int32_t *cell_ptr, int32_t *order)
@@ -307,13 +368,14 @@ static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const 
                 double X = image_coord(x[i], box.x0, box.x1, fx, sx);
                 double Y = image_coord(y[i], box.y0, box.y1, fy, sy);
                 if (X < lox || X > hix || Y < loy || Y > hiy) continue;
-                emit(X, Y, (fx ? XF_MIRROR_X : 0) | (fy ? XF_MIRROR_Y : 0), (sx + 1) + 3 * (sy + 1));
+                emit(X, Y, (fx ? XF_MIRROR_X : 0) | (fy ? XF_MIRROR_Y : 0), (sx + 1) + 3 * (sy + 1),
+                     (a + 1) + 3 * (b + 1));
             }
     };
     auto count = [&](int64_t c) {
         int64_t k = 0;
         for (int32_t i = (int32_t)(c * kChunk); i < std::min<int64_t>(n, (c + 1) * kChunk); i++)
-            visit(i, [&](double, double, int32_t, int32_t) { k++; });
+            visit(i, [&](double, double, int32_t, int32_t, int32_t) { k++; });
         off[c + 1] = k;
     };
     if (pool && nc > 1) pool->parallel_for(nc, count);
@@ -322,11 +384,13 @@ static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const 
     for (int64_t c = 0; c < nc; c++) off[c + 1] += off[c];
     const size_t g = (size_t)off[nc];
     m.gx.resize(g); m.gy.resize(g); m.ghost_src.resize(g); m.ghost_xf.resize(g); m.ghost_shift.resize(g);
+    m.ghost_img.resize(g);
     auto fill = [&](int64_t c) {
         int64_t k = off[c];
         for (int32_t i = (int32_t)(c * kChunk); i < std::min<int64_t>(n, (c + 1) * kChunk); i++)
-            visit(i, [&](double X, double Y, int32_t xf, int32_t sh) {
+            visit(i, [&](double X, double Y, int32_t xf, int32_t sh, int32_t img) {
                 m.gx[k] = X; m.gy[k] = Y; m.ghost_src[k] = i; m.ghost_xf[k] = xf; m.ghost_shift[k] = sh;
+                m.ghost_img[k] = img;
                 k++;
             });
     };
@@ -419,13 +483,6 @@ void build_grid(int32_t np, const double *X, const double *Y, const double ext[4
     g.ids = w.grid_ids.data();
 }
 
-// A tile of the point set: x in [x0, x1), y in [y0, y1); open sides (the
-// first / last along an axis) extend to infinity.
-struct Tile {
-    double x0, x1, y0, y1;
-    bool fx, lx, fy, ly;
-};
-
 // Outcome of one tile: the rings of its real core cells, the triangles they
 // use (global point ids, smallest id first), whether the halo and the ghost
 // band were wide enough, and the halo its stars actually needed.
@@ -440,50 +497,147 @@ struct SlabResult {
     std::vector<int32_t> tris;   // 3 per slab-local triangle
 };
 
-// Triangulate the points of a tile plus a halo of width H, and read off the
-// stars of its real core points.  A star is the true one when the
+// What every tile of one build shares.
+struct SlabCtx {
+    int32_t n = 0, np = 0;
+    const double *X = nullptr, *Y = nullptr;  // real points, then ghosts
+    const BoxConfig *box = nullptr;
+    const HostMesh *m = nullptr;              // ghost sources and images
+    const double *ext = nullptr;              // bounding box of all points
+    const PointGrid *grid = nullptr;
+    const double *band = nullptr;
+    double pad = 0.0;
+    const MeshWork *work = nullptr;           // ghost key lookup of this build
+};
+
+// internal: an updated triangulation cannot be used (a star touches an
+// image that is no longer in the point set): build the tile afresh
+constexpr int kRedo = -100;
+
+inline int64_t point_key(const SlabCtx &c, int32_t q)
+{
+    if (q < c.n) return q;
+    const int32_t g = q - c.n;
+    return (int64_t)c.n + 9 * (int64_t)c.m->ghost_src[g] + c.m->ghost_img[g];
+}
+
+// The tile's rectangle with its halo (a halo that covers every point makes
+// the tile's triangulation the whole one).
+struct Rect {
+    double xlo, xhi, ylo, yhi;
+    bool whole;
+};
+
+Rect tile_rect(const SlabCtx &c, const Tile &tile, double H)
+{
+    Rect R{tile.fx ? -INFINITY : tile.x0 - H, tile.lx ? INFINITY : tile.x1 + H, tile.fy ? -INFINITY : tile.y0 - H,
+           tile.ly ? INFINITY : tile.y1 + H, false};
+    R.whole = R.xlo <= c.ext[0] && R.xhi > c.ext[1] && R.ylo <= c.ext[2] && R.yhi > c.ext[3];
+    if (R.whole) R.xlo = R.ylo = -INFINITY, R.xhi = R.yhi = INFINITY;
+    return R;
+}
+
+// Every point of the rectangle, from the grid buckets it overlaps.
+template <class F> void for_rect_points(const SlabCtx &c, const Rect &R, F &&f)
+{
+    const PointGrid &grid = *c.grid;
+    const int c0 = grid.col(R.xlo), c1 = grid.col(R.xhi), r0 = grid.row(R.ylo), r1 = grid.row(R.yhi);
+    for (int rw = r0; rw <= r1; rw++)
+        for (int32_t k = grid.start[rw * grid.G + c0]; k < grid.start[rw * grid.G + c1 + 1]; k++) {
+            const int32_t q = grid.ids[k];
+            if (c.X[q] >= R.xlo && c.X[q] < R.xhi && c.Y[q] >= R.ylo && c.Y[q] < R.yhi) f(q);
+        }
+}
+
+// Update the tile's last triangulation for this build's points: move every
+// vertex to its point's new position (an image that left the ghost band
+// stays, at its source's new image position: it is still a point of the
+// periodic or mirrored plane), give up if a triangle turned over, flip to
+// Delaunay, and insert the points of the rectangle that are not vertices
+// yet.  Returns false when the tile must be built afresh.
+bool update_slab(const SlabCtx &c, const Rect &R, Delaunay &dt, std::vector<int32_t> &loc,
+                 std::vector<int64_t> &keys, std::vector<uint32_t> &stamp)
+{
+    const int32_t NL = dt.size();
+    if ((int32_t)keys.size() != NL || NL < 3) return false;
+    const MeshWork &w = *c.work;
+    if ((int32_t)stamp.size() < c.np) stamp.resize(c.np, 0u);
+    loc.resize(NL);
+    int32_t stray = 0;
+    for (int32_t v = 0; v < NL; v++) {
+        const int64_t k = keys[v];
+        if (k == -2) {
+            loc[v] = -2;
+            continue;
+        }
+        int32_t q;
+        double px, py;
+        if (k < c.n) {
+            q = (int32_t)k;
+            px = c.X[q];
+            py = c.Y[q];
+        } else {
+            const int64_t gk = k - c.n;
+            const int32_t src = (int32_t)(gk / 9), img = (int32_t)(gk % 9);
+            if (w.gkey_stamp[gk] == w.gen) {
+                q = c.n + w.gkey_idx[gk];
+                px = c.X[q];
+                py = c.Y[q];
+            } else {
+                q = -1;
+                const int a = img % 3 - 1, b = img / 3 - 1;
+                const BoxConfig &box = *c.box;
+                const bool per = box.boundary == 1;
+                px = image_coord(c.X[src], box.x0, box.x1, per ? 0 : a, per ? a : 0);
+                py = image_coord(c.Y[src], box.y0, box.y1, per ? 0 : b, per ? b : 0);
+            }
+        }
+        loc[v] = q;
+        dt.move(v, px, py);
+        if (q >= 0) stamp[q] = w.gen;
+        if (q < 0 || !(px >= R.xlo && px < R.xhi && py >= R.ylo && py < R.yhi)) stray++;
+    }
+    // vertices that are no longer needed are kept; rebuild once they are many
+    if (stray > NL / 4) return false;
+    if (!dt.all_ccw()) return false;
+    dt.make_delaunay();
+    bool ok = true;
+    for_rect_points(c, R, [&](int32_t q) {
+        if (!ok || stamp[q] == w.gen) return;
+        const int32_t v = dt.insert_point(c.X[q], c.Y[q]);
+        if (v < 0) {
+            ok = false;
+            return;
+        }
+        loc.push_back(q);
+        keys.push_back(point_key(c, q));
+        stamp[q] = w.gen;
+    });
+    return ok;
+}
+
+// Read off the stars of the tile's real core points from dt, whose vertex v
+// is point loc[v] (negative: a corner of the enclosing triangle, or an
+// image no longer in the point set).  A star is the true one when the
 // circumdisk of each of its triangles lies inside the triangulated
 // rectangle: every point of the whole set inside such a disk was then
 // triangulated too, and an empty circumdisk among them is empty in the
 // whole set.
-void build_slab(int32_t n, const double *X, const double *Y, const double ext[4], const PointGrid &grid,
-                const Tile &tile, double H, const double band[4], double pad, Delaunay &dt,
-                std::vector<int32_t> &loc, std::vector<double> &LX, std::vector<double> &LY, SlabResult &r)
+void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delaunay &dt,
+                const std::vector<int32_t> &loc, SlabResult &r)
 {
-    r = SlabResult();
-    double xlo = tile.fx ? -INFINITY : tile.x0 - H, xhi = tile.lx ? INFINITY : tile.x1 + H;
-    double ylo = tile.fy ? -INFINITY : tile.y0 - H, yhi = tile.ly ? INFINITY : tile.y1 + H;
-    // a halo that covers every point makes the tile's triangulation the whole one
-    const bool whole = xlo <= ext[0] && xhi > ext[1] && ylo <= ext[2] && yhi > ext[3];
-    if (whole) xlo = ylo = -INFINITY, xhi = yhi = INFINITY;
-    loc.clear();
-    LX.clear();
-    LY.clear();
-    // the points of the rectangle, from the grid buckets it overlaps (the
-    // local order is bucket by bucket; the triangulation does not depend on
-    // it, and the rings and triangles are put in canonical order below)
-    const int c0 = grid.col(xlo), c1 = grid.col(xhi), r0 = grid.row(ylo), r1 = grid.row(yhi);
-    for (int rw = r0; rw <= r1; rw++)
-        for (int32_t k = grid.start[rw * grid.G + c0]; k < grid.start[rw * grid.G + c1 + 1]; k++) {
-            const int32_t q = grid.ids[k];
-            if (X[q] >= xlo && X[q] < xhi && Y[q] >= ylo && Y[q] < yhi) {
-                loc.push_back(q);
-                LX.push_back(X[q]);
-                LY.push_back(Y[q]);
-            }
-        }
-    const int32_t nl = (int32_t)loc.size();
-    if (nl == 0) return;
-    r.rc = dt.build(LX.data(), LY.data(), nl);
-    if (r.rc) return;
+    const int32_t n = c.n, nl = dt.size();
+    const double xlo = R.xlo, xhi = R.xhi, ylo = R.ylo, yhi = R.yhi;
+    const bool whole = R.whole;
+    const double *band = c.band, pad = c.pad;
+    const double *LX = dt.xs(), *LY = dt.ys();
     const std::vector<Tri> &T = dt.tris;
-    // real points of the tile itself (the corners of the enclosing triangle,
-    // nl..nl+2, are not)
-    std::vector<uint8_t> core(nl + 3, 0);
+    // real points of the tile itself
+    std::vector<uint8_t> core(nl, 0);
     int32_t ncore = 0;
     for (int32_t v = 0; v < nl; v++) {
         const double px = LX[v], py = LY[v];
-        core[v] = loc[v] < n && (tile.fx || px >= tile.x0) && (tile.lx || px < tile.x1) &&
+        core[v] = loc[v] >= 0 && loc[v] < n && (tile.fx || px >= tile.x0) && (tile.lx || px < tile.x1) &&
                   (tile.fy || py >= tile.y0) && (tile.ly || py < tile.y1);
         ncore += core[v];
     }
@@ -495,14 +649,18 @@ void build_slab(int32_t n, const double *X, const double *Y, const double ext[4]
     for (size_t t = 0; t < T.size(); t++) {
         const int32_t *v = T[t].v;
         if (!core_real(v[0]) && !core_real(v[1]) && !core_real(v[2])) continue;
-        if (v[0] >= nl || v[1] >= nl || v[2] >= nl) {
+        if (dt.is_corner(v[0]) || dt.is_corner(v[1]) || dt.is_corner(v[2])) {
             // a real point on the hull of the triangulated points: the ghost
             // band, or else the halo, is too narrow
             if (whole) r.band_ok = false;
             else r.halo_ok = false;
             return;
         }
-        const Disk D = circumdisk(LX.data(), LY.data(), v[0], v[1], v[2], pad);
+        if (loc[v[0]] < 0 || loc[v[1]] < 0 || loc[v[2]] < 0) {
+            r.rc = kRedo;
+            return;
+        }
+        const Disk D = circumdisk(LX, LY, v[0], v[1], v[2], pad);
         if (!(D.ux - D.R >= band[0] && D.ux + D.R <= band[1] && D.uy - D.R >= band[2] && D.uy + D.R <= band[3])) {
             r.band_ok = false;
             return;
@@ -593,6 +751,48 @@ void build_slab(int32_t n, const double *X, const double *Y, const double ext[4]
     }
 }
 
+// Triangulate the points of a tile plus a halo of width H (by updating the
+// tile's last triangulation when `update` is set and that succeeds), keep
+// the keys of its vertices for the next build, and read off the stars of its
+// real core points.
+void build_slab(const SlabCtx &c, const Tile &tile, double H, bool update, Delaunay &dt, std::vector<int32_t> &loc,
+                std::vector<double> &LX, std::vector<double> &LY, std::vector<int64_t> &keys,
+                std::vector<uint32_t> &stamp, bool &updated, SlabResult &r)
+{
+    r = SlabResult();
+    updated = false;
+    const Rect R = tile_rect(c, tile, H);
+    if (update && update_slab(c, R, dt, loc, keys, stamp)) {
+        read_stars(c, tile, R, dt, loc, r);
+        if (r.rc != kRedo) {
+            updated = true;
+            return;
+        }
+        r = SlabResult();
+    }
+    // afresh: the points of the rectangle (bucket by bucket; the
+    // triangulation does not depend on their order, and the rings and
+    // triangles are put in canonical order)
+    loc.clear();
+    LX.clear();
+    LY.clear();
+    keys.clear();
+    for_rect_points(c, R, [&](int32_t q) {
+        loc.push_back(q);
+        LX.push_back(c.X[q]);
+        LY.push_back(c.Y[q]);
+    });
+    const int32_t nl = (int32_t)loc.size();
+    if (nl == 0) return;
+    r.rc = dt.build(LX.data(), LY.data(), nl);
+    if (r.rc) return;
+    loc.resize(nl + 3, -2);
+    keys.resize(nl + 3, -2);
+    for (int32_t v = 0; v < nl; v++) keys[v] = point_key(c, loc[v]);
+    read_stars(c, tile, R, dt, loc, r);
+    if (r.rc == kRedo) r.rc = -3;  // (a fresh build has no stale images)
+}
+
 }  // namespace
 
 int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const double *y, MeshWork &work, HostMesh &m,
@@ -616,12 +816,31 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     work.loc.resize(K);
     work.lx.resize(K);
     work.ly.resize(K);
+    work.keys.resize(K);
+    work.stamp.resize(K);
+    // update the last build's tiles in place when there is one for these
+    // points (same count, same tiling)
+    const bool reuse = work.kinetic && work.n_kept == n && (int)work.tiles.size() == K &&
+                       (int)work.tile_halo.size() == K;
+    work.n_kept = -1;  // valid again only once this build succeeds
     std::vector<SlabResult> res(K);
+    std::vector<uint8_t> updated(K, 0);
     std::vector<double> X, Y;
     for (;;) {
         m.attempts++;
         make_ghosts(box, n, x, y, w, m, pool);
         const int32_t np = n + m.g;
+        // ghost key -> this build's ghost index
+        work.gen++;
+        if (work.gkey_idx.size() < 9 * (size_t)n) {
+            work.gkey_idx.assign(9 * (size_t)n, -1);
+            work.gkey_stamp.assign(9 * (size_t)n, 0u);
+        }
+        for (int32_t g = 0; g < m.g; g++) {
+            const size_t k = 9 * (size_t)m.ghost_src[g] + (size_t)m.ghost_img[g];
+            work.gkey_idx[k] = g;
+            work.gkey_stamp[k] = work.gen;
+        }
         X.resize(np);
         Y.resize(np);
         std::memcpy(X.data(), x, sizeof(double) * n);
@@ -657,10 +876,24 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         }
         PointGrid grid;
         build_grid(np, X.data(), Y.data(), ext, work, pool, grid);
+        SlabCtx ctx;
+        ctx.n = n;
+        ctx.np = np;
+        ctx.X = X.data();
+        ctx.Y = Y.data();
+        ctx.box = &box;
+        ctx.m = &m;
+        ctx.ext = ext;
+        ctx.grid = &grid;
+        ctx.band = band;
+        ctx.pad = pad;
+        ctx.work = &work;
         // column cuts at x-quantiles of (a sample of) the real + ghost
-        // points, then row cuts at y-quantiles within each column
+        // points, then row cuts at y-quantiles within each column (or the
+        // last build's tiles, to update them in place)
         std::vector<Tile> tiles(K);
-        {
+        if (reuse) tiles = work.tiles;
+        else {
             std::vector<int32_t> smp;
             smp.reserve(np / 8 + 1);
             for (int32_t q = 0; q < np; q += 8) smp.push_back(q);
@@ -699,15 +932,20 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
             }
         }
         // halo: what the stars needed last time (in mean spacings), else 6 h
+        // (a tile updated in place keeps its own)
         std::vector<double> H(K, (work.halo > 0 ? work.halo : 6.0) * h);
+        if (reuse) H = work.tile_halo;
+        std::vector<uint8_t> upd(K, reuse ? 1 : 0);
         std::vector<int> todo(K);
         for (int s = 0; s < K; s++) todo[s] = s;
         bool band_ok = true;
         while (!todo.empty()) {
             auto run = [&](int64_t k) {
                 const int s = todo[k];
-                build_slab(n, X.data(), Y.data(), ext, grid, tiles[s], H[s], band, pad, work.dts[s], work.loc[s],
-                           work.lx[s], work.ly[s], res[s]);
+                bool up = false;
+                build_slab(ctx, tiles[s], H[s], upd[s] != 0, work.dts[s], work.loc[s], work.lx[s], work.ly[s],
+                           work.keys[s], work.stamp[s], up, res[s]);
+                updated[s] = up ? 1 : 0;
             };
             if (pool && todo.size() > 1) pool->parallel_for((int64_t)todo.size(), run);
             else
@@ -718,6 +956,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
                 if (!res[s].band_ok) band_ok = false;
                 else if (!res[s].halo_ok) {
                     H[s] *= 1.5;
+                    upd[s] = 0;  // a wider rectangle: build afresh
                     again.push_back(s);
                 }
             }
@@ -735,6 +974,12 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         double need = 0.0;
         for (int s = 0; s < K; s++) need = std::max(need, res[s].needed);
         work.halo = std::max(2.0, 1.25 * need / h + 0.5);
+        for (int s = 0; s < K; s++) {
+            if (updated[s]) work.kinetic_tiles++;
+            else work.fresh_tiles++;
+        }
+        work.tiles = tiles;
+        work.tile_halo = H;
         break;
     }
     // triangles: concatenation of the slabs' lists
@@ -872,6 +1117,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         for (int64_t c = 0; c < nchunks; c++) finish(c);
     for (int64_t c = 0; c < nchunks; c++)
         if (missing[c]) return -3;
+    work.n_kept = n;
     return 0;
 }
 

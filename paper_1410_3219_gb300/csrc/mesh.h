@@ -41,6 +41,7 @@ struct HostMesh {
     std::vector<int32_t> ghost_src;     // real cell each ghost copies
     std::vector<int32_t> ghost_xf;      // XF_* flags
     std::vector<int32_t> ghost_shift;   // periodic shift code: (sx+1) + 3*(sy+1)
+    std::vector<int32_t> ghost_img;     // which image of its source: (a+1) + 3*(b+1), a, b in {-1, 0, 1}
     std::vector<int32_t> tri;           // 3 per triangle touching a real cell (point ids; ghosts n..n+g-1)
     std::vector<int32_t> cell_ptr;      // n+1 ring offsets
     std::vector<int32_t> slot_nb;       // neighbour point id
@@ -66,6 +67,29 @@ public:
     int build(const double *x, const double *y, int32_t np);
     std::vector<Tri> tris;
 
+    // Vertices, corners included (corner() .. corner() + 2), and positions.
+    int32_t size() const { return (int32_t)px_.size(); }
+    int32_t corner() const { return corner_; }
+    bool is_corner(int32_t v) const { return v >= corner_ && v < corner_ + 3; }
+    double x(int32_t v) const { return px_[v]; }
+    double y(int32_t v) const { return py_[v]; }
+    const double *xs() const { return px_.data(); }
+    const double *ys() const { return py_.data(); }
+
+    // Updating a built triangulation for moved points (the points keep their
+    // vertex numbers): move vertex v; then check that every triangle is
+    // still strictly counter-clockwise (returns false if not: the
+    // connectivity no longer describes a triangulation); then flip edges
+    // until every edge is locally Delaunay (Lawson), which from any
+    // triangulation of the same points ends at the unique (tie-broken)
+    // Delaunay one; then insert further points, appended after the corners
+    // (returns the new vertex, -2 for a point that coincides with one, -3
+    // if location fails).
+    void move(int32_t v, double x, double y) { px_[v] = x; py_[v] = y; }
+    bool all_ccw() const;
+    void make_delaunay();
+    int32_t insert_point(double x, double y);
+
 private:
     int locate(int32_t p, int32_t &t, int &edge);
     void insert_inside(int32_t t, int32_t p);
@@ -77,11 +101,22 @@ private:
     std::vector<double> px_, py_;
     std::vector<int32_t> order_;
     std::vector<int32_t> stack_;
+    std::vector<int64_t> edges_;
+    int32_t corner_ = 0;
     int32_t hint_ = 0;
     uint32_t rng_ = 12345u;
 };
 
-// Reusable buffers of build_host_mesh (one triangulator per slab).
+// A tile of the point set: x in [x0, x1), y in [y0, y1); open sides (the
+// first / last along an axis) extend to infinity.
+struct Tile {
+    double x0, x1, y0, y1;
+    bool fx, lx, fy, ly;
+};
+
+// Reusable buffers of build_host_mesh (one triangulator per tile), and what
+// the next build needs to update each tile's triangulation instead of
+// building it again.
 struct MeshWork {
     std::vector<Delaunay> dts;
     std::vector<std::vector<int32_t>> loc;
@@ -91,6 +126,24 @@ struct MeshWork {
     // from the buckets it overlaps instead of testing every point
     std::vector<int32_t> grid_start, grid_ids, grid_cell, grid_hist;
     double halo = 0.0;  // slab halo of the last build, in mean point spacings
+    // update in place (false: every build inserts every point again)
+    bool kinetic = true;
+    // the last build's tiles, their halos, and per tile the key of every
+    // local vertex: its real point's id, n + 9 src + image for a ghost (the
+    // image of real point src, see HostMesh::ghost_img), -2 for a corner of
+    // the enclosing triangle; n_kept = the real count they refer to (-1: none)
+    std::vector<Tile> tiles;
+    std::vector<double> tile_halo;
+    std::vector<std::vector<int64_t>> keys;
+    int32_t n_kept = -1;
+    // per tile: build stamp of each point present (sized to the points)
+    std::vector<std::vector<uint32_t>> stamp;
+    uint32_t gen = 0;
+    // new ghost index of each ghost key, valid where gkey_stamp == gen
+    std::vector<int32_t> gkey_idx;
+    std::vector<uint32_t> gkey_stamp;
+    // tiles updated in place and tiles built afresh, over all builds
+    int64_t kinetic_tiles = 0, fresh_tiles = 0;
 };
 
 class ThreadPool;

@@ -2,7 +2,9 @@
 // simulation, runs the host tessellation (a0) and enqueues the device sweep
 // (a1-a9) on a CUDA stream.  There is no CPU fallback: without a CUDA device
 // rich_init_mesh fails with RICH_ENODEV.
+#include <array>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -768,6 +770,43 @@ int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const do
         if (q < n) { nbx[s] = x[q]; nby[s] = y[q]; nbsrc[s] = q; }
         else { nbx[s] = m.gx[q - n]; nby[s] = m.gy[q - n]; nbsrc[s] = m.ghost_src[q - n]; }
     }
+    return RICH_OK;
+}
+
+int rich_mesh_update_check(const rich_config *cfg, int64_t n, int32_t steps, const double *xs, const double *ys,
+                           int32_t threads, int32_t *mismatched, int64_t *updated, int64_t *rebuilt)
+{
+    if (!valid_config(cfg) || n < 3 || n > INT32_MAX || steps < 1 || !xs || !ys || !mismatched || !updated ||
+        !rebuilt || threads < 1)
+        return fail(RICH_EINVAL, "bad arguments");
+    for (int64_t i = 0; i < (int64_t)steps * n; i++)
+        if (!point_inside(cfg, xs[i], ys[i])) return fail(RICH_EINVAL, "point outside the box");
+    const rich::BoxConfig box{cfg->boundary, cfg->x0, cfg->x1, cfg->y0, cfg->y1};
+    rich::ThreadPool pool(threads);
+    rich::MeshWork kept;
+    *mismatched = 0;
+    // a triangle's vertices (smallest id first in both builds)
+    auto tri_of = [](const rich::HostMesh &m, int32_t t) {
+        return std::array<int32_t, 3>{m.tri[3 * (size_t)t], m.tri[3 * (size_t)t + 1], m.tri[3 * (size_t)t + 2]};
+    };
+    for (int32_t k = 0; k < steps; k++) {
+        const double *x = xs + (size_t)k * n, *y = ys + (size_t)k * n;
+        rich::HostMesh a, b;
+        rich::MeshWork fresh;
+        int rc = rich::build_host_mesh(box, (int32_t)n, x, y, kept, a, &pool);
+        if (rc) return mesh_rc(rc);
+        rc = rich::build_host_mesh(box, (int32_t)n, x, y, fresh, b, &pool);
+        if (rc) return mesh_rc(rc);
+        bool same = a.g == b.g && a.gx == b.gx && a.gy == b.gy && a.ghost_src == b.ghost_src &&
+                    a.cell_ptr == b.cell_ptr && a.slot_nb == b.slot_nb && a.slot_edge == b.slot_edge &&
+                    a.edge_l == b.edge_l && a.edge_r == b.edge_r && a.cell_order == b.cell_order;
+        for (size_t s = 0; same && s < a.slot_tri.size(); s++) same = tri_of(a, a.slot_tri[s]) == tri_of(b, b.slot_tri[s]);
+        for (size_t e = 0; same && e < a.edge_ta.size(); e++)
+            same = tri_of(a, a.edge_ta[e]) == tri_of(b, b.edge_ta[e]) && tri_of(a, a.edge_tb[e]) == tri_of(b, b.edge_tb[e]);
+        if (!same) (*mismatched)++;
+    }
+    *updated = kept.kinetic_tiles;
+    *rebuilt = kept.fresh_tiles;
     return RICH_OK;
 }
 

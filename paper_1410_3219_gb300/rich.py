@@ -34,7 +34,7 @@ EXPORTS = ["rich_default_config", "rich_init_mesh", "rich_step", "rich_get_state
            "rich_batch_set_diagnostics", "rich_batch_cells", "rich_batch_destroy", "rich_batch_set_launch",
            "rich_batch_launch_info", "rich_server_create", "rich_server_submit", "rich_server_tick",
            "rich_server_query", "rich_server_fetch", "rich_server_batch", "rich_server_destroy",
-           "rich_init_conserved", "rich_get_order", "rich_time"]
+           "rich_init_conserved", "rich_get_order", "rich_time", "rich_mesh_update_check"]
 
 REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
@@ -104,6 +104,8 @@ def _lib():
         L.rich_num_cells.argtypes = [P]
         L.rich_num_cells.restype = I64
         L.rich_delaunay_host.argtypes = [I64, _D, _D, I64, C.POINTER(C.c_int32), C.POINTER(I64)]
+        L.rich_mesh_update_check.argtypes = [C.POINTER(rich_config), I64, I32, _D, _D, I32, C.POINTER(C.c_int32),
+                                             C.POINTER(I64), C.POINTER(I64)]
         L.rich_rings_host.argtypes = [C.POINTER(rich_config), I64, _D, _D, I64, C.POINTER(I64), _D, _D,
                                       C.POINTER(I64), C.POINTER(I64)]
         L.rich_set_profiling.argtypes = [P, I32]
@@ -299,6 +301,21 @@ def rich_rings_host(cfg, x, y):
                                   src.ctypes.data_as(I64P), C.byref(ns)))
     k = ns.value
     return ptr, nbx[:k], nby[:k], src[:k]
+
+
+def rich_mesh_update_check(cfg, xs, ys, threads=4):
+    """Host meshes of successive point sets (rows of the 2D arrays xs, ys)
+    built with one reused workspace and afresh: (steps whose sweep inputs
+    differ, tiles updated in place, tiles rebuilt)."""
+    c = cfg if isinstance(cfg, rich_config) else rich_config.from_dict(cfg)
+    xs, ys = np.atleast_2d(xs), np.atleast_2d(ys)
+    steps, n = xs.shape
+    xs, ys = _f64(xs.ravel()), _f64(ys.ravel())
+    mis, up, re = C.c_int32(), C.c_int64(), C.c_int64()
+    _check(_lib().rich_mesh_update_check(C.byref(c), n, steps, _p(xs), _p(ys), threads, C.byref(mis), C.byref(up),
+                                         C.byref(re)))
+    return mis.value, up.value, re.value
+
 
 
 def rich_batch_create(precision=0, max_cells=1 << 24, host_threads=0):

@@ -205,3 +205,39 @@ def test_restart_rejects_a_non_permutation_order_on_the_host(R):
         R.rich_init_conserved(wl["cfg"], wl["x"], wl["y"], m, z, z, E, 0.0, np.zeros(n, np.int64))
     # the order is checked once a device exists; without one the device check fails first
     assert e.value.code in (R.RICH_EINVAL, R.RICH_ENODEV)
+
+
+def _positions(oracle, wl, steps, skip=0):
+    s = oracle.Sim(wl)
+    n = len(wl["x"])
+    for _ in range(skip):
+        s.step()
+    xs, ys = [], []
+    for _ in range(steps):
+        X, Y, _ = s.points()
+        xs.append(X[:n].copy())
+        ys.append(Y[:n].copy())
+        s.step()
+    return np.array(xs), np.array(ys)
+
+
+@pytest.mark.parametrize("name,make,steps,skip,must_update", [
+    ("sod_32", lambda: W.sod(n_side=32), 8, 0, False),
+    ("kh_64", lambda: W.kelvin_helmholtz(n_side=64, amp=0.1), 8, 0, False),
+    ("sedov_20000", lambda: W.sedov(n=20000, seed=2), 6, 2, True),
+    ("kh_200", lambda: W.kelvin_helmholtz(n_side=200, amp=0.1), 4, 0, False),
+])
+def test_mesh_updated_in_place_equals_fresh(R, oracle, name, make, steps, skip, must_update):
+    """The host builder keeps each tile's triangulation between steps and
+    updates it (moves the vertices, flips to Delaunay, inserts new points;
+    rebuilds a tile where a triangle turned over): over successive steps of
+    oracle runs the sweep's inputs equal those of fresh builds exactly, with
+    one and with several tiles."""
+    wl = make()
+    xs, ys = _positions(oracle, wl, steps, skip)
+    for threads in (1, 4):
+        mismatched, updated, rebuilt = R.rich_mesh_update_check(wl["cfg"], xs, ys, threads=threads)
+        assert mismatched == 0, (threads, updated, rebuilt)
+        assert updated + rebuilt >= steps
+        if must_update:
+            assert updated >= steps - 1, (threads, updated, rebuilt)
