@@ -145,13 +145,28 @@ int Delaunay::locate(int32_t p, int32_t &t_out, int &edge)
     return -3;
 }
 
+// two triangle slots: freed ones first (a vertex removal frees two)
+void Delaunay::alloc2(int32_t &a, int32_t &b)
+{
+    if (free_.size() >= 2) {
+        a = free_.back();
+        free_.pop_back();
+        b = free_.back();
+        free_.pop_back();
+        return;
+    }
+    a = (int32_t)tris.size();
+    b = a + 1;
+    tris.resize(tris.size() + 2);
+}
+
 void Delaunay::insert_inside(int32_t t, int32_t p)
 {
     Tri old = tris[t];
     int32_t a = old.v[0], b = old.v[1], c = old.v[2];
     int32_t na = old.nb[0], nbb = old.nb[1], nc = old.nb[2];
-    int32_t t1 = (int32_t)tris.size(), t2 = t1 + 1;
-    tris.resize(tris.size() + 2);
+    int32_t t1, t2;
+    alloc2(t1, t2);
     tris[t] = Tri{{p, b, c}, {na, t1, t2}};
     tris[t1] = Tri{{p, c, a}, {nbb, t2, t}};
     tris[t2] = Tri{{p, a, b}, {nc, t, t1}};
@@ -176,8 +191,8 @@ void Delaunay::insert_on_edge(int32_t t, int k, int32_t p)
     int32_t d = U.v[m];
     int32_t u_bd = U.nb[(m + 1) % 3], u_dc = U.nb[(m + 2) % 3];
     int32_t A = t, Cc = u;
-    int32_t B = (int32_t)tris.size(), D = B + 1;
-    tris.resize(tris.size() + 2);
+    int32_t B, D;
+    alloc2(B, D);
     tris[A] = Tri{{p, c, a}, {t_ca, B, Cc}};
     tris[B] = Tri{{p, a, b}, {t_ab, D, A}};
     tris[Cc] = Tri{{p, d, c}, {u_dc, A, D}};
@@ -224,6 +239,7 @@ int Delaunay::build(const double *x, const double *y, int32_t np)
 {
     tris.clear();
     stack_.clear();
+    free_.clear();
     if (np < 1) return -3;
     px_.assign(x, x + np);
     py_.assign(y, y + np);
@@ -260,7 +276,172 @@ int Delaunay::build(const double *x, const double *y, int32_t np)
 bool Delaunay::all_ccw() const
 {
     for (const Tri &T : tris)
-        if (orient2d(px_[T.v[0]], py_[T.v[0]], px_[T.v[1]], py_[T.v[1]], px_[T.v[2]], py_[T.v[2]]) <= 0) return false;
+        if (T.v[0] >= 0 && orient2d(px_[T.v[0]], py_[T.v[0]], px_[T.v[1]], py_[T.v[1]], px_[T.v[2]], py_[T.v[2]]) <= 0)
+            return false;
+    return true;
+}
+
+// Flip the edge opposite vertex k of triangle t: (a, b, c) and (d, c, b)
+// become (a, b, d) and (a, d, c), in the slots of t and of the neighbour.
+void Delaunay::flip(int32_t t, int k)
+{
+    const Tri T = tris[t];
+    const int32_t u = T.nb[k];
+    const Tri U = tris[u];
+    int m = 0;
+    while (U.nb[m] != t) m++;
+    const int32_t a = T.v[k], b = T.v[(k + 1) % 3], c = T.v[(k + 2) % 3], d = U.v[m];
+    const int32_t t_ca = T.nb[(k + 1) % 3], t_ab = T.nb[(k + 2) % 3];
+    const int32_t u_bd = U.nb[(m + 1) % 3], u_dc = U.nb[(m + 2) % 3];
+    tris[t] = Tri{{a, b, d}, {u_bd, u, t_ab}};
+    tris[u] = Tri{{a, d, c}, {u_dc, t_ca, t}};
+    set_nb(u_bd, u, t);
+    set_nb(t_ca, t, u);
+}
+
+// whether that flip leaves two counter-clockwise triangles
+bool Delaunay::flip_ok(int32_t t, int k) const
+{
+    const Tri &T = tris[t];
+    const int32_t u = T.nb[k];
+    if (u < 0) return false;
+    const Tri &U = tris[u];
+    int m = 0;
+    while (m < 3 && U.nb[m] != t) m++;
+    if (m == 3) return false;
+    const int32_t a = T.v[k], b = T.v[(k + 1) % 3], c = T.v[(k + 2) % 3], d = U.v[m];
+    return orient2d(px_[a], py_[a], px_[b], py_[b], px_[d], py_[d]) > 0 &&
+           orient2d(px_[a], py_[a], px_[d], py_[d], px_[c], py_[c]) > 0;
+}
+
+// Take interior vertex v (in live triangle t) out: flip its edges away while
+// it has more than three, then merge its three triangles into the one of
+// its neighbours.  Frees two triangle slots.
+bool Delaunay::remove_vertex(int32_t v, int32_t t)
+{
+    std::vector<int32_t> st, lk;  // v's triangles and neighbours, counter-clockwise
+    for (int guard = 0; guard < 256; guard++) {
+        st.clear();
+        lk.clear();
+        int32_t cur = t;
+        for (int step = 0; step < 64; step++) {
+            const Tri &T = tris[cur];
+            int j = 0;
+            while (j < 3 && T.v[j] != v) j++;
+            if (j == 3) return false;
+            st.push_back(cur);
+            lk.push_back(T.v[(j + 1) % 3]);
+            cur = T.nb[(j + 1) % 3];  // across edge (v, T.v[j + 2])
+            if (cur < 0) return false;  // v on the hull
+            if (cur == t) break;
+        }
+        if (cur != t) return false;
+        const int d = (int)st.size();
+        if (d == 3) {
+            const int32_t l0 = lk[0], l1 = lk[1], l2 = lk[2];
+            if (orient2d(px_[l0], py_[l0], px_[l1], py_[l1], px_[l2], py_[l2]) <= 0) return false;
+            int32_t o[3];
+            for (int i = 0; i < 3; i++) {
+                const Tri &T = tris[st[i]];
+                int j = 0;
+                while (T.v[j] != v) j++;
+                o[i] = T.nb[j];  // across (l_i, l_i+1)
+            }
+            tris[st[0]] = Tri{{l0, l1, l2}, {o[1], o[2], o[0]}};
+            set_nb(o[1], st[1], st[0]);
+            set_nb(o[2], st[2], st[0]);
+            for (int i = 1; i < 3; i++) {
+                tris[st[i]] = Tri{{-1, -1, -1}, {-1, -1, -1}};
+                free_.push_back(st[i]);
+            }
+            hint_ = st[0];
+            return true;
+        }
+        // an edge (v, lk[i]) whose flip keeps both triangles counter-clockwise
+        bool done = false;
+        for (int i = 0; i < d && !done; i++) {
+            const Tri &T = tris[st[i]];
+            int j = 0;
+            while (T.v[j] != v) j++;
+            const int k = (j + 2) % 3;  // opposite lk[i + 1]: the edge (v, lk[i])
+            if (flip_ok(st[i], k)) {
+                flip(st[i], k);
+                t = st[i];  // still has v
+                done = true;
+            }
+        }
+        if (!done) return false;
+    }
+    return false;
+}
+
+int Delaunay::insert_at(int32_t v)
+{
+    int32_t t = -1;
+    int edge = -1;
+    const int r = locate(v, t, edge);
+    if (r == -2) return -2;
+    if (r < 0) return -3;
+    if (r == 0) insert_inside(t, v);
+    else insert_on_edge(t, edge, v);
+    return 0;
+}
+
+bool Delaunay::move_all(const std::vector<double> &nx, const std::vector<double> &ny, int32_t max_back)
+{
+    const int32_t NV = size();
+    const std::vector<double> ox(px_), oy(py_);
+    for (int32_t v = 0; v < NV; v++)
+        if (!is_corner(v)) {
+            px_[v] = nx[v];
+            py_[v] = ny[v];
+        }
+    std::vector<uint8_t> back(NV, 0);
+    std::vector<int32_t> S;
+    bool bad = true;
+    for (int it = 0; it < 16 && bad; it++) {
+        bad = false;
+        for (const Tri &T : tris) {
+            if (T.v[0] < 0) continue;
+            if (orient2d(px_[T.v[0]], py_[T.v[0]], px_[T.v[1]], py_[T.v[1]], px_[T.v[2]], py_[T.v[2]]) > 0) continue;
+            bad = true;
+            for (int k = 0; k < 3; k++) {
+                const int32_t v = T.v[k];
+                if (is_corner(v)) return false;
+                if (back[v]) continue;
+                back[v] = 1;
+                S.push_back(v);
+                px_[v] = ox[v];
+                py_[v] = oy[v];
+            }
+        }
+        if ((int32_t)S.size() > max_back) return false;
+    }
+    if (bad) return false;
+    make_delaunay();
+    if (S.empty()) return true;
+    // out with them (a triangle of each first, from one pass)
+    std::vector<int32_t> where(NV, -1);
+    for (int32_t t = 0; t < (int32_t)tris.size(); t++)
+        for (int k = 0; k < 3; k++)
+            if (tris[t].v[k] >= 0 && back[tris[t].v[k]]) where[tris[t].v[k]] = t;
+    for (int32_t v : S) {
+        int32_t t = where[v];
+        if (t < 0 || !(tris[t].v[0] == v || tris[t].v[1] == v || tris[t].v[2] == v)) {
+            // flips around an earlier removal moved it: look again
+            t = -1;
+            for (int32_t u = 0; u < (int32_t)tris.size() && t < 0; u++)
+                if (tris[u].v[0] == v || tris[u].v[1] == v || tris[u].v[2] == v) t = u;
+            if (t < 0) return false;
+        }
+        if (!remove_vertex(v, t)) return false;
+    }
+    make_delaunay();
+    for (int32_t v : S) {
+        px_[v] = nx[v];
+        py_[v] = ny[v];
+        if (insert_at(v) != 0) return false;
+    }
     return true;
 }
 
@@ -272,8 +453,9 @@ void Delaunay::make_delaunay()
 {
     edges_.clear();
     for (int32_t t = 0; t < (int32_t)tris.size(); t++)
-        for (int k = 0; k < 3; k++)
-            if (tris[t].nb[k] > t) edges_.push_back(((int64_t)t << 2) | k);
+        if (tris[t].v[0] >= 0)
+            for (int k = 0; k < 3; k++)
+                if (tris[t].nb[k] > t) edges_.push_back(((int64_t)t << 2) | k);
     while (!edges_.empty()) {
         const int64_t ek = edges_.back();
         edges_.pop_back();
@@ -289,12 +471,7 @@ void Delaunay::make_delaunay()
         const int32_t a = T.v[k], b = T.v[(k + 1) % 3], c = T.v[(k + 2) % 3], d = U.v[m];
         if (incircle_sos(px_[a], py_[a], px_[b], py_[b], px_[c], py_[c], px_[d], py_[d]) <= 0) continue;
         // flip edge (b, c) of (a, b, c) and (d, c, b) into (a, d)
-        const int32_t t_ca = T.nb[(k + 1) % 3], t_ab = T.nb[(k + 2) % 3];
-        const int32_t u_bd = U.nb[(m + 1) % 3], u_dc = U.nb[(m + 2) % 3];
-        tris[t] = Tri{{a, b, d}, {u_bd, u, t_ab}};
-        tris[u] = Tri{{a, d, c}, {u_dc, t_ca, t}};
-        set_nb(u_bd, u, t);
-        set_nb(t_ca, t, u);
+        flip(t, k);
         edges_.push_back(((int64_t)t << 2) | 0);
         edges_.push_back(((int64_t)t << 2) | 2);
         edges_.push_back(((int64_t)u << 2) | 0);
@@ -552,9 +729,10 @@ template <class F> void for_rect_points(const SlabCtx &c, const Rect &R, F &&f)
 // Update the tile's last triangulation for this build's points: move every
 // vertex to its point's new position (an image that left the ghost band
 // stays, at its source's new image position: it is still a point of the
-// periodic or mirrored plane), give up if a triangle turned over, flip to
-// Delaunay, and insert the points of the rectangle that are not vertices
-// yet.  Returns false when the tile must be built afresh.
+// periodic or mirrored plane; the vertices of triangles that would turn
+// over are taken out and inserted again), flip to Delaunay, and insert the
+// points of the rectangle that are not vertices yet.  Returns false when
+// the tile must be built afresh.
 bool update_slab(const SlabCtx &c, const Rect &R, Delaunay &dt, std::vector<int32_t> &loc,
                  std::vector<int64_t> &keys, std::vector<uint32_t> &stamp)
 {
@@ -563,11 +741,14 @@ bool update_slab(const SlabCtx &c, const Rect &R, Delaunay &dt, std::vector<int3
     const MeshWork &w = *c.work;
     if ((int32_t)stamp.size() < c.np) stamp.resize(c.np, 0u);
     loc.resize(NL);
+    std::vector<double> nx(NL), ny(NL);
     int32_t stray = 0;
     for (int32_t v = 0; v < NL; v++) {
         const int64_t k = keys[v];
         if (k == -2) {
             loc[v] = -2;
+            nx[v] = dt.x(v);
+            ny[v] = dt.y(v);
             continue;
         }
         int32_t q;
@@ -593,14 +774,16 @@ bool update_slab(const SlabCtx &c, const Rect &R, Delaunay &dt, std::vector<int3
             }
         }
         loc[v] = q;
-        dt.move(v, px, py);
+        nx[v] = px;
+        ny[v] = py;
         if (q >= 0) stamp[q] = w.gen;
         if (q < 0 || !(px >= R.xlo && px < R.xhi && py >= R.ylo && py < R.yhi)) stray++;
     }
     // vertices that are no longer needed are kept; rebuild once they are many
     if (stray > NL / 4) return false;
-    if (!dt.all_ccw()) return false;
-    dt.make_delaunay();
+    // (at most 2 % of the vertices taken out and put back where triangles
+    // would turn over; beyond that a fresh build is cheaper)
+    if (!dt.move_all(nx, ny, std::max<int32_t>(16, NL / 50))) return false;
     bool ok = true;
     for_rect_points(c, R, [&](int32_t q) {
         if (!ok || stamp[q] == w.gen) return;

@@ -89,6 +89,15 @@ public:
     bool all_ccw() const;
     void make_delaunay();
     int32_t insert_point(double x, double y);
+    // Where moving every vertex at once turns triangles over: move them
+    // (nx, ny: the new position of every vertex), put the vertices of
+    // turned-over triangles back until none is, flip to Delaunay, take those
+    // vertices out (flipping their edges away until three are left, then
+    // merging the three triangles) and insert them again at their new
+    // positions.  Returns false if that needs more than max_back vertices or
+    // fails (the caller then builds afresh); on success the triangulation
+    // is the Delaunay one of the new positions.
+    bool move_all(const std::vector<double> &nx, const std::vector<double> &ny, int32_t max_back);
 
 private:
     int locate(int32_t p, int32_t &t, int &edge);
@@ -97,11 +106,17 @@ private:
     void legalize(int32_t p);
     int incircle(int32_t t, int32_t d) const;
     void set_nb(int32_t t, int32_t old_nb, int32_t new_nb);
+    void alloc2(int32_t &a, int32_t &b);
+    bool flip_ok(int32_t t, int k) const;
+    void flip(int32_t t, int k);
+    bool remove_vertex(int32_t v, int32_t t);
+    int insert_at(int32_t v);
 
     std::vector<double> px_, py_;
     std::vector<int32_t> order_;
     std::vector<int32_t> stack_;
     std::vector<int64_t> edges_;
+    std::vector<int32_t> free_;
     int32_t corner_ = 0;
     int32_t hint_ = 0;
     uint32_t rng_ = 12345u;

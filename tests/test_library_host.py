@@ -221,23 +221,28 @@ def _positions(oracle, wl, steps, skip=0):
     return np.array(xs), np.array(ys)
 
 
-@pytest.mark.parametrize("name,make,steps,skip,must_update", [
-    ("sod_32", lambda: W.sod(n_side=32), 8, 0, False),
-    ("kh_64", lambda: W.kelvin_helmholtz(n_side=64, amp=0.1), 8, 0, False),
-    ("sedov_20000", lambda: W.sedov(n=20000, seed=2), 6, 2, True),
-    ("kh_200", lambda: W.kelvin_helmholtz(n_side=200, amp=0.1), 4, 0, False),
+@pytest.mark.parametrize("name,make,steps,skip", [
+    ("sod_64", lambda: W.sod(n_side=64), 40, 0),
+    ("kh_64", lambda: W.kelvin_helmholtz(n_side=64, amp=0.1), 30, 0),
+    ("gresho_32", lambda: W.gresho(n_side=32), 30, 0),
+    ("advection_lattice_16", lambda: W.advection(n_side=16), 20, 0),
+    ("random_mixed_reflective", lambda: W.random_mixed(n=3000, seed=8), 20, 0),
+    ("sedov_20000", lambda: W.sedov(n=20000, seed=2), 6, 2),
+    ("kh_200", lambda: W.kelvin_helmholtz(n_side=200, amp=0.1), 4, 0),
 ])
-def test_mesh_updated_in_place_equals_fresh(R, oracle, name, make, steps, skip, must_update):
+def test_mesh_updated_in_place_equals_fresh(R, oracle, name, make, steps, skip):
     """The host builder keeps each tile's triangulation between steps and
-    updates it (moves the vertices, flips to Delaunay, inserts new points;
-    rebuilds a tile where a triangle turned over): over successive steps of
-    oracle runs the sweep's inputs equal those of fresh builds exactly, with
-    one and with several tiles."""
+    updates it: moves the vertices (taking out and inserting again those of
+    triangles that would turn over), flips to Delaunay, inserts new points.
+    Over successive steps of oracle runs (co-circular lattices, mirrored and
+    periodic ghosts, one and several tiles) the sweep's inputs equal those
+    of fresh builds exactly, and after the first build nearly every tile is
+    updated rather than rebuilt."""
     wl = make()
     xs, ys = _positions(oracle, wl, steps, skip)
     for threads in (1, 4):
         mismatched, updated, rebuilt = R.rich_mesh_update_check(wl["cfg"], xs, ys, threads=threads)
         assert mismatched == 0, (threads, updated, rebuilt)
-        assert updated + rebuilt >= steps
-        if must_update:
-            assert updated >= steps - 1, (threads, updated, rebuilt)
+        tiles = updated + rebuilt
+        assert tiles >= steps
+        assert updated >= 0.75 * tiles - (tiles // steps), (threads, updated, rebuilt)
