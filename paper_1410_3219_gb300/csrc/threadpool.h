@@ -1,7 +1,11 @@
-// A small persistent worker pool for the host side of batched steps: the
-// tessellation (a0) of independent simulations runs on all host cores while
-// the device sweeps.  parallel_for hands out task indices dynamically (an
-// atomic counter), so instances of very different sizes balance.
+// A small persistent worker pool for the host side of the steps: the
+// tessellation (a0) tiles of one simulation, or the independent
+// simulations of a batch, run on all host cores.  parallel_for hands out
+// task indices dynamically (an atomic counter), so tasks of very different
+// sizes balance.  A build issues a dozen short parallel passes, so the
+// workers poll for the next batch of tasks for a short while before they
+// sleep, and the caller polls for their completion: waking sleeping
+// threads through a condition variable costs tens of microseconds a pass.
 #pragma once
 
 #include <atomic>
@@ -26,8 +30,8 @@ public:
     {
         {
             std::lock_guard<std::mutex> lk(mu_);
-            stop_ = true;
-            gen_++;
+            stop_.store(true, std::memory_order_relaxed);
+            gen_.fetch_add(1, std::memory_order_release);
         }
         cv_.notify_all();
         for (auto &w : workers_) w.join();
@@ -36,7 +40,9 @@ public:
     int size() const { return (int)workers_.size() + 1; }
 
     // Run fn(i) for i in [0, n) on the pool and the calling thread; returns
-    // when every task has finished.
+    // when every task has finished.  Every worker takes part in every call
+    // (it may find no task left), and the next call starts only after all
+    // of them have left this one.
     void parallel_for(int64_t n, const std::function<void(int64_t)> &fn)
     {
         if (n <= 0) return;
@@ -48,18 +54,20 @@ public:
             std::lock_guard<std::mutex> lk(mu_);
             fn_ = &fn;
             n_ = n;
-            next_.store(0);
-            active_ = (int)workers_.size();
-            gen_++;
+            next_.store(0, std::memory_order_relaxed);
+            active_.store((int)workers_.size(), std::memory_order_relaxed);
+            gen_.fetch_add(1, std::memory_order_release);
         }
         cv_.notify_all();
         run_tasks();
-        std::unique_lock<std::mutex> lk(mu_);
-        done_cv_.wait(lk, [this] { return active_ == 0; });
+        while (active_.load(std::memory_order_acquire) != 0) std::this_thread::yield();
         fn_ = nullptr;
     }
 
 private:
+    // polls of the generation before a worker sleeps (tens of microseconds)
+    static constexpr int kSpin = 1 << 14;
+
     void run_tasks()
     {
         for (;;) {
@@ -73,29 +81,28 @@ private:
     {
         uint64_t seen = 0;
         for (;;) {
-            {
+            bool woke = false;
+            for (int i = 0; i < kSpin && !woke; i++) woke = gen_.load(std::memory_order_acquire) != seen;
+            if (!woke) {
                 std::unique_lock<std::mutex> lk(mu_);
-                cv_.wait(lk, [&] { return gen_ != seen; });
-                seen = gen_;
-                if (stop_) return;
+                cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != seen; });
             }
+            seen = gen_.load(std::memory_order_acquire);
+            if (stop_.load(std::memory_order_relaxed)) return;
             run_tasks();
-            {
-                std::lock_guard<std::mutex> lk(mu_);
-                if (--active_ == 0) done_cv_.notify_one();
-            }
+            active_.fetch_sub(1, std::memory_order_acq_rel);
         }
     }
 
     std::vector<std::thread> workers_;
     std::mutex mu_;
-    std::condition_variable cv_, done_cv_;
+    std::condition_variable cv_;
     const std::function<void(int64_t)> *fn_ = nullptr;
     int64_t n_ = 0;
     std::atomic<int64_t> next_{0};
-    int active_ = 0;
-    uint64_t gen_ = 0;
-    bool stop_ = false;
+    std::atomic<int> active_{0};
+    std::atomic<uint64_t> gen_{0};
+    std::atomic<bool> stop_{false};
 };
 
 }  // namespace rich
