@@ -1008,7 +1008,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     work.n_kept = -1;  // valid again only once this build succeeds
     std::vector<SlabResult> res(K);
     std::vector<uint8_t> updated(K, 0);
-    std::vector<double> X, Y;
+    std::vector<double> &X = work.X, &Y = work.Y;
     for (;;) {
         m.attempts++;
         make_ghosts(box, n, x, y, w, m, pool);
@@ -1026,8 +1026,18 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         }
         X.resize(np);
         Y.resize(np);
-        std::memcpy(X.data(), x, sizeof(double) * n);
-        std::memcpy(Y.data(), y, sizeof(double) * n);
+        {
+            // copied in chunks on the pool (one thread copies ~5 GB/s)
+            const int64_t cc = 32768, ncc = (n + cc - 1) / cc;
+            auto copy = [&](int64_t c) {
+                const int64_t q0 = c * cc, q1 = std::min<int64_t>(n, q0 + cc);
+                std::memcpy(X.data() + q0, x + q0, sizeof(double) * (q1 - q0));
+                std::memcpy(Y.data() + q0, y + q0, sizeof(double) * (q1 - q0));
+            };
+            if (pool && ncc > 1) pool->parallel_for(ncc, copy);
+            else
+                for (int64_t c = 0; c < ncc; c++) copy(c);
+        }
         std::memcpy(X.data() + n, m.gx.data(), sizeof(double) * m.g);
         std::memcpy(Y.data() + n, m.gy.data(), sizeof(double) * m.g);
         const double band[4] = {box.x0 - w, box.x1 + w, box.y0 - w, box.y1 + w};

@@ -140,6 +140,8 @@ struct MeshWork {
     // increasing order within a bucket), so that a tile gathers its points
     // from the buckets it overlaps instead of testing every point
     std::vector<int32_t> grid_start, grid_ids, grid_cell, grid_hist;
+    // real then ghost coordinates of the current build
+    std::vector<double> X, Y;
     double halo = 0.0;  // slab halo of the last build, in mean point spacings
     // update in place (false: every build inserts every point again)
     bool kinetic = true;
