@@ -387,10 +387,12 @@ int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const do
    each, with `threads` host threads, and counts the steps whose sweep
    inputs differ (rings, their neighbours and triangles, the edge list,
    ghosts).  *updated and *rebuilt receive the tile counts of the reused
-   workspace over all steps.  Returns RICH_EINVAL for bad arguments or
-   the builder's error. */
+   workspace over all steps, *reinserted the vertices it took out and put
+   back where triangles would have turned over.  Returns RICH_EINVAL for bad
+   arguments or the builder's error. */
 int rich_mesh_update_check(const rich_config *cfg, int64_t n, int32_t steps, const double *xs, const double *ys,
-                           int32_t threads, int32_t *mismatched, int64_t *updated, int64_t *rebuilt);
+                           int32_t threads, int32_t *mismatched, int64_t *updated, int64_t *rebuilt,
+                           int64_t *reinserted);
 
 #ifdef __cplusplus
 }

@@ -442,6 +442,7 @@ bool Delaunay::move_all(const std::vector<double> &nx, const std::vector<double>
         py_[v] = ny[v];
         if (insert_at(v) != 0) return false;
     }
+    reinserted += (int64_t)S.size();
     return true;
 }
 
@@ -1173,6 +1174,8 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         }
         work.tiles = tiles;
         work.tile_halo = H;
+        work.reinserted = 0;
+        for (const Delaunay &d : work.dts) work.reinserted += d.reinserted;
         break;
     }
     // triangles: concatenation of the slabs' lists

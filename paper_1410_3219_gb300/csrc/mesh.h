@@ -98,6 +98,8 @@ public:
     // fails (the caller then builds afresh); on success the triangulation
     // is the Delaunay one of the new positions.
     bool move_all(const std::vector<double> &nx, const std::vector<double> &ny, int32_t max_back);
+    // vertices taken out and inserted again by move_all, over the object's life
+    int64_t reinserted = 0;
 
 private:
     int locate(int32_t p, int32_t &t, int &edge);
@@ -161,6 +163,8 @@ struct MeshWork {
     std::vector<uint32_t> gkey_stamp;
     // tiles updated in place and tiles built afresh, over all builds
     int64_t kinetic_tiles = 0, fresh_tiles = 0;
+    // vertices taken out and put back by the updates, over all builds
+    int64_t reinserted = 0;
 };
 
 class ThreadPool;

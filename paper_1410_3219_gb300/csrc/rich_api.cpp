@@ -774,10 +774,11 @@ int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const do
 }
 
 int rich_mesh_update_check(const rich_config *cfg, int64_t n, int32_t steps, const double *xs, const double *ys,
-                           int32_t threads, int32_t *mismatched, int64_t *updated, int64_t *rebuilt)
+                           int32_t threads, int32_t *mismatched, int64_t *updated, int64_t *rebuilt,
+                           int64_t *reinserted)
 {
     if (!valid_config(cfg) || n < 3 || n > INT32_MAX || steps < 1 || !xs || !ys || !mismatched || !updated ||
-        !rebuilt || threads < 1)
+        !rebuilt || !reinserted || threads < 1)
         return fail(RICH_EINVAL, "bad arguments");
     for (int64_t i = 0; i < (int64_t)steps * n; i++)
         if (!point_inside(cfg, xs[i], ys[i])) return fail(RICH_EINVAL, "point outside the box");
@@ -807,6 +808,7 @@ int rich_mesh_update_check(const rich_config *cfg, int64_t n, int32_t steps, con
     }
     *updated = kept.kinetic_tiles;
     *rebuilt = kept.fresh_tiles;
+    *reinserted = kept.reinserted;
     return RICH_OK;
 }
 

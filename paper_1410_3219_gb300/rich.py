@@ -105,7 +105,7 @@ def _lib():
         L.rich_num_cells.restype = I64
         L.rich_delaunay_host.argtypes = [I64, _D, _D, I64, C.POINTER(C.c_int32), C.POINTER(I64)]
         L.rich_mesh_update_check.argtypes = [C.POINTER(rich_config), I64, I32, _D, _D, I32, C.POINTER(C.c_int32),
-                                             C.POINTER(I64), C.POINTER(I64)]
+                                             C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]
         L.rich_rings_host.argtypes = [C.POINTER(rich_config), I64, _D, _D, I64, C.POINTER(I64), _D, _D,
                                       C.POINTER(I64), C.POINTER(I64)]
         L.rich_set_profiling.argtypes = [P, I32]
@@ -306,15 +306,16 @@ def rich_rings_host(cfg, x, y):
 def rich_mesh_update_check(cfg, xs, ys, threads=4):
     """Host meshes of successive point sets (rows of the 2D arrays xs, ys)
     built with one reused workspace and afresh: (steps whose sweep inputs
-    differ, tiles updated in place, tiles rebuilt)."""
+    differ, tiles updated in place, tiles rebuilt, vertices taken out and
+    re-inserted by the updates)."""
     c = cfg if isinstance(cfg, rich_config) else rich_config.from_dict(cfg)
     xs, ys = np.atleast_2d(xs), np.atleast_2d(ys)
     steps, n = xs.shape
     xs, ys = _f64(xs.ravel()), _f64(ys.ravel())
-    mis, up, re = C.c_int32(), C.c_int64(), C.c_int64()
+    mis, up, re, ri = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int64()
     _check(_lib().rich_mesh_update_check(C.byref(c), n, steps, _p(xs), _p(ys), threads, C.byref(mis), C.byref(up),
-                                         C.byref(re)))
-    return mis.value, up.value, re.value
+                                         C.byref(re), C.byref(ri)))
+    return mis.value, up.value, re.value, ri.value
 
 
 

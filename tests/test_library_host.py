@@ -221,16 +221,16 @@ def _positions(oracle, wl, steps, skip=0):
     return np.array(xs), np.array(ys)
 
 
-@pytest.mark.parametrize("name,make,steps,skip", [
-    ("sod_64", lambda: W.sod(n_side=64), 40, 0),
-    ("kh_64", lambda: W.kelvin_helmholtz(n_side=64, amp=0.1), 30, 0),
-    ("gresho_32", lambda: W.gresho(n_side=32), 30, 0),
-    ("advection_lattice_16", lambda: W.advection(n_side=16), 20, 0),
-    ("random_mixed_reflective", lambda: W.random_mixed(n=3000, seed=8), 20, 0),
-    ("sedov_20000", lambda: W.sedov(n=20000, seed=2), 6, 2),
-    ("kh_200", lambda: W.kelvin_helmholtz(n_side=200, amp=0.1), 4, 0),
+@pytest.mark.parametrize("name,make,steps,skip,turned", [
+    ("sod_64", lambda: W.sod(n_side=64), 40, 0, True),
+    ("kh_64", lambda: W.kelvin_helmholtz(n_side=64, amp=0.1), 30, 0, True),
+    ("gresho_32", lambda: W.gresho(n_side=32), 30, 0, False),
+    ("advection_lattice_16", lambda: W.advection(n_side=16), 20, 0, False),
+    ("random_mixed_reflective", lambda: W.random_mixed(n=3000, seed=8), 20, 0, False),
+    ("sedov_20000", lambda: W.sedov(n=20000, seed=2), 6, 2, False),
+    ("kh_200", lambda: W.kelvin_helmholtz(n_side=200, amp=0.1), 4, 0, True),
 ])
-def test_mesh_updated_in_place_equals_fresh(R, oracle, name, make, steps, skip):
+def test_mesh_updated_in_place_equals_fresh(R, oracle, name, make, steps, skip, turned):
     """The host builder keeps each tile's triangulation between steps and
     updates it: moves the vertices (taking out and inserting again those of
     triangles that would turn over), flips to Delaunay, inserts new points.
@@ -241,8 +241,12 @@ def test_mesh_updated_in_place_equals_fresh(R, oracle, name, make, steps, skip):
     wl = make()
     xs, ys = _positions(oracle, wl, steps, skip)
     for threads in (1, 4):
-        mismatched, updated, rebuilt = R.rich_mesh_update_check(wl["cfg"], xs, ys, threads=threads)
-        assert mismatched == 0, (threads, updated, rebuilt)
+        mismatched, updated, rebuilt, reinserted = R.rich_mesh_update_check(wl["cfg"], xs, ys, threads=threads)
+        assert mismatched == 0, (threads, updated, rebuilt, reinserted)
         tiles = updated + rebuilt
         assert tiles >= steps
         assert updated >= 0.75 * tiles - (tiles // steps), (threads, updated, rebuilt)
+        if turned:
+            # the runs where triangles would turn over exercise the
+            # take-out-and-re-insert path
+            assert reinserted > 0, (threads, updated, rebuilt)
