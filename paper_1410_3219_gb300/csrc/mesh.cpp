@@ -348,6 +348,7 @@ bool Delaunay::remove_vertex(int32_t v, int32_t t)
                 o[i] = T.nb[j];  // across (l_i, l_i+1)
             }
             tris[st[0]] = Tri{{l0, l1, l2}, {o[1], o[2], o[0]}};
+            touched_.push_back(st[0]);
             set_nb(o[1], st[1], st[0]);
             set_nb(o[2], st[2], st[0]);
             for (int i = 1; i < 3; i++) {
@@ -365,6 +366,8 @@ bool Delaunay::remove_vertex(int32_t v, int32_t t)
             while (T.v[j] != v) j++;
             const int k = (j + 2) % 3;  // opposite lk[i + 1]: the edge (v, lk[i])
             if (flip_ok(st[i], k)) {
+                touched_.push_back(st[i]);
+                touched_.push_back(tris[st[i]].nb[k]);
                 flip(st[i], k);
                 t = st[i];  // still has v
                 done = true;
@@ -426,15 +429,16 @@ bool Delaunay::move_all(const std::vector<double> &nx, const std::vector<double>
         for (int k = 0; k < 3; k++)
             if (tris[t].v[k] >= 0 && back[tris[t].v[k]]) where[tris[t].v[k]] = t;
     for (int32_t v : S) {
-        int32_t t = where[v];
-        if (t < 0 || !(tris[t].v[0] == v || tris[t].v[1] == v || tris[t].v[2] == v)) {
-            // flips around an earlier removal moved it: look again
-            t = -1;
-            for (int32_t u = 0; u < (int32_t)tris.size() && t < 0; u++)
-                if (tris[u].v[0] == v || tris[u].v[1] == v || tris[u].v[2] == v) t = u;
-            if (t < 0) return false;
-        }
+        const int32_t t = where[v];
+        if (t < 0 || !(tris[t].v[0] == v || tris[t].v[1] == v || tris[t].v[2] == v)) return false;
+        touched_.clear();
         if (!remove_vertex(v, t)) return false;
+        // the triangles the removal rewrote are where the remaining
+        // vertices of S around it now are
+        for (int32_t u : touched_)
+            if (tris[u].v[0] >= 0)
+                for (int k = 0; k < 3; k++)
+                    if (back[tris[u].v[k]]) where[tris[u].v[k]] = u;
     }
     make_delaunay();
     for (int32_t v : S) {

@@ -119,6 +119,7 @@ private:
     std::vector<int32_t> stack_;
     std::vector<int64_t> edges_;
     std::vector<int32_t> free_;
+    std::vector<int32_t> touched_;  // triangles remove_vertex rewrote
     int32_t corner_ = 0;
     int32_t hint_ = 0;
     uint32_t rng_ = 12345u;
