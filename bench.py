@@ -351,8 +351,12 @@ def run_ours(args):
             parts[k] += info[k] / e2e_steps
         rc = L.rich_get_conserved(sim2.h, n, *[b.ctypes.data_as(Dp) for b in bufs])
         assert rc == 0
-        h2d = (16 * info["n_ghost"] + 8 * info["n_ghost"] + 12 * info["n_tri"] + 4 * (n + 1)
-               + 12 * info["n_slots"] + 16 * info["n_edges"])
+        # what rich_tessellate uploads: ghost positions, sources, mirror
+        # flags and shifts; triangles; ring offsets, processing order and
+        # first owned edge per cell; ring neighbours and triangles (the
+        # edge list itself is built on the device)
+        h2d = (28 * info["n_ghost"] + 12 * info["n_tri"] + 4 * (n + 1) + 4 * n + 4 * (n + 1)
+               + 8 * info["n_slots"])
         d2h = 16 * n + 12 + 48 * n
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, ws)

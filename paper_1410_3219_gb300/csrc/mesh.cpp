@@ -1238,14 +1238,20 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     const int64_t nchunks = (n + chunk - 1) / chunk;
     std::vector<int64_t> ecount(nchunks + 1, 0);
     std::vector<int> bad(nchunks, 0);
+    // owned edges per cell (kept in edge_off for the device-built list)
+    m.edge_off.resize((size_t)n + 1);
     auto count = [&](int64_t c) {
         int64_t e = 0;
-        for (int32_t i = (int32_t)(c * chunk); i < std::min<int64_t>(n, (c + 1) * chunk); i++)
+        for (int32_t i = (int32_t)(c * chunk); i < std::min<int64_t>(n, (c + 1) * chunk); i++) {
+            int32_t k = 0;
             for (int32_t s = m.cell_ptr[i]; s < m.cell_ptr[i + 1]; s++) {
                 const int o = owns(i, m.slot_nb[s]);
                 if (o < 0) bad[c] = 1;
-                e += o > 0;
+                k += o > 0;
             }
+            m.edge_off[i] = k;
+            e += k;
+        }
         ecount[c + 1] = e;
     };
     if (pool) pool->parallel_for(nchunks, count);
@@ -1256,6 +1262,39 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         ecount[c + 1] += ecount[c];
     }
     const size_t E = (size_t)ecount[nchunks];
+    m.n_edges = (int32_t)E;
+    // counts -> offsets: each chunk from its own start
+    auto offsets = [&](int64_t c) {
+        int64_t run = ecount[c];
+        for (int32_t i = (int32_t)(c * chunk); i < std::min<int64_t>(n, (c + 1) * chunk); i++) {
+            const int32_t k = m.edge_off[i];
+            m.edge_off[i] = (int32_t)run;
+            run += k;
+        }
+    };
+    if (pool) pool->parallel_for(nchunks, offsets);
+    else
+        for (int64_t c = 0; c < nchunks; c++) offsets(c);
+    m.edge_off[n] = (int32_t)E;
+    if (!work.host_edges) {
+        // the device builds the list; the processing order is still needed
+        m.slot_edge.clear();
+        m.edge_l.clear();
+        m.edge_r.clear();
+        m.edge_ta.clear();
+        m.edge_tb.clear();
+        m.cell_order.resize(n);
+        auto order = [&](int64_t c) {
+            const int32_t i0 = (int32_t)(c * chunk), i1 = (int32_t)std::min<int64_t>(n, (c + 1) * chunk);
+            degree_order(i1 - i0, m.cell_ptr.data() + i0, m.cell_order.data() + i0);
+            for (int32_t i = i0; i < i1; i++) m.cell_order[i] += i0;
+        };
+        if (pool) pool->parallel_for(nchunks, order);
+        else
+            for (int64_t c = 0; c < nchunks; c++) order(c);
+        work.n_kept = n;
+        return 0;
+    }
     m.slot_edge.assign(S, -1);
     m.edge_l.resize(E);
     m.edge_r.resize(E);

@@ -50,6 +50,8 @@ struct HostMesh {
     std::vector<int32_t> edge_l, edge_r;   // left (real) and right (real or ghost) points
     std::vector<int32_t> edge_ta, edge_tb; // Voronoi edge runs from cc[ta] to cc[tb], ccw about left
     std::vector<int32_t> cell_order;    // processing order of the per-cell kernels (see degree_order)
+    std::vector<int32_t> edge_off;      // n+1: first edge owned by each cell (edges in ring order)
+    int32_t n_edges = 0;
     double band = 0.0;
     int attempts = 0;
 };
@@ -148,6 +150,9 @@ struct MeshWork {
     double halo = 0.0;  // slab halo of the last build, in mean point spacings
     // update in place (false: every build inserts every point again)
     bool kinetic = true;
+    // build the edge list (slot_edge, edge_l/r/ta/tb) on the host; false:
+    // only edge_off and n_edges, for a device that builds the list itself
+    bool host_edges = true;
     // the last build's tiles, their halos, and per tile the key of every
     // local vertex: its real point's id, n + 9 src + image for a ghost (the
     // image of real point src, see HostMesh::ghost_img), -2 for a corner of

@@ -80,9 +80,10 @@ struct rich_sim {
     int32_t n = 0;
     std::vector<int32_t> perm;  // internal -> caller index
     std::vector<double> hx, hy; // host copy of the points (internal order)
-    rich::MeshWork mw;
+    rich::MeshWork mw;  // (edge list built on the device: see tessellate)
     rich::HostMesh hm;
-    std::unique_ptr<rich::ThreadPool> pool;  // host threads of the slab-parallel tessellation
+    std::unique_ptr<rich::ThreadPool> pool;  // host threads of the tile-parallel tessellation
+    rich_sim() { mw.host_edges = false; }
     double t = 0.0;
     int cur = 0;
     // time-centred scheme: 1 between its two sweeps (buffers [2] then hold
@@ -103,7 +104,7 @@ struct rich_sim {
     DBuf x[3], y[3], U[3];
     DBuf A, o, W, cs, g, gl, alpha, w, tess, cell_ptr, corder, initW, rounding, p64, psrc;
     bool diagnostics = true;
-    DBuf gx, gy, gsrc, gxf;
+    DBuf gx, gy, gsrc, gxf, gshift, eoff;
     DBuf tri, ccx, ccy;
     DBuf slot_nb, slot_tri, slot_edge;
     DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F, ePM;
@@ -145,7 +146,7 @@ struct rich_sim {
         p.n = n;
         p.ng = hm.g;
         p.T = (int32_t)(hm.tri.size() / 3);
-        p.E = (int32_t)hm.edge_l.size();
+        p.E = hm.n_edges;
         p.S = (int32_t)hm.slot_nb.size();
         // extrapolated fluxes: [cur] -> [1 - cur].  Time-centred: [cur] -> [2]
         // by half a step, then primitives and mesh of [2], update of [cur]
@@ -213,7 +214,7 @@ struct rich_sim {
 
     // the mesh sizes of the current tessellation
     int32_t nT() const { return (int32_t)(hm.tri.size() / 3); }
-    int32_t nE() const { return (int32_t)hm.edge_l.size(); }
+    int32_t nE() const { return hm.n_edges; }
 };
 
 namespace {
@@ -254,7 +255,7 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     if (rc) return mesh_rc(rc);
     double t2 = now_ms();
     const rich::HostMesh &m = s->hm;
-    const size_t T = m.tri.size() / 3, E = m.edge_l.size(), d = sizeof(double);
+    const size_t T = m.tri.size() / 3, E = (size_t)m.n_edges, d = sizeof(double);
     CUDA_TRY(upload(s->gx, m.gx, s->stream));
     CUDA_TRY(upload(s->gy, m.gy, s->stream));
     CUDA_TRY(upload(s->gsrc, m.ghost_src, s->stream));
@@ -264,11 +265,21 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     CUDA_TRY(upload(s->corder, m.cell_order, s->stream));
     CUDA_TRY(upload(s->slot_nb, m.slot_nb, s->stream));
     CUDA_TRY(upload(s->slot_tri, m.slot_tri, s->stream));
-    CUDA_TRY(upload(s->slot_edge, m.slot_edge, s->stream));
-    CUDA_TRY(upload(s->edge_l, m.edge_l, s->stream));
-    CUDA_TRY(upload(s->edge_r, m.edge_r, s->stream));
-    CUDA_TRY(upload(s->edge_ta, m.edge_ta, s->stream));
-    CUDA_TRY(upload(s->edge_tb, m.edge_tb, s->stream));
+    // the edge list is built on the device from the rings (the host sends
+    // each cell's first owned edge and the ghosts' periodic shifts)
+    CUDA_TRY(upload(s->eoff, m.edge_off, s->stream));
+    CUDA_TRY(upload(s->gshift, m.ghost_shift, s->stream));
+    const size_t S = m.slot_nb.size();
+    CUDA_TRY(s->slot_edge.ensure((S + 1) * sizeof(int32_t)));
+    for (DBuf *b : {&s->edge_l, &s->edge_r, &s->edge_ta, &s->edge_tb}) CUDA_TRY(b->ensure((E + 1) * sizeof(int32_t)));
+    int32_t *bad = reinterpret_cast<int32_t *>(s->scal.as<char>() + 24);
+    CUDA_TRY(rich::launch_build_edges(s->n, (int32_t)S, s->cell_ptr.as<int32_t>(), s->slot_nb.as<int32_t>(),
+                                      s->slot_tri.as<int32_t>(), s->gsrc.as<int32_t>(), s->gshift.as<int32_t>(),
+                                      s->eoff.as<int32_t>(), s->cfg.boundary == RICH_BC_PERIODIC ? 1 : 0,
+                                      s->slot_edge.as<int32_t>(), s->edge_l.as<int32_t>(), s->edge_r.as<int32_t>(),
+                                      s->edge_ta.as<int32_t>(), s->edge_tb.as<int32_t>(), bad, s->stream));
+    int32_t bad_h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
     const size_t r = s->rsize();
     CUDA_TRY(s->ccx.ensure((T + 1) * d)); CUDA_TRY(s->ccy.ensure((T + 1) * d));
     for (DBuf *b : {&s->eL, &s->emlx, &s->emly, &s->emrx, &s->emry, &s->enx, &s->eny, &s->eqx, &s->eqy})
@@ -277,6 +288,7 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     CUDA_TRY(s->ePM.ensure((4 * E + 4) * r));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     double t3 = now_ms();
+    if (bad_h) return fail(RICH_ETESS, "an edge of a ring has no partner in the other cell's ring");
     s->tess_current = true;
     s->geometry_current = false;
     if (info) {

@@ -828,6 +828,71 @@ __global__ void k_repack(const int32_t *__restrict__ src, int32_t n_new, int32_t
     for (int c = 0; c < 4; c++) U_new[(size_t)c * n_new + i] = U_old[(size_t)c * n_old + k];
 }
 
+// owner of the edge between real cell i and point j (1: i, 0: the other
+// side, -1: inconsistent), the host builder's rule
+__device__ __forceinline__ int edge_owner(int32_t i, int32_t j, int32_t n, int32_t periodic,
+                                          const int32_t *ghost_src, const int32_t *ghost_shift)
+{
+    if (j < n) return j > i ? 1 : (j < i ? 0 : -1);
+    if (!periodic) return 1;
+    const int32_t src = ghost_src[j - n];
+    if (src != i) return src > i ? 1 : 0;
+    const int32_t sh = ghost_shift[j - n];
+    const int32_t sx = sh % 3 - 1, sy = sh / 3 - 1;
+    return (sy < 0 || (sy == 0 && sx < 0)) ? 0 : 1;
+}
+
+__global__ void k_build_edges(int32_t n, const int32_t *__restrict__ cell_ptr, const int32_t *__restrict__ slot_nb,
+                              const int32_t *__restrict__ slot_tri, const int32_t *__restrict__ ghost_src,
+                              const int32_t *__restrict__ ghost_shift, const int32_t *__restrict__ edge_off,
+                              int32_t periodic, int32_t *slot_edge, int32_t *edge_l, int32_t *edge_r,
+                              int32_t *edge_ta, int32_t *edge_tb)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t lo = cell_ptr[i], deg = cell_ptr[i + 1] - lo;
+    int32_t e = edge_off[i];
+    const int32_t e_end = edge_off[i + 1];
+    for (int32_t k = 0; k < deg; k++) {
+        const int32_t s = lo + k, j = slot_nb[s];
+        if (edge_owner(i, j, n, periodic, ghost_src, ghost_shift) <= 0) continue;
+        if (e >= e_end) return;  // more owned slots than the host counted: left unset, caught by the check
+        edge_l[e] = i;
+        edge_r[e] = j;
+        edge_ta[e] = slot_tri[lo + (k + deg - 1) % deg];
+        edge_tb[e] = slot_tri[s];
+        slot_edge[s] = 2 * e;
+        // the same edge seen from the other cell's ring
+        int32_t pc = -1, want = -1;
+        if (j < n) {
+            pc = j;
+        } else if (periodic) {
+            pc = ghost_src[j - n];
+            const int32_t sh = ghost_shift[j - n];
+            want = (1 - (sh % 3 - 1)) + 3 * (1 - (sh / 3 - 1));
+        }
+        if (pc >= 0) {
+            const int32_t q1 = cell_ptr[pc + 1];
+            for (int32_t q = cell_ptr[pc]; q < q1; q++) {
+                const int32_t c2 = slot_nb[q];
+                const bool hit = j < n ? c2 == i
+                                       : (c2 >= n && ghost_src[c2 - n] == i && ghost_shift[c2 - n] == want && q != s);
+                if (hit) {
+                    slot_edge[q] = 2 * e + 1;
+                    break;
+                }
+            }
+        }
+        e++;
+    }
+}
+
+__global__ void k_check_edges(int32_t S, const int32_t *__restrict__ slot_edge, int32_t *bad)
+{
+    const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S && slot_edge[s] < 0) *bad = 1;
+}
+
 inline int blocks(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 // Threads per block of each stage.  Small blocks let the block scheduler
 // balance the SMs at a fine grain: with 256 threads a per-cell stage over
@@ -878,6 +943,21 @@ template <class R> void launch_stage(int k, const SweepParams<R> &p, const doubl
     default:
         break;
     }
+}
+
+cudaError_t launch_build_edges(int32_t n, int32_t S, const int32_t *cell_ptr, const int32_t *slot_nb,
+                               const int32_t *slot_tri, const int32_t *ghost_src, const int32_t *ghost_shift,
+                               const int32_t *edge_off, int32_t periodic, int32_t *slot_edge, int32_t *edge_l,
+                               int32_t *edge_r, int32_t *edge_ta, int32_t *edge_tb, int32_t *bad, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess && S > 0) e = cudaMemsetAsync(slot_edge, 0xff, sizeof(int32_t) * (size_t)S, st);
+    if (e != cudaSuccess) return e;
+    if (n > 0)
+        k_build_edges<<<blocks(n), kBlock, 0, st>>>(n, cell_ptr, slot_nb, slot_tri, ghost_src, ghost_shift, edge_off,
+                                                     periodic, slot_edge, edge_l, edge_r, edge_ta, edge_tb);
+    if (S > 0) k_check_edges<<<blocks(S), kBlock, 0, st>>>(S, slot_edge, bad);
+    return cudaGetLastError();
 }
 
 void launch_repack(const int32_t *src, int32_t n_new, int32_t n_old, const double *U_old, double *U_new,

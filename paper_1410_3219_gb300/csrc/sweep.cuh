@@ -165,4 +165,18 @@ template <class R> int persistent_blocks_per_sm(int block);
 void launch_repack(const int32_t *src, int32_t n_new, int32_t n_old, const double *U_old, double *U_new,
                    cudaStream_t st);
 
+// The edge list from the rings, on the device (the host then ships rings
+// only).  Real cell i owns its edges to larger real cells, to mirror images
+// and (periodic box) to images of larger cells or of itself shifted to the
+// +x / +y side; its owned edges are numbered in ring order from
+// edge_off[i] (edge_off[n] = E, from the host).  Writes slot_edge (2 e, or
+// 2 e + 1 on the partner's slot), edge_l / edge_r / edge_ta / edge_tb
+// (Voronoi edge from circumcentre ta to tb, counter-clockwise about the
+// left cell), and sets *bad to 1 if a slot ends without an edge.  S slots
+// in all; the ghost arrays are read only for a periodic box.
+cudaError_t launch_build_edges(int32_t n, int32_t S, const int32_t *cell_ptr, const int32_t *slot_nb,
+                               const int32_t *slot_tri, const int32_t *ghost_src, const int32_t *ghost_shift,
+                               const int32_t *edge_off, int32_t periodic, int32_t *slot_edge, int32_t *edge_l,
+                               int32_t *edge_r, int32_t *edge_ta, int32_t *edge_tb, int32_t *bad, cudaStream_t st);
+
 }  // namespace rich
