@@ -53,7 +53,7 @@ struct BatchSim {
     std::vector<int32_t> perm;  // internal (Hilbert) -> caller index
     std::vector<double> hx, hy;  // points, internal order
     std::vector<double> W0;      // initial primitives (4n, component-major) until admitted
-    rich::MeshWork mw;
+    rich::MeshWork mw;           // (edge lists built on the device, packed)
     rich::HostMesh hm;
     int mesh_rc = 0;
     double t = 0.0, t_end = 0.0, last_dt = 0.0;
@@ -67,6 +67,7 @@ struct BatchSim {
     // results of a finished simulation (caller order is applied on read)
     std::vector<double> fin;  // x, y, m, px, py, E (n each, internal order)
     double t_submit = 0.0, t_admit = 0.0, t_finish = 0.0;
+    BatchSim() { mw.host_edges = false; }
 };
 
 // One way of launching the sweep: stage by stage, or as one persistent
@@ -103,7 +104,7 @@ struct rich_batch {
     DBuf corder, psrc;
     DBuf gx, gy, gsrc, gxf, tri, ccx, ccy, slot_nb, slot_tri, slot_edge;
     DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F, ePM;
-    DBuf instp, dtmin, dtout, status, dsizes, gsync;
+    DBuf instp, dtmin, dtout, status, dsizes, gsync, eoff, gshift, edgebad;
     // launch shape: autotuned over the first steps unless fixed by the caller
     int launch_mode = 0;  // 0 autotune, 1 staged, 2 persistent
     int fixed_block = 256;
@@ -123,9 +124,9 @@ struct rich_batch {
     int64_t persistent_launches = 0, graph_launches = 0, staged_launches = 0;
     // host staging of the packed mesh
     std::vector<double> h_x, h_y, h_gx, h_gy, h_W0;
-    std::vector<int32_t> h_gsrc, h_gxf, h_tri, h_cell_ptr, h_slot_nb, h_slot_tri, h_slot_edge, h_cell_inst;
+    std::vector<int32_t> h_gsrc, h_gxf, h_tri, h_cell_ptr, h_slot_nb, h_slot_tri, h_cell_inst;
     std::vector<int32_t> h_corder;
-    std::vector<int32_t> h_edge_l, h_edge_r, h_edge_ta, h_edge_tb, h_src;
+    std::vector<int32_t> h_src, h_eoff, h_gshift;
     std::vector<rich::InstParams> h_inst;
     std::vector<double> h_dt;
     std::vector<int32_t> h_status;
@@ -238,24 +239,17 @@ void pack_one(rich_batch *b, BatchSim &s, int32_t k)
         b->h_gy[go + q] = m.gy[q];
         b->h_gsrc[go + q] = (int32_t)(co + m.ghost_src[q]);
         b->h_gxf[go + q] = m.ghost_xf[q];
+        b->h_gshift[go + q] = m.ghost_shift[q];
     }
     const size_t T = m.tri.size() / 3;
     for (size_t t = 0; t < 3 * T; t++) b->h_tri[3 * to + t] = pid(m.tri[t]);
     for (int32_t i = 0; i < n; i++) b->h_cell_ptr[co + i] = (int32_t)(so + m.cell_ptr[i]);
     for (int32_t i = 0; i < n; i++) b->h_corder[co + i] = (int32_t)(co + m.cell_order[i]);
+    for (int32_t i = 0; i < n; i++) b->h_eoff[co + i] = (int32_t)(eo + m.edge_off[i]);
     const size_t S = m.slot_nb.size();
     for (size_t q = 0; q < S; q++) {
         b->h_slot_nb[so + q] = pid(m.slot_nb[q]);
         b->h_slot_tri[so + q] = (int32_t)(to + m.slot_tri[q]);
-        const int32_t es = m.slot_edge[q];
-        b->h_slot_edge[so + q] = (int32_t)(2 * (eo + (es >> 1)) + (es & 1));
-    }
-    const size_t E = m.edge_l.size();
-    for (size_t e = 0; e < E; e++) {
-        b->h_edge_l[eo + e] = (int32_t)(co + m.edge_l[e]);
-        b->h_edge_r[eo + e] = pid(m.edge_r[e]);
-        b->h_edge_ta[eo + e] = (int32_t)(to + m.edge_ta[e]);
-        b->h_edge_tb[eo + e] = (int32_t)(to + m.edge_tb[e]);
     }
     // conserved state: continuing simulations gather from their previous slot
     for (int32_t i = 0; i < n; i++) b->h_src[co + i] = s.prev_cell_off >= 0 ? (int32_t)(s.prev_cell_off + i) : -1;
@@ -570,7 +564,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
         co += s->n;
         go += s->hm.g;
         to += (int64_t)s->hm.tri.size() / 3;
-        eo += (int64_t)s->hm.edge_l.size();
+        eo += (int64_t)s->hm.n_edges;
         so += (int64_t)s->hm.slot_nb.size();
     }
     if (co + go > ((int64_t)1 << 31) - 1 || 3 * to > ((int64_t)1 << 31) - 1 || 2 * eo > ((int64_t)1 << 31) - 1)
@@ -587,11 +581,12 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     b->h_x.resize(N); b->h_y.resize(N); b->h_cell_inst.resize(N); b->h_src.resize(N);
     b->h_gx.resize(go); b->h_gy.resize(go); b->h_gsrc.resize(go); b->h_gxf.resize(go);
     b->h_tri.resize(3 * to); b->h_cell_ptr.resize(N + 1); b->h_corder.resize(N);
-    b->h_slot_nb.resize(so); b->h_slot_tri.resize(so); b->h_slot_edge.resize(so);
-    b->h_edge_l.resize(eo); b->h_edge_r.resize(eo); b->h_edge_ta.resize(eo); b->h_edge_tb.resize(eo);
+    b->h_slot_nb.resize(so); b->h_slot_tri.resize(so);
+    b->h_eoff.resize(N + 1); b->h_gshift.resize(go);
     if (any_pending) b->h_W0.assign(4 * N, 0.0);
     b->pool.parallel_for((int64_t)ok.size(), [&](int64_t k) { pack_one(b, *ok[k], (int32_t)k); });
     b->h_cell_ptr[N] = (int32_t)so;
+    b->h_eoff[N] = (int32_t)eo;
     b->h_inst.resize(ok.size());
     for (size_t k = 0; k < ok.size(); k++) b->h_inst[k] = inst_params(*ok[k], ok[k]->state == PENDING);
     // 4. device buffers and uploads
@@ -625,12 +620,28 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     CUDA_TRY(upload(b->corder, b->h_corder, b->stream));
     CUDA_TRY(upload(b->slot_nb, b->h_slot_nb, b->stream));
     CUDA_TRY(upload(b->slot_tri, b->h_slot_tri, b->stream));
-    CUDA_TRY(upload(b->slot_edge, b->h_slot_edge, b->stream));
-    CUDA_TRY(upload(b->edge_l, b->h_edge_l, b->stream));
-    CUDA_TRY(upload(b->edge_r, b->h_edge_r, b->stream));
-    CUDA_TRY(upload(b->edge_ta, b->h_edge_ta, b->stream));
-    CUDA_TRY(upload(b->edge_tb, b->h_edge_tb, b->stream));
+    CUDA_TRY(upload(b->eoff, b->h_eoff, b->stream));
+    CUDA_TRY(upload(b->gshift, b->h_gshift, b->stream));
     CUDA_TRY(upload(b->instp, b->h_inst, b->stream));
+    // the packed edge list, built on the device from the rings (each cell's
+    // box type from its simulation's parameters); checked before any kernel
+    // reads it
+    {
+        CUDA_TRY(b->slot_edge.ensure((size_t)so * 4 + 4));
+        for (DBuf *e : {&b->edge_l, &b->edge_r, &b->edge_ta, &b->edge_tb}) CUDA_TRY(e->ensure((size_t)eo * 4 + 4));
+        CUDA_TRY(b->edgebad.ensure(8));
+        int32_t *bad = b->edgebad.as<int32_t>();
+        CUDA_TRY(rich::launch_build_edges((int32_t)N, (int32_t)so, b->cell_ptr.as<int32_t>(), b->slot_nb.as<int32_t>(),
+                                          b->slot_tri.as<int32_t>(), b->gsrc.as<int32_t>(), b->gshift.as<int32_t>(),
+                                          b->eoff.as<int32_t>(), 0, b->instp.as<rich::InstParams>(),
+                                          b->cell_inst.as<int32_t>(), b->slot_edge.as<int32_t>(),
+                                          b->edge_l.as<int32_t>(), b->edge_r.as<int32_t>(), b->edge_ta.as<int32_t>(),
+                                          b->edge_tb.as<int32_t>(), bad, b->stream));
+        int32_t bad_h = 0;
+        CUDA_TRY(cudaMemcpyAsync(&bad_h, bad, 4, cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        if (bad_h) return fail(RICH_ETESS, "an edge of a ring has no partner in the other cell's ring");
+    }
     CUDA_TRY(cudaMemsetAsync(b->status.p, 0, ok.size() * 4, b->stream));
     if (any_pending) CUDA_TRY(upload(b->initW, b->h_W0, b->stream));
     // 5. admission: conserved variables of new simulations from their first geometry

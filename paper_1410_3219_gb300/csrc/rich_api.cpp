@@ -276,7 +276,7 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     CUDA_TRY(rich::launch_build_edges(s->n, (int32_t)S, s->cell_ptr.as<int32_t>(), s->slot_nb.as<int32_t>(),
                                       s->slot_tri.as<int32_t>(), s->gsrc.as<int32_t>(), s->gshift.as<int32_t>(),
                                       s->eoff.as<int32_t>(), s->cfg.boundary == RICH_BC_PERIODIC ? 1 : 0,
-                                      s->slot_edge.as<int32_t>(), s->edge_l.as<int32_t>(), s->edge_r.as<int32_t>(),
+                                      nullptr, nullptr, s->slot_edge.as<int32_t>(), s->edge_l.as<int32_t>(), s->edge_r.as<int32_t>(),
                                       s->edge_ta.as<int32_t>(), s->edge_tb.as<int32_t>(), bad, s->stream));
     int32_t bad_h = 0;
     CUDA_TRY(cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));

@@ -845,11 +845,13 @@ __device__ __forceinline__ int edge_owner(int32_t i, int32_t j, int32_t n, int32
 __global__ void k_build_edges(int32_t n, const int32_t *__restrict__ cell_ptr, const int32_t *__restrict__ slot_nb,
                               const int32_t *__restrict__ slot_tri, const int32_t *__restrict__ ghost_src,
                               const int32_t *__restrict__ ghost_shift, const int32_t *__restrict__ edge_off,
-                              int32_t periodic, int32_t *slot_edge, int32_t *edge_l, int32_t *edge_r,
-                              int32_t *edge_ta, int32_t *edge_tb)
+                              int32_t periodic_all, const InstParams *__restrict__ inst,
+                              const int32_t *__restrict__ cell_inst, int32_t *slot_edge, int32_t *edge_l,
+                              int32_t *edge_r, int32_t *edge_ta, int32_t *edge_tb)
 {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int32_t periodic = cell_inst ? (inst[cell_inst[i]].boundary == 1 ? 1 : 0) : periodic_all;
     const int32_t lo = cell_ptr[i], deg = cell_ptr[i + 1] - lo;
     int32_t e = edge_off[i];
     const int32_t e_end = edge_off[i + 1];
@@ -947,15 +949,17 @@ template <class R> void launch_stage(int k, const SweepParams<R> &p, const doubl
 
 cudaError_t launch_build_edges(int32_t n, int32_t S, const int32_t *cell_ptr, const int32_t *slot_nb,
                                const int32_t *slot_tri, const int32_t *ghost_src, const int32_t *ghost_shift,
-                               const int32_t *edge_off, int32_t periodic, int32_t *slot_edge, int32_t *edge_l,
-                               int32_t *edge_r, int32_t *edge_ta, int32_t *edge_tb, int32_t *bad, cudaStream_t st)
+                               const int32_t *edge_off, int32_t periodic, const InstParams *inst,
+                               const int32_t *cell_inst, int32_t *slot_edge, int32_t *edge_l, int32_t *edge_r,
+                               int32_t *edge_ta, int32_t *edge_tb, int32_t *bad, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int32_t), st);
     if (e == cudaSuccess && S > 0) e = cudaMemsetAsync(slot_edge, 0xff, sizeof(int32_t) * (size_t)S, st);
     if (e != cudaSuccess) return e;
     if (n > 0)
         k_build_edges<<<blocks(n), kBlock, 0, st>>>(n, cell_ptr, slot_nb, slot_tri, ghost_src, ghost_shift, edge_off,
-                                                     periodic, slot_edge, edge_l, edge_r, edge_ta, edge_tb);
+                                                     periodic, inst, cell_inst, slot_edge, edge_l, edge_r, edge_ta,
+                                                     edge_tb);
     if (S > 0) k_check_edges<<<blocks(S), kBlock, 0, st>>>(S, slot_edge, bad);
     return cudaGetLastError();
 }

@@ -173,10 +173,13 @@ void launch_repack(const int32_t *src, int32_t n_new, int32_t n_old, const doubl
 // 2 e + 1 on the partner's slot), edge_l / edge_r / edge_ta / edge_tb
 // (Voronoi edge from circumcentre ta to tb, counter-clockwise about the
 // left cell), and sets *bad to 1 if a slot ends without an edge.  S slots
-// in all; the ghost arrays are read only for a periodic box.
+// in all; the ghost arrays are read only for a periodic box.  In a packed
+// batch (cell_inst non-null) each cell's box type comes from its
+// simulation's parameters instead of `periodic`.
 cudaError_t launch_build_edges(int32_t n, int32_t S, const int32_t *cell_ptr, const int32_t *slot_nb,
                                const int32_t *slot_tri, const int32_t *ghost_src, const int32_t *ghost_shift,
-                               const int32_t *edge_off, int32_t periodic, int32_t *slot_edge, int32_t *edge_l,
-                               int32_t *edge_r, int32_t *edge_ta, int32_t *edge_tb, int32_t *bad, cudaStream_t st);
+                               const int32_t *edge_off, int32_t periodic, const InstParams *inst,
+                               const int32_t *cell_inst, int32_t *slot_edge, int32_t *edge_l, int32_t *edge_r,
+                               int32_t *edge_ta, int32_t *edge_tb, int32_t *bad, cudaStream_t st);
 
 }  // namespace rich
