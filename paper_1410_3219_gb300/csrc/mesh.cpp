@@ -273,14 +273,6 @@ int Delaunay::build(const double *x, const double *y, int32_t np)
     return 0;
 }
 
-bool Delaunay::all_ccw() const
-{
-    for (const Tri &T : tris)
-        if (T.v[0] >= 0 && orient2d(px_[T.v[0]], py_[T.v[0]], px_[T.v[1]], py_[T.v[1]], px_[T.v[2]], py_[T.v[2]]) <= 0)
-            return false;
-    return true;
-}
-
 // Flip the edge opposite vertex k of triangle t: (a, b, c) and (d, c, b)
 // become (a, b, d) and (a, d, c), in the slots of t and of the neighbour.
 void Delaunay::flip(int32_t t, int k)

@@ -79,27 +79,21 @@ public:
     const double *ys() const { return py_.data(); }
 
     // Updating a built triangulation for moved points (the points keep their
-    // vertex numbers): move vertex v; then check that every triangle is
-    // still strictly counter-clockwise (returns false if not: the
-    // connectivity no longer describes a triangulation); then flip edges
-    // until every edge is locally Delaunay (Lawson), which from any
-    // triangulation of the same points ends at the unique (tie-broken)
-    // Delaunay one; then insert further points, appended after the corners
-    // (returns the new vertex, -2 for a point that coincides with one, -3
-    // if location fails).
-    void move(int32_t v, double x, double y) { px_[v] = x; py_[v] = y; }
-    bool all_ccw() const;
+    // vertex numbers).  move_all moves every vertex to (nx[v], ny[v]); where
+    // that would turn triangles over it puts their vertices back until none
+    // is, flips to Delaunay, takes those vertices out (flipping their edges
+    // away until three are left, then merging the three triangles) and
+    // inserts them again at their new positions.  It returns false if that
+    // needs more than max_back vertices or fails (the caller then builds
+    // afresh); on success the triangulation is the unique (tie-broken)
+    // Delaunay one of the new positions.  make_delaunay flips edges until
+    // every edge is locally Delaunay (Lawson), which from any triangulation
+    // of the same points ends at that one.  insert_point adds a point after
+    // the corners (returns the new vertex, -2 for a point that coincides
+    // with one, -3 if location fails).
+    bool move_all(const std::vector<double> &nx, const std::vector<double> &ny, int32_t max_back);
     void make_delaunay();
     int32_t insert_point(double x, double y);
-    // Where moving every vertex at once turns triangles over: move them
-    // (nx, ny: the new position of every vertex), put the vertices of
-    // turned-over triangles back until none is, flip to Delaunay, take those
-    // vertices out (flipping their edges away until three are left, then
-    // merging the three triangles) and insert them again at their new
-    // positions.  Returns false if that needs more than max_back vertices or
-    // fails (the caller then builds afresh); on success the triangulation
-    // is the Delaunay one of the new positions.
-    bool move_all(const std::vector<double> &nx, const std::vector<double> &ny, int32_t max_back);
     // vertices taken out and inserted again by move_all, over the object's life
     int64_t reinserted = 0;
 
