@@ -531,18 +531,30 @@ static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const 
     constexpr int32_t kChunk = 16384;
     const int64_t nc = (n + kChunk - 1) / kChunk;
     std::vector<int64_t> off(nc + 1, 0);
-    // visit(i, emit): every image of point i inside the band
+    // visit(i, emit): every image of point i inside the band.  An image's x
+    // depends on a only and its y on b only, so each axis is tested once
+    // (most points, away from the walls, have none).
+    const bool per = box.boundary == 1;
     auto visit = [&](int32_t i, auto &&emit) {
+        double X[3], Y[3];
+        bool okx[3], oky[3];
+        for (int a = -1; a <= 1; a += 2) {
+            X[a + 1] = image_coord(x[i], box.x0, box.x1, per ? 0 : a, per ? a : 0);
+            okx[a + 1] = !(X[a + 1] < lox || X[a + 1] > hix);
+            Y[a + 1] = image_coord(y[i], box.y0, box.y1, per ? 0 : a, per ? a : 0);
+            oky[a + 1] = !(Y[a + 1] < loy || Y[a + 1] > hiy);
+        }
+        if (!(okx[0] || okx[2] || oky[0] || oky[2])) return;
+        X[1] = x[i];
+        Y[1] = y[i];
+        okx[1] = !(X[1] < lox || X[1] > hix);
+        oky[1] = !(Y[1] < loy || Y[1] > hiy);
         for (int a = -1; a <= 1; a++)
             for (int b = -1; b <= 1; b++) {
                 if (a == 0 && b == 0) continue;
-                int fx = 0, fy = 0, sx = 0, sy = 0;
-                if (box.boundary == 1) { sx = a; sy = b; }
-                else { fx = a; fy = b; }
-                double X = image_coord(x[i], box.x0, box.x1, fx, sx);
-                double Y = image_coord(y[i], box.y0, box.y1, fy, sy);
-                if (X < lox || X > hix || Y < loy || Y > hiy) continue;
-                emit(X, Y, (fx ? XF_MIRROR_X : 0) | (fy ? XF_MIRROR_Y : 0), (sx + 1) + 3 * (sy + 1),
+                if (!okx[a + 1] || !oky[b + 1]) continue;
+                const int fx = per ? 0 : a, fy = per ? 0 : b, sx = per ? a : 0, sy = per ? b : 0;
+                emit(X[a + 1], Y[b + 1], (fx ? XF_MIRROR_X : 0) | (fy ? XF_MIRROR_Y : 0), (sx + 1) + 3 * (sy + 1),
                      (a + 1) + 3 * (b + 1));
             }
     };
