@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <array>
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -1203,9 +1204,37 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     size_t owned = 0;
     for (int s = 0; s < K; s++) owned += res[s].cells.size();
     if (owned != (size_t)n) return -3;
-    for (int32_t i = 0; i < n; i++) {
-        if (m.cell_ptr[i + 1] < 3) return -3;
-        m.cell_ptr[i + 1] += m.cell_ptr[i];
+    {
+        // prefix sum of the degrees: chunk sums, their prefix, chunk scans
+        const int64_t pc = 16384, npc = (n + pc - 1) / pc;
+        std::vector<int64_t> csum(npc + 1, 0);
+        std::vector<int> low(npc, 0);
+        auto sums = [&](int64_t c) {
+            int64_t t = 0;
+            for (int64_t i = c * pc; i < std::min<int64_t>(n, (c + 1) * pc); i++) {
+                if (m.cell_ptr[i + 1] < 3) low[c] = 1;
+                t += m.cell_ptr[i + 1];
+            }
+            csum[c + 1] = t;
+        };
+        if (pool && npc > 1) pool->parallel_for(npc, sums);
+        else
+            for (int64_t c = 0; c < npc; c++) sums(c);
+        for (int64_t c = 0; c < npc; c++) {
+            if (low[c]) return -3;
+            csum[c + 1] += csum[c];
+        }
+        if (csum[npc] > INT32_MAX) return -3;
+        auto scan = [&](int64_t c) {
+            int64_t run = csum[c];
+            for (int64_t i = c * pc; i < std::min<int64_t>(n, (c + 1) * pc); i++) {
+                run += m.cell_ptr[i + 1];
+                m.cell_ptr[i + 1] = (int32_t)run;
+            }
+        };
+        if (pool && npc > 1) pool->parallel_for(npc, scan);
+        else
+            for (int64_t c = 0; c < npc; c++) scan(c);
     }
     const size_t S = (size_t)m.cell_ptr[n];
     m.slot_nb.resize(S);
