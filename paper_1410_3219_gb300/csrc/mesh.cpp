@@ -599,9 +599,9 @@ inline Disk circumdisk(const double *X, const double *Y, int32_t a, int32_t b, i
 {
     double ax = X[a], ay = Y[a];
     double bx = X[b] - ax, by = Y[b] - ay, cx = X[c] - ax, cy = Y[c] - ay;
-    double d = 2.0 * (bx * cy - by * cx);
+    const double rd = 1.0 / (2.0 * (bx * cy - by * cx));
     double b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
-    double ux = (cy * b2 - by * c2) / d, uy = (bx * c2 - cx * b2) / d;
+    double ux = (cy * b2 - by * c2) * rd, uy = (bx * c2 - cx * b2) * rd;
     return Disk{ux + ax, uy + ay, std::sqrt(ux * ux + uy * uy) * (1.0 + 1e-9) + pad};
 }
 
