@@ -385,8 +385,9 @@ int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const do
    meshes of `steps` successive point sets (xs, ys: steps x n, row-major,
    the same cells in each) once with one reused workspace and once afresh
    each, with `threads` host threads, and counts the steps whose sweep
-   inputs differ (rings, their neighbours and triangles, the edge list,
-   ghosts).  *updated and *rebuilt receive the tile counts of the reused
+   inputs differ (rings, their neighbours and triangles, the edge list and
+   each cell's first owned edge, ghosts) or whose first owned edges do not
+   match the edge list.  *updated and *rebuilt receive the tile counts of the reused
    workspace over all steps, *reinserted the vertices it took out and put
    back where triangles would have turned over.  Returns RICH_EINVAL for bad
    arguments or the builder's error. */

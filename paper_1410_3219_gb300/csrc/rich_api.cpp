@@ -812,7 +812,12 @@ int rich_mesh_update_check(const rich_config *cfg, int64_t n, int32_t steps, con
         if (rc) return mesh_rc(rc);
         bool same = a.g == b.g && a.gx == b.gx && a.gy == b.gy && a.ghost_src == b.ghost_src &&
                     a.cell_ptr == b.cell_ptr && a.slot_nb == b.slot_nb && a.slot_edge == b.slot_edge &&
-                    a.edge_l == b.edge_l && a.edge_r == b.edge_r && a.cell_order == b.cell_order;
+                    a.edge_l == b.edge_l && a.edge_r == b.edge_r && a.cell_order == b.cell_order &&
+                    a.edge_off == b.edge_off && a.n_edges == b.n_edges && (size_t)b.n_edges == b.edge_l.size();
+        // the per-cell first edges (what the device builder numbers from)
+        // agree with the host's list: cell i owns edges [edge_off[i], edge_off[i + 1])
+        for (int64_t i = 0; same && i < n; i++)
+            for (int32_t e = b.edge_off[i]; same && e < b.edge_off[i + 1]; e++) same = b.edge_l[e] == (int32_t)i;
         for (size_t s = 0; same && s < a.slot_tri.size(); s++) same = tri_of(a, a.slot_tri[s]) == tri_of(b, b.slot_tri[s]);
         for (size_t e = 0; same && e < a.edge_ta.size(); e++)
             same = tri_of(a, a.edge_ta[e]) == tri_of(b, b.edge_ta[e]) && tri_of(a, a.edge_tb[e]) == tri_of(b, b.edge_tb[e]);
