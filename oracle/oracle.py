@@ -60,34 +60,41 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(LIB)
-        d = C.c_double
-        L.orc_orient.argtypes = [d] * 6
-        L.orc_incircle_raw.argtypes = [d] * 8
-        L.orc_incircle_sos.argtypes = [d] * 8
-        L.orc_delaunay.argtypes = [C.c_int, _D, _D, _I, C.POINTER(_I)]
-        L.orc_free.argtypes = [C.c_void_p]
-        L.orc_create.argtypes = [C.POINTER(Config), C.c_int, _D, _D, _D, _D, _D, _D, C.POINTER(C.c_void_p)]
-        L.orc_destroy.argtypes = [C.c_void_p]
-        L.orc_tessellate.argtypes = [C.c_void_p]
-        L.orc_sweep.argtypes = [C.c_void_p, d, _D]
-        L.orc_step.argtypes = [C.c_void_p, d, _D]
-        L.orc_time.argtypes = [C.c_void_p]
-        L.orc_time.restype = d
-        L.orc_band.argtypes = [C.c_void_p]
-        L.orc_band.restype = d
-        L.orc_num_points.argtypes = [C.c_void_p]
-        L.orc_get_points.argtypes = [C.c_void_p, _D, _D, _I]
-        L.orc_ring_total.argtypes = [C.c_void_p]
-        L.orc_get_ring.argtypes = [C.c_void_p, _I, _I]
-        L.orc_get_conserved.argtypes = [C.c_void_p] + [_D] * 6
-        L.orc_get_cells.argtypes = [C.c_void_p, C.c_int, _D]
-        L.orc_get_primitives.argtypes = [C.c_void_p] + [_D] * 5
-        L.orc_hllc.argtypes = [d, _D, _D, _D]
-        L.orc_riemann_exact.argtypes = [d] * 7 + [_D, _D]
-        L.orc_riemann_sample.argtypes = [d] * 9 + [d, _D]
-        _lib = L
+        _lib = load(LIB)
     return _lib
+
+
+def load(path):
+    """ctypes handle of an oracle library built at `path`, with argument
+    types set (the tests also load copies built with planted mistakes)."""
+    L = C.CDLL(path)
+    d = C.c_double
+    L.orc_orient.argtypes = [d] * 6
+    L.orc_incircle_raw.argtypes = [d] * 8
+    L.orc_incircle_sos.argtypes = [d] * 8
+    L.orc_delaunay.argtypes = [C.c_int, _D, _D, _I, C.POINTER(_I)]
+    L.orc_free.argtypes = [C.c_void_p]
+    L.orc_create.argtypes = [C.POINTER(Config), C.c_int, _D, _D, _D, _D, _D, _D, C.POINTER(C.c_void_p)]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_tessellate.argtypes = [C.c_void_p]
+    L.orc_sweep.argtypes = [C.c_void_p, d, _D]
+    L.orc_step.argtypes = [C.c_void_p, d, _D]
+    L.orc_time.argtypes = [C.c_void_p]
+    L.orc_time.restype = d
+    L.orc_band.argtypes = [C.c_void_p]
+    L.orc_band.restype = d
+    L.orc_num_points.argtypes = [C.c_void_p]
+    L.orc_get_points.argtypes = [C.c_void_p, _D, _D, _I]
+    L.orc_ring_total.argtypes = [C.c_void_p]
+    L.orc_get_ring.argtypes = [C.c_void_p, _I, _I]
+    L.orc_get_conserved.argtypes = [C.c_void_p] + [_D] * 6
+    L.orc_get_cells.argtypes = [C.c_void_p, C.c_int, _D]
+    L.orc_get_primitives.argtypes = [C.c_void_p] + [_D] * 5
+    L.orc_hllc.argtypes = [d, _D, _D, _D]
+    L.orc_predict.argtypes = [d, d, _D, _D, d, d, _D, _D]
+    L.orc_riemann_exact.argtypes = [d] * 7 + [_D, _D]
+    L.orc_riemann_sample.argtypes = [d] * 9 + [d, _D]
+    return L
 
 
 def _dp(a):
@@ -125,6 +132,16 @@ def hllc(gamma, WL, WR):
     F = np.zeros(4)
     lib().orc_hllc(gamma, _dp(_f64(WL)), _dp(_f64(WR)), _dp(F))
     return F
+
+
+def predict(gamma, hdt, W, g, off, wf, L=None):
+    """Edge state of one side (Section 2.3, extrapolated fluxes): Eq. 2
+    extrapolation by `off` from the centre of mass, advanced `hdt` in time
+    in the frame moving with `wf`; velocity in the lab frame."""
+    out = np.zeros(4)
+    (L or lib()).orc_predict(gamma, hdt, _dp(_f64(W)), _dp(_f64(g)), float(off[0]), float(off[1]),
+                             _dp(_f64(wf)), _dp(out))
+    return out
 
 
 def riemann_exact(gamma, left, right):

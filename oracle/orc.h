@@ -54,6 +54,8 @@ double orc_band(const orc_sim *s);
 
 /* building blocks exposed for pins */
 void orc_hllc(double gamma, const double WL[4], const double WR[4], double F[4]);
+void orc_predict(double gamma, double hdt, const double W[4], const double g[8], double offx, double offy,
+                 const double wf[2], double out[4]);
 int orc_riemann_exact(double gamma, double rl, double ul, double pl, double rr, double ur, double pr,
                       double *ps, double *us);
 void orc_riemann_sample(double gamma, double rl, double ul, double pl, double rr, double ur, double pr,

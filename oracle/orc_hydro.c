@@ -384,6 +384,14 @@ static void predict(double gam, double hdt, const double W[4], const double g[8]
     out[3] -= hdt * (ux * g[6] + uy * g[7] + gam * p * div);
 }
 
+/* the edge-state prediction on its own, for the pins of Section 2.3's
+   half-step prediction (velocity out in the lab frame) */
+void orc_predict(double gam, double hdt, const double W[4], const double g[8], double offx, double offy,
+                 const double wf[2], double out[4])
+{
+    predict(gam, hdt, W, g, offx, offy, wf, out);
+}
+
 /* ------------------------------------------------------------------------ */
 
 int orc_create(const orc_config *cfg, int n, const double *x, const double *y, const double *rho,
