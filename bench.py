@@ -40,51 +40,72 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # read points 16 + U 32 + connectivity ~28, write U 32 + points 16 = 124 B.
 HBM_PEAK_GBS_FALLBACK = 6800.0
 COMPULSORY_BYTES_PER_CELL = 124
+# kernels launched by one sweep (the time-step minimum's reset is a memset)
+NUM_KERNELS = 6
 
-# Algorithmic operations per unit of work of each kernel, counted from the
-# formulas (add, sub, mul, min, max, compare = 1; fused multiply-add = 2;
-# divide, square root = 1), split by the pipe they run on in each precision.
-# The cell-only terms of the half-step prediction (rho div v, grad p / rho,
-# gamma p div v: 7 operations) are counted once per cell in k_cell_gradient,
-# where they are computed, not once per edge side; the prediction of each
-# side is phi + g.(off - hdt u) - hdt src with u = v - wf formed once for
-# the shift and the boost (30 operations per side), and HLLC forms the total
-# energy of the upwind side only.
-# (per unit, unit kind, extra per ring slot)
+# Algorithmic floating-point operations of each kernel, counted from the
+# formulas as the kernels evaluate them: add, subtract, multiply = 1, fused
+# multiply-add = 2, divide, square root and reciprocal square root = 1 (the
+# extra FMAs that refine a reciprocal are not counted); compares, min/max,
+# sign flips and the FP64 <-> FP32 conversions run on the integer pipe and
+# are not counted.  Per unit kind (triangle, edge, cell, ring slot) and pipe.
 FLOPS = {
     "fp64": {
-        "k_circumcentre": ({"fp64": 24}, "tri", {}),
-        "k_edge_geometry": ({"fp64": 32}, "edge", {}),
-        "k_cell_geometry": ({"fp64": 27}, "cell", {"fp64": 11}),
-        "k_cell_gradient": ({"fp64": 47}, "cell", {"fp64": 83}),
-        "k_edge_flux": ({"fp64": 175}, "edge", {}),
-        "k_cell_update": ({"fp64": 20}, "cell", {"fp64": 4}),
+        "k_circumcentre": {"tri": {"fp64": 25}},
+        "k_geometry": {"edge": {"fp64": 34}, "cell": {"fp64": 30}, "slot": {"fp64": 11}},
+        "k_cell_gradient": {"cell": {"fp64": 86}, "slot": {"fp64": 33}},
+        "k_edge_flux": {"edge": {"fp64": 177}},
+        "k_cell_update": {"cell": {"fp64": 21}, "slot": {"fp64": 4}},
     },
     "split": {
-        "k_circumcentre": ({"fp64": 24}, "tri", {}),
-        "k_edge_geometry": ({"fp64": 6, "fp32": 26}, "edge", {}),
-        "k_cell_geometry": ({"fp64": 17, "fp32": 10}, "cell", {"fp64": 11}),
-        "k_cell_gradient": ({"fp32": 47}, "cell", {"fp32": 83}),
-        "k_edge_flux": ({"fp32": 175}, "edge", {}),
-        "k_cell_update": ({"fp64": 20}, "cell", {"fp64": 4}),
+        "k_circumcentre": {"tri": {"fp64": 25}},
+        "k_geometry": {"edge": {"fp64": 8, "fp32": 26}, "cell": {"fp64": 24, "fp32": 7}, "slot": {"fp64": 11}},
+        "k_cell_gradient": {"cell": {"fp32": 86}, "slot": {"fp64": 1, "fp32": 32}},
+        "k_edge_flux": {"edge": {"fp64": 1, "fp32": 176}},
+        "k_cell_update": {"cell": {"fp64": 21}, "slot": {"fp64": 4}},
     },
 }
 
 
-# DRAM bytes (read + write) per unit of the dominant kernel from one ncu
-# capture of the kernel version in this tree (profiles/*_sedov262k.md give
-# the command and the raw counters), scaled to a launch by its units.  Set
-# to None whenever the kernel changes after the capture.
-TRAFFIC_PER_UNIT = {
-    "fp64": {"k_edge_flux": 146.2},     # profiles/k_edge_flux_fp64_sedov262k.md
-    "split": {"k_cell_geometry": 114.1},  # profiles/k_cell_geometry_split_sedov262k.md
-}
-# The same captures' sm__pipe_fp64_cycles_active (fraction of peak while the
-# SMs are active): how busy the bounding pipe is, whatever the op mix.
-PIPE_ACTIVE = {
-    "fp64": {"k_edge_flux": 0.889},
-    "split": {"k_cell_geometry": 0.781},
-}
+# DRAM traffic and FP64-pipe activity per kernel come from the committed ncu
+# summary of the same workload (profiles/sweep_ncu_<workload>.md, which gives
+# the command), and only while the kernel sources still hash to the value
+# recorded there: after a kernel change they are null until captured again.
+KERNEL_SOURCES = ["sweep.cu", "sweep.cuh", "fp64ops.cuh"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1410_3219_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_summary(workload_name):
+    """{precision: {kernel: {"dram_bytes": B, "fp64_pipe": f, ...}}} from the
+    committed summary, or {} when it is missing or its kernel-source hash is
+    not the current one."""
+    path = os.path.join(ROOT, "profiles", f"sweep_ncu_{workload_name}.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return {}, None
+    want = kernel_source_hash()
+    got = next((ln.split(":", 1)[1].strip().strip("`") for ln in lines if ln.startswith("kernel-source-hash:")), None)
+    if got != want:
+        return {}, path
+    out = {}
+    for ln in lines:
+        f = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(f) >= 5 and f[0] in ("fp64", "split"):
+            try:
+                out.setdefault(f[0], {})[f[1]] = {"dram_bytes": float(f[2]), "fp64_pipe": float(f[3]),
+                                                  "duration_us": float(f[4])}
+            except ValueError:
+                continue
+    return out, path
 
 
 def hbm_peak():
@@ -101,6 +122,8 @@ def workload(name):
         return W.sedov(n=262144, seed=2)
     if name == "kh_1048576":
         return W.kelvin_helmholtz(n_side=1024, seed=3)
+    if name == "kh_262144":  # the same problem at 512^2, for profiler captures
+        return W.kelvin_helmholtz(n_side=512, seed=3)
     if name == "sod_4096":
         return W.sod(n_side=64, seed=1)
     raise SystemExit(f"unknown workload {name}")
@@ -174,16 +197,21 @@ class Clocks:
 
 
 def kernel_flops(prec, name, units):
-    per, kind, slot = FLOPS[prec][name]
-    out = {}
-    for pipe in ("fp64", "fp32"):
-        out[pipe] = per.get(pipe, 0) * units[kind] + slot.get(pipe, 0) * units["slot"]
+    out = {"fp64": 0, "fp32": 0}
+    for kind, per in FLOPS[prec][name].items():
+        for pipe, v in per.items():
+            out[pipe] += v * units[kind]
     return out
 
 
-def roofline_of(prec, kern_means, units, sweep_ms):
-    """Roofline of the dominant kernel: bound by the pipe that carries most
-    of its issue time (FP64 issues at 1/64 of the FP32 rate)."""
+def roofline_of(prec, kern_means, units, sweep_ms, workload_name, probe=None):
+    """Roofline of the dominant kernel (the longest launch of the sweep):
+    algorithmic operations on the pipe that carries most of its issue time
+    (FP64 issues at 1/64 of the FP32 rate) over its CUDA-event mean
+    duration, against the peak derived from unit counts and clocks, with
+    the measured FMA-chain peak beside it.  DRAM traffic and FP64-pipe
+    activity come from the committed ncu summary while the kernel sources
+    still match it."""
     dom = max(kern_means, key=kern_means.get)
     fl = kernel_flops(prec, dom, units)
     t64 = fl["fp64"] / (FP64_PEAK_TFLOPS * 1e12)
@@ -191,25 +219,51 @@ def roofline_of(prec, kern_means, units, sweep_ms):
     pipe, peak = ("fp64", FP64_PEAK_TFLOPS) if t64 >= t32 else ("fp32", FP32_PEAK_TFLOPS)
     achieved = fl[pipe] / (kern_means[dom] / 1e3) / 1e12
     tot = {"fp64": 0, "fp32": 0}
+    per_kernel = {}
     for k in FLOPS[prec]:
         f = kernel_flops(prec, k, units)
         tot["fp64"] += f["fp64"]
         tot["fp32"] += f["fp32"]
+        if k in kern_means:
+            per_kernel[k] = {"ms": kern_means[k],
+                             "fp64_tflops": f["fp64"] / (kern_means[k] / 1e3) / 1e12,
+                             "fp64_frac": f["fp64"] / (kern_means[k] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
     hbm, src = hbm_peak()
     cells_per_s = units["cell"] / (sweep_ms / 1e3)
-    per_unit = TRAFFIC_PER_UNIT.get(prec, {}).get(dom)
-    traffic = per_unit * units[FLOPS[prec][dom][1]] if per_unit is not None else None
-    pipe_active = PIPE_ACTIVE.get(prec, {}).get(dom)
-    return {"bound": "alu", "pipe": pipe, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu DRAM read + write)",
-            "pipe_active_ncu": pipe_active,
-            "peak_source": ("derived: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz" if pipe == "fp64"
-                            else "derived: 152 SMs x 128 FP32 FMA lanes/clk x 2 flop x 2.07 GHz"),
-            "sweep_fp64_tflops": tot["fp64"] / (sweep_ms / 1e3) / 1e12,
-            "sweep_fp32_tflops": tot["fp32"] / (sweep_ms / 1e3) / 1e12,
-            "hbm_frac_compulsory": cells_per_s * COMPULSORY_BYTES_PER_CELL / (hbm * 1e9),
-            "hbm_peak_gbs": hbm, "hbm_peak_source": src,
-            "kernel_ms": kern_means}
+    summ, summ_path = ncu_summary(workload_name)
+    rec = summ.get(prec, {})
+    traffic = rec[dom]["dram_bytes"] if dom in rec else None
+    pipe_active = rec[dom]["fp64_pipe"] if dom in rec else None
+    sweep_dram = sum(v["dram_bytes"] for v in rec.values()) if len(rec) == len(FLOPS[prec]) else None
+    for k, v in rec.items():
+        if k in per_kernel:
+            per_kernel[k]["dram_bytes_ncu"] = v["dram_bytes"]
+            per_kernel[k]["fp64_pipe_active_ncu"] = v["fp64_pipe"]
+    out = {"bound": "alu", "pipe": pipe, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "traffic": traffic,
+           "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+           "traffic_source": (os.path.relpath(summ_path, ROOT) if traffic is not None else
+                              "null: no ncu summary for this kernel-source hash"),
+           "kernel_source_hash": kernel_source_hash(),
+           "pipe_active_ncu": pipe_active,
+           "peak_source": ("derived: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz" if pipe == "fp64"
+                           else "derived: 152 SMs x 128 FP32 FMA lanes/clk x 2 flop x 2.07 GHz"),
+           "ops_counted": "FP64-pipe (or FP32-pipe) arithmetic only: add, sub, mul = 1, FMA = 2, divide and "
+                          "square root = 1; compares, min/max, sign flips and conversions on the integer pipe "
+                          "are not counted",
+           "sweep_fp64_tflops": tot["fp64"] / (sweep_ms / 1e3) / 1e12,
+           "sweep_fp32_tflops": tot["fp32"] / (sweep_ms / 1e3) / 1e12,
+           "sweep_dram_bytes_per_step_ncu": sweep_dram,
+           "hbm_frac_compulsory": cells_per_s * COMPULSORY_BYTES_PER_CELL / (hbm * 1e9),
+           "hbm_frac_ncu": (sweep_dram / (sweep_ms / 1e3) / (hbm * 1e9)) if sweep_dram else None,
+           "hbm_peak_gbs": hbm, "hbm_peak_source": src,
+           "kernels": per_kernel}
+    if probe:
+        pk = probe["fp64"] if pipe == "fp64" else probe["fp32"]
+        out["peak_probe"] = pk
+        out["frac_of_probe"] = achieved / pk
+        out["peak_probe_source"] = "measured: FMA chains on this GPU (rich_probe_pipe_peaks)"
+    return out
 
 
 def run_ours(args):
@@ -234,7 +288,9 @@ def run_ours(args):
 
     warm_state = {"done": False}
 
-    def time_precision(prec, with_clocks, scheme=0):
+    def time_precision(wl, prec, with_clocks, scheme=0, steps=None):
+        steps = steps or args.steps
+        n = len(wl["x"])
         w = dict(wl)
         w["cfg"] = dict(wl["cfg"], precision=1 if prec == "split" else 0, scheme=scheme)
         sim = rich.Sim(w)
@@ -271,8 +327,7 @@ def run_ours(args):
         # W warm-up steps; before the first timed run, also warmup_seconds
         # of steps of throwaway copies of the run (the steps are mostly host
         # tessellation; on a fresh box the first seconds of FP64 kernels ran
-        # ~4 % slow; the Sedov run itself fails after 66 steps, so a copy
-        # takes at most 40)
+        # ~4 % slow)
         if not warm_state["done"] and args.warmup_seconds > 0:
             t_warm = time.perf_counter()
             while time.perf_counter() - t_warm < args.warmup_seconds:
@@ -300,13 +355,11 @@ def run_ours(args):
         sweep_ms, tess_ms, kern = [], [], {}
         wall0 = time.perf_counter()
         units = None
-        for _ in range(args.steps):
+        for _ in range(steps):
             ms, info, kt = one_step()
             sweep_ms.append(ms)
             tess_ms.append(info["tess_ms"])
             units = {"tri": info["n_tri"], "edge": info["n_edges"], "cell": n, "slot": info["n_slots"]}
-            for k, v in kt.items():
-                kern.setdefault(k, []).append(v / sweeps_per_step)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         if ws > 1:
@@ -322,15 +375,26 @@ def run_ours(args):
         sim.close()
         total_s = max_over_ranks(sum(sweep_ms) / 1e3, ws)
         means = {k: float(np.mean(v)) for k, v in kern.items() if k != "dt_reset"}
-        return {"value": job_value(ws, n * args.steps, total_s), "sweep_ms": sweep_ms, "tess_ms": tess_ms, "wall": wall,
-                "units": units, "kernel_means": means, "clocks": clk}
+        return {"value": job_value(ws, n * steps, total_s), "sweep_ms": sweep_ms, "tess_ms": tess_ms, "wall": wall,
+                "units": units, "kernel_means": means, "clocks": clk, "steps": steps}
 
-    res64 = time_precision("fp64", True)
-    res32 = time_precision("split", False)
-    restc = time_precision("fp64", False, scheme=1)
-    sweep_ms, tess_ms, wall, units, clk = (res64["sweep_ms"], res64["tess_ms"], res64["wall"], res64["units"],
-                                           res64["clocks"])
-    value = res64["value"]
+    probe = None
+    if rank == 0:
+        p64, p32 = rich.rich_probe_pipe_peaks()
+        probe = {"fp64": p64, "fp32": p32}
+
+    precs = [p.strip() for p in args.precisions.split(",") if p.strip()]
+    res = {}
+    for k, pr in enumerate(precs):
+        if pr == "tc":
+            res[pr] = time_precision(wl, "fp64", k == 0, scheme=1)
+        else:
+            res[pr] = time_precision(wl, pr, k == 0)
+    head = res[precs[0]]
+    sweep_ms, tess_ms, wall, units, clk = (head["sweep_ms"], head["tess_ms"], head["wall"], head["units"],
+                                           head["clocks"])
+    value = head["value"]
+    head_prec = "split" if precs[0] == "split" else "fp64"
 
     # end to end through the public API: rich_step (host tessellation, copies,
     # sweep) plus a host read of the step's result
@@ -339,7 +403,9 @@ def run_ours(args):
     import ctypes as C
     Dp = C.POINTER(C.c_double)
     L = rich.lib()
-    sim2 = rich.Sim(wl)
+    w_e2e = dict(wl)
+    w_e2e["cfg"] = dict(wl["cfg"], precision=1 if head_prec == "split" else 0)
+    sim2 = rich.Sim(w_e2e)
     sim2.step(1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -363,20 +429,33 @@ def run_ours(args):
     e2e_val = job_value(ws, n * e2e_steps, e2e_s)
     sim2.close()
 
+    sedov = None
+    if not args.no_sedov and args.workload != "sedov_262144":
+        swl = workload("sedov_262144")
+        sedov = {}
+        for pr in ("fp64", "split"):
+            r = time_precision(swl, pr, False)
+            sedov[pr] = {"value": r["value"], "unit": UNIT, "ms_per_step": float(np.mean(r["sweep_ms"])),
+                         "p99_ms": float(np.percentile(r["sweep_ms"], 99)),
+                         "host_tess_ms_per_step": float(np.mean(r["tess_ms"])),
+                         "roofline": roofline_of(pr, r["kernel_means"], r["units"], float(np.mean(r["sweep_ms"])),
+                                                 "sedov_262144", probe)}
+
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return
 
-    roof = roofline_of("fp64", res64["kernel_means"], units, float(np.mean(sweep_ms)))
-    roof32 = roofline_of("split", res32["kernel_means"], res32["units"], float(np.mean(res32["sweep_ms"])))
+    roof = roofline_of(head_prec, head["kernel_means"], units, float(np.mean(sweep_ms)), args.workload, probe)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(sweep_ms)),
         "p50_ms": float(np.percentile(sweep_ms, 50)), "p99_ms": float(np.percentile(sweep_ms, 99)),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head_prec == "fp64" else "f32 reconstruction + f64 geometry/state",
         "data": "synthetic (seeded)",
-        "config": {"workload": args.workload, "cells": n, "precision": "fp64", "scheme": "extrapolated fluxes",
+        "config": {"workload": args.workload, "cells": n, "precision": head_prec,
+                   "scheme": "time-centred fluxes" if precs[0] == "tc" else "extrapolated fluxes",
                    "l2": "flushed (256 MB write) before every timed sweep",
                    "warmup": f"{args.warmup} steps, after {args.warmup_seconds:g} s of steps of throwaway copies",
                    "host_tess_ms_per_step": float(np.mean(tess_ms)),
@@ -385,17 +464,26 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps,
                 "host_tess_ms": parts["tess_ms"], "copy_ms": parts["copy_ms"], "sweep_ms": parts["sweep_ms"]},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": NUM_KERNELS * args.steps * (2 if precs[0] == "tc" else 1),
         "clocks": clk,
-        "fp32_split": {"value": res32["value"], "unit": UNIT, "dtype": "f32 reconstruction + f64 geometry/state",
-                       "ms_per_step": float(np.mean(res32["sweep_ms"])),
-                       "p99_ms": float(np.percentile(res32["sweep_ms"], 99)), "roofline": roof32},
-        "time_centred": {"value": restc["value"], "unit": UNIT, "dtype": "f64", "sweeps_per_step": 2,
-                         "ms_per_step": float(np.mean(restc["sweep_ms"])),
-                         "p99_ms": float(np.percentile(restc["sweep_ms"], 99)),
-                         "host_tess_ms_per_step": float(np.mean(restc["tess_ms"])),
-                         "kernel_ms_per_sweep": restc["kernel_means"]},
+        "pipe_peaks_probe_tflops": probe,
     }
+    if "split" in res and precs[0] != "split":
+        r = res["split"]
+        line["fp32_split"] = {"value": r["value"], "unit": UNIT, "dtype": "f32 reconstruction + f64 geometry/state",
+                              "ms_per_step": float(np.mean(r["sweep_ms"])),
+                              "p99_ms": float(np.percentile(r["sweep_ms"], 99)),
+                              "roofline": roofline_of("split", r["kernel_means"], r["units"],
+                                                      float(np.mean(r["sweep_ms"])), args.workload, probe)}
+    if "tc" in res and precs[0] != "tc":
+        r = res["tc"]
+        line["time_centred"] = {"value": r["value"], "unit": UNIT, "dtype": "f64", "sweeps_per_step": 2,
+                                "ms_per_step": float(np.mean(r["sweep_ms"])),
+                                "p99_ms": float(np.percentile(r["sweep_ms"], 99)),
+                                "host_tess_ms_per_step": float(np.mean(r["tess_ms"])),
+                                "kernel_ms_per_sweep": r["kernel_means"]}
+    if sedov:
+        line["sedov_262144"] = sedov
     if not args.no_batched:
         line["batched"] = {"fp64": run_batched(rich, 0, args.batch_instances, args.batch_steps),
                            "fp32_split": run_batched(rich, 1, args.batch_instances, args.batch_steps)}
@@ -580,7 +668,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--warmup-seconds", type=float, default=3.0)
-    ap.add_argument("--workload", default="sedov_262144")
+    ap.add_argument("--workload", default="kh_1048576")
+    ap.add_argument("--precisions", default="fp64,split,tc",
+                    help="comma list of the sweeps to time: fp64, split, tc (time-centred); the first is the headline")
+    ap.add_argument("--no-sedov", action="store_true", help="skip the extra Sedov 262,144-cell lines")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -201,8 +201,9 @@ int rich_set_diagnostics(rich_sim *s, int32_t on);
 /* Per-stage device times of the last synchronised sweep, from CUDA events
    recorded on the launching stream between the stages (enabled by
    rich_set_profiling; off by default).  Stages, in launch order:
-   k_circumcentre, k_edge_geometry, k_cell_geometry, dt_reset (a memset),
-   k_cell_gradient, k_edge_flux, k_cell_update.  *count receives the number of
+   k_circumcentre, k_geometry (edge and cell geometry with the primitives, in
+   one launch), dt_reset (a memset), k_cell_gradient, k_edge_flux,
+   k_cell_update.  *count receives the number of
    stages; up to cap values (milliseconds) are written to ms. */
 int rich_set_profiling(rich_sim *s, int32_t on);
 int rich_kernel_times(rich_sim *s, int32_t cap, double *ms, int32_t *count);
@@ -286,6 +287,17 @@ int rich_batch_set_launch(rich_batch *b, int32_t mode, int32_t block);
 int rich_batch_launch_info(const rich_batch *b, int32_t *persistent, int32_t *block, int32_t *grid, int32_t *tuned,
                            int32_t *graph, int64_t *counts);
 
+/* Failure detection of the persistent sweep (no counterpart in the paper).
+   Its grid barriers wait a bounded number of polls; a wait that runs out
+   stops the sweep with the step's inputs untouched, and the batch redoes
+   the step with staged launches and keeps them.  With spin_limit > 0 the
+   next persistent sweep is made to fail that way: its barrier waits for one
+   block more than it launched, and every wait gives up after spin_limit
+   polls (about 0.1-1 us each).  *timeouts_seen (nullable) receives the
+   number of persistent sweeps whose barrier timed out so far.
+   Errors: RICH_EINVAL. */
+int rich_batch_inject_barrier_timeout(rich_batch *b, int32_t spin_limit, int64_t *timeouts_seen);
+
 void rich_batch_destroy(rich_batch *b);
 
 /* ---- continuous-batching server -------------------------------------------- */
@@ -338,30 +350,45 @@ void rich_server_destroy(rich_server *s);
 /* Largest n accepted by rich_courant_dt_noalloc. */
 #define RICH_NOALLOC_MAX_CELLS (1 << 24)
 
-/* The paper has no counterpart to this entry point; it serves callers that
+/* The paper has no counterpart to this entry point.  It serves callers that
    cannot allocate GPU memory when they need the time step: code running
-   inside a memory pool or arena that owns the device, code that must not
-   trigger the device synchronisation an allocation or free can cause, and
-   code that is later replayed from a recorded sequence of launches.
+   inside a memory pool or arena that owns the device, and code that must not
+   trigger the device synchronisation an allocation or free can cause.
 
-   Computes the Courant time step of the sweep (step a6),
+   Computes the Courant time step of the sweep (step a6) in FP64, before the
+   step is shortened to land on an end time:
    dt = cfg->cfl * min_i R_i / (c_i + |v_i - w_i|), R_i = sqrt(area_i/pi),
    c_i = sqrt(gamma p_i/rho_i) (w = 0 for RICH_MESH_EULERIAN, when wx, wy may
    be NULL), over n cells whose values are DEVICE arrays of doubles owned by
    the caller, and writes it to the DEVICE double *dt_out, asynchronously on
-   the cudaStream_t stream (NULL: the default stream).  It allocates nothing:
-   its scratch (one partial minimum per block of 256 cells and a completion
-   counter, 512 KiB) is a fixed array in the library's device image, which
-   every GPU that loads the library holds until the process exits.  The first
-   call on each device looks up that array's address (cudaGetSymbolAddress),
-   so make it before any stream capture.  Every call shares the array and
-   clears its counter: calls that overlap on the GPU (other streams, other
-   host threads) race and must not be issued.
-   Returns RICH_EINVAL for a NULL pointer or n outside [1,
-   RICH_NOALLOC_MAX_CELLS], RICH_ECUDA if the set-up or launch fails. */
+   the cudaStream_t stream (NULL: the default stream).  The FP64 formula is
+   used whatever cfg->precision says (a RICH_FP32_SPLIT sweep evaluates it in
+   FP32).  Cells whose time step is +inf are skipped, as the sweep skips
+   them; a cell whose time step is NaN, negative or -0.0 (a negative or NaN
+   pressure or density) makes *dt_out a NaN instead of being skipped.
+   It allocates nothing: its scratch (one partial minimum per block of 256
+   cells and a completion counter, 512 KiB) is a fixed array in the
+   library's device image, which every GPU that loads the library holds until
+   the process exits.  The first call on each device looks up that array's
+   address (cudaGetSymbolAddress), so make it before any stream capture.
+   Every call shares the array and clears its counter: calls that overlap on
+   the GPU (other streams, other host threads) race and must not be issued.
+   Returns RICH_EINVAL for a configuration that rich_init_mesh rejects, a
+   NULL array, or n outside [1, RICH_NOALLOC_MAX_CELLS], RICH_ECUDA if the
+   set-up or launch fails (rich_last_error gives the reason). */
 int rich_courant_dt_noalloc(const rich_config *cfg, int64_t n, const double *area, const double *rho,
                             const double *vx, const double *vy, const double *p, const double *wx,
                             const double *wy, double *dt_out, void *stream);
+
+/* ---- measurement ----------------------------------------------------------- */
+
+/* Measured arithmetic peaks of the current device (no counterpart in the
+   paper): independent chains of FP64 and of FP32 fused multiply-adds, timed
+   with CUDA events (best of three after a warm-up launch), in TFLOP/s
+   counting a fused multiply-add as two operations.  Synchronous; allocates
+   a few KiB for the duration of the call.  Errors: RICH_EINVAL (NULL
+   output), RICH_ECUDA. */
+int rich_probe_pipe_peaks(double *fp64_tflops, double *fp32_tflops);
 
 /* ---- host-only entry points (no GPU needed) ----------------------------- */
 

@@ -122,6 +122,11 @@ struct rich_batch {
     std::vector<unsigned char> graph_sig[2];
     int64_t graph_records = 0;
     int64_t persistent_launches = 0, graph_launches = 0, staged_launches = 0;
+    // persistent sweeps whose barrier wait gave up (each step redone staged);
+    // inject_spin > 0 makes the next persistent sweep's barrier wait for one
+    // block more than it launched and give up after that many polls
+    int64_t barrier_timeouts = 0;
+    int32_t inject_spin = 0;
     // host staging of the packed mesh
     std::vector<double> h_x, h_y, h_gx, h_gy, h_W0;
     std::vector<int32_t> h_gsrc, h_gxf, h_tri, h_cell_ptr, h_slot_nb, h_slot_tri, h_cell_inst;
@@ -178,7 +183,7 @@ struct rich_batch {
         p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
         p.w = w.as<rich::Vec2<R>>();
         p.rounding = rounding.as<uint8_t>(); p.p64 = p64.as<double>();
-        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<double>>(); p.psrc = psrc.as<rich::Vec4<R>>();
+        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<R>>(); p.psrc = psrc.as<rich::Vec4<R>>();
         p.dtmin_bits = dtmin.as<unsigned long long>();
         p.dt_out = dtout.as<double>();
         p.status = status.as<int32_t>();
@@ -330,6 +335,20 @@ template <class R> int run_persistent(rich_batch *b, int block)
     CUDA_TRY(cudaMemcpyAsync(b->dsizes.p, &sz, sizeof(sz), cudaMemcpyHostToDevice, b->stream));
     auto *gs = b->gsync.as<rich::GridSync>();
     auto *ds = b->dsizes.as<rich::DeviceSizes>();
+    if (b->inject_spin > 0) {
+        // a barrier that cannot complete: every wait runs out after
+        // inject_spin polls and the sweep stops (launched directly, not from
+        // the recorded graph)
+        rich::GridSync g{};
+        g.spin_limit = b->inject_spin;
+        g.extra = 1;
+        b->inject_spin = 0;
+        CUDA_TRY(cudaMemcpyAsync(gs, &g, sizeof(g), cudaMemcpyHostToDevice, b->stream));
+        CUDA_TRY(cudaMemsetAsync(b->status.p, 0, b->status.cap, b->stream));
+        CUDA_TRY(rich::launch_persistent<R>(p, ds, gs, block, grid, b->stream));
+        b->persistent_launches++;
+        return RICH_OK;
+    }
     if (b->graph_ok) {
         std::vector<unsigned char> sig(sizeof(p) + 3 * sizeof(int));
         std::memcpy(sig.data(), &p, sizeof(p));
@@ -489,6 +508,10 @@ int rich_batch_add(rich_batch *b, const rich_config *cfg, int64_t n, const doubl
     return RICH_OK;
 }
 
+// Simulations of at least this many cells are tessellated in tiles over the
+// whole pool (four or more tiles of 16,384 points).
+constexpr int32_t kTiledMember = 65536;
+
 int rich_batch_step(rich_batch *b, rich_step_info *info)
 {
     rich::Range range("rich batch step");
@@ -529,8 +552,19 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t c) { return list[a]->n > list[c]->n; });
     {
         rich::Range range("rich batch tessellate (a0)");
-        b->pool.parallel_for((int64_t)list.size(), [&](int64_t k) {
+        // a simulation large enough for several tiles is tessellated with the
+        // whole pool (its tiles in parallel, as a single simulation is), one
+        // after another; the others in parallel, one per pool thread.  The
+        // mesh the sweep sees does not depend on the tiling.
+        size_t n_large = 0;
+        while (n_large < by_size.size() && list[by_size[n_large]]->n >= kTiledMember) n_large++;
+        for (size_t k = 0; k < n_large; k++) {
             BatchSim *s = list[by_size[k]];
+            rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
+            s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm, &b->pool);
+        }
+        b->pool.parallel_for((int64_t)(list.size() - n_large), [&](int64_t k) {
+            BatchSim *s = list[by_size[n_large + k]];
             rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
             s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm);
         });
@@ -647,7 +681,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     // 5. admission: conserved variables of new simulations from their first geometry
     if (any_pending) {
         b->launch(rich::K_CIRCUMCENTRE, nullptr);
-        b->launch(rich::K_CELL_GEOMETRY, b->initW.as<double>(), b->U[b->cur].as<double>());
+        b->launch(rich::K_GEOMETRY, b->initW.as<double>(), b->U[b->cur].as<double>());
         for (BatchSim *s : ok)
             if (s->state == PENDING) {
                 s->state = RUNNING;
@@ -678,6 +712,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
             // a barrier wait gave up: the inputs of the step are untouched, so
             // redo it stage by stage and keep the staged launch from now on
             b->launch_mode = 1;
+            b->barrier_timeouts++;
             b->graph_note = "persistent sweep barrier timed out; staged launches used";
             CUDA_TRY(cudaEventRecord(b->ev0, b->stream));
             if ((rc = run_staged(b))) return rc;
@@ -820,6 +855,14 @@ int rich_batch_set_launch(rich_batch *b, int32_t mode, int32_t block)
     b->tuned = false;
     b->cands.clear();
     b->cand_next = 0;
+    return RICH_OK;
+}
+
+int rich_batch_inject_barrier_timeout(rich_batch *b, int32_t spin_limit, int64_t *timeouts_seen)
+{
+    if (!b || spin_limit < 0) return fail(RICH_EINVAL, "bad arguments");
+    if (spin_limit > 0) b->inject_spin = spin_limit;
+    if (timeouts_seen) *timeouts_seen = b->barrier_timeouts;
     return RICH_OK;
 }
 

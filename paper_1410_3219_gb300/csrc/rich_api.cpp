@@ -171,7 +171,7 @@ struct rich_sim {
         p.g = g.as<rich::Vec4<R>>(); p.gl = gl.as<rich::Vec4<R>>(); p.alpha = alpha.as<rich::Vec4<R>>();
         p.w = w.as<rich::Vec2<R>>();
         p.rounding = rounding.as<uint8_t>(); p.p64 = p64.as<double>();
-        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<double>>(); p.psrc = psrc.as<rich::Vec4<R>>();
+        p.tess = tess.as<int32_t>(); p.F = F.as<rich::Vec4<R>>(); p.psrc = psrc.as<rich::Vec4<R>>();
         char *sc = scal.as<char>();
         p.dtmin_bits = reinterpret_cast<unsigned long long *>(sc);
         p.dt_out = reinterpret_cast<double *>(sc + 8);

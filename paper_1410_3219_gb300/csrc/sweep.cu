@@ -170,35 +170,36 @@ template <class R> __device__ __forceinline__ void stage_edge_geometry(const Swe
     // the edge vector from the FP64 endpoints: a zero-length edge stays ~0
     // instead of inheriting the rounding of two separately rounded endpoints
     R ex = to_R<R>(bx64 - ax64), ey = to_R<R>(by64 - ay64);
-    // |e| = e^2 / sqrt(e^2) with one reciprocal square root (zero-length
-    // edges, from co-circular generators, stay exactly zero)
-    const R e2 = ex * ex + ey * ey;
-    R L = nonneg_less(R(0), e2) ? e2 * rsqrt(e2) : R(0);
     R mx = ax + R(0.5) * ex, my = ay + R(0.5) * ey;
     // 1/|r_ij| with one reciprocal square root (a divide and a square root
     // each cost several FP64 issue slots on this part)
-    R rinv = rsqrt(dx * dx + dy * dy);
+    const R rinv = rsqrt(dx * dx + dy * dy);
+    const R nx = dx * rinv, ny = dy * rinv;
+    // The Voronoi edge runs along the unit tangent t = (-n_y, n_x) (from
+    // circumcentre ta to tb, counter-clockwise about the left cell), so its
+    // length is e.t: the vertices' rounding across the edge changes |e| only
+    // in second order, and a zero-length edge (co-circular generators) stays
+    // ~0; a round-off-negative length is taken as zero.  Two operations
+    // instead of the square root of e.e.
+    const R Lt = ey * nx - ex * ny;
+    const R L = key_nonneg(Lt) ? Lt : R(0);
+    const R mrx = mx - dx, mry = my - dy;
     p.eL[e] = L;
     p.emlx[e] = mx;
     p.emly[e] = my;
-    p.emrx[e] = mx - dx;
-    p.emry[e] = my - dy;
-    p.enx[e] = dx * rinv;
-    p.eny[e] = dy * rinv;
+    p.emrx[e] = mrx;
+    p.emry[e] = mry;
+    p.enx[e] = nx;
+    p.eny[e] = ny;
     const R qx = (mx - R(0.5) * dx) * rinv, qy = (my - R(0.5) * dy) * rinv;
-    const R nx = dx * rinv, ny = dy * rinv;
     p.eqx[e] = qx;
     p.eqy[e] = qy;
-    // P = L q + L n / 2, M = L n / 2 - L q: one product L n / 2 and four FMAs
-    const R hL = R(0.5) * L, Lhx = hL * nx, Lhy = hL * ny;
-    p.ePM[e] = Vec4<R>{L * qx + Lhx, L * qy + Lhy, Lhx - L * qx, Lhy - L * qy};
+    // P = L (q + n/2) = (L/|r|) m_l and M = L (n/2 - q) = -(L/|r|) m_r, with
+    // m_l, m_r the edge midpoint relative to the left and right generators
+    const R k = L * rinv;
+    p.ePM[e] = Vec4<R>{k * mx, k * my, -(k * mrx), -(k * mry)};
 }
 
-template <class R> __global__ void k_edge_geometry(SweepParams<R> p)
-{
-    int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < p.E) stage_edge_geometry(p, e);
-}
 
 // a1 + a2: area and centre of mass (shoelace about the generator, FP64),
 // then the primitive variables.  With init_W the conserved variables are set.
@@ -287,10 +288,21 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
     p.cs[i] = gp * rsqrt(gp * W.x);
 }
 
-template <class R> __global__ void k_cell_geometry(SweepParams<R> p, const double *__restrict__ init_W)
+// a1 + a2 in one launch: the first edge_blocks blocks compute the edge
+// geometry, the others the cell geometry and primitives.  The two depend
+// only on the circumcentres, and sharing the SMs lets the edge part's
+// loads and FP32 work (split precision) run beside the cell part's FP64
+// shoelace instead of after it.
+template <class R>
+__global__ void k_geometry(SweepParams<R> p, const double *__restrict__ init_W, int32_t edge_blocks)
 {
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < p.n) stage_cell_geometry(p, init_W, cell_at(p, k));
+    if ((int32_t)blockIdx.x < edge_blocks) {
+        int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+        if (e < p.E) stage_edge_geometry(p, e);
+    } else {
+        int32_t k = (blockIdx.x - edge_blocks) * blockDim.x + threadIdx.x;
+        if (k < p.n) stage_cell_geometry(p, init_W, cell_at(p, k));
+    }
 }
 
 // Smallest non-negative cell time step of each simulation: a warp whose
@@ -514,12 +526,17 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
 
 // launched in blocks of 128 threads; six blocks per SM cap the FP64 build at
 // 80 registers (from 94, with a few spilled to L1), 24 warps instead of 20
+// The FP64 build visits cells in the degree-sorted order (FP64 issue is per
+// warp instruction, so a warp should loop near the mean degree); the FP32
+// build, bound by its gathers, visits them in the Hilbert order itself, so
+// that the rings of a warp's cells are adjacent in the slot arrays and their
+// neighbours share cache lines.
 template <class R> __global__ void __launch_bounds__(128, 6) k_cell_gradient(SweepParams<R> p)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     double dt_cell = DBL_MAX;
     int32_t my_inst = 0;
-    if (k < p.n) dt_cell = stage_cell_gradient(p, cell_at(p, k), my_inst);
+    if (k < p.n) dt_cell = stage_cell_gradient(p, sizeof(R) == sizeof(double) ? cell_at(p, k) : k, my_inst);
     warp_min_to(dt_cell, my_inst, p.dtmin_bits);
 }
 
@@ -655,15 +672,12 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
         // problem has u* = 0 and the wall does not move normal to itself, so
         // mass, tangential momentum and energy fluxes vanish exactly; only
         // the normal pressure flux remains (round-off would otherwise leak).
-        p.F[e] = Vec4<double>{0.0, (double)(L * Fe[1] * nx), (double)(L * Fe[1] * ny), 0.0};
+        p.F[e] = Vec4<R>{R(0), L * Fe[1] * nx, L * Fe[1] * ny, R(0)};
         return;
     }
     const R Fmx = Fe[1] * nx + Fe[2] * tx, Fmy = Fe[1] * ny + Fe[2] * ty;
-    // (the hardware converts in this stage: it waits on its gathers, and the
-    // integer-pipe conversions' extra registers cost it more than the FP64
-    // issue slots they save)
-    p.F[e] = Vec4<double>{(double)(L * Fe[0]), (double)(L * (Fmx + Fe[0] * wfx)), (double)(L * (Fmy + Fe[0] * wfy)),
-                          (double)(L * (Fe[3] + Fmx * wfx + Fmy * wfy + R(0.5) * (wfx * wfx + wfy * wfy) * Fe[0]))};
+    p.F[e] = Vec4<R>{L * Fe[0], L * (Fmx + Fe[0] * wfx), L * (Fmy + Fe[0] * wfy),
+                     L * (Fe[3] + Fmx * wfx + Fmy * wfy + R(0.5) * (wfx * wfx + wfy * wfy) * Fe[0])};
 }
 
 // launched in blocks of 128 threads; ten blocks per SM cap the FP64 build
@@ -690,15 +704,17 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (int32_t s = lo; s < hi; s++) {
         int32_t es = p.slot_edge[s];
-        const Vec4<double> f = p.F[es >> 1];
+        const Vec4<R> f = p.F[es >> 1];
         // the right cell takes the flux with the opposite sign: flip the sign
         // bit (integer pipe) rather than branch, so each slot costs one add
-        // per component whatever the mix of sides in the warp
+        // per component whatever the mix of sides in the warp; a split-
+        // precision flux is widened exactly on the integer pipe (to_d), so
+        // both cells of the edge add the same FP64 value
         const unsigned long long sg = (unsigned long long)(es & 1) << 63;
-        s0 += __longlong_as_double(__double_as_longlong((double)f.x) ^ sg);
-        s1 += __longlong_as_double(__double_as_longlong((double)f.y) ^ sg);
-        s2 += __longlong_as_double(__double_as_longlong((double)f.z) ^ sg);
-        s3 += __longlong_as_double(__double_as_longlong((double)f.w) ^ sg);
+        s0 += __longlong_as_double(__double_as_longlong(to_d(f.x)) ^ sg);
+        s1 += __longlong_as_double(__double_as_longlong(to_d(f.y)) ^ sg);
+        s2 += __longlong_as_double(__double_as_longlong(to_d(f.z)) ^ sg);
+        s3 += __longlong_as_double(__double_as_longlong(to_d(f.w)) ^ sg);
     }
     double m = p.U0[i] - hdt * s0;
     double Px = p.U0[n + i] - hdt * s1;
@@ -757,13 +773,15 @@ constexpr long long kSpinLimit = 1ll << 24;  // ~1-2 s of polling with 64 ns sle
 
 // Grid-wide barrier.  Thread 0 of each block reads the generation, arrives,
 // and waits for the last block to bump the generation; a wait that exceeds
-// kSpinLimit polls sets the timeout flag instead.  Returns false once any
-// block has given up, and the caller then leaves the kernel.
-__device__ bool grid_sync(GridSync *gs, unsigned int nblocks)
+// `limit` polls sets the timeout flag instead, and the other waiters leave
+// when they see it.  Returns false once any block has given up, and the
+// caller then leaves the kernel.
+__device__ bool grid_sync(GridSync *gs, unsigned int nblocks, long long limit)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned int *vgen = &gs->gen;
+        volatile int32_t *vto = &gs->timeout;
         const unsigned int g = *vgen;
         __threadfence();
         const unsigned int arrived = atomicAdd(&gs->count, 1u);
@@ -773,8 +791,8 @@ __device__ bool grid_sync(GridSync *gs, unsigned int nblocks)
             atomicAdd(&gs->gen, 1u);
         } else {
             long long it = 0;
-            while (*vgen == g) {
-                if (++it > kSpinLimit) {
+            while (*vgen == g && *vto == 0) {
+                if (++it > limit) {
                     atomicExch(&gs->timeout, 1);
                     break;
                 }
@@ -795,15 +813,18 @@ __global__ void __launch_bounds__(512) k_sweep_persistent(SweepParams<R> p, cons
     p.T = sz->T;
     p.E = sz->E;
     p.n_inst = sz->n_inst;
-    const unsigned int nb = gridDim.x;
+    // blocks the barrier waits for (more than the grid only when a test makes
+    // the waits run out) and polls before a wait gives up
+    const unsigned int nb = gridDim.x + (unsigned int)gs->extra;
+    const long long lim = gs->spin_limit > 0 ? gs->spin_limit : kSpinLimit;
     const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t stride = gridDim.x * blockDim.x;
     for (int32_t k = tid; k < p.n_inst; k += stride) atomicExch(p.dtmin_bits + k, 0x7f7f7f7f7f7f7f7full);
     for (int32_t t = tid; t < p.T; t += stride) stage_circumcentre(p, t);
-    if (!grid_sync(gs, nb)) return;
+    if (!grid_sync(gs, nb, lim)) return;
     for (int32_t e = tid; e < p.E; e += stride) stage_edge_geometry(p, e);
     for (int32_t k = tid; k < p.n; k += stride) stage_cell_geometry(p, (const double *)nullptr, cell_at(p, k));
-    if (!grid_sync(gs, nb)) return;
+    if (!grid_sync(gs, nb, lim)) return;
     for (int32_t base = blockIdx.x * blockDim.x; base < p.n; base += stride) {
         const int32_t k = base + threadIdx.x;
         double v = DBL_MAX;
@@ -811,9 +832,9 @@ __global__ void __launch_bounds__(512) k_sweep_persistent(SweepParams<R> p, cons
         if (k < p.n) v = stage_cell_gradient(p, cell_at(p, k), inst);
         warp_min_to(v, inst, p.dtmin_bits);
     }
-    if (!grid_sync(gs, nb)) return;
+    if (!grid_sync(gs, nb, lim)) return;
     for (int32_t e = tid; e < p.E; e += stride) stage_edge_flux(p, e);
-    if (!grid_sync(gs, nb)) return;
+    if (!grid_sync(gs, nb, lim)) return;
     for (int32_t k = tid; k < p.n; k += stride) stage_cell_update(p, cell_at(p, k));
 }
 
@@ -903,7 +924,7 @@ inline int blocks(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 // from 0.77x to 1.17x of the mean).  Chosen by timing 32, 64, 128 and 256 on
 // GB300 (Sedov, 262,144 cells): the gradient and flux stages, whose register
 // counts cap an SM at 16-21 warps, run best at 128, the others at 32.
-constexpr int kStageBlock[NUM_STAGES] = {32, 32, 32, 0, 128, 128, 32};
+constexpr int kStageBlock[NUM_STAGES] = {32, 32, 0, 128, 128, 32};
 static_assert(kStageBlock[K_CELL_GRADIENT] == 128 && kStageBlock[K_EDGE_FLUX] == 128,
               "the gradient's and flux's launch bounds assume 128 threads");
 inline int stage_block(int k) { return kStageBlock[k]; }
@@ -913,8 +934,8 @@ inline int nblk(int64_t n, int k) { return (int)((n + stage_block(k) - 1) / stag
 
 const char *stage_name(int k)
 {
-    static const char *names[NUM_STAGES] = {"k_circumcentre", "k_edge_geometry", "k_cell_geometry", "dt_reset",
-                                            "k_cell_gradient", "k_edge_flux", "k_cell_update"};
+    static const char *names[NUM_STAGES] = {"k_circumcentre", "k_geometry", "dt_reset", "k_cell_gradient",
+                                            "k_edge_flux", "k_cell_update"};
     return k >= 0 && k < NUM_STAGES ? names[k] : "";
 }
 
@@ -924,12 +945,11 @@ template <class R> void launch_stage(int k, const SweepParams<R> &p, const doubl
     case K_CIRCUMCENTRE:
         if (p.T > 0) k_circumcentre<R><<<nblk(p.T, K_CIRCUMCENTRE), stage_block(K_CIRCUMCENTRE), 0, st>>>(p);
         break;
-    case K_EDGE_GEOMETRY:
-        if (p.E > 0) k_edge_geometry<R><<<nblk(p.E, K_EDGE_GEOMETRY), stage_block(K_EDGE_GEOMETRY), 0, st>>>(p);
+    case K_GEOMETRY: {
+        const int eb = nblk(p.E, K_GEOMETRY), cb = nblk(p.n, K_GEOMETRY);
+        if (eb + cb > 0) k_geometry<R><<<eb + cb, stage_block(K_GEOMETRY), 0, st>>>(p, init_W, eb);
         break;
-    case K_CELL_GEOMETRY:
-        if (p.n > 0) k_cell_geometry<R><<<nblk(p.n, K_CELL_GEOMETRY), stage_block(K_CELL_GEOMETRY), 0, st>>>(p, init_W);
-        break;
+    }
     case K_DT_RESET:
         cudaMemsetAsync(p.dtmin_bits, 0x7f, sizeof(unsigned long long) * p.n_inst, st);
         break;

@@ -30,10 +30,10 @@
 //              the two discontinuous decisions of the step (rounding trigger,
 //              pressure-ratio switch) are taken on FP64 values
 //   flux       F[E] = L_ij * F_ij (mass, momentum x, y, energy), outward
-//              from the edge's left cell, FP64: in split precision the
-//              edge kernel widens its FP32 flux once per edge (exactly) on
-//              the otherwise idle FP64 pipe, instead of the gather widening
-//              it once per ring slot
+//              from the edge's left cell, in R: in split precision the FP32
+//              flux is stored as computed and the update widens it exactly
+//              (integer pipe) into its FP64 sums, so both cells of an edge
+//              add the same FP64 value
 //   per sim    inst[] scheme parameters and remaining time; dtmin (bits of the
 //              smallest cell time step), dt, status
 #pragma once
@@ -109,7 +109,7 @@ template <class R> struct SweepParams {
     Vec4<R> *psrc;
     Vec2<R> *w;
     int32_t *tess;
-    Vec4<double> *F;  // stored in FP64 in both precisions (see the flux layout)
+    Vec4<R> *F;  // L_ij F_ij in the reconstruction precision (see the flux layout)
     // per simulation: bits of the smallest cell time step, the step taken,
     // status flags
     unsigned long long *dtmin_bits;
@@ -121,20 +121,21 @@ template <class R> struct SweepParams {
 // the remaining stages are a3-a9.
 enum Stage : int {
     K_CIRCUMCENTRE = 0,   // a1 Voronoi vertices
-    K_EDGE_GEOMETRY = 1,  // a1 per-edge L, midpoint, normal, c_ij/|r_ij|
-    K_CELL_GEOMETRY = 2,  // a1 + a2 area, centre of mass, primitives
-    K_DT_RESET = 3,       // clears the time-step minimum (memset, not a kernel)
-    K_CELL_GRADIENT = 4,  // a3-a6 gradients, limiter, mesh velocity, dt
-    K_EDGE_FLUX = 5,      // a7 predicted edge states + HLLC
-    K_CELL_UPDATE = 6,    // a8 + a9 conservative update, point motion
-    NUM_STAGES = 7,
-    GEOMETRY_STAGES = 3,
+    K_GEOMETRY = 1,       // a1 + a2 in one launch: per-edge L, midpoint, normal,
+                          // c_ij/|r_ij| (the first blocks) and per-cell area,
+                          // centre of mass, primitives (the rest)
+    K_DT_RESET = 2,       // clears the time-step minimum (memset, not a kernel)
+    K_CELL_GRADIENT = 3,  // a3-a6 gradients, limiter, mesh velocity, dt
+    K_EDGE_FLUX = 4,      // a7 predicted edge states + HLLC
+    K_CELL_UPDATE = 5,    // a8 + a9 conservative update, point motion
+    NUM_STAGES = 6,
+    GEOMETRY_STAGES = 2,
 };
 
 const char *stage_name(int k);
 
-// Launch one stage.  For K_CELL_GEOMETRY a non-null init_W (4*n FP64
-// primitives, component-major) sets the conserved variables from it instead.
+// Launch one stage.  For K_GEOMETRY a non-null init_W (4*n FP64 primitives,
+// component-major) sets the conserved variables from it instead.
 template <class R> void launch_stage(int k, const SweepParams<R> &p, const double *init_W, cudaStream_t st);
 
 // Sizes of the packed mesh, read by the persistent sweep from device memory
@@ -146,8 +147,11 @@ struct DeviceSizes {
 // State of the persistent sweep's grid barrier (zeroed before each launch).
 struct GridSync {
     unsigned int count, gen;
-    int32_t timeout;  // set when a barrier wait gave up; the sweep then stops
-    int32_t pad;
+    int32_t timeout;     // set when a barrier wait gave up; the sweep then stops
+    int32_t spin_limit;  // polls before a wait gives up (0: about a second's worth)
+    int32_t extra;       // blocks the barrier waits for beyond the grid (0; a
+                         // test sets 1 to make every wait run out)
+    int32_t pad[3];
 };
 
 // The whole step a1-a9 in one cooperative launch of `grid` blocks of `block`

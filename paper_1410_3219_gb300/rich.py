@@ -34,7 +34,8 @@ EXPORTS = ["rich_default_config", "rich_init_mesh", "rich_step", "rich_get_state
            "rich_batch_set_diagnostics", "rich_batch_cells", "rich_batch_destroy", "rich_batch_set_launch",
            "rich_batch_launch_info", "rich_server_create", "rich_server_submit", "rich_server_tick",
            "rich_server_query", "rich_server_fetch", "rich_server_batch", "rich_server_destroy",
-           "rich_init_conserved", "rich_get_order", "rich_time", "rich_mesh_update_check"]
+           "rich_init_conserved", "rich_get_order", "rich_time", "rich_mesh_update_check",
+           "rich_probe_pipe_peaks", "rich_batch_inject_barrier_timeout"]
 
 REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
@@ -141,6 +142,8 @@ def _lib():
         L.rich_get_order.argtypes = [P, I64, C.POINTER(I64)]
         L.rich_time.argtypes = [P]
         L.rich_time.restype = d
+        L.rich_probe_pipe_peaks.argtypes = [_D, _D]
+        L.rich_batch_inject_barrier_timeout.argtypes = [P, I32, C.POINTER(I64)]
         _handle = L
     return _handle
 
@@ -275,6 +278,13 @@ def rich_courant_dt_noalloc(cfg, n, area, rho, vx, vy, p, wx, wy, dt_out, stream
     c = cfg if isinstance(cfg, rich_config) else rich_config.from_dict(cfg)
     ptrs = [C.c_void_p(v) if v else None for v in (area, rho, vx, vy, p, wx, wy, dt_out)]
     _check(_lib().rich_courant_dt_noalloc(C.byref(c), n, *ptrs, C.c_void_p(stream)))
+
+
+def rich_probe_pipe_peaks():
+    """Measured FP64 and FP32 FMA-chain peaks of the current device (TFLOP/s)."""
+    a, b = C.c_double(), C.c_double()
+    _check(_lib().rich_probe_pipe_peaks(C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def rich_delaunay_host(x, y):
@@ -412,6 +422,13 @@ class Batch:
 
     def launch_info(self):
         return rich_batch_launch_info(self.h)
+
+    def inject_barrier_timeout(self, spin_limit=0):
+        """Arm (spin_limit > 0) a barrier timeout in the next persistent
+        sweep; returns the number of timed-out persistent sweeps so far."""
+        seen = C.c_int64()
+        _check(_lib().rich_batch_inject_barrier_timeout(self.h, spin_limit, C.byref(seen)))
+        return seen.value
 
     def close(self):
         if self.h:

@@ -90,39 +90,6 @@ RUNS = {
 }
 
 
-def fp64_noise_response(R, make, steps, eps=2.0 ** -23, seed=1):
-    """L1(rho) between the FP64 run and the same run given relative noise
-    eps on its conserved variables after every step (checkpoint, perturb,
-    restart): the FP64 scheme's own response to FP32-size perturbations.
-    The slope limiter and shock switch (Eqs. 4-8) and the Section 6 rounding
-    trigger are discontinuous in the state, so the response is far above
-    eps on long runs."""
-    wl = make()
-    ref = R.Sim(wl)
-    ref.step(steps)
-    r0 = ref.state()["rho"]
-    ref.close()
-    rng = np.random.default_rng(seed)
-    s = R.Sim(wl)
-    for k in range(steps):
-        s.step(1)
-        if k == steps - 1:
-            break
-        ck = s.checkpoint()
-        z = rng.standard_normal((4, len(ck["m"])))
-        # momentum noise against mass times the flow's speed scale
-        vs = float(np.max(np.hypot(ck["px"], ck["py"]) / ck["m"]))
-        ck["m"] = ck["m"] * (1 + eps * z[0])
-        ck["E"] = ck["E"] * (1 + eps * z[1])
-        ck["px"] = ck["px"] + eps * z[2] * ck["m"] * vs
-        ck["py"] = ck["py"] + eps * z[3] * ck["m"] * vs
-        s.close()
-        s = R.Sim.restart(wl["cfg"], ck)
-    r1 = s.state()["rho"]
-    s.close()
-    return float(np.sum(np.abs(r1 - r0)) / np.sum(np.abs(r0)))
-
-
 @pytest.mark.parametrize("name", list(RUNS))
 def test_full_size_split_run(R, name):
     make, t_end, steps = RUNS[name]
@@ -137,15 +104,8 @@ def test_full_size_split_run(R, name):
     ra, rb = a.state()["rho"], b.state()["rho"]
     l1 = float(np.sum(np.abs(ra - rb)) / np.sum(np.abs(ra)))
     print(f"{name}: {ia['steps_done']} steps, L1(rho) split vs FP64 = {l1:.3e}")
-    bound = 1e-5
-    if l1 > bound:
-        # at the edge of the target: compare with the FP64 scheme's own
-        # response to FP32-size noise on the same run (KH 1024^2 over 200
-        # steps: ~8e-6 against ~1e-5 for the split run)
-        env = fp64_noise_response(R, make, ia["steps_done"])
-        print(f"{name}: FP64 response to 2^-23 per-step noise = {env:.3e}")
-        bound = 2.0 * env
-    assert l1 <= bound, (l1, bound)
+    # the stated target of the split precision, not loosened to the result
+    assert l1 <= 1e-5, l1
     c1 = b.conserved()
     qs = ("m", "E") + (("px", "py") if ws["cfg"]["boundary"] == W.BC_PERIODIC else ())
     for q in qs:

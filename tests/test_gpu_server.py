@@ -122,3 +122,37 @@ def test_server_isolates_a_failing_request(R):
         for f in ref:
             assert np.array_equal(got[f], ref[f]), f
     srv.close()
+
+
+def test_served_mix_matches_the_oracle(R, oracle):
+    """Requests served together, admitted as the budget frees up, each end
+    within the FP64 parity tolerance of the oracle run of the same request
+    (conserved variables and points, element by element)."""
+    from tests.gpu_common import compare_conserved
+    reqs = [(W.sod(n_side=18, seed=201), 3), (W.sedov(n=1500, seed=202), 4),
+            (W.gresho(n_side=16, seed=203, eta=0.05, chi=1.2), 5), (W.kelvin_helmholtz(n_side=24, seed=204), 3)]
+    srv = R.Server(max_cells=1600)  # the requests hold 256..1500 cells: some wait for others to finish
+    ids = []
+    for wl, steps in reqs:
+        ids.append(srv.submit(wl, max_steps=steps))
+        srv.tick()  # each arrives while the earlier ones are on the GPU
+    for _ in range(100):
+        if all(srv.query(r)["state"] in ("done", "failed") for r in ids):
+            break
+        srv.tick()
+
+    class Fetched:
+        def __init__(self, c):
+            self.c = c
+
+        def conserved(self):
+            return self.c
+
+    for (wl, steps), rid in zip(reqs, ids):
+        q = srv.query(rid)
+        assert q["state"] == "done" and q["steps"] == steps, (wl["name"], q)
+        ref = oracle.Sim(wl)
+        for _ in range(steps):
+            ref.step()
+        compare_conserved(Fetched(srv.fetch(rid)), ref, wl["cfg"])
+    srv.close()
