@@ -411,10 +411,13 @@ def run_ours(args):
     t0 = time.perf_counter()
     h2d = d2h = 0
     parts = {"tess_ms": 0.0, "copy_ms": 0.0, "sweep_ms": 0.0}
+    phases = {}
     for _ in range(e2e_steps):
         info = sim2.step(1)
         for k in parts:
             parts[k] += info[k] / e2e_steps
+        for k, v in rich.rich_tess_phases(sim2.h).items():
+            phases[k] = phases.get(k, 0.0) + v / e2e_steps
         rc = L.rich_get_conserved(sim2.h, n, *[b.ctypes.data_as(Dp) for b in bufs])
         assert rc == 0
         # what rich_tessellate uploads: ghost positions, sources, mirror
@@ -463,7 +466,8 @@ def run_ours(args):
         "roofline": roof,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps,
-                "host_tess_ms": parts["tess_ms"], "copy_ms": parts["copy_ms"], "sweep_ms": parts["sweep_ms"]},
+                "host_tess_ms": parts["tess_ms"], "host_tess_phases_ms": phases, "copy_ms": parts["copy_ms"],
+                "sweep_ms": parts["sweep_ms"]},
         "gpu_launches": NUM_KERNELS * args.steps * (2 if precs[0] == "tc" else 1),
         "clocks": clk,
         "pipe_peaks_probe_tflops": probe,
@@ -488,7 +492,7 @@ def run_ours(args):
         line["batched"] = {"fp64": run_batched(rich, 0, args.batch_instances, args.batch_steps),
                            "fp32_split": run_batched(rich, 1, args.batch_instances, args.batch_steps)}
     if not args.no_serving:
-        line["serving"] = run_serving(rich, 1, args.serve_requests, args.serve_steps, 4000, 64000, 0.8)
+        line["serving"] = run_serving(rich, 1, args.serve_requests, args.serve_steps, 4000, 1 << 20, 0.8)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     print(json.dumps(line))
@@ -517,8 +521,15 @@ def run_batched(rich, precision, n_inst, steps, seed=4):
         sweep_ms.append(info["sweep_ms"])
         tess_ms.append(info["tess_ms"])
     li = b.launch_info()
+    # both launch shapes timed on the same batch, the autotuner's choice first
+    shapes = {}
+    for name, mode, block in (("staged_graph", 1, 256), ("persistent_256", 2, 256), ("persistent_512", 2, 512)):
+        b.set_launch(mode, block)
+        b.step()  # records the graph of this shape
+        shapes[name] = float(np.mean([b.step()["sweep_ms"] for _ in range(3)]))
     b.close()
     return {"value": cells * steps / (sum(sweep_ms) / 1e3), "unit": UNIT, "instances": n_inst, "cells": cells,
+            "shape_ms_per_step": shapes,
             "ms_per_step": float(np.mean(sweep_ms)), "p99_ms": float(np.percentile(sweep_ms, 99)),
             "host_tess_ms_per_step": float(np.mean(tess_ms)),
             "e2e": {"value": cells * steps / (sum(wall) / 1e3), "unit": UNIT,
@@ -528,14 +539,16 @@ def run_batched(rich, precision, n_inst, steps, seed=4):
             "gpu_launches_per_step": 1 if li["persistent"] else 6}
 
 
-def run_serving(rich, precision, n_req, steps_per_req, n_min, n_max, load, seed=5):
+def run_serving(rich, precision, n_req, steps_per_req, n_min, n_max, load, seed=5, lanes=2, split=65536,
+                max_cells=1 << 22, top_lane_cells=1 << 20):
     """Requests (Sod / Sedov / Gresho, sizes log-uniform in [n_min, n_max],
-    Lloyd eta in [0.01, 0.1], chi in [0.5, 1.5]) served two ways on the same
-    GPU: one at a time through rich_step (FIFO), and through the
-    continuous-batching server.  Both see the same Poisson arrival stream,
-    whose rate is `load` times the one-at-a-time service capacity measured
-    first; latency is arrival to result on the host.  Capacity is also
-    measured with every request submitted at once."""
+    Lloyd eta in [0.01, 0.1], chi in [0.5, 1.5], steps_per_req steps each)
+    served two ways on the same GPU: one at a time through rich_step (FIFO),
+    and through the continuous-batching server running `lanes` lane threads
+    (requests of at least `split` cells in the second lane).  Both see the
+    same Poisson arrival stream, whose rate is `load` times the one-at-a-time
+    service capacity measured first; latency is arrival to result on the
+    host.  Capacity is also measured with every request submitted at once."""
     import math
     from paper_1410_3219_gb300 import workloads as W
     rng = np.random.default_rng(seed)
@@ -554,18 +567,27 @@ def run_serving(rich, precision, n_req, steps_per_req, n_min, n_max, load, seed=
         wl["cfg"].update(eta=eta, chi=chi, precision=precision)
         reqs.append(wl)
     cells = [len(w["x"]) for w in reqs]
-    total = sum(cells) * steps_per_req
 
     def solo(wl):
+        # one step per call, so that a run the scheme stops (a Sedov blast
+        # emptying a cell) still counts the steps it made
         sim = rich.Sim(wl)
-        sim.step(steps_per_req)
+        done = 0
+        try:
+            for _ in range(steps_per_req):
+                sim.step(1)
+                done += 1
+        except rich.RichError:
+            pass
         sim.conserved()
         sim.close()
+        return done
 
-    # one-at-a-time capacity
+    # one-at-a-time capacity (cell-updates actually done, failed runs included)
     t0 = time.perf_counter()
+    solo_updates = 0
     for wl in reqs:
-        solo(wl)
+        solo_updates += len(wl["x"]) * solo(wl)
     t_solo = time.perf_counter() - t0
     rate = load * n_req / t_solo
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
@@ -581,35 +603,44 @@ def run_serving(rich, precision, n_req, steps_per_req, n_min, n_max, load, seed=
         solo_lat.append(1e3 * (time.perf_counter() - t0 - arrivals[k]))
 
     def serve(arr):
-        srv = rich.Server(precision=precision, max_cells=1 << 24)
+        srv = rich.Server(precision=precision, max_cells=max_cells)
+        srv.start(lanes=lanes, split_cells=split, top_lane_cells=top_lane_cells)
         ids, k = [], 0
         t0 = time.perf_counter()
-        sweep_ms = 0.0
-        while k < n_req or any(srv.query(r)["state"] in ("queued", "running") for r in ids):
+        while k < n_req:
             now = time.perf_counter() - t0
             while k < n_req and arr[k] <= now:
                 ids.append(srv.submit(reqs[k], max_steps=steps_per_req))
                 k += 1
-            if not ids or all(srv.query(r)["state"] in ("done", "failed") for r in ids):
-                if k < n_req:
-                    time.sleep(max(0.0, arr[k] - (time.perf_counter() - t0)))
-                continue
-            sweep_ms += srv.tick()["sweep_ms"]
+            if k < n_req:
+                time.sleep(max(0.0, min(0.002, arr[k] - (time.perf_counter() - t0))))
+        while any(srv.query(r)["state"] in ("queued", "running") for r in ids):
+            time.sleep(0.002)
         span = time.perf_counter() - t0
         lat = [srv.query(r)["latency_ms"] for r in ids]
+        updates = sum(c * srv.query(r)["steps"] for c, r in zip(cells, ids))
+        st = srv.stats()
         for r in ids:
             srv.fetch(r)
         srv.close()
-        return span, lat, sweep_ms
+        return span, lat, updates, st
 
-    span, lat, sweep_ms = serve(arrivals)
-    burst_span, _, burst_sweep = serve(np.zeros(n_req))
+    span, lat, updates, st = serve(arrivals)
+    burst_span, _, burst_updates, bst = serve(np.zeros(n_req))
     return {"requests": n_req, "steps_per_request": steps_per_req, "cells_range": [n_min, n_max],
+            "cells_total": int(sum(cells)), "eta_range": [0.01, 0.1], "chi_range": [0.5, 1.5],
+            "kinds": "Sod / Sedov / Gresho in turn (Sedov requests stop where the scheme empties a cell)",
             "offered_load": load, "unit": UNIT, "latency": "arrival to result on the host",
             "served": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                       "capacity": total / burst_span, "device_value": total / (burst_sweep / 1e3)},
+                       "value": updates / span, "capacity": burst_updates / burst_span,
+                       "device_value": burst_updates / (bst["sweep_ms"] / 1e3) if bst["sweep_ms"] else None,
+                       "lanes": lanes, "lane_split_cells": split, "top_lane_cells": top_lane_cells,
+                       "budget_cells": max_cells,
+                       "burst_device_busy": bst["sweep_ms"] / bst["wall_ms"] if bst["wall_ms"] else None,
+                       "burst_host_tess_busy": bst["tess_ms"] / bst["wall_ms"] if bst["wall_ms"] else None,
+                       "burst_lane_steps": bst["steps"]},
             "one_at_a_time": {"p50_ms": float(np.percentile(solo_lat, 50)),
-                              "p99_ms": float(np.percentile(solo_lat, 99)), "capacity": total / t_solo}}
+                              "p99_ms": float(np.percentile(solo_lat, 99)), "capacity": solo_updates / t_solo}}
 
 
 def cpu_baseline(wl, budget_s):
@@ -679,8 +710,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=5)
-    ap.add_argument("--serve-requests", type=int, default=48)
-    ap.add_argument("--serve-steps", type=int, default=20)
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-steps", type=int, default=100)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

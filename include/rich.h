@@ -209,6 +209,12 @@ int rich_set_profiling(rich_sim *s, int32_t on);
 int rich_kernel_times(rich_sim *s, int32_t cap, double *ms, int32_t *count);
 const char *rich_kernel_name(int32_t stage);
 
+/* Wall time (ms) of the phases of the handle's last host tessellation (a0):
+   ms[0] ghost images, point copies, bounding box and bucket grid; ms[1] the
+   tiles (triangulation or in-place update, star checks, rings); ms[2]
+   triangle and ring assembly; ms[3] edge counts and processing order. */
+int rich_tess_phases(const rich_sim *s, double *ms);
+
 /* Number of cells of the handle. */
 int64_t rich_num_cells(const rich_sim *s);
 
@@ -340,7 +346,33 @@ int rich_server_query(rich_server *s, int64_t req, int32_t *state, int32_t *erro
 int rich_server_fetch(rich_server *s, int64_t req, int64_t n, double *x, double *y, double *m, double *px,
                       double *py, double *E);
 
-/* The batch the server steps (for rich_batch_set_launch / launch_info). */
+/* Hand the server to lane threads (asynchronous mode; no counterpart in the
+   paper): `lanes` (1-4) threads each step their own batch, with its own CUDA
+   stream, in a loop for as long as it has admitted requests; the lanes share
+   the server's host threads, taking them in turn one parallel pass at a
+   time.  A request goes to lane k when its cell count is at
+   least split_cells * 8^(k-1) (lane 0 below split_cells), so small requests
+   never wait on the host tessellation of large ones, and one lane's host
+   tessellation overlaps another's device sweep.  Admission takes each
+   lane's queue in arrival order against the shared cell budget; the lane of
+   the largest requests also holds at most top_lane_cells cells at once (a
+   larger request alone; 0: no limit but the budget), so that its requests
+   run nearly one at a time with the whole worker pool instead of all
+   sharing it for their whole run.  Each lane's device memory grows to the
+   cells it has held.  Call it before any request is admitted; afterwards
+   rich_server_tick returns RICH_ESTATE and the caller polls
+   rich_server_query.  Errors: RICH_EINVAL, RICH_ESTATE. */
+int rich_server_start(rich_server *s, int32_t lanes, int64_t split_cells, int64_t top_lane_cells);
+
+/* Totals over the server's steps (each output may be NULL): batched steps
+   taken by all lanes, summed device sweep time, host tessellation time and
+   other host time (ms), and the wall time since rich_server_start (ms; 0 in
+   tick mode).  (sweep + tessellation) / wall above one shows host and
+   device work overlapping. */
+int rich_server_stats(rich_server *s, int64_t *steps, double *sweep_ms, double *tess_ms, double *other_ms,
+                      double *wall_ms);
+
+/* The batch of lane 0 (for rich_batch_set_launch / launch_info). */
 rich_batch *rich_server_batch(rich_server *s);
 
 void rich_server_destroy(rich_server *s);
@@ -405,6 +437,15 @@ int rich_delaunay_host(int64_t n, const double *x, const double *y, int64_t cap,
    cap is the capacity of nbx/nby/nbsrc; *nslots receives the size needed. */
 int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const double *y, int64_t cap,
                     int64_t *ptr, double *nbx, double *nby, int64_t *nbsrc, int64_t *nslots);
+
+/* The device's edge-list builder against the host's (a0 support; needs a
+   GPU): builds the mesh of the n points on the host with its own edge list,
+   runs the device builder on the same rings, and counts the entries of the
+   slot-to-edge map and of the edge arrays (left and right points, the two
+   Voronoi vertices) that differ.  *edges receives the number of edges.
+   Errors: RICH_EINVAL, RICH_ENODEV, RICH_ECUDA, tessellation errors. */
+int rich_edge_list_check(const rich_config *cfg, int64_t n, const double *x, const double *y, int64_t *edges,
+                         int64_t *mismatched);
 
 /* Check of the host builder's in-place update (a0 keeps each tile's last
    triangulation, moves its vertices, flips to Delaunay and inserts new

@@ -72,6 +72,11 @@ inline double now_ms()
 }
 
 bool valid_config(const rich_config *c);
+
+class ThreadPool;
+// rich_batch_create whose host work runs on a pool shared with other
+// batches (nullptr: its own pool of host_threads threads)
+int batch_create(int32_t precision, int64_t max_cells, int32_t host_threads, ThreadPool *shared, rich_batch **out);
 bool point_inside(const rich_config *c, double x, double y);
 
 }  // namespace rich

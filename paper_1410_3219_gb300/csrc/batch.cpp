@@ -94,7 +94,10 @@ struct rich_batch {
     std::vector<std::unique_ptr<BatchSim>> sims;
     std::vector<BatchSim *> packed;  // running simulations in packed order (last step)
     int64_t n_packed = 0;            // cells in the packed arrays
-    rich::ThreadPool pool;
+    // host workers: the batch's own, or a pool it shares with other
+    // batches (the server's lanes)
+    std::unique_ptr<rich::ThreadPool> own_pool;
+    rich::ThreadPool *pool = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool diagnostics = false;
@@ -137,7 +140,8 @@ struct rich_batch {
     std::vector<int32_t> h_status;
     int64_t nG = 0, nT = 0, nE = 0, nS = 0;
 
-    explicit rich_batch(int threads) : pool(threads) {}
+    explicit rich_batch(int threads) : own_pool(new rich::ThreadPool(threads)), pool(own_pool.get()) {}
+    explicit rich_batch(rich::ThreadPool *shared) : pool(shared) {}
     ~rich_batch()
     {
         if (stream) cudaStreamSynchronize(stream);
@@ -227,7 +231,16 @@ rich::InstParams inst_params(const BatchSim &s, bool init)
 }
 
 // Fill the staging arrays of simulation s (index k in packing order) at its offsets.
-void pack_one(rich_batch *b, BatchSim &s, int32_t k)
+// One piece of the packing of simulation k into the batch's index space:
+// part 0 its cells [i0, i1) (points, simulation id, ring offsets, order,
+// first owned edges, state sources, initial primitives), part 1 its ring
+// slots [i0, i1), part 2 its triangle corners [i0, i1), part 3 its ghosts.
+struct PackTask {
+    int32_t k, part;
+    int64_t i0, i1;
+};
+
+void pack_part(rich_batch *b, BatchSim &s, const PackTask &t)
 {
     const rich::HostMesh &m = s.hm;
     const int32_t n = s.n;
@@ -236,31 +249,61 @@ void pack_one(rich_batch *b, BatchSim &s, int32_t k)
     auto pid = [&](int32_t q) -> int32_t {
         return q < n ? (int32_t)(co + q) : (int32_t)(N + go + (q - n));
     };
-    std::memcpy(&b->h_x[co], s.hx.data(), sizeof(double) * n);
-    std::memcpy(&b->h_y[co], s.hy.data(), sizeof(double) * n);
-    for (int32_t i = 0; i < n; i++) b->h_cell_inst[co + i] = k;
-    for (int32_t q = 0; q < m.g; q++) {
-        b->h_gx[go + q] = m.gx[q];
-        b->h_gy[go + q] = m.gy[q];
-        b->h_gsrc[go + q] = (int32_t)(co + m.ghost_src[q]);
-        b->h_gxf[go + q] = m.ghost_xf[q];
-        b->h_gshift[go + q] = m.ghost_shift[q];
+    const int64_t i0 = t.i0, i1 = t.i1;
+    switch (t.part) {
+    case 0:
+        std::memcpy(&b->h_x[co + i0], s.hx.data() + i0, sizeof(double) * (i1 - i0));
+        std::memcpy(&b->h_y[co + i0], s.hy.data() + i0, sizeof(double) * (i1 - i0));
+        for (int64_t i = i0; i < i1; i++) {
+            b->h_cell_inst[co + i] = t.k;
+            b->h_cell_ptr[co + i] = (int32_t)(so + m.cell_ptr[i]);
+            b->h_corder[co + i] = (int32_t)(co + m.cell_order[i]);
+            b->h_eoff[co + i] = (int32_t)(eo + m.edge_off[i]);
+            // conserved state: continuing simulations gather from their previous slot
+            b->h_src[co + i] = s.prev_cell_off >= 0 ? (int32_t)(s.prev_cell_off + i) : -1;
+        }
+        if (s.state == PENDING)
+            for (int c = 0; c < 4; c++)
+                for (int64_t i = i0; i < i1; i++) b->h_W0[(size_t)c * N + co + i] = s.W0[(size_t)c * n + i];
+        break;
+    case 1:
+        for (int64_t q = i0; q < i1; q++) {
+            b->h_slot_nb[so + q] = pid(m.slot_nb[q]);
+            b->h_slot_tri[so + q] = (int32_t)(to + m.slot_tri[q]);
+        }
+        break;
+    case 2:
+        for (int64_t c = i0; c < i1; c++) b->h_tri[3 * to + c] = pid(m.tri[c]);
+        break;
+    default:
+        for (int64_t q = i0; q < i1; q++) {
+            b->h_gx[go + q] = m.gx[q];
+            b->h_gy[go + q] = m.gy[q];
+            b->h_gsrc[go + q] = (int32_t)(co + m.ghost_src[q]);
+            b->h_gxf[go + q] = m.ghost_xf[q];
+            b->h_gshift[go + q] = m.ghost_shift[q];
+        }
+        break;
     }
-    const size_t T = m.tri.size() / 3;
-    for (size_t t = 0; t < 3 * T; t++) b->h_tri[3 * to + t] = pid(m.tri[t]);
-    for (int32_t i = 0; i < n; i++) b->h_cell_ptr[co + i] = (int32_t)(so + m.cell_ptr[i]);
-    for (int32_t i = 0; i < n; i++) b->h_corder[co + i] = (int32_t)(co + m.cell_order[i]);
-    for (int32_t i = 0; i < n; i++) b->h_eoff[co + i] = (int32_t)(eo + m.edge_off[i]);
-    const size_t S = m.slot_nb.size();
-    for (size_t q = 0; q < S; q++) {
-        b->h_slot_nb[so + q] = pid(m.slot_nb[q]);
-        b->h_slot_tri[so + q] = (int32_t)(to + m.slot_tri[q]);
+}
+
+// The packing of every simulation as pieces of bounded size, so that one
+// large simulation packs on all the pool's threads.
+void pack_all(rich_batch *b, const std::vector<BatchSim *> &ok)
+{
+    constexpr int64_t kPiece = 1 << 16;
+    std::vector<PackTask> tasks;
+    auto split = [&](int32_t k, int32_t part, int64_t len, int64_t piece) {
+        for (int64_t i = 0; i < len; i += piece) tasks.push_back(PackTask{k, part, i, std::min(len, i + piece)});
+    };
+    for (size_t k = 0; k < ok.size(); k++) {
+        const BatchSim &s = *ok[k];
+        split((int32_t)k, 0, s.n, kPiece);
+        split((int32_t)k, 1, (int64_t)s.hm.slot_nb.size(), 4 * kPiece);
+        split((int32_t)k, 2, (int64_t)s.hm.tri.size(), 4 * kPiece);
+        split((int32_t)k, 3, s.hm.g, 4 * kPiece);
     }
-    // conserved state: continuing simulations gather from their previous slot
-    for (int32_t i = 0; i < n; i++) b->h_src[co + i] = s.prev_cell_off >= 0 ? (int32_t)(s.prev_cell_off + i) : -1;
-    if (s.state == PENDING)
-        for (int c = 0; c < 4; c++)
-            for (int32_t i = 0; i < n; i++) b->h_W0[(size_t)c * N + co + i] = s.W0[(size_t)c * n + i];
+    b->pool->parallel_for((int64_t)tasks.size(), [&](int64_t j) { pack_part(b, *ok[tasks[j].k], tasks[j]); });
 }
 
 int ensure_device(rich_batch *b)
@@ -437,9 +480,11 @@ void record_timing(rich_batch *b, const LaunchShape &s, double ms)
 
 }  // namespace
 
-extern "C" {
-
-int rich_batch_create(int32_t precision, int64_t max_cells, int32_t host_threads, rich_batch **out)
+namespace rich {
+// A batch whose host work runs on `shared` (owned by the caller, who keeps
+// it alive longer than the batch); host_threads <= 0 and shared == nullptr:
+// its own pool of one thread per hardware thread.
+int batch_create(int32_t precision, int64_t max_cells, int32_t host_threads, ThreadPool *shared, rich_batch **out)
 {
     if (!out) return fail(RICH_EINVAL, "out is NULL");
     *out = nullptr;
@@ -448,7 +493,7 @@ int rich_batch_create(int32_t precision, int64_t max_cells, int32_t host_threads
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(RICH_ENODEV, "no CUDA device");
     int threads = host_threads > 0 ? host_threads : (int)std::max(1u, std::thread::hardware_concurrency());
-    rich_batch *b = new (std::nothrow) rich_batch(threads);
+    rich_batch *b = shared ? new (std::nothrow) rich_batch(shared) : new (std::nothrow) rich_batch(threads);
     if (!b) return fail(RICH_ENOMEM, "host allocation");
     b->precision = precision;
     b->max_cells = max_cells;
@@ -459,6 +504,15 @@ int rich_batch_create(int32_t precision, int64_t max_cells, int32_t host_threads
     }
     *out = b;
     return RICH_OK;
+}
+}  // namespace rich
+
+extern "C" {
+
+
+int rich_batch_create(int32_t precision, int64_t max_cells, int32_t host_threads, rich_batch **out)
+{
+    return rich::batch_create(precision, max_cells, host_threads, nullptr, out);
 }
 
 void rich_batch_destroy(rich_batch *b) { delete b; }
@@ -561,9 +615,9 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
         for (size_t k = 0; k < n_large; k++) {
             BatchSim *s = list[by_size[k]];
             rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
-            s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm, &b->pool);
+            s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm, b->pool);
         }
-        b->pool.parallel_for((int64_t)(list.size() - n_large), [&](int64_t k) {
+        b->pool->parallel_for((int64_t)(list.size() - n_large), [&](int64_t k) {
             BatchSim *s = list[by_size[n_large + k]];
             rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
             s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm);
@@ -618,7 +672,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     b->h_slot_nb.resize(so); b->h_slot_tri.resize(so);
     b->h_eoff.resize(N + 1); b->h_gshift.resize(go);
     if (any_pending) b->h_W0.assign(4 * N, 0.0);
-    b->pool.parallel_for((int64_t)ok.size(), [&](int64_t k) { pack_one(b, *ok[k], (int32_t)k); });
+    pack_all(b, ok);
     b->h_cell_ptr[N] = (int32_t)so;
     b->h_eoff[N] = (int32_t)eo;
     b->h_inst.resize(ok.size());

@@ -4,6 +4,7 @@
 #include "mesh.h"
 
 #include <algorithm>
+#include <chrono>
 #include <array>
 #include <climits>
 #include <cmath>
@@ -988,9 +989,22 @@ void build_slab(const SlabCtx &c, const Tile &tile, double H, bool update, Delau
 
 }  // namespace
 
+static double wall_ms()
+{
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
 int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const double *y, MeshWork &work, HostMesh &m,
                     ThreadPool *pool)
 {
+    double t_mark = wall_ms();
+    for (double &v : work.phase_ms) v = 0.0;
+    auto lap = [&](int k) {
+        const double t = wall_ms();
+        work.phase_ms[k] += t - t_mark;
+        t_mark = t;
+    };
     const double Lx = box.x1 - box.x0, Ly = box.y1 - box.y0;
     const double h = std::sqrt(Lx * Ly / std::max(n, 1));
     const double wmax = std::min(Lx, Ly);
@@ -1079,6 +1093,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         }
         PointGrid grid;
         build_grid(np, X.data(), Y.data(), ext, work, pool, grid);
+        lap(0);
         SlabCtx ctx;
         ctx.n = n;
         ctx.np = np;
@@ -1166,6 +1181,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
             if (!band_ok) break;
             todo.swap(again);
         }
+        lap(1);
         if (!band_ok) {
             if (w >= wmax) return -4;
             w = std::min(2.0 * w, wmax);
@@ -1254,6 +1270,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     if (pool && K > 1) pool->parallel_for(K, fill);
     else
         for (int s = 0; s < K; s++) fill(s);
+    lap(2);
     // edges: each physical edge once, owned by its smaller real cell; a
     // periodic edge between a cell and its own copy by the +shift slot
     auto owns = [&](int32_t i, int32_t j) -> int {  // 1 own, 0 partner's, -1 inconsistent
@@ -1326,6 +1343,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         else
             for (int64_t c = 0; c < nchunks; c++) order(c);
         work.n_kept = n;
+        lap(3);
         return 0;
     }
     m.slot_edge.assign(S, -1);
@@ -1390,6 +1408,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     for (int64_t c = 0; c < nchunks; c++)
         if (missing[c]) return -3;
     work.n_kept = n;
+    lap(3);
     return 0;
 }
 

@@ -165,6 +165,10 @@ struct MeshWork {
     int64_t kinetic_tiles = 0, fresh_tiles = 0;
     // vertices taken out and put back by the updates, over all builds
     int64_t reinserted = 0;
+    // wall time of the last build's phases (ms): ghosts, point copies,
+    // bounding box and bucket grid; the tiles (triangulation, star checks,
+    // rings per tile); triangle and ring assembly; edge counts and order
+    double phase_ms[4] = {0.0, 0.0, 0.0, 0.0};
 };
 
 class ThreadPool;

@@ -785,6 +785,78 @@ int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const do
     return RICH_OK;
 }
 
+int rich_tess_phases(const rich_sim *s, double *ms)
+{
+    if (!s || !ms) return fail(RICH_EINVAL, "bad arguments");
+    for (int k = 0; k < 4; k++) ms[k] = s->mw.phase_ms[k];
+    return RICH_OK;
+}
+
+int rich_edge_list_check(const rich_config *cfg, int64_t n, const double *x, const double *y, int64_t *edges,
+                         int64_t *mismatched)
+{
+    if (!valid_config(cfg) || n < 3 || n > INT32_MAX || !x || !y || !edges || !mismatched)
+        return fail(RICH_EINVAL, "bad arguments");
+    for (int64_t i = 0; i < n; i++)
+        if (!point_inside(cfg, x[i], y[i])) return fail(RICH_EINVAL, "point outside the box");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(RICH_ENODEV, "no CUDA device");
+    const rich::BoxConfig box{cfg->boundary, cfg->x0, cfg->x1, cfg->y0, cfg->y1};
+    rich::ThreadPool pool((int)std::max(1u, std::thread::hardware_concurrency()));
+    rich::MeshWork mw;  // host_edges: the host builds the reference list too
+    rich::HostMesh m;
+    int rc = rich::build_host_mesh(box, (int32_t)n, x, y, mw, m, &pool);
+    if (rc) return mesh_rc(rc);
+    const size_t S = m.slot_nb.size(), E = (size_t)m.n_edges;
+    cudaStream_t st = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    DBuf cell_ptr, slot_nb, slot_tri, gsrc, gshift, eoff, slot_edge, el, er, eta, etb, bad;
+    auto up = [&](DBuf &d, const std::vector<int32_t> &h) -> cudaError_t {
+        cudaError_t e = d.ensure((h.size() + 1) * sizeof(int32_t));
+        if (e == cudaSuccess && !h.empty())
+            e = cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        return e;
+    };
+    std::vector<int32_t> dse(S), del(E), der(E), deta(E), detb(E);
+    int32_t bad_h = 0;
+    cudaError_t e = up(cell_ptr, m.cell_ptr);
+    if (e == cudaSuccess) e = up(slot_nb, m.slot_nb);
+    if (e == cudaSuccess) e = up(slot_tri, m.slot_tri);
+    if (e == cudaSuccess) e = up(gsrc, m.ghost_src);
+    if (e == cudaSuccess) e = up(gshift, m.ghost_shift);
+    if (e == cudaSuccess) e = up(eoff, m.edge_off);
+    for (DBuf *b : {&slot_edge}) if (e == cudaSuccess) e = b->ensure((S + 1) * sizeof(int32_t));
+    for (DBuf *b : {&el, &er, &eta, &etb}) if (e == cudaSuccess) e = b->ensure((E + 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = bad.ensure(sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = rich::launch_build_edges((int32_t)n, (int32_t)S, cell_ptr.as<int32_t>(), slot_nb.as<int32_t>(),
+                                     slot_tri.as<int32_t>(), gsrc.as<int32_t>(), gshift.as<int32_t>(),
+                                     eoff.as<int32_t>(), cfg->boundary == RICH_BC_PERIODIC ? 1 : 0, nullptr, nullptr,
+                                     slot_edge.as<int32_t>(), el.as<int32_t>(), er.as<int32_t>(), eta.as<int32_t>(),
+                                     etb.as<int32_t>(), bad.as<int32_t>(), st);
+    auto down = [&](std::vector<int32_t> &h, DBuf &d) {
+        if (e == cudaSuccess && !h.empty())
+            e = cudaMemcpyAsync(h.data(), d.p, h.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    };
+    down(dse, slot_edge);
+    down(del, el);
+    down(der, er);
+    down(deta, eta);
+    down(detb, etb);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (e != cudaSuccess) return fail(RICH_ECUDA, cudaGetErrorString(e));
+    int64_t bad_count = bad_h ? 1 : 0;
+    for (size_t k = 0; k < S; k++) bad_count += dse[k] != m.slot_edge[k];
+    for (size_t k = 0; k < E; k++)
+        bad_count += (del[k] != m.edge_l[k]) + (der[k] != m.edge_r[k]) + (deta[k] != m.edge_ta[k]) +
+                     (detb[k] != m.edge_tb[k]);
+    *edges = (int64_t)E;
+    *mismatched = bad_count;
+    return RICH_OK;
+}
+
 int rich_mesh_update_check(const rich_config *cfg, int64_t n, int32_t steps, const double *xs, const double *ys,
                            int32_t threads, int32_t *mismatched, int64_t *updated, int64_t *rebuilt,
                            int64_t *reinserted)

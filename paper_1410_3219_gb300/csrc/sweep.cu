@@ -214,20 +214,27 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
     // its two crosses (v_{m-1} last, when c_{m-1} + c_0 is known).
     int32_t tl = p.slot_tri[hi - 1];
     const double zx = p.ccx[tl] - xi, zy = p.ccy[tl] - yi;
-    double ax = zx, ay = zy, c0 = 0.0, cp = 0.0;
+    double ax = zx, ay = zy, c0, cp;
     double A2 = 0.0, sx = 0.0, sy = 0.0;
-    for (int32_t s = lo; s < hi; s++) {
-        int32_t t = p.slot_tri[s];
-        double bx = p.ccx[t] - xi, by = p.ccy[t] - yi;
-        double cr = ax * by - ay * bx;
+    {
+        const int32_t t = p.slot_tri[lo];
+        const double bx = p.ccx[t] - xi, by = p.ccy[t] - yi;
+        const double cr = ax * by - ay * bx;
         A2 += cr;
-        if (s == lo) {
-            c0 = cr;
-        } else {
-            const double wv = cp + cr;
-            sx += ax * wv;
-            sy += ay * wv;
-        }
+        c0 = cp = cr;
+        ax = bx;
+        ay = by;
+    }
+    // two slots per pass: the next vertex's loads issue before this one's sums
+#pragma unroll 2
+    for (int32_t s = lo + 1; s < hi; s++) {
+        const int32_t t = p.slot_tri[s];
+        const double bx = p.ccx[t] - xi, by = p.ccy[t] - yi;
+        const double cr = ax * by - ay * bx;
+        A2 += cr;
+        const double wv = cp + cr;
+        sx += ax * wv;
+        sy += ay * wv;
         cp = cr;
         ax = bx;
         ay = by;
@@ -329,15 +336,52 @@ __device__ __forceinline__ void warp_min_to(double v, int32_t inst, unsigned lon
     }
 }
 
+// What the gradient stage reads per ring slot s of a cell: the edge length
+// L, the cell's Eq. 1 weights for the neighbour (A = P, or -M for the
+// edge's right cell) and for itself (B), the edge midpoint relative to the
+// cell's generator, and the neighbour's primitives (mirrored for an image)
+// with its FP64 pressure, here read from the sweep's arrays.
+template <class R> struct GlobalSlots {
+    const SweepParams<R> &p;
+    __device__ __forceinline__ R L(int32_t s) const { return p.eL[p.slot_edge[s] >> 1]; }
+    __device__ __forceinline__ void weights(int32_t s, R &Ax, R &Ay, R &Bx, R &By) const
+    {
+        const int32_t es = p.slot_edge[s];
+        const Vec4<R> pm = p.ePM[es >> 1];
+        // the right cell of an edge takes -M, -P (sign flips on the integer pipe)
+        const unsigned long long ms = (es & 1) ? 0x8000000000000000ull : 0ull;
+        Ax = flip((es & 1) ? pm.z : pm.x, ms);
+        Ay = flip((es & 1) ? pm.w : pm.y, ms);
+        Bx = flip((es & 1) ? pm.x : pm.z, ms);
+        By = flip((es & 1) ? pm.y : pm.w, ms);
+    }
+    __device__ __forceinline__ void midpoint(int32_t s, R &mx, R &my) const
+    {
+        const int32_t es = p.slot_edge[s];
+        const int32_t e = es >> 1;
+        mx = (es & 1) ? p.emrx[e] : p.emlx[e];
+        my = (es & 1) ? p.emry[e] : p.emly[e];
+    }
+    __device__ __forceinline__ Vec4<R> W(int32_t s) const { return load_W(p, p.slot_nb[s]); }
+    __device__ __forceinline__ double p64(int32_t s, R pj) const
+    {
+        if (sizeof(R) == sizeof(double)) return (double)pj;
+        int32_t xf;
+        return p.p64[src_of(p, p.slot_nb[s], xf)];
+    }
+};
+
 // a3-a6: Green-Gauss gradient (Eq. 1), limiter with the shock switch
-// (Eqs. 3-8), cell-rounding mesh velocity (Section 6), per-cell time step.
-template <class R> __device__ __forceinline__ double stage_cell_gradient(const SweepParams<R> &p, int32_t i, int32_t &my_inst)
+// (Eqs. 3-8), cell-rounding mesh velocity (Section 6), per-cell time step,
+// for cell i whose ring slots are [lo, hi) of the accessor `sl`.
+template <class R, class Slots>
+__device__ __forceinline__ double stage_cell_gradient(const SweepParams<R> &p, int32_t i, int32_t lo, int32_t hi,
+                                                      const Slots &sl, int32_t &my_inst)
 {
     double dt_cell = DBL_MAX;
     {
         my_inst = inst_of(p, i);
         const InstParams &ip = p.inst[my_inst];
-        const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
         const Vec4<R> W4 = p.W[i];
         const R Wi[4] = {W4.x, W4.y, W4.z, W4.w};
         R acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -359,17 +403,13 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
         // presence depends on round-off
         const R Lmin = R(1.7724538509055160273e-9) * Rad;
         for (int32_t s = lo; s < hi; s++) {
-            const int32_t es = p.slot_edge[s];
-            const int32_t e = es >> 1;
-            const R L = p.eL[e];
-            const Vec4<R> pm = p.ePM[e];
+            const R L = sl.L(s);
             // Eq. 1: g_i A_i = sum_j phi_j P_ij + phi_i sum_j M_ij
-            // the right cell of an edge takes -M, -P (sign flips on the integer pipe)
-            const unsigned long long ms = (es & 1) ? 0x8000000000000000ull : 0ull;
-            const R Ax = flip((es & 1) ? pm.z : pm.x, ms), Ay = flip((es & 1) ? pm.w : pm.y, ms);
-            Bx += flip((es & 1) ? pm.x : pm.z, ms);
-            By += flip((es & 1) ? pm.y : pm.w, ms);
-            const Vec4<R> Wv = load_W(p, p.slot_nb[s]);
+            R Ax, Ay, bx, by;
+            sl.weights(s, Ax, Ay, bx, by);
+            Bx += bx;
+            By += by;
+            const Vec4<R> Wv = sl.W(s);
             const R Wj[4] = {Wv.x, Wv.y, Wv.z, Wv.w};
 #pragma unroll
             for (int v = 0; v < 4; v++) {
@@ -379,13 +419,7 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             if (nonneg_less(Lmin, L)) {
 #pragma unroll
                 for (int v = 0; v < 4; v++) ext[v].add(Wj[v]);
-                double pj64;
-                if (sizeof(R) == sizeof(double)) {
-                    pj64 = (double)Wj[3];
-                } else {
-                    int32_t xf;
-                    pj64 = p.p64[src_of(p, p.slot_nb[s], xf)];
-                }
+                const double pj64 = sl.p64(s, Wj[3]);
                 const bool jl = nonneg_less(pj64, pi64);
                 const double pmin = jl ? pj64 : pi64, pmax = jl ? pi64 : pj64;
                 if (nonneg_less(pmin, dp * pmax)) shock = true;
@@ -426,11 +460,10 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
 #pragma unroll
             for (int v = 0; v < 4; v++) dex[v].init(R(0));
             for (int32_t s = lo; s < hi; s++) {
-                int32_t es = p.slot_edge[s];
-                int32_t e = es >> 1;
-                if (!nonneg_less(Lmin, p.eL[e])) continue;
-                R offx = ((es & 1) ? p.emrx[e] : p.emlx[e]) - ox;
-                R offy = ((es & 1) ? p.emry[e] : p.emly[e]) - oy;
+                if (!nonneg_less(Lmin, sl.L(s))) continue;
+                R mx, my;
+                sl.midpoint(s, mx, my);
+                const R offx = mx - ox, offy = my - oy;
 #pragma unroll
                 for (int v = 0; v < 4; v++) dex[v].add(g[2 * v] * offx + g[2 * v + 1] * offy);
             }
@@ -455,12 +488,11 @@ template <class R> __device__ __forceinline__ double stage_cell_gradient(const S
             R bn[4] = {0, 0, 0, 0}, bd[4] = {0, 0, 0, 0};  // smallest |N|/|D| so far (bd == 0: none)
             bool zero[4] = {false, false, false, false};
             for (int32_t s = lo; s < hi; s++) {
-                int32_t es = p.slot_edge[s];
-                int32_t e = es >> 1;
-                if (!nonneg_less(Lmin, p.eL[e])) continue;
-                R offx = ((es & 1) ? p.emrx[e] : p.emlx[e]) - ox;
-                R offy = ((es & 1) ? p.emry[e] : p.emly[e]) - oy;
-                const Vec4<R> Wv = load_W(p, p.slot_nb[s]);
+                if (!nonneg_less(Lmin, sl.L(s))) continue;
+                R mx, my;
+                sl.midpoint(s, mx, my);
+                const R offx = mx - ox, offy = my - oy;
+                const Vec4<R> Wv = sl.W(s);
                 const R Wj[4] = {Wv.x, Wv.y, Wv.z, Wv.w};
 #pragma unroll
                 for (int v = 0; v < 4; v++) {
@@ -536,7 +568,10 @@ template <class R> __global__ void __launch_bounds__(128, 6) k_cell_gradient(Swe
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     double dt_cell = DBL_MAX;
     int32_t my_inst = 0;
-    if (k < p.n) dt_cell = stage_cell_gradient(p, sizeof(R) == sizeof(double) ? cell_at(p, k) : k, my_inst);
+    if (k < p.n) {
+        const int32_t i = sizeof(R) == sizeof(double) ? cell_at(p, k) : k;
+        dt_cell = stage_cell_gradient(p, i, p.cell_ptr[i], p.cell_ptr[i + 1], GlobalSlots<R>{p}, my_inst);
+    }
     warp_min_to(dt_cell, my_inst, p.dtmin_bits);
 }
 
@@ -625,6 +660,9 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
     const int32_t l = p.edge_l[e];
     const int32_t li = inst_of(p, l);
     // edge states advance half a step in time only in the extrapolated scheme
+    // (the hardware converts FP64 -> R in this stage: the integer-pipe
+    // conversions' extra registers cost it more than the FP64 issue slots
+    // they save)
     const R hdt = p.inst[li].phase == 0 ? R(0.5) * (R)step_dt(p, li) : R(0);
     int32_t xf;
     const int32_t k = src_of(p, p.edge_r[e], xf);
@@ -829,7 +867,10 @@ __global__ void __launch_bounds__(512) k_sweep_persistent(SweepParams<R> p, cons
         const int32_t k = base + threadIdx.x;
         double v = DBL_MAX;
         int32_t inst = 0;
-        if (k < p.n) v = stage_cell_gradient(p, cell_at(p, k), inst);
+        if (k < p.n) {
+            const int32_t i = cell_at(p, k);
+            v = stage_cell_gradient(p, i, p.cell_ptr[i], p.cell_ptr[i + 1], GlobalSlots<R>{p}, inst);
+        }
         warp_min_to(v, inst, p.dtmin_bits);
     }
     if (!grid_sync(gs, nb, lim)) return;

@@ -3,15 +3,23 @@
 // simulations of a batch, run on all host cores.  parallel_for hands out
 // task indices dynamically (an atomic counter), so tasks of very different
 // sizes balance.  A build issues a dozen short parallel passes, so the
-// workers poll for the next batch of tasks for a short while before they
-// sleep, and the caller polls for their completion: waking sleeping
-// threads through a condition variable costs tens of microseconds a pass.
+// workers poll for new tasks for a short while before they sleep, and the
+// caller polls for the completion of its own tasks: waking sleeping threads
+// through a condition variable costs tens of microseconds a pass.
+//
+// Several threads may call parallel_for at once (the server's lanes share
+// one pool): each call is a group of tasks, the workers take tasks from the
+// groups in their order of arrival, a group's caller works only on its own
+// group, and a call returns when its group is done.  So a long task of one
+// caller (a whole simulation tessellated on one thread) holds one worker,
+// not the pool, while another caller's tiles run on the rest.
 #pragma once
 
 #include <atomic>
 #include <condition_variable>
 #include <cstdint>
 #include <functional>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -31,7 +39,7 @@ public:
         {
             std::lock_guard<std::mutex> lk(mu_);
             stop_.store(true, std::memory_order_relaxed);
-            gen_.fetch_add(1, std::memory_order_release);
+            posted_.fetch_add(1, std::memory_order_release);
         }
         cv_.notify_all();
         for (auto &w : workers_) w.join();
@@ -40,9 +48,7 @@ public:
     int size() const { return (int)workers_.size() + 1; }
 
     // Run fn(i) for i in [0, n) on the pool and the calling thread; returns
-    // when every task has finished.  Every worker takes part in every call
-    // (it may find no task left), and the next call starts only after all
-    // of them have left this one.
+    // when every task of this call has finished.
     void parallel_for(int64_t n, const std::function<void(int64_t)> &fn)
     {
         if (n <= 0) return;
@@ -50,58 +56,85 @@ public:
             for (int64_t i = 0; i < n; i++) fn(i);
             return;
         }
+        auto g = std::make_shared<Group>();
+        g->fn = &fn;
+        g->n = n;
         {
             std::lock_guard<std::mutex> lk(mu_);
-            fn_ = &fn;
-            n_ = n;
-            next_.store(0, std::memory_order_relaxed);
-            active_.store((int)workers_.size(), std::memory_order_relaxed);
-            gen_.fetch_add(1, std::memory_order_release);
+            groups_.push_back(g);
+            posted_.fetch_add(1, std::memory_order_release);
         }
         cv_.notify_all();
-        run_tasks();
-        while (active_.load(std::memory_order_acquire) != 0) std::this_thread::yield();
-        fn_ = nullptr;
+        run_group(*g);
+        // the other tasks of the group may still run on workers
+        while (g->done.load(std::memory_order_acquire) != n) std::this_thread::yield();
+        std::lock_guard<std::mutex> lk(mu_);
+        for (size_t k = 0; k < groups_.size(); k++)
+            if (groups_[k] == g) {
+                groups_.erase(groups_.begin() + k);
+                break;
+            }
     }
 
 private:
-    // polls of the generation before a worker sleeps (tens of microseconds)
+    struct Group {
+        const std::function<void(int64_t)> *fn = nullptr;
+        int64_t n = 0;
+        std::atomic<int64_t> next{0}, done{0};
+    };
+
+    // polls for new tasks before a worker sleeps (tens of microseconds)
     static constexpr int kSpin = 1 << 14;
 
-    void run_tasks()
+    static bool run_one(Group &g)
     {
-        for (;;) {
-            int64_t i = next_.fetch_add(1);
-            if (i >= n_) break;
-            (*fn_)(i);
+        const int64_t i = g.next.fetch_add(1, std::memory_order_relaxed);
+        if (i >= g.n) return false;
+        (*g.fn)(i);
+        g.done.fetch_add(1, std::memory_order_acq_rel);
+        return true;
+    }
+
+    static void run_group(Group &g)
+    {
+        while (run_one(g)) {
         }
+    }
+
+    // the oldest group with a task left, or null
+    std::shared_ptr<Group> pick()
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        for (auto &g : groups_)
+            if (g->next.load(std::memory_order_relaxed) < g->n) return g;
+        return nullptr;
     }
 
     void loop()
     {
         uint64_t seen = 0;
         for (;;) {
+            if (stop_.load(std::memory_order_relaxed)) return;
+            std::shared_ptr<Group> g = pick();
+            if (g) {
+                run_one(*g);
+                continue;
+            }
             bool woke = false;
-            for (int i = 0; i < kSpin && !woke; i++) woke = gen_.load(std::memory_order_acquire) != seen;
+            for (int i = 0; i < kSpin && !woke; i++) woke = posted_.load(std::memory_order_acquire) != seen;
             if (!woke) {
                 std::unique_lock<std::mutex> lk(mu_);
-                cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != seen; });
+                cv_.wait(lk, [&] { return posted_.load(std::memory_order_acquire) != seen; });
             }
-            seen = gen_.load(std::memory_order_acquire);
-            if (stop_.load(std::memory_order_relaxed)) return;
-            run_tasks();
-            active_.fetch_sub(1, std::memory_order_acq_rel);
+            seen = posted_.load(std::memory_order_acquire);
         }
     }
 
     std::vector<std::thread> workers_;
-    std::mutex mu_;
+    std::mutex mu_;  // the list of groups; the sleep of idle workers
     std::condition_variable cv_;
-    const std::function<void(int64_t)> *fn_ = nullptr;
-    int64_t n_ = 0;
-    std::atomic<int64_t> next_{0};
-    std::atomic<int> active_{0};
-    std::atomic<uint64_t> gen_{0};
+    std::vector<std::shared_ptr<Group>> groups_;
+    std::atomic<uint64_t> posted_{0};  // bumped when a group is posted (and at shutdown)
     std::atomic<bool> stop_{false};
 };
 

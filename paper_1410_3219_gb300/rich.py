@@ -35,7 +35,8 @@ EXPORTS = ["rich_default_config", "rich_init_mesh", "rich_step", "rich_get_state
            "rich_batch_launch_info", "rich_server_create", "rich_server_submit", "rich_server_tick",
            "rich_server_query", "rich_server_fetch", "rich_server_batch", "rich_server_destroy",
            "rich_init_conserved", "rich_get_order", "rich_time", "rich_mesh_update_check",
-           "rich_probe_pipe_peaks", "rich_batch_inject_barrier_timeout"]
+           "rich_probe_pipe_peaks", "rich_batch_inject_barrier_timeout", "rich_server_start",
+           "rich_server_stats", "rich_edge_list_check", "rich_tess_phases"]
 
 REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
@@ -144,6 +145,10 @@ def _lib():
         L.rich_time.restype = d
         L.rich_probe_pipe_peaks.argtypes = [_D, _D]
         L.rich_batch_inject_barrier_timeout.argtypes = [P, I32, C.POINTER(I64)]
+        L.rich_server_start.argtypes = [P, I32, I64, I64]
+        L.rich_tess_phases.argtypes = [P, _D]
+        L.rich_edge_list_check.argtypes = [C.POINTER(rich_config), I64, _D, _D, C.POINTER(I64), C.POINTER(I64)]
+        L.rich_server_stats.argtypes = [P, C.POINTER(I64)] + [_D] * 4
         _handle = L
     return _handle
 
@@ -285,6 +290,24 @@ def rich_probe_pipe_peaks():
     a, b = C.c_double(), C.c_double()
     _check(_lib().rich_probe_pipe_peaks(C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def rich_tess_phases(h):
+    """Wall time (ms) of the phases of the last host tessellation: ghosts and
+    grid, tiles, assembly, edges and order."""
+    ms = np.zeros(4)
+    _check(_lib().rich_tess_phases(h, _p(ms)))
+    return dict(zip(("ghosts_grid", "tiles", "assembly", "edges_order"), ms.tolist()))
+
+
+def rich_edge_list_check(cfg, x, y):
+    """(edges, mismatched entries) of the device edge-list builder against
+    the host's on the same rings."""
+    c = cfg if isinstance(cfg, rich_config) else rich_config.from_dict(cfg)
+    x, y = _f64(x), _f64(y)
+    e, m = C.c_int64(), C.c_int64()
+    _check(_lib().rich_edge_list_check(C.byref(c), len(x), _p(x), _p(y), C.byref(e), C.byref(m)))
+    return e.value, m.value
 
 
 def rich_delaunay_host(x, y):
@@ -484,6 +507,17 @@ class Server:
 
     def launch_info(self):
         return rich_batch_launch_info(_lib().rich_server_batch(self.h))
+
+    def start(self, lanes=2, split_cells=65536, top_lane_cells=0):
+        """Asynchronous mode: lane threads step the requests (see rich.h)."""
+        _check(_lib().rich_server_start(self.h, lanes, split_cells, top_lane_cells))
+
+    def stats(self):
+        st = C.c_int64()
+        v = [C.c_double() for _ in range(4)]
+        _check(_lib().rich_server_stats(self.h, C.byref(st), *[C.byref(x) for x in v]))
+        return {"steps": st.value, "sweep_ms": v[0].value, "tess_ms": v[1].value, "other_ms": v[2].value,
+                "wall_ms": v[3].value}
 
     def close(self):
         if self.h:

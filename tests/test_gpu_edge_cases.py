@@ -87,3 +87,25 @@ def test_last_step_lands_on_t_end(R, oracle):
     assert info["t"] == t_end and R.rich_time(gpu.h) == t_end
     compare_conserved(gpu, ref, wl["cfg"])
     gpu.close()
+
+
+@pytest.mark.parametrize("name", ["sod_reflective", "kh_periodic", "random_reflective", "tiny_periodic",
+                                  "lattice_periodic"])
+def test_device_edge_list_equals_host_list(R, name):
+    """The edge list the sweep uses is built on the device from the rings;
+    it must equal, entry by entry, the list the host builder makes for the
+    same mesh: a reflective box, a periodic box, random points, a periodic
+    box so small that cells neighbour their own images, and a co-circular
+    lattice."""
+    if name == "sod_reflective":
+        wl = W.sod(n_side=40, seed=31)
+    elif name == "kh_periodic":
+        wl = W.kelvin_helmholtz(n_side=48, seed=32)
+    elif name == "random_reflective":
+        wl = W.random_mixed(n=3000, seed=33)
+    elif name == "tiny_periodic":
+        wl = W.uniform(n_side=2, jitter=0.2, seed=34)
+    else:
+        wl = W.uniform(n_side=12, jitter=0.0, seed=35)
+    edges, bad = R.rich_edge_list_check(wl["cfg"], wl["x"], wl["y"])
+    assert edges > 0 and bad == 0, (name, edges, bad)

@@ -156,3 +156,55 @@ def test_served_mix_matches_the_oracle(R, oracle):
             ref.step()
         compare_conserved(Fetched(srv.fetch(rid)), ref, wl["cfg"])
     srv.close()
+
+
+def wait_all(srv, ids, limit_s=120.0):
+    import time
+    t0 = time.time()
+    while not all(srv.query(r)["state"] in ("done", "failed") for r in ids):
+        assert time.time() - t0 < limit_s, [srv.query(r) for r in ids]
+        time.sleep(0.005)
+
+
+def test_lanes_results_equal_solo_runs(R):
+    """Asynchronous lanes: requests of both size classes, submitted while
+    others run, end bit for bit as their solo runs, within the budget."""
+    import time
+    reqs = requests() + [(W.kelvin_helmholtz(n_side=48, seed=150), 4), (W.sedov(n=3000, seed=151), 3)]
+    srv = R.Server(max_cells=6000)
+    # the KH and Sedov requests go to lane 1, which holds at most 3000 cells at once
+    srv.start(lanes=2, split_cells=2000, top_lane_cells=3000)
+    ids = []
+    for wl, steps in reqs:
+        ids.append(srv.submit(wl, max_steps=steps))
+        time.sleep(0.002)
+    wait_all(srv, ids)
+    for (wl, steps), rid in zip(reqs, ids):
+        q = srv.query(rid)
+        assert q["state"] == "done" and q["steps"] == steps, (wl["name"], q)
+        got = srv.fetch(rid)
+        ref = solo(R, wl, steps)
+        for f in ref:
+            assert np.array_equal(got[f], ref[f]), (wl["name"], f)
+    st = srv.stats()
+    assert st["steps"] > 0 and st["sweep_ms"] > 0 and st["tess_ms"] > 0
+    with pytest.raises(R.RichError):
+        srv.tick()  # the lanes own the stepping
+    srv.close()
+
+
+def test_lanes_small_requests_do_not_wait_for_large_ones(R):
+    """A large request submitted first does not hold back small ones in the
+    other lane: they finish while it is still running."""
+    srv = R.Server(max_cells=1 << 20)
+    srv.start(lanes=2, split_cells=20000)
+    big = srv.submit(W.kelvin_helmholtz(n_side=256, seed=160), max_steps=40)
+    small = [srv.submit(W.sod(n_side=16, seed=161 + k), max_steps=3) for k in range(4)]
+    wait_all(srv, small)
+    assert srv.query(big)["state"] == "running", srv.query(big)
+    wait_all(srv, [big])
+    lat_small = max(srv.query(r)["latency_ms"] for r in small)
+    assert lat_small < srv.query(big)["latency_ms"]
+    for r in small + [big]:
+        srv.fetch(r)
+    srv.close()
