@@ -41,7 +41,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 HBM_PEAK_GBS_FALLBACK = 6800.0
 COMPULSORY_BYTES_PER_CELL = 124
 # kernels launched by one sweep (the time-step minimum's reset is a memset)
-NUM_KERNELS = 6
+NUM_KERNELS = 5
 
 # Algorithmic floating-point operations of each kernel, counted from the
 # formulas as the kernels evaluate them: add, subtract, multiply = 1, fused
@@ -92,8 +92,10 @@ def ncu_summary(workload_name):
         lines = open(path).read().splitlines()
     except OSError:
         return {}, None
+    import re
     want = kernel_source_hash()
-    got = next((ln.split(":", 1)[1].strip().strip("`") for ln in lines if ln.startswith("kernel-source-hash:")), None)
+    got = next((re.search(r"`([0-9a-f]+)`", ln) for ln in lines if ln.startswith("kernel-source-hash:")), None)
+    got = got.group(1) if got else None
     if got != want:
         return {}, path
     out = {}
@@ -102,7 +104,7 @@ def ncu_summary(workload_name):
         if len(f) >= 5 and f[0] in ("fp64", "split"):
             try:
                 out.setdefault(f[0], {})[f[1]] = {"dram_bytes": float(f[2]), "fp64_pipe": float(f[3]),
-                                                  "duration_us": float(f[4])}
+                                                  "duration_us": float(f[4]), "fp64_warp_instr": float(f[5])}
             except ValueError:
                 continue
     return out, path
@@ -235,6 +237,10 @@ def roofline_of(prec, kern_means, units, sweep_ms, workload_name, probe=None):
     traffic = rec[dom]["dram_bytes"] if dom in rec else None
     pipe_active = rec[dom]["fp64_pipe"] if dom in rec else None
     sweep_dram = sum(v["dram_bytes"] for v in rec.values()) if len(rec) == len(FLOPS[prec]) else None
+    # the FP64 issue bound: GB300 issues one FP64 warp-instruction per 16
+    # clocks per SM; the instructions a sweep issues (ncu) at that rate
+    sweep_fp64_instr = sum(v["fp64_warp_instr"] for v in rec.values()) if len(rec) == len(FLOPS[prec]) else None
+    issue_floor_ms = (sweep_fp64_instr * 16 / 152 / 2.07e9 * 1e3) if sweep_fp64_instr else None
     for k, v in rec.items():
         if k in per_kernel:
             per_kernel[k]["dram_bytes_ncu"] = v["dram_bytes"]
@@ -254,6 +260,11 @@ def roofline_of(prec, kern_means, units, sweep_ms, workload_name, probe=None):
            "sweep_fp64_tflops": tot["fp64"] / (sweep_ms / 1e3) / 1e12,
            "sweep_fp32_tflops": tot["fp32"] / (sweep_ms / 1e3) / 1e12,
            "sweep_dram_bytes_per_step_ncu": sweep_dram,
+           "sweep_fp64_warp_instructions_ncu": sweep_fp64_instr,
+           "fp64_issue_floor_ms": issue_floor_ms,
+           "fp64_issue_frac": (issue_floor_ms / sweep_ms) if issue_floor_ms else None,
+           "fp64_issue_note": "the sweep's FP64 warp-instructions (ncu) at one per 16 clocks per SM, 152 SMs, "
+                              "2.07 GHz, over the measured sweep time",
            "hbm_frac_compulsory": cells_per_s * COMPULSORY_BYTES_PER_CELL / (hbm * 1e9),
            "hbm_frac_ncu": (sweep_dram / (sweep_ms / 1e3) / (hbm * 1e9)) if sweep_dram else None,
            "hbm_peak_gbs": hbm, "hbm_peak_source": src,
@@ -536,7 +547,7 @@ def run_batched(rich, precision, n_inst, steps, seed=4):
                     "wall_ms_per_step": float(np.mean(wall))},
             "launch": {"persistent": li["persistent"], "block": li["block"], "grid": li["grid"],
                        "graph_replay": li["graph"]},
-            "gpu_launches_per_step": 1 if li["persistent"] else 6}
+            "gpu_launches_per_step": 1 if li["persistent"] else NUM_KERNELS}
 
 
 def run_serving(rich, precision, n_req, steps_per_req, n_min, n_max, load, seed=5, lanes=2, split=65536,

@@ -88,11 +88,13 @@ public:
     // afresh); on success the triangulation is the unique (tie-broken)
     // Delaunay one of the new positions.  make_delaunay flips edges until
     // every edge is locally Delaunay (Lawson), which from any triangulation
-    // of the same points ends at that one.  insert_point adds a point after
+    // of the same points ends at that one; given `seed`, it starts from the
+    // edges of those triangles only (valid when every other edge is locally
+    // Delaunay already).  insert_point adds a point after
     // the corners (returns the new vertex, -2 for a point that coincides
     // with one, -3 if location fails).
     bool move_all(const std::vector<double> &nx, const std::vector<double> &ny, int32_t max_back);
-    void make_delaunay();
+    void make_delaunay(const std::vector<int32_t> *seed = nullptr);
     int32_t insert_point(double x, double y);
     // vertices taken out and inserted again by move_all, over the object's life
     int64_t reinserted = 0;
@@ -116,6 +118,7 @@ private:
     std::vector<int64_t> edges_;
     std::vector<int32_t> free_;
     std::vector<int32_t> touched_;  // triangles remove_vertex rewrote
+    std::vector<int32_t> rewritten_;  // all of them, over one move_all
     int32_t corner_ = 0;
     int32_t hint_ = 0;
     uint32_t rng_ = 12345u;
