@@ -912,22 +912,27 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delauna
     // whole array); in the bucket of v, triangle (v, a, b) is followed by the
     // one whose a is this b.
     for (int32_t v = 0; v < nl; v++) cnt[v + 1] += cnt[v];
-    std::vector<int32_t> ba(cnt[nl]), bb(cnt[nl]), bt(cnt[nl]), fillp(cnt.begin(), cnt.end() - 1);
+    // one entry {a, b, t} per (core vertex, triangle): a single scattered
+    // write per entry
+    struct Entry {
+        int32_t a, b, t;
+    };
+    std::vector<Entry> be(cnt[nl]);
+    std::vector<int32_t> fillp(cnt.begin(), cnt.end() - 1);
     for (size_t t = 0; t < T.size(); t++) {
         if (tnum[t] < 0) continue;
         const int32_t *tv = T[t].v;
         for (int k = 0; k < 3; k++) {
             if (!core_real(tv[k])) continue;
-            const int32_t q = fillp[tv[k]]++;
-            ba[q] = tv[(k + 1) % 3];
-            bb[q] = tv[(k + 2) % 3];
-            bt[q] = tnum[t];
+            be[fillp[tv[k]]++] = Entry{tv[(k + 1) % 3], tv[(k + 2) % 3], tnum[t]};
         }
     }
-    r.cells.reserve(ncore);
-    r.deg.reserve(ncore);
-    r.nb.reserve(cnt[nl]);
-    r.tri.reserve(cnt[nl]);
+    // the outputs, written in place (core vertices in local order)
+    r.cells.resize(ncore);
+    r.deg.resize(ncore);
+    r.nb.resize(cnt[nl]);
+    r.tri.resize(cnt[nl]);
+    int32_t oc = 0, os = 0;
     constexpr int32_t kMaxStar = 64;
     for (int32_t v = 0; v < nl; v++) {
         if (!core_real(v)) continue;
@@ -936,30 +941,30 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delauna
             r.rc = -3;
             return;
         }
-        const int32_t *A = &ba[lo], *B = &bb[lo], *TT = &bt[lo];
+        const Entry *E = &be[lo];
         // the triangle after each one around v (its a is this one's b),
         // found without branches; then start at the smallest neighbour id
         int32_t nxt[kMaxStar];
         for (int32_t i = 0; i < deg; i++) {
-            const int32_t want = B[i];
+            const int32_t want = E[i].b;
             int32_t f = -1;
-            for (int32_t j = 0; j < deg; j++) f = A[j] == want ? j : f;
+            for (int32_t j = 0; j < deg; j++) f = E[j].a == want ? j : f;
             nxt[i] = f;
         }
-        int32_t k = 0, kid = loc[A[0]];
+        int32_t k = 0, kid = loc[E[0].a];
         for (int32_t q = 1; q < deg; q++) {
-            const int32_t id = loc[A[q]];
+            const int32_t id = loc[E[q].a];
             if (id < kid) {
                 kid = id;
                 k = q;
             }
         }
         const int32_t start = k;
-        r.cells.push_back(loc[v]);
-        r.deg.push_back(deg);
+        r.cells[oc] = loc[v];
+        r.deg[oc++] = deg;
         for (int32_t j = 0; j < deg; j++) {
-            r.nb.push_back(loc[A[k]]);
-            r.tri.push_back(TT[k]);
+            r.nb[os] = loc[E[k].a];
+            r.tri[os++] = E[k].t;
             k = nxt[k];
             if (k < 0) {
                 r.rc = -3;  // the star is not closed

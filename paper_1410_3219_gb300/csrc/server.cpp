@@ -188,6 +188,9 @@ struct rich_server {
     void lane_loop(int k)
     {
         cudaSetDevice(device);
+        // the lanes of larger requests get the shared workers first: their
+        // steps are long and sequential, the small lane fills idle workers
+        rich::ThreadPool::set_priority(k);
         Lane &L = *lanes[k];
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {

@@ -9,10 +9,12 @@
 //
 // Several threads may call parallel_for at once (the server's lanes share
 // one pool): each call is a group of tasks, the workers take tasks from the
-// groups in their order of arrival, a group's caller works only on its own
-// group, and a call returns when its group is done.  So a long task of one
-// caller (a whole simulation tessellated on one thread) holds one worker,
-// not the pool, while another caller's tiles run on the rest.
+// group of the highest priority with tasks left (the calling thread's, set
+// by set_priority; the oldest first among equals), a group's caller works
+// only on its own group, and a call returns when its group is done.  So a
+// long task of one caller (a whole simulation tessellated on one thread)
+// holds one worker, not the pool, while another caller's tiles run on the
+// rest.
 #pragma once
 
 #include <atomic>
@@ -47,6 +49,10 @@ public:
 
     int size() const { return (int)workers_.size() + 1; }
 
+    // Priority of the groups the calling thread posts from now on (0 by
+    // default; higher first).
+    static void set_priority(int p) { caller_priority() = p; }
+
     // Run fn(i) for i in [0, n) on the pool and the calling thread; returns
     // when every task of this call has finished.
     void parallel_for(int64_t n, const std::function<void(int64_t)> &fn)
@@ -59,6 +65,7 @@ public:
         auto g = std::make_shared<Group>();
         g->fn = &fn;
         g->n = n;
+        g->priority = caller_priority();
         {
             std::lock_guard<std::mutex> lk(mu_);
             groups_.push_back(g);
@@ -80,8 +87,15 @@ private:
     struct Group {
         const std::function<void(int64_t)> *fn = nullptr;
         int64_t n = 0;
+        int priority = 0;
         std::atomic<int64_t> next{0}, done{0};
     };
+
+    static int &caller_priority()
+    {
+        thread_local int p = 0;
+        return p;
+    }
 
     // polls for new tasks before a worker sleeps (tens of microseconds)
     static constexpr int kSpin = 1 << 14;
@@ -101,13 +115,15 @@ private:
         }
     }
 
-    // the oldest group with a task left, or null
+    // the group of the highest priority with a task left (the oldest among
+    // equals), or null
     std::shared_ptr<Group> pick()
     {
         std::lock_guard<std::mutex> lk(mu_);
+        std::shared_ptr<Group> best;
         for (auto &g : groups_)
-            if (g->next.load(std::memory_order_relaxed) < g->n) return g;
-        return nullptr;
+            if (g->next.load(std::memory_order_relaxed) < g->n && (!best || g->priority > best->priority)) best = g;
+        return best;
     }
 
     void loop()

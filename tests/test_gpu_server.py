@@ -208,3 +208,30 @@ def test_lanes_small_requests_do_not_wait_for_large_ones(R):
     for r in small + [big]:
         srv.fetch(r)
     srv.close()
+
+
+def test_lanes_isolate_a_failing_request_and_admit_an_oversized_one(R):
+    """Lanes: a request whose simulation fails (the Sedov blast with 16,384
+    points empties a cell at step 21) ends failed with its last good state
+    while the others finish and equal their solo runs; a request larger
+    than the top lane's cell cap still runs, alone in its lane."""
+    srv = R.Server(max_cells=1 << 20)
+    srv.start(lanes=2, split_cells=4000, top_lane_cells=5000)
+    crash = W.sedov(n=16384, seed=2)  # lane 1, above the cap: admitted alone
+    others = [W.sod(n_side=16, seed=7), W.gresho(n_side=14, seed=8), W.kelvin_helmholtz(n_side=64, seed=9)]
+    rc = srv.submit(crash, max_steps=40)
+    ro = [srv.submit(wl, max_steps=12) for wl in others]
+    wait_all(srv, [rc] + ro)
+    q = srv.query(rc)
+    assert q["state"] == "failed" and q["error"] == R.RICH_ENEGATIVE and q["steps"] == 20, q
+    got = srv.fetch(rc)
+    ref = solo(R, crash, 20)
+    for f in ref:
+        assert np.array_equal(got[f], ref[f]), f
+    for rid, wl in zip(ro, others):
+        assert srv.query(rid)["state"] == "done"
+        got = srv.fetch(rid)
+        ref = solo(R, wl, 12)
+        for f in ref:
+            assert np.array_equal(got[f], ref[f]), (wl["name"], f)
+    srv.close()
