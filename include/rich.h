@@ -349,8 +349,8 @@ int rich_server_fetch(rich_server *s, int64_t req, int64_t n, double *x, double 
 /* Hand the server to lane threads (asynchronous mode; no counterpart in the
    paper): `lanes` (1-4) threads each step their own batch, with its own CUDA
    stream, in a loop for as long as it has admitted requests; the lanes share
-   the server's host threads, taking them in turn one parallel pass at a
-   time.  A request goes to lane k when its cell count is at
+   the server's host threads task by task, the lanes of larger requests
+   first.  A request goes to lane k when its cell count is at
    least split_cells * 8^(k-1) (lane 0 below split_cells), so small requests
    never wait on the host tessellation of large ones, and one lane's host
    tessellation overlaps another's device sweep.  Admission takes each

@@ -14,8 +14,8 @@
 //   ticks  the caller's thread admits and steps one batch (rich_server_tick);
 //   lanes  rich_server_start hands the work to lane threads, each stepping
 //          its own batch (own CUDA stream) in a loop; the lanes share one
-//          pool of host workers, taking it in turn one parallel pass at a
-//          time.  Requests go to a lane by size, so a small request's step
+//          pool of host workers task by task, the lanes of larger requests
+//          first.  Requests go to a lane by size, so a small request's step
 //          never waits for the whole host tessellation of a large one, and
 //          one lane's host work overlaps another lane's device sweep.
 //          Admission against the shared cell budget stays in arrival order
@@ -90,8 +90,8 @@ struct rich_server {
     std::condition_variable cv;
     std::map<int64_t, std::unique_ptr<Request>> reqs;
     double t_start = 0.0;
-    // lanes mode: one pool of host workers for every lane; the lanes take
-    // it in turn one parallel pass at a time, so a lane alone gets all of it
+    // lanes mode: one pool of host workers for every lane, shared task by
+    // task (larger lanes first), so a lane alone gets all of it
     std::unique_ptr<rich::ThreadPool> pool;
 
     ~rich_server()
