@@ -524,13 +524,14 @@ def run_batched(rich, precision, n_inst, steps, seed=4):
     cells = sum(len(wl["x"]) for wl in wls)
     for _ in range(8):
         b.step()
-    sweep_ms, tess_ms, wall = [], [], []
+    sweep_ms, tess_ms, copy_ms, wall = [], [], [], []
     for _ in range(steps):
         t0 = time.perf_counter()
         info = b.step()
         wall.append(1e3 * (time.perf_counter() - t0))
         sweep_ms.append(info["sweep_ms"])
         tess_ms.append(info["tess_ms"])
+        copy_ms.append(info["copy_ms"])
     li = b.launch_info()
     # both launch shapes timed on the same batch, the autotuner's choice first
     shapes = {}
@@ -543,6 +544,7 @@ def run_batched(rich, precision, n_inst, steps, seed=4):
             "shape_ms_per_step": shapes,
             "ms_per_step": float(np.mean(sweep_ms)), "p99_ms": float(np.percentile(sweep_ms, 99)),
             "host_tess_ms_per_step": float(np.mean(tess_ms)),
+            "host_other_ms_per_step": float(np.mean(copy_ms)),
             "e2e": {"value": cells * steps / (sum(wall) / 1e3), "unit": UNIT,
                     "wall_ms_per_step": float(np.mean(wall))},
             "launch": {"persistent": li["persistent"], "block": li["block"], "grid": li["grid"],

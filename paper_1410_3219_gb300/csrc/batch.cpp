@@ -132,6 +132,7 @@ struct rich_batch {
     int32_t inject_spin = 0;
     // host staging of the packed mesh
     std::vector<double> h_x, h_y, h_gx, h_gy, h_W0;
+    std::vector<double> h_dlx, h_dly;  // the points downloaded at the start of a step
     std::vector<int32_t> h_gsrc, h_gxf, h_tri, h_cell_ptr, h_slot_nb, h_slot_tri, h_cell_inst;
     std::vector<int32_t> h_corder;
     std::vector<int32_t> h_src, h_eoff, h_gshift;
@@ -574,15 +575,22 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     const double t0 = now_ms();
     // 1. points of the running simulations back to the host
     if (b->n_packed > 0 && !b->packed.empty()) {
-        std::vector<double> hx(b->n_packed), hy(b->n_packed);
+        // (kept between steps: a fresh vector would zero 16 B per cell first)
+        std::vector<double> &hx = b->h_dlx, &hy = b->h_dly;
+        if (hx.size() < (size_t)b->n_packed) {
+            hx.resize(b->n_packed);
+            hy.resize(b->n_packed);
+        }
         CUDA_TRY(cudaMemcpyAsync(hx.data(), b->x[b->cur].p, b->n_packed * 8, cudaMemcpyDeviceToHost, b->stream));
         CUDA_TRY(cudaMemcpyAsync(hy.data(), b->y[b->cur].p, b->n_packed * 8, cudaMemcpyDeviceToHost, b->stream));
         CUDA_TRY(cudaStreamSynchronize(b->stream));
-        for (BatchSim *s : b->packed) {
-            if (s->state != RUNNING) continue;
+        // to each simulation's own arrays, on the pool
+        b->pool->parallel_for((int64_t)b->packed.size(), [&](int64_t k) {
+            BatchSim *s = b->packed[k];
+            if (s->state != RUNNING) return;
             std::memcpy(s->hx.data(), &hx[s->cell_off], sizeof(double) * s->n);
             std::memcpy(s->hy.data(), &hy[s->cell_off], sizeof(double) * s->n);
-        }
+        });
     }
     // the simulations of this step: running ones in their previous order, then new ones
     std::vector<BatchSim *> list;
