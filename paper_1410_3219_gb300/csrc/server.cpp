@@ -275,8 +275,11 @@ int rich_server_start(rich_server *s, int32_t lanes, int64_t split_cells, int64_
         return fail(RICH_EINVAL, "1-4 lanes, split >= 3, top_lane_cells >= 0");
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->async) return fail(RICH_ESTATE, "the server's lanes run already");
-    if (s->cells_admitted > 0 || rich_batch_cells(s->lanes[0]->batch) > 0)
-        return fail(RICH_ESTATE, "start the lanes before any request is admitted");
+    // (a request that ran in tick mode keeps its results in the tick batch,
+    // which the lanes replace)
+    bool ran = s->cells_admitted > 0 || rich_batch_cells(s->lanes[0]->batch) > 0;
+    for (auto &kv : s->reqs) ran = ran || kv.second->state != QUEUED;
+    if (ran) return fail(RICH_ESTATE, "start the lanes before any request is admitted");
     s->lanes.clear();
     if (!s->pool) s->pool = std::make_unique<rich::ThreadPool>(s->host_threads);
     for (int k = 0; k < lanes; k++) {

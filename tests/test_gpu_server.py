@@ -235,3 +235,24 @@ def test_lanes_isolate_a_failing_request_and_admit_an_oversized_one(R):
         for f in ref:
             assert np.array_equal(got[f], ref[f]), (wl["name"], f)
     srv.close()
+
+
+def test_lanes_start_only_before_any_admission(R):
+    """The lanes replace the tick-mode batch, so they start only while no
+    request has been admitted yet; queued requests move to their lanes."""
+    srv = R.Server(max_cells=4000)
+    a = srv.submit(W.sod(n_side=12, seed=21), max_steps=2)
+    srv.tick()
+    with pytest.raises(R.RichError) as e:
+        srv.start(lanes=2, split_cells=1000)
+    assert e.value.code == R.RICH_ESTATE
+    srv.close()
+    srv = R.Server(max_cells=4000)
+    b = srv.submit(W.sod(n_side=12, seed=22), max_steps=2)  # queued before the start
+    srv.start(lanes=2, split_cells=1000)
+    wait_all(srv, [b])
+    got = srv.fetch(b)
+    ref = solo(R, W.sod(n_side=12, seed=22), 2)
+    for f in ref:
+        assert np.array_equal(got[f], ref[f]), f
+    srv.close()
