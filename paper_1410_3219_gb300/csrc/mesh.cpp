@@ -387,14 +387,18 @@ int Delaunay::insert_at(int32_t v)
 bool Delaunay::move_all(const std::vector<double> &nx, const std::vector<double> &ny, int32_t max_back)
 {
     const int32_t NV = size();
-    const std::vector<double> ox(px_), oy(py_);
+    old_x_.assign(px_.begin(), px_.end());
+    old_y_.assign(py_.begin(), py_.end());
+    const std::vector<double> &ox = old_x_, &oy = old_y_;
     for (int32_t v = 0; v < NV; v++)
         if (!is_corner(v)) {
             px_[v] = nx[v];
             py_[v] = ny[v];
         }
-    std::vector<uint8_t> back(NV, 0);
-    std::vector<int32_t> S;
+    std::vector<uint8_t> &back = back_;
+    back.assign(NV, 0);
+    std::vector<int32_t> &S = back_list_;
+    S.clear();
     bool bad = true;
     for (int it = 0; it < 16 && bad; it++) {
         bad = false;
@@ -419,7 +423,8 @@ bool Delaunay::move_all(const std::vector<double> &nx, const std::vector<double>
     if (S.empty()) return true;
     // out with them (a triangle of each first, from one pass)
     rewritten_.clear();
-    std::vector<int32_t> where(NV, -1);
+    std::vector<int32_t> &where = where_;
+    where.assign(NV, -1);
     for (int32_t t = 0; t < (int32_t)tris.size(); t++)
         for (int k = 0; k < 3; k++)
             if (tris[t].v[k] >= 0 && back[tris[t].v[k]]) where[tris[t].v[k]] = t;
@@ -462,17 +467,33 @@ void Delaunay::make_delaunay(const std::vector<int32_t> *seed)
     } else {
         // one pass over the triangles tests each edge once where it lies in
         // memory; only the edges that fail start the flipping
-        for (int32_t t = 0; t < (int32_t)tris.size(); t++) {
-            const Tri &T = tris[t];
-            if (T.v[0] < 0) continue;
-            for (int k = 0; k < 3; k++) {
-                const int32_t u = T.nb[k];
-                if (u <= t) continue;
-                const Tri &U = tris[u];
-                int m = 0;
-                while (m < 3 && U.nb[m] != t) m++;
-                if (m == 3) continue;
-                const int32_t a = T.v[k], b = T.v[(k + 1) % 3], c = T.v[(k + 2) % 3], d = U.v[m];
+        // (candidates are gathered a block of triangles at a time without
+        // a branch on the neighbour's index, whose outcome is random, then
+        // tested)
+        const int32_t NT = (int32_t)tris.size();
+        constexpr int32_t kBlock = 256;
+        int32_t cand[3 * kBlock];
+        for (int32_t t0 = 0; t0 < NT; t0 += kBlock) {
+            const int32_t t1 = std::min(NT, t0 + kBlock);
+            int nc = 0;
+            for (int32_t t = t0; t < t1; t++) {
+                const Tri &T = tris[t];
+                const bool live = T.v[0] >= 0;
+                for (int k = 0; k < 3; k++) {
+                    cand[nc] = (t << 2) | k;
+                    nc += live & (T.nb[k] > t);
+                }
+            }
+            for (int q = 0; q < nc; q++) {
+                const int32_t t = cand[q] >> 2;
+                const int k = cand[q] & 3;
+                const Tri &T = tris[t];
+                // U shares the edge (b, c): its third vertex is the one that
+                // is neither (no search of U's links, whose outcome the
+                // branch predictor cannot learn either)
+                const Tri &U = tris[T.nb[k]];
+                const int32_t a = T.v[k], b = T.v[(k + 1) % 3], c = T.v[(k + 2) % 3];
+                const int32_t d = U.v[0] ^ U.v[1] ^ U.v[2] ^ b ^ c;
                 if (incircle_sos(px_[a], py_[a], px_[b], py_[b], px_[c], py_[c], px_[d], py_[d]) > 0)
                     edges_.push_back(((int64_t)t << 2) | k);
             }
@@ -486,11 +507,9 @@ void Delaunay::make_delaunay(const std::vector<int32_t> *seed)
         const Tri T = tris[t];
         const int32_t u = T.nb[k];
         if (u < 0) continue;
-        const Tri U = tris[u];
-        int m = 0;
-        while (m < 3 && U.nb[m] != t) m++;
-        if (m == 3) continue;
-        const int32_t a = T.v[k], b = T.v[(k + 1) % 3], c = T.v[(k + 2) % 3], d = U.v[m];
+        const Tri &U = tris[u];
+        const int32_t a = T.v[k], b = T.v[(k + 1) % 3], c = T.v[(k + 2) % 3];
+        const int32_t d = U.v[0] ^ U.v[1] ^ U.v[2] ^ b ^ c;
         if (incircle_sos(px_[a], py_[a], px_[b], py_[b], px_[c], py_[c], px_[d], py_[d]) <= 0) continue;
         // flip edge (b, c) of (a, b, c) and (d, c, b) into (a, d)
         flip(t, k);
@@ -697,16 +716,7 @@ void build_grid(int32_t np, const double *X, const double *Y, const double ext[4
 // Outcome of one tile: the rings of its real core cells, the triangles they
 // use (global point ids, smallest id first), whether the halo and the ghost
 // band were wide enough, and the halo its stars actually needed.
-struct SlabResult {
-    int rc = 0;
-    bool halo_ok = true, band_ok = true;
-    double needed = 0.0;
-    std::vector<int32_t> cells;  // real core cells
-    std::vector<int32_t> deg;    // ring length of each
-    std::vector<int32_t> nb;     // concatenated rings: neighbour point ids
-    std::vector<int32_t> tri;    // concatenated rings: slab-local triangle number
-    std::vector<int32_t> tris;   // 3 per slab-local triangle
-};
+using SlabResult = TileStars;
 
 // What every tile of one build shares.
 struct SlabCtx {
@@ -768,14 +778,16 @@ template <class F> void for_rect_points(const SlabCtx &c, const Rect &R, F &&f)
 // points of the rectangle that are not vertices yet.  Returns false when
 // the tile must be built afresh.
 bool update_slab(const SlabCtx &c, const Rect &R, Delaunay &dt, std::vector<int32_t> &loc,
-                 std::vector<int64_t> &keys, std::vector<uint32_t> &stamp)
+                 std::vector<int64_t> &keys, std::vector<uint32_t> &stamp, std::vector<double> &nx,
+                 std::vector<double> &ny)
 {
     const int32_t NL = dt.size();
     if ((int32_t)keys.size() != NL || NL < 3) return false;
     const MeshWork &w = *c.work;
     if ((int32_t)stamp.size() < c.np) stamp.resize(c.np, 0u);
     loc.resize(NL);
-    std::vector<double> nx(NL), ny(NL);
+    nx.resize(NL);
+    ny.resize(NL);
     int32_t stray = 0;
     for (int32_t v = 0; v < NL; v++) {
         const int64_t k = keys[v];
@@ -850,7 +862,8 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delauna
     const double *LX = dt.xs(), *LY = dt.ys();
     const std::vector<Tri> &T = dt.tris;
     // real points of the tile itself
-    std::vector<uint8_t> core(nl, 0);
+    std::vector<uint8_t> &core = r.core;
+    core.assign(nl, 0);
     int32_t ncore = 0;
     for (int32_t v = 0; v < nl; v++) {
         const double px = LX[v], py = LY[v];
@@ -861,9 +874,11 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delauna
     auto core_real = [&](int32_t v) { return core[v] != 0; };
     // the stars of the real core points: check, number, and find one
     // triangle incident to each such point
-    std::vector<int32_t> tnum(T.size(), -1);
+    std::vector<int32_t> &tnum = r.tnum;
+    tnum.assign(T.size(), -1);
     // star sizes of the core points, counted while their triangles are checked
-    std::vector<int32_t> cnt(nl + 1, 0);
+    std::vector<int32_t> &cnt = r.cnt;
+    cnt.assign(nl + 1, 0);
     int32_t nt = 0;
     for (size_t t = 0; t < T.size(); t++) {
         const int32_t *v = T[t].v;
@@ -914,11 +929,11 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delauna
     for (int32_t v = 0; v < nl; v++) cnt[v + 1] += cnt[v];
     // one entry {a, b, t} per (core vertex, triangle): a single scattered
     // write per entry
-    struct Entry {
-        int32_t a, b, t;
-    };
-    std::vector<Entry> be(cnt[nl]);
-    std::vector<int32_t> fillp(cnt.begin(), cnt.end() - 1);
+    using Entry = TileStars::Entry;
+    std::vector<Entry> &be = r.entries;
+    be.resize(cnt[nl]);
+    std::vector<int32_t> &fillp = r.fillp;
+    fillp.assign(cnt.begin(), cnt.end() - 1);
     for (size_t t = 0; t < T.size(); t++) {
         if (tnum[t] < 0) continue;
         const int32_t *tv = T[t].v;
@@ -942,28 +957,34 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delauna
             return;
         }
         const Entry *E = &be[lo];
-        // the triangle after each one around v (its a is this one's b),
-        // found without branches; then start at the smallest neighbour id
-        int32_t nxt[kMaxStar];
+        // the triangle after each one around v (its a is this one's b):
+        // the a's padded to a multiple of 8, and per triangle the sum of
+        // (j + 1) over the matches, which has no dependency from one j to
+        // the next (a valid star has exactly one match; none, or a sum out
+        // of range, gives -1 and fails the walk); then start at the
+        // smallest neighbour id
+        int32_t A[kMaxStar], G[kMaxStar], nxt[kMaxStar];
+        const int32_t dp = (deg + 7) & ~7;
+        for (int32_t j = 0; j < dp; j++) A[j] = j < deg ? E[j].a : -1;
         for (int32_t i = 0; i < deg; i++) {
             const int32_t want = E[i].b;
-            int32_t f = -1;
-            for (int32_t j = 0; j < deg; j++) f = E[j].a == want ? j : f;
-            nxt[i] = f;
+            int32_t f = 0;
+            for (int32_t j0 = 0; j0 < dp; j0 += 8)
+                for (int32_t j = j0; j < j0 + 8; j++) f += A[j] == want ? j + 1 : 0;
+            nxt[i] = f <= deg ? f - 1 : -1;
         }
-        int32_t k = 0, kid = loc[E[0].a];
-        for (int32_t q = 1; q < deg; q++) {
+        int32_t k = 0, kid = INT32_MAX;
+        for (int32_t q = 0; q < deg; q++) {
             const int32_t id = loc[E[q].a];
-            if (id < kid) {
-                kid = id;
-                k = q;
-            }
+            G[q] = id;
+            k = id < kid ? q : k;
+            kid = id < kid ? id : kid;
         }
         const int32_t start = k;
         r.cells[oc] = loc[v];
         r.deg[oc++] = deg;
         for (int32_t j = 0; j < deg; j++) {
-            r.nb[os] = loc[E[k].a];
+            r.nb[os] = G[k];
             r.tri[os++] = E[k].t;
             k = nxt[k];
             if (k < 0) {
@@ -986,16 +1007,16 @@ void build_slab(const SlabCtx &c, const Tile &tile, double H, bool update, Delau
                 std::vector<double> &LX, std::vector<double> &LY, std::vector<int64_t> &keys,
                 std::vector<uint32_t> &stamp, bool &updated, SlabResult &r)
 {
-    r = SlabResult();
+    r.reset();
     updated = false;
     const Rect R = tile_rect(c, tile, H);
-    if (update && update_slab(c, R, dt, loc, keys, stamp)) {
+    if (update && update_slab(c, R, dt, loc, keys, stamp, r.nx, r.ny)) {
         read_stars(c, tile, R, dt, loc, r);
         if (r.rc != kRedo) {
             updated = true;
             return;
         }
-        r = SlabResult();
+        r.reset();
     }
     // afresh: the points of the rectangle (bucket by bucket; the
     // triangulation does not depend on their order, and the rings and
@@ -1066,7 +1087,8 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     const bool reuse = work.kinetic && work.n_kept == n && (int)work.tiles.size() == K &&
                        (int)work.tile_halo.size() == K;
     work.n_kept = -1;  // valid again only once this build succeeds
-    std::vector<SlabResult> res(K);
+    if ((int)work.stars.size() < K) work.stars.resize(K);
+    std::vector<TileStars> &res = work.stars;
     std::vector<uint8_t> updated(K, 0);
     std::vector<double> &X = work.X, &Y = work.Y;
     for (;;) {

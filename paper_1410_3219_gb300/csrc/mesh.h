@@ -119,6 +119,11 @@ private:
     std::vector<int32_t> free_;
     std::vector<int32_t> touched_;  // triangles remove_vertex rewrote
     std::vector<int32_t> rewritten_;  // all of them, over one move_all
+    // move_all's scratch: old positions, the vertices put back, and a
+    // triangle of each
+    std::vector<double> old_x_, old_y_;
+    std::vector<uint8_t> back_;
+    std::vector<int32_t> back_list_, where_;
     int32_t corner_ = 0;
     int32_t hint_ = 0;
     uint32_t rng_ = 12345u;
@@ -131,11 +136,48 @@ struct Tile {
     bool fx, lx, fy, ly;
 };
 
+// One tile's part of a build: the stars of its real core points, and the
+// buffers the tile works in.  Kept per tile from build to build, so that a
+// build reuses their capacity instead of allocating (and page-faulting) the
+// same sizes again.
+struct TileStars {
+    int rc = 0;
+    bool halo_ok = true, band_ok = true;
+    double needed = 0.0;          // how far the stars' circumdisks reach past the tile
+    std::vector<int32_t> cells;   // real core cells
+    std::vector<int32_t> deg;     // ring length of each
+    std::vector<int32_t> nb;      // concatenated rings: neighbour point ids
+    std::vector<int32_t> tri;     // concatenated rings: tile-local triangle number
+    std::vector<int32_t> tris;    // 3 per tile-local triangle (point ids)
+    // scratch of the star read-off: per local vertex, per triangle, and one
+    // entry {a, b, t} per (core vertex, triangle (vertex, a, b))
+    struct Entry {
+        int32_t a, b, t;
+    };
+    std::vector<uint8_t> core;
+    std::vector<int32_t> tnum, cnt, fillp;
+    std::vector<Entry> entries;
+    // scratch of the in-place update: the local vertices' new positions
+    std::vector<double> nx, ny;
+    void reset()
+    {
+        rc = 0;
+        halo_ok = band_ok = true;
+        needed = 0.0;
+        cells.clear();
+        deg.clear();
+        nb.clear();
+        tri.clear();
+        tris.clear();
+    }
+};
+
 // Reusable buffers of build_host_mesh (one triangulator per tile), and what
 // the next build needs to update each tile's triangulation instead of
 // building it again.
 struct MeshWork {
     std::vector<Delaunay> dts;
+    std::vector<TileStars> stars;
     std::vector<std::vector<int32_t>> loc;
     std::vector<std::vector<double>> lx, ly;
     // the points bucketed on a uniform grid over their bounding box (ids in

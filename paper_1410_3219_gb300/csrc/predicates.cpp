@@ -1,10 +1,8 @@
 // Exact orientation / in-circle predicates (see predicates.h).
 //
-// Fast path: the determinant in plain double arithmetic with a forward error
-// bound proportional to its "permanent" (the same sum with absolute values).
-// The bounds used here are deliberately a few times looser than the tight
-// ones of Shewchuk (1997), which only sends more near-degenerate cases to the
-// exact path.
+// Fast path (inline, in the header): the determinant in plain double
+// arithmetic with a forward error bound proportional to its "permanent" (the
+// same sum with absolute values).
 //
 // Exact path: non-overlapping floating-point expansions.  TwoSum (Knuth) and
 // an FMA-based TwoProduct give exact sums and products of two doubles as
@@ -98,7 +96,9 @@ int sign_of(const Exp &e)
     return 0;
 }
 
-int orient_exact(double ax, double ay, double bx, double by, double cx, double cy)
+}  // namespace
+
+int orient2d_exact(double ax, double ay, double bx, double by, double cx, double cy)
 {
     Exp l = mul(diff(bx, ax), diff(cy, ay));
     Exp r = mul(diff(by, ay), diff(cx, ax));
@@ -120,8 +120,7 @@ int incircle_exact(double ax, double ay, double bx, double by, double cx, double
     return sign_of(det);
 }
 
-constexpr double kOrientBound = 1e-15;   // >= (3 + 16 eps) eps
-constexpr double kIncircleBound = 1e-14; // >= (10 + 96 eps) eps
+namespace {
 
 inline bool lex_less(double px, double py, double qx, double qy)
 {
@@ -130,37 +129,8 @@ inline bool lex_less(double px, double py, double qx, double qy)
 
 }  // namespace
 
-int orient2d(double ax, double ay, double bx, double by, double cx, double cy)
+int incircle_tiebreak(double ax, double ay, double bx, double by, double cx, double cy, double dx, double dy)
 {
-    double l = (bx - ax) * (cy - ay);
-    double r = (by - ay) * (cx - ax);
-    double det = l - r;
-    double bound = kOrientBound * (std::fabs(l) + std::fabs(r));
-    if (det > bound) return 1;
-    if (-det > bound) return -1;
-    return orient_exact(ax, ay, bx, by, cx, cy);
-}
-
-int incircle_exact_sign(double ax, double ay, double bx, double by, double cx, double cy, double dx, double dy)
-{
-    double adx = ax - dx, ady = ay - dy, bdx = bx - dx, bdy = by - dy, cdx = cx - dx, cdy = cy - dy;
-    double p1 = bdx * cdy, p2 = cdx * bdy, p3 = cdx * ady, p4 = adx * cdy, p5 = adx * bdy, p6 = bdx * ady;
-    double la = adx * adx + ady * ady, lb = bdx * bdx + bdy * bdy, lc = cdx * cdx + cdy * cdy;
-    double det = la * (p1 - p2) + lb * (p3 - p4) + lc * (p5 - p6);
-    double perm = la * (std::fabs(p1) + std::fabs(p2)) + lb * (std::fabs(p3) + std::fabs(p4)) +
-                  lc * (std::fabs(p5) + std::fabs(p6));
-    double bound = kIncircleBound * perm;
-    if (std::isfinite(det) && std::isfinite(bound)) {
-        if (det > bound) return 1;
-        if (-det > bound) return -1;
-    }
-    return incircle_exact(ax, ay, bx, by, cx, cy, dx, dy);
-}
-
-int incircle_sos(double ax, double ay, double bx, double by, double cx, double cy, double dx, double dy)
-{
-    int s = incircle_exact_sign(ax, ay, bx, by, cx, cy, dx, dy);
-    if (s != 0) return s;
     // First-order change of the lifting determinant when each height |p|^2
     // grows by d_p:  d_a*orient(b,c,d) - d_b*orient(a,c,d) + d_c*orient(a,b,d)
     // - d_d*orient(a,b,c).  The lexicographically smallest point dominates.
