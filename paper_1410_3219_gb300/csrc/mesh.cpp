@@ -172,6 +172,9 @@ void Delaunay::insert_inside(int32_t t, int32_t p)
     tris[t] = Tri{{p, b, c}, {na, t1, t2}};
     tris[t1] = Tri{{p, c, a}, {nbb, t2, t}};
     tris[t2] = Tri{{p, a, b}, {nc, t, t1}};
+    note(t);
+    note(t1);
+    note(t2);
     set_nb(nbb, t, t1);
     set_nb(nc, t, t2);
     stack_.push_back(t);
@@ -199,6 +202,10 @@ void Delaunay::insert_on_edge(int32_t t, int k, int32_t p)
     tris[B] = Tri{{p, a, b}, {t_ab, D, A}};
     tris[Cc] = Tri{{p, d, c}, {u_dc, A, D}};
     tris[D] = Tri{{p, b, d}, {u_bd, Cc, B}};
+    note(A);
+    note(B);
+    note(Cc);
+    note(D);
     set_nb(t_ab, t, B);
     set_nb(u_bd, u, D);
     stack_.push_back(A);
@@ -230,6 +237,8 @@ void Delaunay::legalize(int32_t p)
         int32_t u_bd = U.nb[(m + 1) % 3], u_dc = U.nb[(m + 2) % 3];
         tris[t] = Tri{{p, b, d}, {u_bd, u, T_pb}};
         tris[u] = Tri{{p, d, c}, {u_dc, T_cp, t}};
+        note(t);
+        note(u);
         set_nb(u_bd, u, t);
         set_nb(T_cp, t, u);
         stack_.push_back(t);
@@ -239,6 +248,8 @@ void Delaunay::legalize(int32_t p)
 
 int Delaunay::build(const double *x, const double *y, int32_t np)
 {
+    log_.clear();
+    log_all_ = true;
     tris.clear();
     stack_.clear();
     free_.clear();
@@ -289,6 +300,8 @@ void Delaunay::flip(int32_t t, int k)
     const int32_t u_bd = U.nb[(m + 1) % 3], u_dc = U.nb[(m + 2) % 3];
     tris[t] = Tri{{a, b, d}, {u_bd, u, t_ab}};
     tris[u] = Tri{{a, d, c}, {u_dc, t_ca, t}};
+    note(t);
+    note(u);
     set_nb(u_bd, u, t);
     set_nb(t_ca, t, u);
 }
@@ -342,6 +355,7 @@ bool Delaunay::remove_vertex(int32_t v, int32_t t)
                 o[i] = T.nb[j];  // across (l_i, l_i+1)
             }
             tris[st[0]] = Tri{{l0, l1, l2}, {o[1], o[2], o[0]}};
+            note(st[0]);
             touched_.push_back(st[0]);
             set_nb(o[1], st[1], st[0]);
             set_nb(o[2], st[2], st[0]);
@@ -852,7 +866,7 @@ bool update_slab(const SlabCtx &c, const Rect &R, Delaunay &dt, std::vector<int3
 // rectangle: every point of the whole set inside such a disk was then
 // triangulated too, and an empty circumdisk among them is empty in the
 // whole set.
-void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delaunay &dt,
+void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
                 const std::vector<int32_t> &loc, SlabResult &r)
 {
     const int32_t n = c.n, nl = dt.size();
@@ -872,13 +886,9 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delauna
         ncore += core[v];
     }
     auto core_real = [&](int32_t v) { return core[v] != 0; };
-    // the stars of the real core points: check, number, and find one
-    // triangle incident to each such point
+    // the stars of the real core points: check and number their triangles
     std::vector<int32_t> &tnum = r.tnum;
     tnum.assign(T.size(), -1);
-    // star sizes of the core points, counted while their triangles are checked
-    std::vector<int32_t> &cnt = r.cnt;
-    cnt.assign(nl + 1, 0);
     int32_t nt = 0;
     for (size_t t = 0; t < T.size(); t++) {
         const int32_t *v = T[t].v;
@@ -909,7 +919,6 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delauna
         if (!tile.fy) r.needed = std::max(r.needed, tile.y0 - (D.uy - D.R));
         if (!tile.ly) r.needed = std::max(r.needed, D.uy + D.R - tile.y1);
         tnum[t] = nt++;
-        for (int k = 0; k < 3; k++) cnt[v[k] + 1] += core[v[k]];
     }
     // triangles with global ids, rotated so that the smallest id comes first
     // (a shared triangle then gives the same circumcentre in every slab)
@@ -921,82 +930,135 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, const Delauna
         int32_t gg[3] = {g0, g1, g2};
         for (int k = 0; k < 3; k++) r.tris[3 * (size_t)tnum[t] + k] = gg[(rot + k) % 3];
     }
-    // rings, counter-clockwise, starting at the smallest neighbour id.  The
-    // triangles are bucketed by core vertex in one pass over the triangle
-    // array (walking each star through the neighbour links jumps across the
-    // whole array); in the bucket of v, triangle (v, a, b) is followed by the
-    // one whose a is this b.
-    for (int32_t v = 0; v < nl; v++) cnt[v + 1] += cnt[v];
-    // one entry {a, b, t} per (core vertex, triangle): a single scattered
-    // write per entry
-    using Entry = TileStars::Entry;
-    std::vector<Entry> &be = r.entries;
-    be.resize(cnt[nl]);
-    std::vector<int32_t> &fillp = r.fillp;
-    fillp.assign(cnt.begin(), cnt.end() - 1);
-    for (size_t t = 0; t < T.size(); t++) {
-        if (tnum[t] < 0) continue;
-        const int32_t *tv = T[t].v;
-        for (int k = 0; k < 3; k++) {
-            if (!core_real(tv[k])) continue;
-            be[fillp[tv[k]]++] = Entry{tv[(k + 1) % 3], tv[(k + 2) % 3], tnum[t]};
+    // rings, counter-clockwise, starting at the smallest neighbour id.  A
+    // vertex's local ring (its neighbours, each with the triangle slot after
+    // it) changes only where a triangle slot holding the vertex was written
+    // since the last read-off (the triangulation's log; every slot after a
+    // fresh build): those rings, and those of vertices with no ring from the
+    // last read-off, are walked through the neighbour links from a slot
+    // incident to the vertex; the others are copied.  The global ids and
+    // triangle numbers are applied to every ring afterwards (ghost ids and
+    // the numbering change from build to build).
+    const bool all = dt.log_all();
+    std::vector<uint8_t> &dirty = r.dirty;
+    std::vector<int32_t> &vt = r.vt;
+    if (all) {
+        dirty.assign(nl, 1);
+        vt.assign(nl, -1);
+        for (size_t t = 0; t < T.size(); t++)
+            if (T[t].v[0] >= 0)
+                for (int k = 0; k < 3; k++) vt[T[t].v[k]] = (int32_t)t;
+    } else {
+        dirty.assign(nl, 0);
+        vt.resize(nl, -1);
+        for (const int32_t t : dt.log()) {
+            if (t < 0 || t >= (int32_t)T.size() || T[t].v[0] < 0) continue;
+            for (int k = 0; k < 3; k++) {
+                dirty[T[t].v[k]] = 1;
+                vt[T[t].v[k]] = t;
+            }
         }
     }
-    // the outputs, written in place (core vertices in local order)
+    dt.clear_log();
+    const int32_t nprev = all ? 0 : (int32_t)r.ring_off.size();
+    std::vector<int32_t> &noff = r.next_off, &nlen = r.next_len;
+    std::vector<TileStars::Slot> &nring = r.next_ring;
+    noff.resize(nl);
+    nlen.resize(nl);
+    // the outputs (core vertices in local order), sized for a mean degree
+    // of 8 and grown if that is not enough (the mean is 6)
     r.cells.resize(ncore);
     r.deg.resize(ncore);
-    r.nb.resize(cnt[nl]);
-    r.tri.resize(cnt[nl]);
-    int32_t oc = 0, os = 0;
+    size_t cap = std::max<size_t>(r.nb.size(), 8 * (size_t)ncore + 64);
+    r.nb.resize(cap);
+    r.tri.resize(cap);
+    nring.resize(std::max(nring.size(), cap));
+    size_t os = 0, ns = 0;
+    int32_t oc = 0;
     constexpr int32_t kMaxStar = 64;
+    TileStars::Slot walked[kMaxStar];
     for (int32_t v = 0; v < nl; v++) {
+        noff[v] = -1;
+        nlen[v] = 0;
         if (!core_real(v)) continue;
-        const int32_t lo = cnt[v], deg = cnt[v + 1] - lo;
-        if (deg < 3 || deg > kMaxStar) {
+        const TileStars::Slot *ring;
+        int32_t deg;
+        if (!dirty[v] && v < nprev && r.ring_off[v] >= 0) {
+            ring = &r.ring[r.ring_off[v]];
+            deg = r.ring_len[v];
+        } else {
+            // walk: in slot t with v at position k, the neighbour after v is
+            // a = v[k+1]; the next slot counter-clockwise about v shares the
+            // edge (v, v[k+2]), the one opposite a
+            int32_t t = vt[v];
+            int k = t < 0 ? -1 : (T[t].v[0] == v ? 0 : (T[t].v[1] == v ? 1 : (T[t].v[2] == v ? 2 : -1)));
+            if (k < 0) {
+                r.rc = kRedo;  // no slot known to hold v
+                return;
+            }
+            const int32_t t0 = t;
+            deg = 0;
+            do {
+                if (deg == kMaxStar) {
+                    r.rc = -3;
+                    return;
+                }
+                const Tri &U = T[t];
+                walked[deg++] = TileStars::Slot{U.v[(k + 1) % 3], t};
+                const int32_t b = U.v[(k + 2) % 3];
+                t = U.nb[(k + 1) % 3];
+                if (t < 0) {
+                    r.rc = -3;  // the star is not closed
+                    return;
+                }
+                const Tri &V = T[t];
+                k = V.v[0] == v ? 0 : (V.v[1] == v ? 1 : (V.v[2] == v ? 2 : -1));
+                if (k < 0 || V.v[(k + 1) % 3] != b) {
+                    r.rc = -3;  // inconsistent links
+                    return;
+                }
+            } while (t != t0);
+            ring = walked;
+        }
+        if (deg < 3) {
             r.rc = -3;
             return;
         }
-        const Entry *E = &be[lo];
-        // the triangle after each one around v (its a is this one's b):
-        // the a's padded to a multiple of 8, and per triangle the sum of
-        // (j + 1) over the matches, which has no dependency from one j to
-        // the next (a valid star has exactly one match; none, or a sum out
-        // of range, gives -1 and fails the walk); then start at the
-        // smallest neighbour id
-        int32_t A[kMaxStar], G[kMaxStar], nxt[kMaxStar];
-        const int32_t dp = (deg + 7) & ~7;
-        for (int32_t j = 0; j < dp; j++) A[j] = j < deg ? E[j].a : -1;
-        for (int32_t i = 0; i < deg; i++) {
-            const int32_t want = E[i].b;
-            int32_t f = 0;
-            for (int32_t j0 = 0; j0 < dp; j0 += 8)
-                for (int32_t j = j0; j < j0 + 8; j++) f += A[j] == want ? j + 1 : 0;
-            nxt[i] = f <= deg ? f - 1 : -1;
+        if (os + deg > cap) {
+            cap = 2 * cap + kMaxStar;
+            r.nb.resize(cap);
+            r.tri.resize(cap);
+            nring.resize(cap);
         }
+        noff[v] = (int32_t)ns;
+        nlen[v] = deg;
+        std::copy(ring, ring + deg, nring.data() + ns);
+        ns += deg;
+        // start at the smallest neighbour id
+        int32_t G[kMaxStar];
         int32_t k = 0, kid = INT32_MAX;
         for (int32_t q = 0; q < deg; q++) {
-            const int32_t id = loc[E[q].a];
+            const int32_t id = loc[ring[q].nb];
             G[q] = id;
             k = id < kid ? q : k;
             kid = id < kid ? id : kid;
         }
-        const int32_t start = k;
         r.cells[oc] = loc[v];
         r.deg[oc++] = deg;
+        int32_t *onb = r.nb.data() + os, *otr = r.tri.data() + os;
         for (int32_t j = 0; j < deg; j++) {
-            r.nb[os] = G[k];
-            r.tri[os++] = E[k].t;
-            k = nxt[k];
-            if (k < 0) {
-                r.rc = -3;  // the star is not closed
-                return;
-            }
+            const int32_t q = k + j < deg ? k + j : k + j - deg;
+            onb[j] = G[q];
+            otr[j] = tnum[ring[q].t];
         }
-        if (k != start) {
-            r.rc = -3;  // the star is not one cycle
-            return;
-        }
+        os += deg;
     }
+    // (a ring's triangles all touch its core vertex, so all are numbered)
+    r.nb.resize(os);
+    r.tri.resize(os);
+    r.ring_off.swap(noff);
+    r.ring_len.swap(nlen);
+    r.ring.swap(nring);
 }
 
 // Triangulate the points of a tile plus a halo of width H (by updating the

@@ -78,6 +78,17 @@ public:
     const double *xs() const { return px_.data(); }
     const double *ys() const { return py_.data(); }
 
+    // Triangle slots written since the last clear_log() (log_all(): every
+    // slot, after a build): only the stars of their vertices can have
+    // changed.  Moving vertices (move_all without flips) writes none.
+    bool log_all() const { return log_all_; }
+    const std::vector<int32_t> &log() const { return log_; }
+    void clear_log()
+    {
+        log_.clear();
+        log_all_ = false;
+    }
+
     // Updating a built triangulation for moved points (the points keep their
     // vertex numbers).  move_all moves every vertex to (nx[v], ny[v]); where
     // that would turn triangles over it puts their vertices back until none
@@ -124,6 +135,12 @@ private:
     std::vector<double> old_x_, old_y_;
     std::vector<uint8_t> back_;
     std::vector<int32_t> back_list_, where_;
+    void note(int32_t t)
+    {
+        if (!log_all_) log_.push_back(t);
+    }
+    std::vector<int32_t> log_;
+    bool log_all_ = true;
     int32_t corner_ = 0;
     int32_t hint_ = 0;
     uint32_t rng_ = 12345u;
@@ -149,14 +166,19 @@ struct TileStars {
     std::vector<int32_t> nb;      // concatenated rings: neighbour point ids
     std::vector<int32_t> tri;     // concatenated rings: tile-local triangle number
     std::vector<int32_t> tris;    // 3 per tile-local triangle (point ids)
-    // scratch of the star read-off: per local vertex, per triangle, and one
-    // entry {a, b, t} per (core vertex, triangle (vertex, a, b))
-    struct Entry {
-        int32_t a, b, t;
+    // the local rings of the last read-off, by local vertex: neighbours
+    // (local ids) counter-clockwise from ring_off[v] (-1: none), ring_len[v]
+    // of them, each with the triangle slot after it; the next ones are
+    // written beside them and swapped in
+    struct Slot {
+        int32_t nb, t;
     };
-    std::vector<uint8_t> core;
-    std::vector<int32_t> tnum, cnt, fillp;
-    std::vector<Entry> entries;
+    std::vector<int32_t> ring_off, ring_len, next_off, next_len;
+    std::vector<Slot> ring, next_ring;
+    // scratch of the read-off: core flags, triangle numbers, rings to walk
+    // again, and a triangle slot holding each local vertex
+    std::vector<uint8_t> core, dirty;
+    std::vector<int32_t> tnum, vt;
     // scratch of the in-place update: the local vertices' new positions
     std::vector<double> nx, ny;
     void reset()
@@ -164,10 +186,10 @@ struct TileStars {
         rc = 0;
         halo_ok = band_ok = true;
         needed = 0.0;
+        // (nb and tri keep their size: they are read only through cells
+        // and deg, and a read-off sets them)
         cells.clear();
         deg.clear();
-        nb.clear();
-        tri.clear();
         tris.clear();
     }
 };
