@@ -593,7 +593,14 @@ static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const 
     // depends on a only and its y on b only, so each axis is tested once
     // (most points, away from the walls, have none).
     const bool per = box.boundary == 1;
+    // an image (mirrored or shifted) reaches the band only from a point
+    // within w of a wall: the points well inside, by a margin far above the
+    // images' round-off, are skipped before any image is formed
+    const double margin = 1e-9 * (std::fabs(box.x0) + std::fabs(box.x1) + std::fabs(box.y0) + std::fabs(box.y1) + w);
+    const double in_x0 = box.x0 + w + margin, in_x1 = box.x1 - w - margin;
+    const double in_y0 = box.y0 + w + margin, in_y1 = box.y1 - w - margin;
     auto visit = [&](int32_t i, auto &&emit) {
+        if (x[i] > in_x0 && x[i] < in_x1 && y[i] > in_y0 && y[i] < in_y1) return;
         double X[3], Y[3];
         bool okx[3], oky[3];
         for (int a = -1; a <= 1; a += 2) {
@@ -616,10 +623,16 @@ static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const 
                      (a + 1) + 3 * (b + 1));
             }
     };
+    // the points with images, per chunk, found by the counting pass so that
+    // the filling pass visits only them
+    std::vector<std::vector<int32_t>> cand(nc);
     auto count = [&](int64_t c) {
         int64_t k = 0;
-        for (int32_t i = (int32_t)(c * kChunk); i < std::min<int64_t>(n, (c + 1) * kChunk); i++)
+        for (int32_t i = (int32_t)(c * kChunk); i < std::min<int64_t>(n, (c + 1) * kChunk); i++) {
+            const int64_t k0 = k;
             visit(i, [&](double, double, int32_t, int32_t, int32_t) { k++; });
+            if (k != k0) cand[c].push_back(i);
+        }
         off[c + 1] = k;
     };
     if (pool && nc > 1) pool->parallel_for(nc, count);
@@ -631,7 +644,7 @@ static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const 
     m.ghost_img.resize(g);
     auto fill = [&](int64_t c) {
         int64_t k = off[c];
-        for (int32_t i = (int32_t)(c * kChunk); i < std::min<int64_t>(n, (c + 1) * kChunk); i++)
+        for (const int32_t i : cand[c])
             visit(i, [&](double X, double Y, int32_t xf, int32_t sh, int32_t img) {
                 m.gx[k] = X; m.gy[k] = Y; m.ghost_src[k] = i; m.ghost_xf[k] = xf; m.ghost_shift[k] = sh;
                 m.ghost_img[k] = img;
@@ -704,17 +717,36 @@ void build_grid(int32_t np, const double *X, const double *Y, const double ext[4
     if (pool && C > 1) pool->parallel_for(C, count);
     else
         for (int64_t c = 0; c < C; c++) count(c);
-    // offsets: bucket-major, chunk-minor, so ids stay increasing in a bucket
-    int32_t run = 0;
-    for (int64_t b = 0; b < GG; b++) {
-        w.grid_start[b] = run;
-        for (int64_t c = 0; c < C; c++) {
-            const int32_t k = w.grid_hist[c * GG + b];
-            w.grid_hist[c * GG + b] = run;
-            run += k;
+    // offsets: bucket-major, chunk-minor, so ids stay increasing in a
+    // bucket; in ranges of buckets on the pool (their totals, a prefix over
+    // the ranges, then each range from its start)
+    const int64_t BR = 4096, nbr = (GG + BR - 1) / BR;
+    std::vector<int64_t> rsum(nbr + 1, 0);
+    auto range_total = [&](int64_t r) {
+        int64_t t = 0;
+        for (int64_t b = r * BR; b < std::min(GG, (r + 1) * BR); b++)
+            for (int64_t c = 0; c < C; c++) t += w.grid_hist[c * GG + b];
+        rsum[r + 1] = t;
+    };
+    auto range_offsets = [&](int64_t r) {
+        int32_t run = (int32_t)rsum[r];
+        for (int64_t b = r * BR; b < std::min(GG, (r + 1) * BR); b++) {
+            w.grid_start[b] = run;
+            for (int64_t c = 0; c < C; c++) {
+                const int32_t k = w.grid_hist[c * GG + b];
+                w.grid_hist[c * GG + b] = run;
+                run += k;
+            }
         }
-    }
-    w.grid_start[GG] = run;
+    };
+    if (pool && nbr > 1) pool->parallel_for(nbr, range_total);
+    else
+        for (int64_t r = 0; r < nbr; r++) range_total(r);
+    for (int64_t r = 0; r < nbr; r++) rsum[r + 1] += rsum[r];
+    if (pool && nbr > 1) pool->parallel_for(nbr, range_offsets);
+    else
+        for (int64_t r = 0; r < nbr; r++) range_offsets(r);
+    w.grid_start[GG] = (int32_t)rsum[nbr];
     auto scatter = [&](int64_t c) {
         int32_t *off = w.grid_hist.data() + c * GG;
         for (int64_t q = c * chunk; q < std::min<int64_t>(np, (c + 1) * chunk); q++)
@@ -887,8 +919,13 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
     }
     auto core_real = [&](int32_t v) { return core[v] != 0; };
     // the stars of the real core points: check and number their triangles
+    // and, numbered, with global ids, rotated so that the smallest id comes
+    // first (a shared triangle then gives the same circumcentre in every
+    // slab)
     std::vector<int32_t> &tnum = r.tnum;
     tnum.assign(T.size(), -1);
+    r.tris.resize(3 * T.size());
+    int32_t *otris = r.tris.data();
     int32_t nt = 0;
     for (size_t t = 0; t < T.size(); t++) {
         const int32_t *v = T[t].v;
@@ -900,7 +937,8 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
             else r.halo_ok = false;
             return;
         }
-        if (loc[v[0]] < 0 || loc[v[1]] < 0 || loc[v[2]] < 0) {
+        const int32_t g0 = loc[v[0]], g1 = loc[v[1]], g2 = loc[v[2]];
+        if (g0 < 0 || g1 < 0 || g2 < 0) {
             r.rc = kRedo;
             return;
         }
@@ -918,18 +956,15 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
         if (!tile.lx) r.needed = std::max(r.needed, D.ux + D.R - tile.x1);
         if (!tile.fy) r.needed = std::max(r.needed, tile.y0 - (D.uy - D.R));
         if (!tile.ly) r.needed = std::max(r.needed, D.uy + D.R - tile.y1);
+        const int rot = (g0 < g1 && g0 < g2) ? 0 : (g1 < g2 ? 1 : 2);
+        const int32_t gg[5] = {g0, g1, g2, g0, g1};
+        int32_t *o = otris + 3 * (size_t)nt;
+        o[0] = gg[rot];
+        o[1] = gg[rot + 1];
+        o[2] = gg[rot + 2];
         tnum[t] = nt++;
     }
-    // triangles with global ids, rotated so that the smallest id comes first
-    // (a shared triangle then gives the same circumcentre in every slab)
     r.tris.resize(3 * (size_t)nt);
-    for (size_t t = 0; t < T.size(); t++) {
-        if (tnum[t] < 0) continue;
-        int32_t g0 = loc[T[t].v[0]], g1 = loc[T[t].v[1]], g2 = loc[T[t].v[2]];
-        int rot = (g0 < g1 && g0 < g2) ? 0 : (g1 < g2 ? 1 : 2);
-        int32_t gg[3] = {g0, g1, g2};
-        for (int k = 0; k < 3; k++) r.tris[3 * (size_t)tnum[t] + k] = gg[(rot + k) % 3];
-    }
     // rings, counter-clockwise, starting at the smallest neighbour id.  A
     // vertex's local ring (its neighbours, each with the triangle slot after
     // it) changes only where a triangle slot holding the vertex was written
