@@ -413,47 +413,83 @@ bool Delaunay::move_all(const std::vector<double> &nx, const std::vector<double>
     back.assign(NV, 0);
     std::vector<int32_t> &S = back_list_;
     S.clear();
-    bool bad = true;
-    for (int it = 0; it < 16 && bad; it++) {
-        bad = false;
-        for (const Tri &T : tris) {
-            if (T.v[0] < 0) continue;
-            if (orient2d(px_[T.v[0]], py_[T.v[0]], px_[T.v[1]], py_[T.v[1]], px_[T.v[2]], py_[T.v[2]]) > 0) continue;
-            bad = true;
-            for (int k = 0; k < 3; k++) {
-                const int32_t v = T.v[k];
-                if (is_corner(v)) return false;
-                if (back[v]) continue;
-                back[v] = 1;
-                S.push_back(v);
-                px_[v] = ox[v];
-                py_[v] = oy[v];
-            }
-        }
-        if ((int32_t)S.size() > max_back) return false;
-    }
-    if (bad) return false;
-    make_delaunay();
-    if (S.empty()) return true;
-    // out with them (a triangle of each first, from one pass)
-    rewritten_.clear();
+    // where[v]: a triangle holding v, for the vertices put back
     std::vector<int32_t> &where = where_;
     where.assign(NV, -1);
+    // The vertices of a triangle that the new positions turn over go back to
+    // their old positions (they are taken out and inserted again below).  A
+    // vertex put back can turn over only triangles of its own star, so after
+    // one pass over all triangles only the stars of the vertices put back
+    // are tested again (S doubles as the queue of stars to test).
+    auto put_back = [&](int32_t t) -> bool {
+        const Tri &T = tris[t];
+        for (int k = 0; k < 3; k++) {
+            const int32_t v = T.v[k];
+            if (is_corner(v)) return false;
+            if (back[v]) continue;
+            back[v] = 1;
+            S.push_back(v);
+            where[v] = t;
+            px_[v] = ox[v];
+            py_[v] = oy[v];
+        }
+        return true;
+    };
+    auto turned = [&](int32_t t) {
+        const Tri &T = tris[t];
+        return orient2d(px_[T.v[0]], py_[T.v[0]], px_[T.v[1]], py_[T.v[1]], px_[T.v[2]], py_[T.v[2]]) <= 0;
+    };
     for (int32_t t = 0; t < (int32_t)tris.size(); t++)
-        for (int k = 0; k < 3; k++)
-            if (tris[t].v[k] >= 0 && back[tris[t].v[k]]) where[tris[t].v[k]] = t;
+        if (tris[t].v[0] >= 0 && turned(t) && !put_back(t)) return false;
+    for (size_t q = 0; q < S.size(); q++) {
+        if ((int32_t)S.size() > max_back) return false;
+        // the star of S[q], through the neighbour links
+        const int32_t v = S[q], t0 = where[v];
+        int32_t t = t0;
+        for (int step = 0;; step++) {
+            if (step == 64) return false;
+            if (turned(t) && !put_back(t)) return false;
+            const Tri &T = tris[t];
+            const int k = T.v[0] == v ? 0 : (T.v[1] == v ? 1 : 2);
+            t = T.nb[(k + 1) % 3];
+            if (t < 0) return false;  // v on the hull
+            if (t == t0) break;
+        }
+    }
+    if ((int32_t)S.size() > max_back) return false;
+    const size_t mark = log_.size();
+    make_delaunay();
+    if (S.empty()) return true;
+    // out with them.  A triangle of each: the one it was put back from,
+    // unless the flips rewrote it (then the vertex is in a rewritten slot,
+    // which the log holds); one pass over all triangles if the log is off
+    if (log_all_) {
+        for (int32_t t = 0; t < (int32_t)tris.size(); t++)
+            for (int k = 0; k < 3; k++)
+                if (tris[t].v[k] >= 0 && back[tris[t].v[k]]) where[tris[t].v[k]] = t;
+    } else {
+        for (size_t i = mark; i < log_.size(); i++) {
+            const int32_t t = log_[i];
+            if (tris[t].v[0] >= 0)
+                for (int k = 0; k < 3; k++)
+                    if (back[tris[t].v[k]]) where[tris[t].v[k]] = t;
+        }
+    }
+    rewritten_.clear();
     for (int32_t v : S) {
         const int32_t t = where[v];
         if (t < 0 || !(tris[t].v[0] == v || tris[t].v[1] == v || tris[t].v[2] == v)) return false;
         touched_.clear();
         if (!remove_vertex(v, t)) return false;
+        // where the vertex was: a start for locating it again
+        where[v] = hint_;
         rewritten_.insert(rewritten_.end(), touched_.begin(), touched_.end());
         // the triangles the removal rewrote are where the remaining
         // vertices of S around it now are
         for (int32_t u : touched_)
             if (tris[u].v[0] >= 0)
                 for (int k = 0; k < 3; k++)
-                    if (back[tris[u].v[k]]) where[tris[u].v[k]] = u;
+                    if (back[tris[u].v[k]] && tris[u].v[k] != v) where[tris[u].v[k]] = u;
     }
     // the triangulation was Delaunay before the removals, and they rewrote
     // only these triangles: Lawson from their edges
@@ -461,6 +497,8 @@ bool Delaunay::move_all(const std::vector<double> &nx, const std::vector<double>
     for (int32_t v : S) {
         px_[v] = nx[v];
         py_[v] = ny[v];
+        const int32_t h = where[v];
+        if (h >= 0 && h < (int32_t)tris.size() && tris[h].v[0] >= 0) hint_ = h;
         if (insert_at(v) != 0) return false;
     }
     reinserted += (int64_t)S.size();
@@ -925,6 +963,12 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
     std::vector<int32_t> &tnum = r.tnum;
     tnum.assign(T.size(), -1);
     r.tris.resize(3 * T.size());
+    // the strictest bound on each side: the band, the halo rectangle, and
+    // the tile's own side where it is not open (the halo needed)
+    const double fL = std::max(std::max(band[0], xlo), tile.fx ? -INFINITY : tile.x0);
+    const double fR = std::min(std::min(band[1], xhi), tile.lx ? INFINITY : tile.x1);
+    const double fB = std::max(std::max(band[2], ylo), tile.fy ? -INFINITY : tile.y0);
+    const double fT = std::min(std::min(band[3], yhi), tile.ly ? INFINITY : tile.y1);
     int32_t *otris = r.tris.data();
     int32_t nt = 0;
     for (size_t t = 0; t < T.size(); t++) {
@@ -942,20 +986,39 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
             r.rc = kRedo;
             return;
         }
-        const Disk D = circumdisk(LX, LY, v[0], v[1], v[2], pad);
-        if (!(D.ux - D.R >= band[0] && D.ux + D.R <= band[1] && D.uy - D.R >= band[2] && D.uy + D.R <= band[3])) {
-            r.band_ok = false;
-            return;
+        // most disks clear the strictest bound on every side (band, halo
+        // rectangle, tile side) by far: that is decided on the squared
+        // radius, with a margin well above the round-off of both sides, and
+        // such a disk passes every test below and adds nothing to the halo
+        // needed
+        bool clear;
+        {
+            const double ax = LX[v[0]], ay = LY[v[0]];
+            const double bx = LX[v[1]] - ax, by = LY[v[1]] - ay, cx = LX[v[2]] - ax, cy = LY[v[2]] - ay;
+            const double rd = 1.0 / (2.0 * (bx * cy - by * cx));
+            const double b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+            const double ux = (cy * b2 - by * c2) * rd, uy = (bx * c2 - cx * b2) * rd;
+            const double cl = std::min(ux + ax - fL, fR - (ux + ax)), cb = std::min(uy + ay - fB, fT - (uy + ay));
+            const double mg = std::min(cl, cb) - pad;
+            clear = mg > 0.0 && mg * mg > (ux * ux + uy * uy) * 1.00000001;
         }
-        if (!(D.ux - D.R >= xlo && D.ux + D.R <= xhi && D.uy - D.R >= ylo && D.uy + D.R <= yhi)) {
-            r.halo_ok = false;
-            return;
+        if (!clear) {
+            const Disk D = circumdisk(LX, LY, v[0], v[1], v[2], pad);
+            if (!(D.ux - D.R >= band[0] && D.ux + D.R <= band[1] && D.uy - D.R >= band[2] &&
+                  D.uy + D.R <= band[3])) {
+                r.band_ok = false;
+                return;
+            }
+            if (!(D.ux - D.R >= xlo && D.ux + D.R <= xhi && D.uy - D.R >= ylo && D.uy + D.R <= yhi)) {
+                r.halo_ok = false;
+                return;
+            }
+            // how far this disk reaches past the tile: the halo it needs
+            if (!tile.fx) r.needed = std::max(r.needed, tile.x0 - (D.ux - D.R));
+            if (!tile.lx) r.needed = std::max(r.needed, D.ux + D.R - tile.x1);
+            if (!tile.fy) r.needed = std::max(r.needed, tile.y0 - (D.uy - D.R));
+            if (!tile.ly) r.needed = std::max(r.needed, D.uy + D.R - tile.y1);
         }
-        // how far this disk reaches past the tile: the halo it needs
-        if (!tile.fx) r.needed = std::max(r.needed, tile.x0 - (D.ux - D.R));
-        if (!tile.lx) r.needed = std::max(r.needed, D.ux + D.R - tile.x1);
-        if (!tile.fy) r.needed = std::max(r.needed, tile.y0 - (D.uy - D.R));
-        if (!tile.ly) r.needed = std::max(r.needed, D.uy + D.R - tile.y1);
         const int rot = (g0 < g1 && g0 < g2) ? 0 : (g1 < g2 ? 1 : 2);
         const int32_t gg[5] = {g0, g1, g2, g0, g1};
         int32_t *o = otris + 3 * (size_t)nt;
