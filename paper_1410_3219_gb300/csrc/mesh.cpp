@@ -1185,11 +1185,16 @@ void build_slab(const SlabCtx &c, const Tile &tile, double H, bool update, Delau
     LX.clear();
     LY.clear();
     keys.clear();
-    for_rect_points(c, R, [&](int32_t q) {
-        loc.push_back(q);
+    for_rect_points(c, R, [&](int32_t q) { loc.push_back(q); });
+    // local vertices in increasing point id: the real points' ids follow a
+    // space-filling curve, so the tile's rings land in the assembled arrays
+    // in long ascending runs instead of scattered (the ghosts, with the
+    // largest ids, come last)
+    std::sort(loc.begin(), loc.end());
+    for (const int32_t q : loc) {
         LX.push_back(c.X[q]);
         LY.push_back(c.Y[q]);
-    });
+    }
     const int32_t nl = (int32_t)loc.size();
     if (nl == 0) return;
     r.rc = dt.build(LX.data(), LY.data(), nl);
@@ -1510,16 +1515,26 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     m.edge_off.resize((size_t)n + 1);
     auto count = [&](int64_t c) {
         int64_t e = 0;
+        int self = 0;
         for (int32_t i = (int32_t)(c * chunk); i < std::min<int64_t>(n, (c + 1) * chunk); i++) {
             int32_t k = 0;
             for (int32_t s = m.cell_ptr[i]; s < m.cell_ptr[i + 1]; s++) {
-                const int o = owns(i, m.slot_nb[s]);
-                if (o < 0) bad[c] = 1;
+                const int32_t j = m.slot_nb[s];
+                if (j < n) {
+                    // a real neighbour: without a branch on the comparison,
+                    // whose outcome is random
+                    k += j > i;
+                    self |= j == i;
+                    continue;
+                }
+                const int o = owns(i, j);
+                if (o < 0) self = 1;
                 k += o > 0;
             }
             m.edge_off[i] = k;
             e += k;
         }
+        if (self) bad[c] = 1;
         ecount[c + 1] = e;
     };
     if (pool) pool->parallel_for(nchunks, count);
