@@ -432,11 +432,11 @@ def run_ours(args):
         rc = L.rich_get_conserved(sim2.h, n, *[b.ctypes.data_as(Dp) for b in bufs])
         assert rc == 0
         # what rich_tessellate uploads: ghost positions, sources, mirror
-        # flags and shifts; triangles; ring offsets, processing order and
-        # first owned edge per cell; ring neighbours and triangles (the
-        # edge list itself is built on the device)
-        h2d = (28 * info["n_ghost"] + 12 * info["n_tri"] + 4 * (n + 1) + 4 * n + 4 * (n + 1)
-               + 8 * info["n_slots"])
+        # flags and shifts; ring offsets, processing order, first owned
+        # edge and first owned triangle per cell; ring neighbours (the
+        # triangle and edge lists themselves are built on the device)
+        h2d = (28 * info["n_ghost"] + 4 * (n + 1) + 4 * n + 4 * (n + 1) + 4 * (n + 1)
+               + 4 * info["n_slots"])
         d2h = 16 * n + 12 + 48 * n
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, ws)

@@ -172,7 +172,9 @@ const char *rich_last_error(void);
 int rich_set_stream(rich_sim *s, void *cuda_stream);
 
 /* a0 for the current points: copy points device->host, tessellate on the
-   host, upload the connectivity.  Synchronous. */
+   host, upload the rings (with each cell's first owned triangle and edge)
+   and build the triangle and edge lists from them on the device.
+   Synchronous.  RICH_ETESS if the device lists do not close. */
 int rich_tessellate(rich_sim *s, rich_step_info *info);
 
 /* Enqueue a1-a9 for one step on the current connectivity (asynchronous; no
@@ -438,11 +440,14 @@ int rich_delaunay_host(int64_t n, const double *x, const double *y, int64_t cap,
 int rich_rings_host(const rich_config *cfg, int64_t n, const double *x, const double *y, int64_t cap,
                     int64_t *ptr, double *nbx, double *nby, int64_t *nbsrc, int64_t *nslots);
 
-/* The device's edge-list builder against the host's (a0 support; needs a
-   GPU): builds the mesh of the n points on the host with its own edge list,
-   runs the device builder on the same rings, and counts the entries of the
-   slot-to-edge map and of the edge arrays (left and right points, the two
-   Voronoi vertices) that differ.  *edges receives the number of edges.
+/* The device's edge-list and triangle-list builders against the host's
+   (a0 support; needs a GPU): builds the mesh of the n points on the host with
+   its own lists, runs the device builders on the same rings, and counts the
+   entries of the slot-to-edge map and of the edge arrays (left and right
+   points, the two Voronoi vertices) that differ, and the vertices of each
+   ring slot's triangle that differ (the triangles' numbering differs: the
+   host's is per tile, the device's per owning cell).  *edges receives the
+   number of edges.
    Errors: RICH_EINVAL, RICH_ENODEV, RICH_ECUDA, tessellation errors. */
 int rich_edge_list_check(const rich_config *cfg, int64_t n, const double *x, const double *y, int64_t *edges,
                          int64_t *mismatched);

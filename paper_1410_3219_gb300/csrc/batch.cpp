@@ -107,7 +107,7 @@ struct rich_batch {
     DBuf corder, psrc;
     DBuf gx, gy, gsrc, gxf, tri, ccx, ccy, slot_nb, slot_tri, slot_edge;
     DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F, ePM;
-    DBuf instp, dtmin, dtout, status, dsizes, gsync, eoff, gshift, edgebad;
+    DBuf instp, dtmin, dtout, status, dsizes, gsync, eoff, toff, gshift, edgebad;
     // launch shape: autotuned over the first steps unless fixed by the caller
     int launch_mode = 0;  // 0 autotune, 1 staged, 2 persistent
     int fixed_block = 256;
@@ -133,9 +133,9 @@ struct rich_batch {
     // host staging of the packed mesh
     std::vector<double> h_x, h_y, h_gx, h_gy, h_W0;
     std::vector<double> h_dlx, h_dly;  // the points downloaded at the start of a step
-    std::vector<int32_t> h_gsrc, h_gxf, h_tri, h_cell_ptr, h_slot_nb, h_slot_tri, h_cell_inst;
+    std::vector<int32_t> h_gsrc, h_gxf, h_cell_ptr, h_slot_nb, h_cell_inst;
     std::vector<int32_t> h_corder;
-    std::vector<int32_t> h_src, h_eoff, h_gshift;
+    std::vector<int32_t> h_src, h_eoff, h_toff, h_gshift;
     std::vector<rich::InstParams> h_inst;
     std::vector<double> h_dt;
     std::vector<int32_t> h_status;
@@ -260,6 +260,7 @@ void pack_part(rich_batch *b, BatchSim &s, const PackTask &t)
             b->h_cell_ptr[co + i] = (int32_t)(so + m.cell_ptr[i]);
             b->h_corder[co + i] = (int32_t)(co + m.cell_order[i]);
             b->h_eoff[co + i] = (int32_t)(eo + m.edge_off[i]);
+            b->h_toff[co + i] = (int32_t)(to + m.tri_off[i]);
             // conserved state: continuing simulations gather from their previous slot
             b->h_src[co + i] = s.prev_cell_off >= 0 ? (int32_t)(s.prev_cell_off + i) : -1;
         }
@@ -268,13 +269,7 @@ void pack_part(rich_batch *b, BatchSim &s, const PackTask &t)
                 for (int64_t i = i0; i < i1; i++) b->h_W0[(size_t)c * N + co + i] = s.W0[(size_t)c * n + i];
         break;
     case 1:
-        for (int64_t q = i0; q < i1; q++) {
-            b->h_slot_nb[so + q] = pid(m.slot_nb[q]);
-            b->h_slot_tri[so + q] = (int32_t)(to + m.slot_tri[q]);
-        }
-        break;
-    case 2:
-        for (int64_t c = i0; c < i1; c++) b->h_tri[3 * to + c] = pid(m.tri[c]);
+        for (int64_t q = i0; q < i1; q++) b->h_slot_nb[so + q] = pid(m.slot_nb[q]);
         break;
     default:
         for (int64_t q = i0; q < i1; q++) {
@@ -301,7 +296,6 @@ void pack_all(rich_batch *b, const std::vector<BatchSim *> &ok)
         const BatchSim &s = *ok[k];
         split((int32_t)k, 0, s.n, kPiece);
         split((int32_t)k, 1, (int64_t)s.hm.slot_nb.size(), 4 * kPiece);
-        split((int32_t)k, 2, (int64_t)s.hm.tri.size(), 4 * kPiece);
         split((int32_t)k, 3, s.hm.g, 4 * kPiece);
     }
     b->pool->parallel_for((int64_t)tasks.size(), [&](int64_t j) { pack_part(b, *ok[tasks[j].k], tasks[j]); });
@@ -659,7 +653,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
         s->cell_off = co; s->ghost_off = go; s->tri_off = to; s->edge_off = eo; s->slot_off = so;
         co += s->n;
         go += s->hm.g;
-        to += (int64_t)s->hm.tri.size() / 3;
+        to += (int64_t)s->hm.n_tris;
         eo += (int64_t)s->hm.n_edges;
         so += (int64_t)s->hm.slot_nb.size();
     }
@@ -676,13 +670,14 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     for (BatchSim *s : ok) any_pending |= s->state == PENDING;
     b->h_x.resize(N); b->h_y.resize(N); b->h_cell_inst.resize(N); b->h_src.resize(N);
     b->h_gx.resize(go); b->h_gy.resize(go); b->h_gsrc.resize(go); b->h_gxf.resize(go);
-    b->h_tri.resize(3 * to); b->h_cell_ptr.resize(N + 1); b->h_corder.resize(N);
-    b->h_slot_nb.resize(so); b->h_slot_tri.resize(so);
-    b->h_eoff.resize(N + 1); b->h_gshift.resize(go);
+    b->h_cell_ptr.resize(N + 1); b->h_corder.resize(N);
+    b->h_slot_nb.resize(so);
+    b->h_eoff.resize(N + 1); b->h_toff.resize(N + 1); b->h_gshift.resize(go);
     if (any_pending) b->h_W0.assign(4 * N, 0.0);
     pack_all(b, ok);
     b->h_cell_ptr[N] = (int32_t)so;
     b->h_eoff[N] = (int32_t)eo;
+    b->h_toff[N] = (int32_t)to;
     b->h_inst.resize(ok.size());
     for (size_t k = 0; k < ok.size(); k++) b->h_inst[k] = inst_params(*ok[k], ok[k]->state == PENDING);
     // 4. device buffers and uploads
@@ -711,32 +706,37 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     CUDA_TRY(upload(b->gy, b->h_gy, b->stream));
     CUDA_TRY(upload(b->gsrc, b->h_gsrc, b->stream));
     CUDA_TRY(upload(b->gxf, b->h_gxf, b->stream));
-    CUDA_TRY(upload(b->tri, b->h_tri, b->stream));
     CUDA_TRY(upload(b->cell_ptr, b->h_cell_ptr, b->stream));
     CUDA_TRY(upload(b->corder, b->h_corder, b->stream));
     CUDA_TRY(upload(b->slot_nb, b->h_slot_nb, b->stream));
-    CUDA_TRY(upload(b->slot_tri, b->h_slot_tri, b->stream));
+    CUDA_TRY(upload(b->toff, b->h_toff, b->stream));
     CUDA_TRY(upload(b->eoff, b->h_eoff, b->stream));
     CUDA_TRY(upload(b->gshift, b->h_gshift, b->stream));
     CUDA_TRY(upload(b->instp, b->h_inst, b->stream));
-    // the packed edge list, built on the device from the rings (each cell's
-    // box type from its simulation's parameters); checked before any kernel
-    // reads it
+    // the packed triangle and edge lists, built on the device from the rings
+    // (each cell's box type from its simulation's parameters); checked before
+    // any kernel reads them
     {
+        CUDA_TRY(b->tri.ensure((size_t)to * 12 + 12));
+        CUDA_TRY(b->slot_tri.ensure((size_t)so * 4 + 4));
         CUDA_TRY(b->slot_edge.ensure((size_t)so * 4 + 4));
         for (DBuf *e : {&b->edge_l, &b->edge_r, &b->edge_ta, &b->edge_tb}) CUDA_TRY(e->ensure((size_t)eo * 4 + 4));
         CUDA_TRY(b->edgebad.ensure(8));
         int32_t *bad = b->edgebad.as<int32_t>();
+        CUDA_TRY(rich::launch_build_tris((int32_t)N, (int32_t)so, b->cell_ptr.as<int32_t>(), b->slot_nb.as<int32_t>(),
+                                         b->toff.as<int32_t>(), b->tri.as<int32_t>(), b->slot_tri.as<int32_t>(),
+                                         bad + 1, b->stream));
         CUDA_TRY(rich::launch_build_edges((int32_t)N, (int32_t)so, b->cell_ptr.as<int32_t>(), b->slot_nb.as<int32_t>(),
                                           b->slot_tri.as<int32_t>(), b->gsrc.as<int32_t>(), b->gshift.as<int32_t>(),
                                           b->eoff.as<int32_t>(), 0, b->instp.as<rich::InstParams>(),
                                           b->cell_inst.as<int32_t>(), b->slot_edge.as<int32_t>(),
                                           b->edge_l.as<int32_t>(), b->edge_r.as<int32_t>(), b->edge_ta.as<int32_t>(),
                                           b->edge_tb.as<int32_t>(), bad, b->stream));
-        int32_t bad_h = 0;
-        CUDA_TRY(cudaMemcpyAsync(&bad_h, bad, 4, cudaMemcpyDeviceToHost, b->stream));
+        int32_t bad_h[2] = {0, 0};
+        CUDA_TRY(cudaMemcpyAsync(bad_h, bad, 8, cudaMemcpyDeviceToHost, b->stream));
         CUDA_TRY(cudaStreamSynchronize(b->stream));
-        if (bad_h) return fail(RICH_ETESS, "an edge of a ring has no partner in the other cell's ring");
+        if (bad_h[1]) return fail(RICH_ETESS, "a triangle of a ring is missing from its owner's ring");
+        if (bad_h[0]) return fail(RICH_ETESS, "an edge of a ring has no partner in the other cell's ring");
     }
     CUDA_TRY(cudaMemsetAsync(b->status.p, 0, ok.size() * 4, b->stream));
     if (any_pending) CUDA_TRY(upload(b->initW, b->h_W0, b->stream));

@@ -957,19 +957,22 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
     }
     auto core_real = [&](int32_t v) { return core[v] != 0; };
     // the stars of the real core points: check and number their triangles
-    // and, numbered, with global ids, rotated so that the smallest id comes
-    // first (a shared triangle then gives the same circumcentre in every
-    // slab)
+    // and, when the host builds the triangle list, number them and write
+    // them with global ids, rotated so that the smallest id comes first (a
+    // shared triangle then gives the same circumcentre in every slab)
+    const bool host_tris = c.work->host_edges;
     std::vector<int32_t> &tnum = r.tnum;
-    tnum.assign(T.size(), -1);
-    r.tris.resize(3 * T.size());
+    if (host_tris) {
+        tnum.assign(T.size(), -1);
+        r.tris.resize(3 * T.size());
+    }
     // the strictest bound on each side: the band, the halo rectangle, and
     // the tile's own side where it is not open (the halo needed)
     const double fL = std::max(std::max(band[0], xlo), tile.fx ? -INFINITY : tile.x0);
     const double fR = std::min(std::min(band[1], xhi), tile.lx ? INFINITY : tile.x1);
     const double fB = std::max(std::max(band[2], ylo), tile.fy ? -INFINITY : tile.y0);
     const double fT = std::min(std::min(band[3], yhi), tile.ly ? INFINITY : tile.y1);
-    int32_t *otris = r.tris.data();
+    int32_t *otris = host_tris ? r.tris.data() : nullptr;
     int32_t nt = 0;
     for (size_t t = 0; t < T.size(); t++) {
         const int32_t *v = T[t].v;
@@ -1019,6 +1022,7 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
             if (!tile.fy) r.needed = std::max(r.needed, tile.y0 - (D.uy - D.R));
             if (!tile.ly) r.needed = std::max(r.needed, D.uy + D.R - tile.y1);
         }
+        if (!host_tris) continue;
         const int rot = (g0 < g1 && g0 < g2) ? 0 : (g1 < g2 ? 1 : 2);
         const int32_t gg[5] = {g0, g1, g2, g0, g1};
         int32_t *o = otris + 3 * (size_t)nt;
@@ -1147,8 +1151,12 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
         for (int32_t j = 0; j < deg; j++) {
             const int32_t q = k + j < deg ? k + j : k + j - deg;
             onb[j] = G[q];
-            otr[j] = tnum[ring[q].t];
         }
+        if (host_tris)
+            for (int32_t j = 0; j < deg; j++) {
+                const int32_t q = k + j < deg ? k + j : k + j - deg;
+                otr[j] = tnum[ring[q].t];
+            }
         os += deg;
     }
     // (a ring's triangles all touch its core vertex, so all are numbered)
@@ -1426,9 +1434,11 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         for (const Delaunay &d : work.dts) work.reinserted += d.reinserted;
         break;
     }
-    // triangles: concatenation of the slabs' lists
+    // triangles (when the host builds their list): concatenation of the
+    // slabs' lists
+    const bool host_tris = work.host_edges;
     std::vector<int64_t> toff(K + 1, 0);
-    for (int s = 0; s < K; s++) toff[s + 1] = toff[s] + (int64_t)res[s].tris.size() / 3;
+    for (int s = 0; s < K; s++) toff[s + 1] = toff[s] + (host_tris ? (int64_t)res[s].tris.size() / 3 : 0);
     m.tri.resize(3 * (size_t)toff[K]);
     // ring offsets
     // (tiles own disjoint cells: each writes its own cells' degrees; a cell
@@ -1477,11 +1487,19 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     }
     const size_t S = (size_t)m.cell_ptr[n];
     m.slot_nb.resize(S);
-    m.slot_tri.resize(S);
+    m.slot_tri.resize(host_tris ? S : 0);
     auto fill = [&](int64_t s) {
         const SlabResult &r = res[s];
-        std::copy(r.tris.begin(), r.tris.end(), m.tri.begin() + 3 * toff[s]);
         size_t q = 0;
+        if (!host_tris) {
+            for (size_t k = 0; k < r.cells.size(); k++) {
+                const int32_t d = r.deg[k];
+                std::copy(r.nb.begin() + q, r.nb.begin() + q + d, m.slot_nb.begin() + m.cell_ptr[r.cells[k]]);
+                q += d;
+            }
+            return;
+        }
+        std::copy(r.tris.begin(), r.tris.end(), m.tri.begin() + 3 * toff[s]);
         for (size_t k = 0; k < r.cells.size(); k++) {
             const int32_t i = r.cells[k];
             for (int32_t j = 0; j < r.deg[k]; j++, q++) {
@@ -1509,16 +1527,20 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     const int64_t chunk = 8192;
     static_assert(8192 % kOrderWindow == 0, "ordering windows must not straddle chunks");
     const int64_t nchunks = (n + chunk - 1) / chunk;
-    std::vector<int64_t> ecount(nchunks + 1, 0);
+    std::vector<int64_t> ecount(nchunks + 1, 0), tcount(nchunks + 1, 0);
     std::vector<int> bad(nchunks, 0);
-    // owned edges per cell (kept in edge_off for the device-built list)
+    // owned edges per cell (kept in edge_off for the device-built list) and,
+    // for a device-built triangle list, owned triangles per cell: those of
+    // the cell's ring slots whose other two vertices have larger ids
     m.edge_off.resize((size_t)n + 1);
+    m.tri_off.resize(host_tris ? 0 : (size_t)n + 1);
     auto count = [&](int64_t c) {
-        int64_t e = 0;
+        int64_t e = 0, tc = 0;
         int self = 0;
         for (int32_t i = (int32_t)(c * chunk); i < std::min<int64_t>(n, (c + 1) * chunk); i++) {
             int32_t k = 0;
-            for (int32_t s = m.cell_ptr[i]; s < m.cell_ptr[i + 1]; s++) {
+            const int32_t lo = m.cell_ptr[i], hi = m.cell_ptr[i + 1];
+            for (int32_t s = lo; s < hi; s++) {
                 const int32_t j = m.slot_nb[s];
                 if (j < n) {
                     // a real neighbour: without a branch on the comparison,
@@ -1533,9 +1555,17 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
             }
             m.edge_off[i] = k;
             e += k;
+            if (!host_tris) {
+                int32_t kt = 0;
+                for (int32_t s = lo; s < hi; s++)
+                    kt += (m.slot_nb[s] > i) & (m.slot_nb[s + 1 < hi ? s + 1 : lo] > i);
+                m.tri_off[i] = kt;
+                tc += kt;
+            }
         }
         if (self) bad[c] = 1;
         ecount[c + 1] = e;
+        tcount[c + 1] = tc;
     };
     if (pool) pool->parallel_for(nchunks, count);
     else
@@ -1543,22 +1573,31 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     for (int64_t c = 0; c < nchunks; c++) {
         if (bad[c]) return -3;
         ecount[c + 1] += ecount[c];
+        tcount[c + 1] += tcount[c];
     }
     const size_t E = (size_t)ecount[nchunks];
+    if (E > (size_t)INT32_MAX / 2 || (size_t)tcount[nchunks] > (size_t)INT32_MAX / 3) return -3;
     m.n_edges = (int32_t)E;
+    m.n_tris = host_tris ? (int32_t)(m.tri.size() / 3) : (int32_t)tcount[nchunks];
     // counts -> offsets: each chunk from its own start
     auto offsets = [&](int64_t c) {
-        int64_t run = ecount[c];
+        int64_t run = ecount[c], trun = tcount[c];
         for (int32_t i = (int32_t)(c * chunk); i < std::min<int64_t>(n, (c + 1) * chunk); i++) {
             const int32_t k = m.edge_off[i];
             m.edge_off[i] = (int32_t)run;
             run += k;
+            if (!host_tris) {
+                const int32_t kt = m.tri_off[i];
+                m.tri_off[i] = (int32_t)trun;
+                trun += kt;
+            }
         }
     };
     if (pool) pool->parallel_for(nchunks, offsets);
     else
         for (int64_t c = 0; c < nchunks; c++) offsets(c);
     m.edge_off[n] = (int32_t)E;
+    if (!host_tris) m.tri_off[n] = m.n_tris;
     if (!work.host_edges) {
         // the device builds the list; the processing order is still needed
         m.slot_edge.clear();

@@ -46,6 +46,13 @@ struct HostMesh {
     std::vector<int32_t> cell_ptr;      // n+1 ring offsets
     std::vector<int32_t> slot_nb;       // neighbour point id
     std::vector<int32_t> slot_tri;      // triangle (i, nb[k], nb[k+1])
+    // tri and slot_tri are filled only with MeshWork::host_edges; otherwise
+    // the device builds them from the rings, and the host gives tri_off
+    // (n+1): the first triangle owned by each cell, a triangle being owned by
+    // its smallest vertex id (always a real cell: ghost ids follow the real
+    // ones) and numbered in its owner's ring order
+    std::vector<int32_t> tri_off;
+    int32_t n_tris = 0;
     std::vector<int32_t> slot_edge;     // 2*edge + (1 if the cell is the edge's right side)
     std::vector<int32_t> edge_l, edge_r;   // left (real) and right (real or ghost) points
     std::vector<int32_t> edge_ta, edge_tb; // Voronoi edge runs from cc[ta] to cc[tb], ccw about left
@@ -211,8 +218,9 @@ struct MeshWork {
     double halo = 0.0;  // slab halo of the last build, in mean point spacings
     // update in place (false: every build inserts every point again)
     bool kinetic = true;
-    // build the edge list (slot_edge, edge_l/r/ta/tb) on the host; false:
-    // only edge_off and n_edges, for a device that builds the list itself
+    // build the edge list (slot_edge, edge_l/r/ta/tb) and the triangle list
+    // (tri, slot_tri) on the host; false: only edge_off, n_edges, tri_off and
+    // n_tris, for a device that builds both lists itself
     bool host_edges = true;
     // the last build's tiles, their halos, and per tile the key of every
     // local vertex: its real point's id, n + 9 src + image for a ghost (the

@@ -104,7 +104,7 @@ struct rich_sim {
     DBuf x[3], y[3], U[3];
     DBuf A, o, W, cs, g, gl, alpha, w, tess, cell_ptr, corder, initW, rounding, p64, psrc;
     bool diagnostics = true;
-    DBuf gx, gy, gsrc, gxf, gshift, eoff;
+    DBuf gx, gy, gsrc, gxf, gshift, eoff, toff;
     DBuf tri, ccx, ccy;
     DBuf slot_nb, slot_tri, slot_edge;
     DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F, ePM;
@@ -145,7 +145,7 @@ struct rich_sim {
         p.diagnostics = diagnostics ? 1 : 0;
         p.n = n;
         p.ng = hm.g;
-        p.T = (int32_t)(hm.tri.size() / 3);
+        p.T = hm.n_tris;
         p.E = hm.n_edges;
         p.S = (int32_t)hm.slot_nb.size();
         // extrapolated fluxes: [cur] -> [1 - cur].  Time-centred: [cur] -> [2]
@@ -213,7 +213,7 @@ struct rich_sim {
     }
 
     // the mesh sizes of the current tessellation
-    int32_t nT() const { return (int32_t)(hm.tri.size() / 3); }
+    int32_t nT() const { return hm.n_tris; }
     int32_t nE() const { return hm.n_edges; }
 };
 
@@ -255,31 +255,37 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     if (rc) return mesh_rc(rc);
     double t2 = now_ms();
     const rich::HostMesh &m = s->hm;
-    const size_t T = m.tri.size() / 3, E = (size_t)m.n_edges, d = sizeof(double);
+    const size_t T = (size_t)m.n_tris, E = (size_t)m.n_edges, d = sizeof(double);
     CUDA_TRY(upload(s->gx, m.gx, s->stream));
     CUDA_TRY(upload(s->gy, m.gy, s->stream));
     CUDA_TRY(upload(s->gsrc, m.ghost_src, s->stream));
     CUDA_TRY(upload(s->gxf, m.ghost_xf, s->stream));
-    CUDA_TRY(upload(s->tri, m.tri, s->stream));
     CUDA_TRY(upload(s->cell_ptr, m.cell_ptr, s->stream));
     CUDA_TRY(upload(s->corder, m.cell_order, s->stream));
     CUDA_TRY(upload(s->slot_nb, m.slot_nb, s->stream));
-    CUDA_TRY(upload(s->slot_tri, m.slot_tri, s->stream));
-    // the edge list is built on the device from the rings (the host sends
-    // each cell's first owned edge and the ghosts' periodic shifts)
+    // the triangle and edge lists are built on the device from the rings
+    // (the host sends each cell's first owned triangle and edge, and the
+    // ghosts' periodic shifts)
+    CUDA_TRY(upload(s->toff, m.tri_off, s->stream));
     CUDA_TRY(upload(s->eoff, m.edge_off, s->stream));
     CUDA_TRY(upload(s->gshift, m.ghost_shift, s->stream));
     const size_t S = m.slot_nb.size();
+    CUDA_TRY(s->tri.ensure((3 * T + 3) * sizeof(int32_t)));
+    CUDA_TRY(s->slot_tri.ensure((S + 1) * sizeof(int32_t)));
     CUDA_TRY(s->slot_edge.ensure((S + 1) * sizeof(int32_t)));
     for (DBuf *b : {&s->edge_l, &s->edge_r, &s->edge_ta, &s->edge_tb}) CUDA_TRY(b->ensure((E + 1) * sizeof(int32_t)));
     int32_t *bad = reinterpret_cast<int32_t *>(s->scal.as<char>() + 24);
+    int32_t *bad_tri = reinterpret_cast<int32_t *>(s->scal.as<char>() + 28);
+    CUDA_TRY(rich::launch_build_tris(s->n, (int32_t)S, s->cell_ptr.as<int32_t>(), s->slot_nb.as<int32_t>(),
+                                     s->toff.as<int32_t>(), s->tri.as<int32_t>(), s->slot_tri.as<int32_t>(), bad_tri,
+                                     s->stream));
     CUDA_TRY(rich::launch_build_edges(s->n, (int32_t)S, s->cell_ptr.as<int32_t>(), s->slot_nb.as<int32_t>(),
                                       s->slot_tri.as<int32_t>(), s->gsrc.as<int32_t>(), s->gshift.as<int32_t>(),
                                       s->eoff.as<int32_t>(), s->cfg.boundary == RICH_BC_PERIODIC ? 1 : 0,
                                       nullptr, nullptr, s->slot_edge.as<int32_t>(), s->edge_l.as<int32_t>(), s->edge_r.as<int32_t>(),
                                       s->edge_ta.as<int32_t>(), s->edge_tb.as<int32_t>(), bad, s->stream));
-    int32_t bad_h = 0;
-    CUDA_TRY(cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    int32_t bad_h[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(bad_h, bad, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
     const size_t r = s->rsize();
     CUDA_TRY(s->ccx.ensure((T + 1) * d)); CUDA_TRY(s->ccy.ensure((T + 1) * d));
     for (DBuf *b : {&s->eL, &s->emlx, &s->emly, &s->emrx, &s->emry, &s->enx, &s->eny, &s->eqx, &s->eqy})
@@ -288,7 +294,8 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     CUDA_TRY(s->ePM.ensure((4 * E + 4) * r));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     double t3 = now_ms();
-    if (bad_h) return fail(RICH_ETESS, "an edge of a ring has no partner in the other cell's ring");
+    if (bad_h[1]) return fail(RICH_ETESS, "a triangle of a ring is missing from its owner's ring");
+    if (bad_h[0]) return fail(RICH_ETESS, "an edge of a ring has no partner in the other cell's ring");
     s->tess_current = true;
     s->geometry_current = false;
     if (info) {
@@ -803,22 +810,29 @@ int rich_edge_list_check(const rich_config *cfg, int64_t n, const double *x, con
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(RICH_ENODEV, "no CUDA device");
     const rich::BoxConfig box{cfg->boundary, cfg->x0, cfg->x1, cfg->y0, cfg->y1};
     rich::ThreadPool pool((int)std::max(1u, std::thread::hardware_concurrency()));
-    rich::MeshWork mw;  // host_edges: the host builds the reference list too
+    rich::MeshWork mw;  // host_edges: the host builds the reference lists too
     rich::HostMesh m;
     int rc = rich::build_host_mesh(box, (int32_t)n, x, y, mw, m, &pool);
     if (rc) return mesh_rc(rc);
-    const size_t S = m.slot_nb.size(), E = (size_t)m.n_edges;
+    // the same points as a simulation builds them: rings and tri_off only
+    rich::MeshWork mw2;
+    mw2.host_edges = false;
+    rich::HostMesh m2;
+    rc = rich::build_host_mesh(box, (int32_t)n, x, y, mw2, m2, &pool);
+    if (rc) return mesh_rc(rc);
+    if (m2.slot_nb != m.slot_nb || m2.cell_ptr != m.cell_ptr) return fail(RICH_ETESS, "rings differ between builds");
+    const size_t S = m.slot_nb.size(), E = (size_t)m.n_edges, T2 = (size_t)m2.n_tris;
     cudaStream_t st = nullptr;
     CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    DBuf cell_ptr, slot_nb, slot_tri, gsrc, gshift, eoff, slot_edge, el, er, eta, etb, bad;
+    DBuf cell_ptr, slot_nb, slot_tri, gsrc, gshift, eoff, slot_edge, el, er, eta, etb, bad, toff, dtri, dslot_tri, bad2;
     auto up = [&](DBuf &d, const std::vector<int32_t> &h) -> cudaError_t {
         cudaError_t e = d.ensure((h.size() + 1) * sizeof(int32_t));
         if (e == cudaSuccess && !h.empty())
             e = cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
         return e;
     };
-    std::vector<int32_t> dse(S), del(E), der(E), deta(E), detb(E);
-    int32_t bad_h = 0;
+    std::vector<int32_t> dse(S), del(E), der(E), deta(E), detb(E), dt(3 * T2), dst(S);
+    int32_t bad_h = 0, bad2_h = 0;
     cudaError_t e = up(cell_ptr, m.cell_ptr);
     if (e == cudaSuccess) e = up(slot_nb, m.slot_nb);
     if (e == cudaSuccess) e = up(slot_tri, m.slot_tri);
@@ -828,6 +842,14 @@ int rich_edge_list_check(const rich_config *cfg, int64_t n, const double *x, con
     for (DBuf *b : {&slot_edge}) if (e == cudaSuccess) e = b->ensure((S + 1) * sizeof(int32_t));
     for (DBuf *b : {&el, &er, &eta, &etb}) if (e == cudaSuccess) e = b->ensure((E + 1) * sizeof(int32_t));
     if (e == cudaSuccess) e = bad.ensure(sizeof(int32_t));
+    if (e == cudaSuccess) e = up(toff, m2.tri_off);
+    if (e == cudaSuccess) e = dtri.ensure((3 * T2 + 3) * sizeof(int32_t));
+    if (e == cudaSuccess) e = dslot_tri.ensure((S + 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = bad2.ensure(sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = rich::launch_build_tris((int32_t)n, (int32_t)S, cell_ptr.as<int32_t>(), slot_nb.as<int32_t>(),
+                                    toff.as<int32_t>(), dtri.as<int32_t>(), dslot_tri.as<int32_t>(),
+                                    bad2.as<int32_t>(), st);
     if (e == cudaSuccess)
         e = rich::launch_build_edges((int32_t)n, (int32_t)S, cell_ptr.as<int32_t>(), slot_nb.as<int32_t>(),
                                      slot_tri.as<int32_t>(), gsrc.as<int32_t>(), gshift.as<int32_t>(),
@@ -843,12 +865,25 @@ int rich_edge_list_check(const rich_config *cfg, int64_t n, const double *x, con
     down(der, er);
     down(deta, eta);
     down(detb, etb);
+    down(dt, dtri);
+    down(dst, dslot_tri);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad2_h, bad2.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     if (e != cudaSuccess) return fail(RICH_ECUDA, cudaGetErrorString(e));
-    int64_t bad_count = bad_h ? 1 : 0;
+    int64_t bad_count = (bad_h ? 1 : 0) + (bad2_h ? 1 : 0);
     for (size_t k = 0; k < S; k++) bad_count += dse[k] != m.slot_edge[k];
+    // the device's triangle of every slot: the host's, vertex for vertex
+    // (the numbering differs: the host's is per tile)
+    for (size_t k = 0; k < S; k++) {
+        const int32_t a = dst[k], h = m.slot_tri[k];
+        if (a < 0 || (size_t)a >= T2) {
+            bad_count++;
+            continue;
+        }
+        for (int c = 0; c < 3; c++) bad_count += dt[3 * (size_t)a + c] != m.tri[3 * (size_t)h + c];
+    }
     for (size_t k = 0; k < E; k++)
         bad_count += (del[k] != m.edge_l[k]) + (der[k] != m.edge_r[k]) + (deta[k] != m.edge_ta[k]) +
                      (detb[k] != m.edge_tb[k]);

@@ -951,10 +951,63 @@ __global__ void k_build_edges(int32_t n, const int32_t *__restrict__ cell_ptr, c
     }
 }
 
+// a slot left without its edge (or triangle): any negative entry
 __global__ void k_check_edges(int32_t S, const int32_t *__restrict__ slot_edge, int32_t *bad)
 {
     const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < S && slot_edge[s] < 0) *bad = 1;
+}
+
+// One thread per real cell: its owned triangles (both other vertices with
+// larger ids) numbered in ring order, and for every other slot the number
+// its owner gave the triangle, found by walking the owner's ring.
+__global__ void k_build_tris(int32_t n, const int32_t *__restrict__ cell_ptr, const int32_t *__restrict__ slot_nb,
+                             const int32_t *__restrict__ tri_off, int32_t *tri, int32_t *slot_tri, int32_t *bad)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t lo = cell_ptr[i], deg = cell_ptr[i + 1] - lo;
+    int32_t t = tri_off[i];
+    const int32_t t_end = tri_off[i + 1];
+    for (int32_t k = 0; k < deg; k++) {
+        const int32_t a = slot_nb[lo + k], b = slot_nb[lo + (k + 1 == deg ? 0 : k + 1)];
+        if (i < a && i < b) {
+            if (t >= t_end) {
+                *bad = 1;
+                return;
+            }
+            tri[3 * t] = i;
+            tri[3 * t + 1] = a;
+            tri[3 * t + 2] = b;
+            slot_tri[lo + k] = t++;
+            continue;
+        }
+        // the owner o is the smaller of a and b (a real cell, below i); in
+        // its ring the triangle (i, a, b) reads (o, p, q): (a, b, i) or
+        // (b, i, a)
+        const int32_t o = a < b ? a : b;
+        if (o < 0 || o >= n) {
+            *bad = 1;
+            return;
+        }
+        const int32_t p = o == a ? b : i, q = o == a ? i : a;
+        const int32_t olo = cell_ptr[o], odeg = cell_ptr[o + 1] - olo;
+        int32_t num = tri_off[o], found = -1;
+        for (int32_t kk = 0; kk < odeg; kk++) {
+            const int32_t x = slot_nb[olo + kk], y = slot_nb[olo + (kk + 1 == odeg ? 0 : kk + 1)];
+            if (x == p && y == q) {
+                found = num;
+                break;
+            }
+            num += (o < x && o < y) ? 1 : 0;
+        }
+        if (found < 0) {
+            *bad = 1;
+            return;
+        }
+        slot_tri[lo + k] = found;
+    }
+    if (t != t_end) *bad = 1;
 }
 
 inline int blocks(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
@@ -1006,6 +1059,17 @@ template <class R> void launch_stage(int k, const SweepParams<R> &p, const doubl
     default:
         break;
     }
+}
+
+cudaError_t launch_build_tris(int32_t n, int32_t S, const int32_t *cell_ptr, const int32_t *slot_nb,
+                              const int32_t *tri_off, int32_t *tri, int32_t *slot_tri, int32_t *bad, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess && S > 0) e = cudaMemsetAsync(slot_tri, 0xff, sizeof(int32_t) * (size_t)S, st);
+    if (e != cudaSuccess) return e;
+    if (n > 0) k_build_tris<<<blocks(n), kBlock, 0, st>>>(n, cell_ptr, slot_nb, tri_off, tri, slot_tri, bad);
+    if (S > 0) k_check_edges<<<blocks(S), kBlock, 0, st>>>(S, slot_tri, bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_build_edges(int32_t n, int32_t S, const int32_t *cell_ptr, const int32_t *slot_nb,

@@ -169,6 +169,17 @@ template <class R> int persistent_blocks_per_sm(int block);
 void launch_repack(const int32_t *src, int32_t n_new, int32_t n_old, const double *U_old, double *U_new,
                    cudaStream_t st);
 
+// The triangle list from the rings, on the device.  The triangle of ring
+// slot k of real cell i is (i, nb[k], nb[k+1]); it is owned by its smallest
+// vertex id (a real cell: ghost ids follow the real ones), numbered in its
+// owner's ring order from tri_off[owner] (tri_off[n] = T, from the host) and
+// written rotated to start at the owner, as the host builder writes it.
+// Writes tri (3 T) and slot_tri (S), and sets *bad to 1 if a cell owns more
+// or fewer triangles than tri_off gives, if a slot's triangle is missing
+// from its owner's ring, or if a slot ends without a triangle.
+cudaError_t launch_build_tris(int32_t n, int32_t S, const int32_t *cell_ptr, const int32_t *slot_nb,
+                              const int32_t *tri_off, int32_t *tri, int32_t *slot_tri, int32_t *bad, cudaStream_t st);
+
 // The edge list from the rings, on the device (the host then ships rings
 // only).  Real cell i owns its edges to larger real cells, to mirror images
 // and (periodic box) to images of larger cells or of itself shifted to the
