@@ -460,7 +460,11 @@ int rich_edge_list_check(const rich_config *cfg, int64_t n, const double *x, con
    each, with `threads` host threads, and counts the steps whose sweep
    inputs differ (rings, their neighbours and triangles, the edge list and
    each cell's first owned edge, ghosts) or whose first owned edges do not
-   match the edge list.  *updated and *rebuilt receive the tile counts of the reused
+   match the edge list.  A third reused workspace builds the sequence as a
+   simulation does (rings only, read off incrementally, with each cell's
+   first owned edge and triangle for the device's lists); a step whose
+   rings, ghosts, first owned edges or processing order differ from the
+   fresh build's counts as well.  *updated and *rebuilt receive the tile counts of the reused
    workspace over all steps, *reinserted the vertices it took out and put
    back where triangles would have turned over.  Returns RICH_EINVAL for bad
    arguments or the builder's error. */

@@ -1033,25 +1033,24 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
     }
     r.tris.resize(3 * (size_t)nt);
     // rings, counter-clockwise, starting at the smallest neighbour id.  A
-    // vertex's local ring (its neighbours, each with the triangle slot after
-    // it) changes only where a triangle slot holding the vertex was written
-    // since the last read-off (the triangulation's log; every slot after a
-    // fresh build): those rings, and those of vertices with no ring from the
-    // last read-off, are walked through the neighbour links from a slot
-    // incident to the vertex; the others are copied.  The global ids and
-    // triangle numbers are applied to every ring afterwards (ghost ids and
-    // the numbering change from build to build).
-    const bool all = dt.log_all();
+    // vertex's ring changes only where a triangle slot holding it was
+    // written since the last read-off (the triangulation's log; every slot
+    // after a fresh build), or where a neighbour's global id changed (ghost
+    // ids follow this build's ghost list): those rings, those of vertices
+    // with no ring in the last read-off's output, and every ring when the
+    // host builds the triangle list (whose numbers change from build to
+    // build), are walked through the neighbour links from a slot holding the
+    // vertex; the others are copied from the last output as they were.
+    const bool all = dt.log_all() || host_tris;
     std::vector<uint8_t> &dirty = r.dirty;
     std::vector<int32_t> &vt = r.vt;
-    if (all) {
-        dirty.assign(nl, 1);
+    dirty.assign(nl, all ? 1 : 0);
+    if (dt.log_all()) {
         vt.assign(nl, -1);
         for (size_t t = 0; t < T.size(); t++)
             if (T[t].v[0] >= 0)
                 for (int k = 0; k < 3; k++) vt[T[t].v[k]] = (int32_t)t;
     } else {
-        dirty.assign(nl, 0);
         vt.resize(nl, -1);
         for (const int32_t t : dt.log()) {
             if (t < 0 || t >= (int32_t)T.size() || T[t].v[0] < 0) continue;
@@ -1062,65 +1061,82 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
         }
     }
     dt.clear_log();
-    const int32_t nprev = all ? 0 : (int32_t)r.ring_off.size();
-    std::vector<int32_t> &noff = r.next_off, &nlen = r.next_len;
-    std::vector<TileStars::Slot> &nring = r.next_ring;
+    // the star of local vertex v through the neighbour links from vt[v]:
+    // neighbour after v in each slot, and the slot; its size, or -1 when the
+    // star does not close (or no slot is known to hold v: -2)
+    constexpr int32_t kMaxStar = 64;
+    auto walk = [&](int32_t v, int32_t *wnb, int32_t *wt) -> int32_t {
+        int32_t t = vt[v];
+        int k = t < 0 ? -1 : (T[t].v[0] == v ? 0 : (T[t].v[1] == v ? 1 : (T[t].v[2] == v ? 2 : -1)));
+        if (k < 0) return -2;
+        const int32_t t0 = t;
+        int32_t deg = 0;
+        do {
+            if (deg == kMaxStar) return -1;
+            // in slot t with v at position k the neighbour after v is
+            // a = v[k+1]; the next slot counter-clockwise about v shares the
+            // edge (v, v[k+2]), the one opposite a
+            const Tri &U = T[t];
+            wnb[deg] = U.v[(k + 1) % 3];
+            wt[deg++] = t;
+            const int32_t b = U.v[(k + 2) % 3];
+            t = U.nb[(k + 1) % 3];
+            if (t < 0) return -1;
+            const Tri &V = T[t];
+            k = V.v[0] == v ? 0 : (V.v[1] == v ? 1 : (V.v[2] == v ? 2 : -1));
+            if (k < 0 || V.v[(k + 1) % 3] != b) return -1;
+        } while (t != t0);
+        return deg;
+    };
+    // a neighbour whose global id changed: walk the rings around it again
+    std::vector<int32_t> &ploc = r.prev_loc;
+    const int32_t nprev = all ? 0 : (int32_t)std::min<size_t>(r.out_off.size(), ploc.size());
+    int32_t wnb[kMaxStar], wt[kMaxStar];
+    for (int32_t v = 0; v < nprev; v++) {
+        if (loc[v] == ploc[v]) continue;
+        dirty[v] = 1;
+        const int32_t d = walk(v, wnb, wt);
+        if (d == -2) {
+            r.rc = kRedo;  // no slot known to hold v
+            return;
+        }
+        for (int32_t j = 0; j < d; j++) dirty[wnb[j]] = 1;
+        if (d < 0)
+            for (int32_t u = 0; u < nl; u++) dirty[u] = 1;  // (not expected) walk everything
+    }
+    ploc.assign(loc.begin(), loc.begin() + nl);
+    // the outputs (core vertices in local order), sized for a mean degree
+    // of 8 and grown if that is not enough (the mean is 6); the last output
+    // is kept beside them until the copies are done
+    std::vector<int32_t> &nb_prev = r.nb_prev, &noff = r.next_off, &nlen = r.next_len;
+    r.nb.swap(nb_prev);
     noff.resize(nl);
     nlen.resize(nl);
-    // the outputs (core vertices in local order), sized for a mean degree
-    // of 8 and grown if that is not enough (the mean is 6)
     r.cells.resize(ncore);
     r.deg.resize(ncore);
-    size_t cap = std::max<size_t>(r.nb.size(), 8 * (size_t)ncore + 64);
+    size_t cap = std::max<size_t>(std::max(r.nb.size(), nb_prev.size()), 8 * (size_t)ncore + 64);
     r.nb.resize(cap);
-    r.tri.resize(cap);
-    nring.resize(std::max(nring.size(), cap));
-    size_t os = 0, ns = 0;
+    if (host_tris) r.tri.resize(cap);
+    size_t os = 0;
     int32_t oc = 0;
-    constexpr int32_t kMaxStar = 64;
-    TileStars::Slot walked[kMaxStar];
     for (int32_t v = 0; v < nl; v++) {
         noff[v] = -1;
         nlen[v] = 0;
         if (!core_real(v)) continue;
-        const TileStars::Slot *ring;
         int32_t deg;
-        if (!dirty[v] && v < nprev && r.ring_off[v] >= 0) {
-            ring = &r.ring[r.ring_off[v]];
-            deg = r.ring_len[v];
+        const bool copy = !dirty[v] && v < nprev && r.out_off[v] >= 0;
+        if (copy) {
+            deg = r.out_len[v];
         } else {
-            // walk: in slot t with v at position k, the neighbour after v is
-            // a = v[k+1]; the next slot counter-clockwise about v shares the
-            // edge (v, v[k+2]), the one opposite a
-            int32_t t = vt[v];
-            int k = t < 0 ? -1 : (T[t].v[0] == v ? 0 : (T[t].v[1] == v ? 1 : (T[t].v[2] == v ? 2 : -1)));
-            if (k < 0) {
-                r.rc = kRedo;  // no slot known to hold v
+            deg = walk(v, wnb, wt);
+            if (deg == -2) {
+                r.rc = kRedo;
                 return;
             }
-            const int32_t t0 = t;
-            deg = 0;
-            do {
-                if (deg == kMaxStar) {
-                    r.rc = -3;
-                    return;
-                }
-                const Tri &U = T[t];
-                walked[deg++] = TileStars::Slot{U.v[(k + 1) % 3], t};
-                const int32_t b = U.v[(k + 2) % 3];
-                t = U.nb[(k + 1) % 3];
-                if (t < 0) {
-                    r.rc = -3;  // the star is not closed
-                    return;
-                }
-                const Tri &V = T[t];
-                k = V.v[0] == v ? 0 : (V.v[1] == v ? 1 : (V.v[2] == v ? 2 : -1));
-                if (k < 0 || V.v[(k + 1) % 3] != b) {
-                    r.rc = -3;  // inconsistent links
-                    return;
-                }
-            } while (t != t0);
-            ring = walked;
+            if (deg < 0) {
+                r.rc = -3;  // the star is not closed, or inconsistent links
+                return;
+            }
         }
         if (deg < 3) {
             r.rc = -3;
@@ -1129,42 +1145,38 @@ void read_stars(const SlabCtx &c, const Tile &tile, const Rect &R, Delaunay &dt,
         if (os + deg > cap) {
             cap = 2 * cap + kMaxStar;
             r.nb.resize(cap);
-            r.tri.resize(cap);
-            nring.resize(cap);
+            if (host_tris) r.tri.resize(cap);
         }
-        noff[v] = (int32_t)ns;
+        noff[v] = (int32_t)os;
         nlen[v] = deg;
-        std::copy(ring, ring + deg, nring.data() + ns);
-        ns += deg;
-        // start at the smallest neighbour id
-        int32_t G[kMaxStar];
-        int32_t k = 0, kid = INT32_MAX;
-        for (int32_t q = 0; q < deg; q++) {
-            const int32_t id = loc[ring[q].nb];
-            G[q] = id;
-            k = id < kid ? q : k;
-            kid = id < kid ? id : kid;
-        }
         r.cells[oc] = loc[v];
         r.deg[oc++] = deg;
-        int32_t *onb = r.nb.data() + os, *otr = r.tri.data() + os;
-        for (int32_t j = 0; j < deg; j++) {
-            const int32_t q = k + j < deg ? k + j : k + j - deg;
-            onb[j] = G[q];
-        }
-        if (host_tris)
-            for (int32_t j = 0; j < deg; j++) {
-                const int32_t q = k + j < deg ? k + j : k + j - deg;
-                otr[j] = tnum[ring[q].t];
+        int32_t *onb = r.nb.data() + os;
+        if (copy) {
+            std::copy(nb_prev.data() + r.out_off[v], nb_prev.data() + r.out_off[v] + deg, onb);
+        } else {
+            // start at the smallest neighbour id
+            int32_t G[kMaxStar];
+            int32_t k = 0, kid = INT32_MAX;
+            for (int32_t q = 0; q < deg; q++) {
+                const int32_t id = loc[wnb[q]];
+                G[q] = id;
+                k = id < kid ? q : k;
+                kid = id < kid ? id : kid;
             }
+            for (int32_t j = 0; j < deg; j++) onb[j] = G[k + j < deg ? k + j : k + j - deg];
+            if (host_tris) {
+                // (a ring's triangles all touch its core vertex, so all are numbered)
+                int32_t *otr = r.tri.data() + os;
+                for (int32_t j = 0; j < deg; j++) otr[j] = tnum[wt[k + j < deg ? k + j : k + j - deg]];
+            }
+        }
         os += deg;
     }
-    // (a ring's triangles all touch its core vertex, so all are numbered)
     r.nb.resize(os);
-    r.tri.resize(os);
-    r.ring_off.swap(noff);
-    r.ring_len.swap(nlen);
-    r.ring.swap(nring);
+    if (host_tris) r.tri.resize(os);
+    r.out_off.swap(noff);
+    r.out_len.swap(nlen);
 }
 
 // Triangulate the points of a tile plus a halo of width H (by updating the

@@ -173,17 +173,15 @@ struct TileStars {
     std::vector<int32_t> nb;      // concatenated rings: neighbour point ids
     std::vector<int32_t> tri;     // concatenated rings: tile-local triangle number
     std::vector<int32_t> tris;    // 3 per tile-local triangle (point ids)
-    // the local rings of the last read-off, by local vertex: neighbours
-    // (local ids) counter-clockwise from ring_off[v] (-1: none), ring_len[v]
-    // of them, each with the triangle slot after it; the next ones are
-    // written beside them and swapped in
-    struct Slot {
-        int32_t nb, t;
-    };
-    std::vector<int32_t> ring_off, ring_len, next_off, next_len;
-    std::vector<Slot> ring, next_ring;
+    // the last read-off's output by local vertex: where the vertex's ring
+    // starts in nb (-1: not a core vertex then) and its length, and each
+    // local vertex's point id then; the next ones are written beside them
+    // and swapped in (nb_prev holds the last output while the next is
+    // written)
+    std::vector<int32_t> out_off, out_len, next_off, next_len, prev_loc, nb_prev;
     // scratch of the read-off: core flags, triangle numbers, rings to walk
-    // again, and a triangle slot holding each local vertex
+    // again, and a triangle slot holding each local vertex (kept between
+    // read-offs, updated from the triangulation's log)
     std::vector<uint8_t> core, dirty;
     std::vector<int32_t> tnum, vt;
     // scratch of the in-place update: the local vertices' new positions

@@ -904,6 +904,10 @@ int rich_mesh_update_check(const rich_config *cfg, int64_t n, int32_t steps, con
     const rich::BoxConfig box{cfg->boundary, cfg->x0, cfg->x1, cfg->y0, cfg->y1};
     rich::ThreadPool pool(threads);
     rich::MeshWork kept;
+    // the same sequence as a simulation builds it (no host lists: the rings
+    // are read off incrementally and copied where unchanged)
+    rich::MeshWork kept_dev;
+    kept_dev.host_edges = false;
     *mismatched = 0;
     // a triangle's vertices (smallest id first in both builds)
     auto tri_of = [](const rich::HostMesh &m, int32_t t) {
@@ -911,12 +915,18 @@ int rich_mesh_update_check(const rich_config *cfg, int64_t n, int32_t steps, con
     };
     for (int32_t k = 0; k < steps; k++) {
         const double *x = xs + (size_t)k * n, *y = ys + (size_t)k * n;
-        rich::HostMesh a, b;
+        rich::HostMesh a, b, c;
         rich::MeshWork fresh;
         int rc = rich::build_host_mesh(box, (int32_t)n, x, y, kept, a, &pool);
         if (rc) return mesh_rc(rc);
         rc = rich::build_host_mesh(box, (int32_t)n, x, y, fresh, b, &pool);
         if (rc) return mesh_rc(rc);
+        rc = rich::build_host_mesh(box, (int32_t)n, x, y, kept_dev, c, &pool);
+        if (rc) return mesh_rc(rc);
+        if (!(c.g == b.g && c.gx == b.gx && c.gy == b.gy && c.ghost_src == b.ghost_src && c.cell_ptr == b.cell_ptr &&
+              c.slot_nb == b.slot_nb && c.edge_off == b.edge_off && c.n_edges == b.n_edges &&
+              c.cell_order == b.cell_order && (int64_t)c.tri_off.size() == n + 1 && c.tri_off[n] == c.n_tris))
+            (*mismatched)++;
         bool same = a.g == b.g && a.gx == b.gx && a.gy == b.gy && a.ghost_src == b.ghost_src &&
                     a.cell_ptr == b.cell_ptr && a.slot_nb == b.slot_nb && a.slot_edge == b.slot_edge &&
                     a.edge_l == b.edge_l && a.edge_r == b.edge_r && a.cell_order == b.cell_order &&
