@@ -535,7 +535,7 @@ def run_batched(rich, precision, n_inst, steps, seed=4):
     li = b.launch_info()
     # both launch shapes timed on the same batch, the autotuner's choice first
     shapes = {}
-    for name, mode, block in (("staged_graph", 1, 256), ("persistent_256", 2, 256), ("persistent_512", 2, 512)):
+    for name, mode, block in (("staged", 1, 256), ("persistent_256", 2, 256), ("persistent_512", 2, 512)):
         b.set_launch(mode, block)
         b.step()  # records the graph of this shape
         shapes[name] = float(np.mean([b.step()["sweep_ms"] for _ in range(3)]))
