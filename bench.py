@@ -409,7 +409,9 @@ def run_ours(args):
 
     # end to end through the public API: rich_step (host tessellation, copies,
     # sweep) plus a host read of the step's result
-    e2e_steps = max(2, min(args.steps, 5))
+    # (the same K timed steps after the same W warm-up steps as the device
+    # measurement, each a whole step with its copies)
+    e2e_steps = max(2, args.steps)
     bufs = [np.empty(n) for _ in range(6)]
     import ctypes as C
     Dp = C.POINTER(C.c_double)
@@ -417,7 +419,9 @@ def run_ours(args):
     w_e2e = dict(wl)
     w_e2e["cfg"] = dict(wl["cfg"], precision=1 if head_prec == "split" else 0)
     sim2 = rich.Sim(w_e2e)
-    sim2.step(1)
+    for _ in range(max(1, args.warmup)):
+        sim2.step(1)
+        L.rich_get_conserved(sim2.h, n, *[b.ctypes.data_as(Dp) for b in bufs])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2d = d2h = 0
