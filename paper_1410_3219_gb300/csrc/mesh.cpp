@@ -537,6 +537,11 @@ void Delaunay::make_delaunay(const std::vector<int32_t> *seed)
                 }
             }
             for (int q = 0; q < nc; q++) {
+                if (q + 8 < nc) {
+                    // the neighbour triangle of a candidate a few ahead
+                    const int32_t t8 = cand[q + 8] >> 2;
+                    __builtin_prefetch(&tris[tris[t8].nb[cand[q + 8] & 3]]);
+                }
                 const int32_t t = cand[q] >> 2;
                 const int k = cand[q] & 3;
                 const Tri &T = tris[t];
