@@ -113,3 +113,25 @@ def test_full_size_split_run(R, name):
         assert drift <= 1e-10, (q, drift)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("name,steps", [("kh_1048576", 8), ("sedov_262144", 8)])
+def test_full_size_mesh_updates_equal_fresh_builds(R, name, steps):
+    """The host builder's in-place updates at full size, over the positions
+    of a GPU run: every step's sweep inputs equal a fresh build's, both with
+    the host lists and in the simulation's own mode (rings read off
+    incrementally), on all host threads (several tiles per thread)."""
+    wl = FULL[name]()
+    sim = R.Sim(wl)
+    xs, ys = [], []
+    for _ in range(steps):
+        c = sim.conserved()
+        xs.append(c["x"].copy())
+        ys.append(c["y"].copy())
+        sim.step(1)
+    sim.close()
+    threads = max(2, min(16, os.cpu_count() or 2))
+    mismatched, updated, rebuilt, reinserted = R.rich_mesh_update_check(wl["cfg"], np.array(xs), np.array(ys),
+                                                                          threads=threads)
+    assert mismatched == 0, (updated, rebuilt, reinserted)
+    assert updated > 0.75 * (updated + rebuilt), (updated, rebuilt)
