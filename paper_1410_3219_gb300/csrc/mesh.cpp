@@ -1291,54 +1291,65 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
             work.gkey_idx.assign(9 * (size_t)n, -1);
             work.gkey_stamp.assign(9 * (size_t)n, 0u);
         }
-        for (int32_t g = 0; g < m.g; g++) {
-            const size_t k = 9 * (size_t)m.ghost_src[g] + (size_t)m.ghost_img[g];
-            work.gkey_idx[k] = g;
-            work.gkey_stamp[k] = work.gen;
+        {
+            // (each ghost has its own key: chunks on the pool write apart)
+            const int64_t gc = 8192, ngc = ((int64_t)m.g + gc - 1) / gc;
+            auto keys = [&](int64_t c) {
+                for (int32_t g = (int32_t)(c * gc); g < (int32_t)std::min<int64_t>(m.g, (c + 1) * gc); g++) {
+                    const size_t k = 9 * (size_t)m.ghost_src[g] + (size_t)m.ghost_img[g];
+                    work.gkey_idx[k] = g;
+                    work.gkey_stamp[k] = work.gen;
+                }
+            };
+            if (pool && ngc > 1) pool->parallel_for(ngc, keys);
+            else
+                for (int64_t c = 0; c < ngc; c++) keys(c);
         }
         X.resize(np);
         Y.resize(np);
+        // the points copied in chunks on the pool (one thread copies ~5
+        // GB/s), each chunk's bounding box taken on the way; the ghosts' box
+        // from their own list
+        double ext[4];
         {
-            // copied in chunks on the pool (one thread copies ~5 GB/s)
             const int64_t cc = 32768, ncc = (n + cc - 1) / cc;
+            std::vector<std::array<double, 4>> part(ncc + 1);
             auto copy = [&](int64_t c) {
                 const int64_t q0 = c * cc, q1 = std::min<int64_t>(n, q0 + cc);
-                std::memcpy(X.data() + q0, x + q0, sizeof(double) * (q1 - q0));
-                std::memcpy(Y.data() + q0, y + q0, sizeof(double) * (q1 - q0));
+                std::array<double, 4> bb = {x[q0], x[q0], y[q0], y[q0]};
+                for (int64_t q = q0; q < q1; q++) {
+                    const double xq = x[q], yq = y[q];
+                    X[q] = xq;
+                    Y[q] = yq;
+                    bb[0] = std::min(bb[0], xq);
+                    bb[1] = std::max(bb[1], xq);
+                    bb[2] = std::min(bb[2], yq);
+                    bb[3] = std::max(bb[3], yq);
+                }
+                part[c] = bb;
             };
             if (pool && ncc > 1) pool->parallel_for(ncc, copy);
             else
                 for (int64_t c = 0; c < ncc; c++) copy(c);
-        }
-        std::memcpy(X.data() + n, m.gx.data(), sizeof(double) * m.g);
-        std::memcpy(Y.data() + n, m.gy.data(), sizeof(double) * m.g);
-        const double band[4] = {box.x0 - w, box.x1 + w, box.y0 - w, box.y1 + w};
-        // bounding box of all points, in chunks
-        double ext[4] = {X[0], X[0], Y[0], Y[0]};
-        {
-            const int64_t ec = 65536, nec = (np + ec - 1) / ec;
-            std::vector<std::array<double, 4>> part(nec);
-            auto bbox = [&](int64_t c) {
-                const int32_t q0 = (int32_t)(c * ec), q1 = (int32_t)std::min<int64_t>(np, (c + 1) * ec);
-                std::array<double, 4> b = {X[q0], X[q0], Y[q0], Y[q0]};
-                for (int32_t q = q0 + 1; q < q1; q++) {
-                    b[0] = std::min(b[0], X[q]);
-                    b[1] = std::max(b[1], X[q]);
-                    b[2] = std::min(b[2], Y[q]);
-                    b[3] = std::max(b[3], Y[q]);
-                }
-                part[c] = b;
-            };
-            if (pool && nec > 1) pool->parallel_for(nec, bbox);
-            else
-                for (int64_t c = 0; c < nec; c++) bbox(c);
-            for (const auto &b : part) {
-                ext[0] = std::min(ext[0], b[0]);
-                ext[1] = std::max(ext[1], b[1]);
-                ext[2] = std::min(ext[2], b[2]);
-                ext[3] = std::max(ext[3], b[3]);
+            std::memcpy(X.data() + n, m.gx.data(), sizeof(double) * m.g);
+            std::memcpy(Y.data() + n, m.gy.data(), sizeof(double) * m.g);
+            part[ncc] = part[0];
+            for (int32_t g = 0; g < m.g; g++) {
+                part[ncc][0] = std::min(part[ncc][0], m.gx[g]);
+                part[ncc][1] = std::max(part[ncc][1], m.gx[g]);
+                part[ncc][2] = std::min(part[ncc][2], m.gy[g]);
+                part[ncc][3] = std::max(part[ncc][3], m.gy[g]);
+            }
+            ext[0] = ext[1] = X[0];
+            ext[2] = ext[3] = Y[0];
+            for (const auto &bb : part) {
+                ext[0] = std::min(ext[0], bb[0]);
+                ext[1] = std::max(ext[1], bb[1]);
+                ext[2] = std::min(ext[2], bb[2]);
+                ext[3] = std::max(ext[3], bb[3]);
             }
         }
+        const double band[4] = {box.x0 - w, box.x1 + w, box.y0 - w, box.y1 + w};
         PointGrid grid;
         build_grid(np, X.data(), Y.data(), ext, work, pool, grid);
         lap(0);
