@@ -671,7 +671,10 @@ static void make_ghosts(const BoxConfig &box, int32_t n, const double *x, const 
     std::vector<std::vector<int32_t>> cand(nc);
     auto count = [&](int64_t c) {
         int64_t k = 0;
-        for (int32_t i = (int32_t)(c * kChunk); i < std::min<int64_t>(n, (c + 1) * kChunk); i++) {
+        const int32_t i0 = (int32_t)(c * kChunk), i1 = (int32_t)std::min<int64_t>(n, (c + 1) * kChunk);
+        for (int32_t i = i0; i < i1; i++) {
+            // (the test that skips most points, in the loop itself)
+            if (x[i] > in_x0 && x[i] < in_x1 && y[i] > in_y0 && y[i] < in_y1) continue;
             const int64_t k0 = k;
             visit(i, [&](double, double, int32_t, int32_t, int32_t) { k++; });
             if (k != k0) cand[c].push_back(i);
