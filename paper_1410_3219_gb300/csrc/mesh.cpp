@@ -1519,30 +1519,6 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     const size_t S = (size_t)m.cell_ptr[n];
     m.slot_nb.resize(S);
     m.slot_tri.resize(host_tris ? S : 0);
-    auto fill = [&](int64_t s) {
-        const SlabResult &r = res[s];
-        size_t q = 0;
-        if (!host_tris) {
-            for (size_t k = 0; k < r.cells.size(); k++) {
-                const int32_t d = r.deg[k];
-                std::copy(r.nb.begin() + q, r.nb.begin() + q + d, m.slot_nb.begin() + m.cell_ptr[r.cells[k]]);
-                q += d;
-            }
-            return;
-        }
-        std::copy(r.tris.begin(), r.tris.end(), m.tri.begin() + 3 * toff[s]);
-        for (size_t k = 0; k < r.cells.size(); k++) {
-            const int32_t i = r.cells[k];
-            for (int32_t j = 0; j < r.deg[k]; j++, q++) {
-                m.slot_nb[m.cell_ptr[i] + j] = r.nb[q];
-                m.slot_tri[m.cell_ptr[i] + j] = (int32_t)(toff[s] + r.tri[q]);
-            }
-        }
-    };
-    if (pool && K > 1) pool->parallel_for(K, fill);
-    else
-        for (int s = 0; s < K; s++) fill(s);
-    lap(2);
     // edges: each physical edge once, owned by its smaller real cell; a
     // periodic edge between a cell and its own copy by the +shift slot
     auto owns = [&](int32_t i, int32_t j) -> int {  // 1 own, 0 partner's, -1 inconsistent
@@ -1555,54 +1531,71 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         const int32_t sx = sh % 3 - 1, sy = sh / 3 - 1;
         return (sy < 0 || (sy == 0 && sx < 0)) ? 0 : 1;
     };
+    // owned edges per cell (kept in edge_off for the device-built list) and,
+    // for a device-built triangle list, owned triangles per cell: those of
+    // the cell's ring slots whose other two vertices have larger ids; both
+    // counted while each tile's rings are placed (still in cache)
+    m.edge_off.resize((size_t)n + 1);
+    m.tri_off.resize(host_tris ? 0 : (size_t)n + 1);
+    std::vector<int> tile_bad(K, 0);
+    auto fill = [&](int64_t s) {
+        const SlabResult &r = res[s];
+        size_t q = 0;
+        int self = 0;
+        if (host_tris) std::copy(r.tris.begin(), r.tris.end(), m.tri.begin() + 3 * toff[s]);
+        for (size_t k = 0; k < r.cells.size(); k++) {
+            const int32_t i = r.cells[k], d = r.deg[k];
+            const int32_t *ring = r.nb.data() + q;
+            std::copy(ring, ring + d, m.slot_nb.begin() + m.cell_ptr[i]);
+            if (host_tris)
+                for (int32_t j = 0; j < d; j++) m.slot_tri[m.cell_ptr[i] + j] = (int32_t)(toff[s] + r.tri[q + j]);
+            int32_t ke = 0;
+            for (int32_t j = 0; j < d; j++) {
+                const int32_t nb = ring[j];
+                if (nb < n) {
+                    // a real neighbour: without a branch on the comparison,
+                    // whose outcome is random
+                    ke += nb > i;
+                    self |= nb == i;
+                    continue;
+                }
+                const int o = owns(i, nb);
+                if (o < 0) self = 1;
+                ke += o > 0;
+            }
+            m.edge_off[i] = ke;
+            if (!host_tris) {
+                int32_t kt = 0;
+                for (int32_t j = 0; j < d; j++) kt += (ring[j] > i) & (ring[j + 1 < d ? j + 1 : 0] > i);
+                m.tri_off[i] = kt;
+            }
+            q += d;
+        }
+        if (self) tile_bad[s] = 1;
+    };
+    if (pool && K > 1) pool->parallel_for(K, fill);
+    else
+        for (int s = 0; s < K; s++) fill(s);
+    for (int s = 0; s < K; s++)
+        if (tile_bad[s]) return -3;
+    lap(2);
     const int64_t chunk = 8192;
     static_assert(8192 % kOrderWindow == 0, "ordering windows must not straddle chunks");
     const int64_t nchunks = (n + chunk - 1) / chunk;
     std::vector<int64_t> ecount(nchunks + 1, 0), tcount(nchunks + 1, 0);
-    std::vector<int> bad(nchunks, 0);
-    // owned edges per cell (kept in edge_off for the device-built list) and,
-    // for a device-built triangle list, owned triangles per cell: those of
-    // the cell's ring slots whose other two vertices have larger ids
-    m.edge_off.resize((size_t)n + 1);
-    m.tri_off.resize(host_tris ? 0 : (size_t)n + 1);
-    auto count = [&](int64_t c) {
+    auto sums = [&](int64_t c) {
         int64_t e = 0, tc = 0;
-        int self = 0;
         for (int32_t i = (int32_t)(c * chunk); i < std::min<int64_t>(n, (c + 1) * chunk); i++) {
-            int32_t k = 0;
-            const int32_t lo = m.cell_ptr[i], hi = m.cell_ptr[i + 1];
-            for (int32_t s = lo; s < hi; s++) {
-                const int32_t j = m.slot_nb[s];
-                if (j < n) {
-                    // a real neighbour: without a branch on the comparison,
-                    // whose outcome is random
-                    k += j > i;
-                    self |= j == i;
-                    continue;
-                }
-                const int o = owns(i, j);
-                if (o < 0) self = 1;
-                k += o > 0;
-            }
-            m.edge_off[i] = k;
-            e += k;
-            if (!host_tris) {
-                int32_t kt = 0;
-                for (int32_t s = lo; s < hi; s++)
-                    kt += (m.slot_nb[s] > i) & (m.slot_nb[s + 1 < hi ? s + 1 : lo] > i);
-                m.tri_off[i] = kt;
-                tc += kt;
-            }
+            e += m.edge_off[i];
+            if (!host_tris) tc += m.tri_off[i];
         }
-        if (self) bad[c] = 1;
         ecount[c + 1] = e;
         tcount[c + 1] = tc;
     };
-    if (pool) pool->parallel_for(nchunks, count);
+    if (pool) pool->parallel_for(nchunks, sums);
     else
-        for (int64_t c = 0; c < nchunks; c++) count(c);
+        for (int64_t c = 0; c < nchunks; c++) sums(c);
     for (int64_t c = 0; c < nchunks; c++) {
-        if (bad[c]) return -3;
         ecount[c + 1] += ecount[c];
         tcount[c + 1] += tcount[c];
     }
