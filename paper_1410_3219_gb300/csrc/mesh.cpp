@@ -1474,7 +1474,16 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
     // ring offsets
     // (tiles own disjoint cells: each writes its own cells' degrees; a cell
     // no tile wrote keeps degree 0 and fails the check)
-    m.cell_ptr.assign(n + 1, 0);
+    m.cell_ptr.resize((size_t)n + 1);
+    {
+        const int64_t zc = 65536, nzc = ((int64_t)n + 1 + zc - 1) / zc;
+        auto zero = [&](int64_t c) {
+            std::fill(m.cell_ptr.begin() + c * zc, m.cell_ptr.begin() + std::min<int64_t>(n + 1, (c + 1) * zc), 0);
+        };
+        if (pool && nzc > 1) pool->parallel_for(nzc, zero);
+        else
+            for (int64_t c = 0; c < nzc; c++) zero(c);
+    }
     auto degs = [&](int64_t s) {
         for (size_t k = 0; k < res[s].cells.size(); k++) m.cell_ptr[res[s].cells[k] + 1] = res[s].deg[k];
     };
