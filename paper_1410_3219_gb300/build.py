@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librich.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["sweep.cu", "courant_noalloc.cu", "probe.cu"]
+CUDA_SOURCES = ["sweep.cu", "courant_noalloc.cu", "probe.cu", "layout.cu"]
 HOST_SOURCES = ["predicates.cpp", "mesh.cpp", "rich_api.cpp", "batch.cpp", "server.cpp"]
 
 

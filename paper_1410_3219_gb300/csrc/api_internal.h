@@ -79,4 +79,8 @@ class ThreadPool;
 int batch_create(int32_t precision, int64_t max_cells, int32_t host_threads, ThreadPool *shared, rich_batch **out);
 bool point_inside(const rich_config *c, double x, double y);
 
+// dst[f * n + perm[k]] = src[f][k] for the six fields (null sources skipped)
+cudaError_t launch_unpermute(int32_t n, const int32_t *perm, const double *const src[6], double *dst,
+                             cudaStream_t st);
+
 }  // namespace rich

@@ -105,6 +105,7 @@ struct rich_sim {
     DBuf A, o, W, cs, g, gl, alpha, w, tess, cell_ptr, corder, initW, rounding, p64, psrc;
     bool diagnostics = true;
     DBuf gx, gy, gsrc, gxf, gshift, eoff, toff;
+    DBuf perm_dev, unperm;  // caller index of each internal cell; reordered state for reads
     DBuf tri, ccx, ccy;
     DBuf slot_nb, slot_tri, slot_edge;
     DBuf edge_l, edge_r, edge_ta, edge_tb, eL, emlx, emly, emrx, emry, enx, eny, eqx, eqy, F, ePM;
@@ -112,23 +113,8 @@ struct rich_sim {
     DBuf instp;  // one InstParams
     rich::InstParams inst_host{};  // staging for the parameter upload
 
-    // pinned host staging for reads of the state (grown as needed)
-    double *pinned = nullptr;
-    size_t pinned_cap = 0;
-    cudaError_t pinned_ensure(size_t count)
-    {
-        if (count <= pinned_cap) return cudaSuccess;
-        if (pinned) cudaFreeHost(pinned);
-        pinned = nullptr;
-        pinned_cap = 0;
-        cudaError_t e = cudaMallocHost(&pinned, count * sizeof(double));
-        if (e == cudaSuccess) pinned_cap = count;
-        return e;
-    }
-
     ~rich_sim()
     {
-        if (pinned) cudaFreeHost(pinned);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         for (cudaEvent_t e : kev)
@@ -417,6 +403,7 @@ static int create_sim(const rich_config *cfg, int64_t n, const double *x, const 
         return bail(fail(RICH_ECUDA, "event creation failed"));
     if ((rc = alloc_cells(s)) != RICH_OK) return bail(rc);
     if (s->x[0].ensure(n * 8) != cudaSuccess) return bail(fail(RICH_ENOMEM, "device points"));
+    if (upload(s->perm_dev, s->perm, s->stream) != cudaSuccess) return bail(fail(RICH_ENOMEM, "device order"));
     cudaMemcpyAsync(s->x[0].p, s->hx.data(), n * 8, cudaMemcpyHostToDevice, s->stream);
     cudaMemcpyAsync(s->y[0].p, s->hy.data(), n * 8, cudaMemcpyHostToDevice, s->stream);
     if ((rc = tessellate(s, nullptr, false)) != RICH_OK) return bail(rc);
@@ -689,24 +676,19 @@ int rich_get_conserved(rich_sim *s, int64_t n, double *x, double *y, double *m, 
     if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
     const size_t N = (size_t)s->n;
     const int q = s->pts();
-    // points and state into pinned staging with one wait, then put back in
-    // the caller's order on the host threads
-    CUDA_TRY(s->pinned_ensure(6 * N));
-    double *st = s->pinned;
-    CUDA_TRY(cudaMemcpyAsync(st, s->x[q].p, N * 8, cudaMemcpyDeviceToHost, s->stream));
-    CUDA_TRY(cudaMemcpyAsync(st + N, s->y[q].p, N * 8, cudaMemcpyDeviceToHost, s->stream));
-    CUDA_TRY(cudaMemcpyAsync(st + 2 * N, s->U[q].p, 4 * N * 8, cudaMemcpyDeviceToHost, s->stream));
-    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    // points and state put in the caller's order on the device, then copied
+    // straight into the caller's arrays with one wait
     double *outs[6] = {x, y, m, px, py, E};
-    const int64_t chunk = 65536, nch = ((int64_t)N + chunk - 1) / chunk;
-    s->pool->parallel_for(6 * nch, [&](int64_t t) {
-        const int f = (int)(t / nch);
-        if (!outs[f]) return;
-        const int64_t k0 = (t % nch) * chunk, k1 = std::min<int64_t>((int64_t)N, k0 + chunk);
-        const double *src = st + (size_t)f * N;
-        double *dst = outs[f];
-        for (int64_t k = k0; k < k1; k++) dst[s->perm[k]] = src[k];
-    });
+    const double *src[6] = {s->x[q].as<double>(), s->y[q].as<double>(), s->U[q].as<double>(),
+                            s->U[q].as<double>() + N, s->U[q].as<double>() + 2 * N, s->U[q].as<double>() + 3 * N};
+    for (int f = 0; f < 6; f++)
+        if (!outs[f]) src[f] = nullptr;
+    CUDA_TRY(s->unperm.ensure(6 * N * sizeof(double)));
+    double *st = s->unperm.as<double>();
+    CUDA_TRY(rich::launch_unpermute(s->n, s->perm_dev.as<int32_t>(), src, st, s->stream));
+    for (int f = 0; f < 6; f++)
+        if (outs[f]) CUDA_TRY(cudaMemcpyAsync(outs[f], st + (size_t)f * N, N * 8, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
     return RICH_OK;
 }
 
