@@ -721,11 +721,16 @@ inline Disk circumdisk(const double *X, const double *Y, int32_t a, int32_t b, i
     return Disk{ux + ax, uy + ay, std::sqrt(ux * ux + uy * uy) * (1.0 + 1e-9) + pad};
 }
 
-// The points bucketed on a G x G grid over their bounding box.
+// Points bucketed on a G x G grid over a rectangle.
 struct PointGrid {
     int G = 1;
     double x0 = 0.0, y0 = 0.0, sx = 0.0, sy = 0.0;
     const int32_t *start = nullptr, *ids = nullptr;
+    PointGrid() = default;
+    explicit PointGrid(const MeshWork::GridBufs &b)
+        : G(b.G), x0(b.x0), y0(b.y0), sx(b.sx), sy(b.sy), start(b.start.data()), ids(b.ids.data())
+    {
+    }
     // bucket column / row of a coordinate, clamped to the grid (infinite
     // and NaN coordinates included)
     int col(double x) const { return clampi((x - x0) * sx); }
@@ -733,30 +738,32 @@ struct PointGrid {
     int clampi(double f) const { return !(f > 0.0) ? 0 : (f >= G ? G - 1 : (int)f); }
 };
 
-// Counting sort of the point ids by bucket, in chunks on the pool: a
-// histogram per chunk, offsets per (bucket, chunk), then each chunk scatters
-// its ids in increasing order.
-void build_grid(int32_t np, const double *X, const double *Y, const double ext[4], MeshWork &w, ThreadPool *pool,
-                PointGrid &g)
+// Counting sort of the point ids q0 .. q1-1 by bucket of a grid over the
+// rectangle ext, in chunks on the pool: a histogram per chunk, offsets per
+// (bucket, chunk), then each chunk scatters its ids in increasing order.
+void build_grid(int32_t q0, int32_t q1, const double *X, const double *Y, const double ext[4],
+                MeshWork::GridBufs &w, ThreadPool *pool)
 {
-    g.G = std::max(1, std::min(1024, (int)std::sqrt(np / 32.0)));
-    const int G = g.G;
+    const int32_t np = q1 - q0;
+    w.G = std::max(1, std::min(1024, (int)std::sqrt(np / 32.0)));
+    const int G = w.G;
     const int64_t GG = (int64_t)G * G;
-    g.x0 = ext[0];
-    g.y0 = ext[2];
-    g.sx = ext[1] > ext[0] ? G / (ext[1] - ext[0]) : 0.0;
-    g.sy = ext[3] > ext[2] ? G / (ext[3] - ext[2]) : 0.0;
+    w.x0 = ext[0];
+    w.y0 = ext[2];
+    w.sx = ext[1] > ext[0] ? G / (ext[1] - ext[0]) : 0.0;
+    w.sy = ext[3] > ext[2] ? G / (ext[3] - ext[2]) : 0.0;
+    PointGrid g(w);
     const int64_t C = pool ? std::max(1, std::min(pool->size(), (int)(np / 8192) + 1)) : 1;
     const int64_t chunk = (np + C - 1) / C;
-    w.grid_cell.resize(np);
-    w.grid_hist.assign(C * GG, 0);
-    w.grid_start.assign(GG + 1, 0);
-    w.grid_ids.resize(np);
+    w.cell.resize(np);
+    w.hist.assign(C * GG, 0);
+    w.start.assign(GG + 1, 0);
+    w.ids.resize(np);
     auto count = [&](int64_t c) {
-        int32_t *h = w.grid_hist.data() + c * GG;
+        int32_t *h = w.hist.data() + c * GG;
         for (int64_t q = c * chunk; q < std::min<int64_t>(np, (c + 1) * chunk); q++) {
-            const int32_t b = g.row(Y[q]) * G + g.col(X[q]);
-            w.grid_cell[q] = b;
+            const int32_t b = g.row(Y[q0 + q]) * G + g.col(X[q0 + q]);
+            w.cell[q] = b;
             h[b]++;
         }
     };
@@ -771,16 +778,16 @@ void build_grid(int32_t np, const double *X, const double *Y, const double ext[4
     auto range_total = [&](int64_t r) {
         int64_t t = 0;
         for (int64_t b = r * BR; b < std::min(GG, (r + 1) * BR); b++)
-            for (int64_t c = 0; c < C; c++) t += w.grid_hist[c * GG + b];
+            for (int64_t c = 0; c < C; c++) t += w.hist[c * GG + b];
         rsum[r + 1] = t;
     };
     auto range_offsets = [&](int64_t r) {
         int32_t run = (int32_t)rsum[r];
         for (int64_t b = r * BR; b < std::min(GG, (r + 1) * BR); b++) {
-            w.grid_start[b] = run;
+            w.start[b] = run;
             for (int64_t c = 0; c < C; c++) {
-                const int32_t k = w.grid_hist[c * GG + b];
-                w.grid_hist[c * GG + b] = run;
+                const int32_t k = w.hist[c * GG + b];
+                w.hist[c * GG + b] = run;
                 run += k;
             }
         }
@@ -792,17 +799,15 @@ void build_grid(int32_t np, const double *X, const double *Y, const double ext[4
     if (pool && nbr > 1) pool->parallel_for(nbr, range_offsets);
     else
         for (int64_t r = 0; r < nbr; r++) range_offsets(r);
-    w.grid_start[GG] = (int32_t)rsum[nbr];
+    w.start[GG] = (int32_t)rsum[nbr];
     auto scatter = [&](int64_t c) {
-        int32_t *off = w.grid_hist.data() + c * GG;
+        int32_t *off = w.hist.data() + c * GG;
         for (int64_t q = c * chunk; q < std::min<int64_t>(np, (c + 1) * chunk); q++)
-            w.grid_ids[off[w.grid_cell[q]]++] = (int32_t)q;
+            w.ids[off[w.cell[q]]++] = (int32_t)(q0 + q);
     };
     if (pool && C > 1) pool->parallel_for(C, scatter);
     else
         for (int64_t c = 0; c < C; c++) scatter(c);
-    g.start = w.grid_start.data();
-    g.ids = w.grid_ids.data();
 }
 
 // Outcome of one tile: the rings of its real core cells, the triangles they
@@ -817,7 +822,9 @@ struct SlabCtx {
     const BoxConfig *box = nullptr;
     const HostMesh *m = nullptr;              // ghost sources and images
     const double *ext = nullptr;              // bounding box of all points
-    const PointGrid *grid = nullptr;
+    const PointGrid *grid = nullptr;   // real points, possibly from an earlier build
+    double slack = 0.0;                // how far a real point can be from where that grid saw it
+    const PointGrid *ggrid = nullptr;  // ghosts of this build
     const double *band = nullptr;
     double pad = 0.0;
     const MeshWork *work = nullptr;           // ghost key lookup of this build
@@ -850,16 +857,24 @@ Rect tile_rect(const SlabCtx &c, const Tile &tile, double H)
     return R;
 }
 
-// Every point of the rectangle, from the grid buckets it overlaps.
-template <class F> void for_rect_points(const SlabCtx &c, const Rect &R, F &&f)
+// Every point of the rectangle: the real points from the buckets of their
+// grid that the rectangle widened by the grid's slack overlaps, the ghosts
+// from theirs; each tested on its current position.
+template <class F> void scan_grid(const SlabCtx &c, const PointGrid &grid, const Rect &R, double slack, F &&f)
 {
-    const PointGrid &grid = *c.grid;
-    const int c0 = grid.col(R.xlo), c1 = grid.col(R.xhi), r0 = grid.row(R.ylo), r1 = grid.row(R.yhi);
+    const int c0 = grid.col(R.xlo - slack), c1 = grid.col(R.xhi + slack);
+    const int r0 = grid.row(R.ylo - slack), r1 = grid.row(R.yhi + slack);
     for (int rw = r0; rw <= r1; rw++)
         for (int32_t k = grid.start[rw * grid.G + c0]; k < grid.start[rw * grid.G + c1 + 1]; k++) {
             const int32_t q = grid.ids[k];
             if (c.X[q] >= R.xlo && c.X[q] < R.xhi && c.Y[q] >= R.ylo && c.Y[q] < R.yhi) f(q);
         }
+}
+
+template <class F> void for_rect_points(const SlabCtx &c, const Rect &R, F &&f)
+{
+    scan_grid(c, *c.grid, R, c.slack, f);
+    if (c.np > c.n) scan_grid(c, *c.ggrid, R, 0.0, f);
 }
 
 // Update the tile's last triangulation for this build's points: move every
@@ -1317,11 +1332,17 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         {
             const int64_t cc = 32768, ncc = (n + cc - 1) / cc;
             std::vector<std::array<double, 4>> part(ncc + 1);
+            // (and each chunk's largest move of a coordinate since the last
+            // build, whose points X, Y still hold when the grid is kept)
+            std::vector<double> moved(ncc, 0.0);
+            const bool track = work.grid_n == n;
             auto copy = [&](int64_t c) {
                 const int64_t q0 = c * cc, q1 = std::min<int64_t>(n, q0 + cc);
                 std::array<double, 4> bb = {x[q0], x[q0], y[q0], y[q0]};
+                double mv = 0.0;
                 for (int64_t q = q0; q < q1; q++) {
                     const double xq = x[q], yq = y[q];
+                    if (track) mv = std::max(mv, std::max(std::fabs(xq - X[q]), std::fabs(yq - Y[q])));
                     X[q] = xq;
                     Y[q] = yq;
                     bb[0] = std::min(bb[0], xq);
@@ -1330,6 +1351,7 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
                     bb[3] = std::max(bb[3], yq);
                 }
                 part[c] = bb;
+                moved[c] = mv;
             };
             if (pool && ncc > 1) pool->parallel_for(ncc, copy);
             else
@@ -1343,6 +1365,8 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
                 part[ncc][2] = std::min(part[ncc][2], m.gy[g]);
                 part[ncc][3] = std::max(part[ncc][3], m.gy[g]);
             }
+            if (track)
+                for (const double mv : moved) work.grid_slack += mv;
             ext[0] = ext[1] = X[0];
             ext[2] = ext[3] = Y[0];
             for (const auto &bb : part) {
@@ -1353,8 +1377,20 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
             }
         }
         const double band[4] = {box.x0 - w, box.x1 + w, box.y0 - w, box.y1 + w};
-        PointGrid grid;
-        build_grid(np, X.data(), Y.data(), ext, work, pool, grid);
+        // the real points' grid over the box, kept while they have moved
+        // less than half a bucket since it was built (a NaN move rebuilds)
+        {
+            const MeshWork::GridBufs &gr = work.grid_real;
+            const double half_bucket = 0.5 / std::max(gr.sx, gr.sy);
+            if (work.grid_n != n || !(work.grid_slack < half_bucket)) {
+                const double bext[4] = {box.x0, box.x1, box.y0, box.y1};
+                build_grid(0, n, X.data(), Y.data(), bext, work.grid_real, pool);
+                work.grid_n = n;
+                work.grid_slack = 0.0;
+            }
+        }
+        build_grid(n, np, X.data(), Y.data(), ext, work.grid_ghost, pool);
+        const PointGrid grid(work.grid_real), ggrid(work.grid_ghost);
         lap(0);
         SlabCtx ctx;
         ctx.n = n;
@@ -1365,6 +1401,13 @@ int build_host_mesh(const BoxConfig &box, int32_t n, const double *x, const doub
         ctx.m = &m;
         ctx.ext = ext;
         ctx.grid = &grid;
+        // (widened a little beyond the summed moves against their rounding)
+        ctx.slack = work.grid_slack > 0.0
+                        ? work.grid_slack * (1.0 + 1e-6) +
+                              1e-12 * std::max({std::fabs(box.x0), std::fabs(box.x1), std::fabs(box.y0),
+                                                std::fabs(box.y1)})
+                        : 0.0;
+        ctx.ggrid = &ggrid;
         ctx.band = band;
         ctx.pad = pad;
         ctx.work = &work;

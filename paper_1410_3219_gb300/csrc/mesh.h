@@ -207,10 +207,21 @@ struct MeshWork {
     std::vector<TileStars> stars;
     std::vector<std::vector<int32_t>> loc;
     std::vector<std::vector<double>> lx, ly;
-    // the points bucketed on a uniform grid over their bounding box (ids in
-    // increasing order within a bucket), so that a tile gathers its points
-    // from the buckets it overlaps instead of testing every point
-    std::vector<int32_t> grid_start, grid_ids, grid_cell, grid_hist;
+    // the points bucketed on uniform grids (ids in increasing order within a
+    // bucket), so that a tile gathers its points from the buckets it
+    // overlaps instead of testing every point: the real points on a grid
+    // over the box, kept from build to build while they have moved less
+    // than half a bucket since (grid_slack: the sum over builds of the
+    // largest move of a coordinate; grid_n: the point count it holds, -1
+    // none), the ghosts on a grid of their own every build
+    struct GridBufs {
+        std::vector<int32_t> start, ids, cell, hist;
+        int G = 1;
+        double x0 = 0.0, y0 = 0.0, sx = 0.0, sy = 0.0;
+    };
+    GridBufs grid_real, grid_ghost;
+    double grid_slack = 0.0;
+    int32_t grid_n = -1;
     // real then ghost coordinates of the current build
     std::vector<double> X, Y;
     double halo = 0.0;  // slab halo of the last build, in mean point spacings

@@ -221,6 +221,30 @@ def _positions(oracle, wl, steps, skip=0):
     return np.array(xs), np.array(ys)
 
 
+@pytest.mark.parametrize("step_cells", [0.02, 0.3, 2.0])
+def test_mesh_updates_follow_points_across_grid_buckets(R, step_cells):
+    """The host builder keeps its bucketing of the points from build to
+    build while they have moved less than half a bucket and rebuilds it
+    after: in a periodic shear flow moving every point by up to step_cells
+    cell widths a step (buckets are about six cells wide at this size, so
+    points cross buckets, and the bucketing is kept for tens of steps, a few
+    or none), the sweep's inputs still equal those of fresh builds."""
+    # 65,536 points: four tiles on four threads, so that tiles gather
+    # their points from the buckets (one tile takes every point)
+    wl = W.kelvin_helmholtz(n_side=256, amp=0.1)
+    x, y = wl["x"].copy(), wl["y"].copy()
+    d = step_cells / 256.0
+    xs, ys = [], []
+    for k in range(10):
+        xs.append(x.copy())
+        ys.append(y.copy())
+        x = np.mod(x + d * np.sin(2.0 * np.pi * y), 1.0)
+        y = np.mod(y + 0.5 * d * np.cos(2.0 * np.pi * x), 1.0)
+    mismatched, updated, rebuilt, _ = R.rich_mesh_update_check(wl["cfg"], np.array(xs), np.array(ys), threads=4)
+    assert mismatched == 0, (updated, rebuilt)
+    assert updated + rebuilt >= 4 * 10
+
+
 @pytest.mark.parametrize("name,make,steps,skip,turned", [
     ("sod_64", lambda: W.sod(n_side=64), 40, 0, True),
     ("kh_64", lambda: W.kelvin_helmholtz(n_side=64, amp=0.1), 30, 0, True),
