@@ -124,7 +124,14 @@ int rich_init_mesh(const rich_config *cfg, int64_t n, const double *x, const dou
 /* Advance up to max_steps steps, stopping early once the time reaches t_end
    (the last step is shortened to land on t_end).  Each step: a0 on the host
    for the current points, then a1-a9 on the device (twice, with a0 for the
-   half-step points in between, in the time-centred scheme).  info may be NULL.
+   half-step points in between, in the time-centred scheme).  The points'
+   motion (a9) needs only the mesh velocity and dt, known after the geometry
+   stage, so each sweep writes the moved points first; the call reads them
+   back then and runs a0 for them on the host while the device computes the
+   gradients, fluxes and update.  A step that does not land on t_end thus
+   leaves the mesh of its points built, and the next step or call starts
+   with the sweep.  Results equal those of rich_tessellate / rich_sweep /
+   rich_sync in turn, bit for bit.  info may be NULL.
    Errors: RICH_ENEGATIVE / RICH_ENAN (state left at the last good step),
    RICH_ETESS, RICH_EDUPLICATE, RICH_ECUDA. */
 int rich_step(rich_sim *s, int32_t max_steps, double t_end, rich_step_info *info);
@@ -192,7 +199,9 @@ int rich_sync(rich_sim *s, rich_step_info *info);
 /* Per-cell diagnostics of the last sweep, caller's order, n doubles:
    0 area, 1-2 centre of mass, 3-6 rho vx vy p, 7 c_s, 8-15 unlimited gradient
    (d/dx, d/dy of rho, vx, vy, p), 16-23 limited gradient, 24-25 w,
-   26 TESS flag, 27-30 alpha (rho, vx, vy, p), 31 dt (same value in every cell). */
+   26 TESS flag, 27-30 alpha (rho, vx, vy, p), 31 dt (same value in every cell).
+   A later tessellation leaves them alone; rich_get_state's geometry pass
+   replaces fields 0-7 with those of the current points. */
 int rich_get_field(rich_sim *s, int32_t field, int64_t n, double *out);
 
 /* Write (on, the default) or skip (off) the inspection-only per-cell arrays

@@ -48,6 +48,31 @@ struct DBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+// Page-locked host memory: copies to and from it run at the link's speed
+// and can run beside kernels (grown like DBuf; freed with the handle).
+struct HBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    HBuf() = default;
+    HBuf(const HBuf &) = delete;
+    HBuf &operator=(const HBuf &) = delete;
+    ~HBuf()
+    {
+        if (p) cudaFreeHost(p);
+    }
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= cap && p) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMallocHost(&p, bytes);
+        if (e == cudaSuccess) cap = bytes;
+        return e;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
 template <class T> cudaError_t upload(DBuf &b, const std::vector<T> &v, cudaStream_t st)
 {
     cudaError_t e = b.ensure(sizeof(T) * (v.size() + 1));

@@ -164,6 +164,7 @@ struct rich_batch {
         p.cell_inst = cell_inst.as<int32_t>();
         p.n_inst = (int32_t)packed.size();
         p.diagnostics = diagnostics ? 1 : 0;
+        p.motion = 1;
         p.n = (int32_t)n_packed;
         p.ng = (int32_t)nG;
         p.T = (int32_t)nT;

@@ -79,7 +79,11 @@ struct rich_sim {
     rich_config cfg{};
     int32_t n = 0;
     std::vector<int32_t> perm;  // internal -> caller index
-    std::vector<double> hx, hy; // host copy of the points (internal order)
+    // host copy of the points (internal order), page-locked: x at [0, n),
+    // y at [n, 2n), then the dt of the sweep that moved them
+    rich::HBuf hpts;
+    double *hx() const { return hpts.as<double>(); }
+    double *hy() const { return hpts.as<double>() + n; }
     rich::MeshWork mw;  // (edge list built on the device: see tessellate)
     rich::HostMesh hm;
     std::unique_ptr<rich::ThreadPool> pool;  // host threads of the tile-parallel tessellation
@@ -96,6 +100,10 @@ struct rich_sim {
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // early read of a sweep's new points (rich_step): copied on their own
+    // stream once the point motion is done, while the sweep goes on
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_moved = nullptr, ev_copied = nullptr;
     bool profiling = false;
     cudaEvent_t kev[rich::NUM_STAGES + 1] = {};
     double kms[rich::NUM_STAGES] = {};
@@ -117,6 +125,9 @@ struct rich_sim {
     {
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        if (ev_moved) cudaEventDestroy(ev_moved);
+        if (ev_copied) cudaEventDestroy(ev_copied);
+        if (copy_stream) cudaStreamDestroy(copy_stream);
         for (cudaEvent_t e : kev)
             if (e) cudaEventDestroy(e);
         if (own_stream) cudaStreamDestroy(own_stream);
@@ -129,6 +140,7 @@ struct rich_sim {
         p.cell_inst = nullptr;
         p.n_inst = 1;
         p.diagnostics = diagnostics ? 1 : 0;
+        p.motion = 1;
         p.n = n;
         p.ng = hm.g;
         p.T = hm.n_tris;
@@ -137,7 +149,7 @@ struct rich_sim {
         // extrapolated fluxes: [cur] -> [1 - cur].  Time-centred: [cur] -> [2]
         // by half a step, then primitives and mesh of [2], update of [cur]
         // into [1 - cur]
-        const int src = pts(), dst = time_centred() && tc_phase == 0 ? 2 : 1 - cur;
+        const int src = pts(), dst = next_pts();
         p.x = x[src].as<double>(); p.y = y[src].as<double>();
         p.xn = x[dst].as<double>(); p.yn = y[dst].as<double>();
         p.x0 = x[cur].as<double>(); p.y0 = y[cur].as<double>();
@@ -169,6 +181,8 @@ struct rich_sim {
     bool time_centred() const { return cfg.scheme == RICH_SCHEME_TIME_CENTRED; }
     // buffer of the points (and state) that the current mesh and sweep describe
     int pts() const { return tc_phase == 1 ? 2 : cur; }
+    // buffer the sweep writes its moved points (and state) to
+    int next_pts() const { return time_centred() && tc_phase == 0 ? 2 : 1 - cur; }
 
     // scheme parameters of this simulation with the time left to t_end
     rich::InstParams inst_params(double remaining, bool init = false) const
@@ -184,16 +198,19 @@ struct rich_sim {
         return ip;
     }
 
-    // launch stage k of the sweep in the handle's precision
-    void launch(int k, const double *init_W, double *Un_override = nullptr) const
+    // launch stage k of the sweep in the handle's precision (motion false:
+    // the geometry stage leaves the mesh velocity and time step alone)
+    void launch(int k, const double *init_W, double *Un_override = nullptr, bool motion = true) const
     {
         if (cfg.precision == RICH_FP32_SPLIT) {
             rich::SweepParams<float> p = params<float>();
             if (Un_override) p.Un = Un_override;
+            p.motion = motion ? 1 : 0;
             rich::launch_stage<float>(k, p, init_W, stream);
         } else {
             rich::SweepParams<double> p = params<double>();
             if (Un_override) p.Un = Un_override;
+            p.motion = motion ? 1 : 0;
             rich::launch_stage<double>(k, p, init_W, stream);
         }
     }
@@ -224,22 +241,25 @@ int alloc_cells(rich_sim *s)
     return RICH_OK;
 }
 
-// host tessellation of the current points + upload of the connectivity
-int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
+// a0 on the host: the mesh of the points in hx, hy (the device mesh is
+// then out of date until upload_mesh)
+int build_mesh(rich_sim *s, rich_step_info *info)
 {
     rich::Range range("rich tessellate (a0)");
-    double t0 = now_ms();
-    if (fetch_points) {
-        const int q = s->pts();
-        CUDA_TRY(cudaMemcpyAsync(s->hx.data(), s->x[q].p, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(s->hy.data(), s->y[q].p, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
-        CUDA_TRY(cudaStreamSynchronize(s->stream));
-    }
-    double t1 = now_ms();
+    const double t1 = now_ms();
     rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
-    int rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm, s->pool.get());
-    if (rc) return mesh_rc(rc);
-    double t2 = now_ms();
+    const int rc = rich::build_host_mesh(box, s->n, s->hx(), s->hy(), s->mw, s->hm, s->pool.get());
+    if (info) info->tess_ms += now_ms() - t1;
+    return rc ? mesh_rc(rc) : RICH_OK;
+}
+
+// upload of the host mesh; the triangle and edge lists are built on the
+// device from the rings (the host sends each cell's first owned triangle
+// and edge, and the ghosts' periodic shifts).  Nothing on the stream may
+// still read the old mesh: buffers that grow are reallocated.
+int upload_mesh(rich_sim *s, rich_step_info *info)
+{
+    const double t2 = now_ms();
     const rich::HostMesh &m = s->hm;
     const size_t T = (size_t)m.n_tris, E = (size_t)m.n_edges, d = sizeof(double);
     CUDA_TRY(upload(s->gx, m.gx, s->stream));
@@ -249,9 +269,6 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     CUDA_TRY(upload(s->cell_ptr, m.cell_ptr, s->stream));
     CUDA_TRY(upload(s->corder, m.cell_order, s->stream));
     CUDA_TRY(upload(s->slot_nb, m.slot_nb, s->stream));
-    // the triangle and edge lists are built on the device from the rings
-    // (the host sends each cell's first owned triangle and edge, and the
-    // ghosts' periodic shifts)
     CUDA_TRY(upload(s->toff, m.tri_off, s->stream));
     CUDA_TRY(upload(s->eoff, m.edge_off, s->stream));
     CUDA_TRY(upload(s->gshift, m.ghost_shift, s->stream));
@@ -279,20 +296,35 @@ int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
     CUDA_TRY(s->F.ensure((4 * E + 4) * sizeof(double)));
     CUDA_TRY(s->ePM.ensure((4 * E + 4) * r));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
-    double t3 = now_ms();
+    const double t3 = now_ms();
     if (bad_h[1]) return fail(RICH_ETESS, "a triangle of a ring is missing from its owner's ring");
     if (bad_h[0]) return fail(RICH_ETESS, "an edge of a ring has no partner in the other cell's ring");
     s->tess_current = true;
-    s->geometry_current = false;
     if (info) {
-        info->tess_ms += t2 - t1;
-        info->copy_ms += (t1 - t0) + (t3 - t2);
+        info->copy_ms += t3 - t2;
         info->n_ghost = m.g;
         info->n_tri = (int64_t)T;
         info->n_edges = (int64_t)E;
         info->n_slots = (int64_t)m.slot_nb.size();
     }
     return RICH_OK;
+}
+
+// host tessellation of the current points + upload of the connectivity
+int tessellate(rich_sim *s, rich_step_info *info, bool fetch_points)
+{
+    if (fetch_points) {
+        const double t0 = now_ms();
+        const int q = s->pts();
+        CUDA_TRY(cudaMemcpyAsync(s->hx(), s->x[q].p, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(s->hy(), s->y[q].p, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (info) info->copy_ms += now_ms() - t0;
+    }
+    s->tess_current = false;
+    int rc = build_mesh(s, info);
+    if (rc) return rc;
+    return upload_mesh(s, info);
 }
 
 }  // namespace
@@ -385,27 +417,32 @@ static int create_sim(const rich_config *cfg, int64_t n, const double *x, const 
         // renumber cells along a Hilbert curve for locality
         rich::hilbert_order(s->n, x, y, s->perm);
     }
-    s->hx.resize(n);
-    s->hy.resize(n);
-    std::vector<double> Fh(4 * (size_t)n);
-    for (int32_t k = 0; k < s->n; k++) {
-        int32_t u = s->perm[k];
-        s->hx[k] = x[u];
-        s->hy[k] = y[u];
-        for (int c = 0; c < 4; c++) Fh[(size_t)c * n + k] = f[c][u];
-    }
     int rc = RICH_OK;
     auto bail = [&](int code) { delete s; return code; };
+    if (s->hpts.ensure((2 * (size_t)n + 1) * sizeof(double)) != cudaSuccess)
+        return bail(fail(RICH_ENOMEM, "page-locked host points"));
+    std::vector<double> Fh(4 * (size_t)n);
+    double *hx = s->hx(), *hy = s->hy();
+    for (int32_t k = 0; k < s->n; k++) {
+        int32_t u = s->perm[k];
+        hx[k] = x[u];
+        hy[k] = y[u];
+        for (int c = 0; c < 4; c++) Fh[(size_t)c * n + k] = f[c][u];
+    }
     if (cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(RICH_ECUDA, "stream creation failed"));
     s->stream = s->own_stream;
-    if (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess)
+    if (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_moved, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_copied, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(RICH_ECUDA, "event creation failed"));
+    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(RICH_ECUDA, "stream creation failed"));
     if ((rc = alloc_cells(s)) != RICH_OK) return bail(rc);
     if (s->x[0].ensure(n * 8) != cudaSuccess) return bail(fail(RICH_ENOMEM, "device points"));
     if (upload(s->perm_dev, s->perm, s->stream) != cudaSuccess) return bail(fail(RICH_ENOMEM, "device order"));
-    cudaMemcpyAsync(s->x[0].p, s->hx.data(), n * 8, cudaMemcpyHostToDevice, s->stream);
-    cudaMemcpyAsync(s->y[0].p, s->hy.data(), n * 8, cudaMemcpyHostToDevice, s->stream);
+    cudaMemcpyAsync(s->x[0].p, hx, n * 8, cudaMemcpyHostToDevice, s->stream);
+    cudaMemcpyAsync(s->y[0].p, hy, n * 8, cudaMemcpyHostToDevice, s->stream);
     if ((rc = tessellate(s, nullptr, false)) != RICH_OK) return bail(rc);
     if (conserved) {
         if (cudaMemcpyAsync(s->U[0].p, Fh.data(), 4 * n * 8, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
@@ -501,7 +538,10 @@ int rich_tessellate(rich_sim *s, rich_step_info *info)
     return tessellate(s, info, true);
 }
 
-int rich_sweep(rich_sim *s, double t_end)
+// Launch the sweep; with read_points the moved points and the step's dt
+// are copied into hpts on the copy stream as soon as the point motion is
+// done (ev_copied marks their arrival) while the rest of the sweep runs.
+static int launch_sweep(rich_sim *s, double t_end, bool read_points)
 {
     rich::Range range("rich sweep launch (a1-a9)");
     if (!s) return fail(RICH_EINVAL, "NULL handle");
@@ -515,6 +555,16 @@ int rich_sweep(rich_sim *s, double t_end)
     for (int k = 0; k < rich::NUM_STAGES; k++) {
         if (s->profiling) CUDA_TRY(cudaEventRecord(s->kev[k], s->stream));
         s->launch(k, nullptr);
+        if (read_points && k == rich::K_ADVANCE) {
+            const size_t N = (size_t)s->n;
+            const int q = s->next_pts();
+            CUDA_TRY(cudaEventRecord(s->ev_moved, s->stream));
+            CUDA_TRY(cudaStreamWaitEvent(s->copy_stream, s->ev_moved, 0));
+            CUDA_TRY(cudaMemcpyAsync(s->hx(), s->x[q].p, N * 8, cudaMemcpyDeviceToHost, s->copy_stream));
+            CUDA_TRY(cudaMemcpyAsync(s->hy(), s->y[q].p, N * 8, cudaMemcpyDeviceToHost, s->copy_stream));
+            CUDA_TRY(cudaMemcpyAsync(s->hy() + N, s->scal.as<char>() + 8, 8, cudaMemcpyDeviceToHost, s->copy_stream));
+            CUDA_TRY(cudaEventRecord(s->ev_copied, s->copy_stream));
+        }
     }
     if (s->profiling) CUDA_TRY(cudaEventRecord(s->kev[rich::NUM_STAGES], s->stream));
     CUDA_TRY(cudaGetLastError());
@@ -522,6 +572,8 @@ int rich_sweep(rich_sim *s, double t_end)
     s->pending = true;
     return RICH_OK;
 }
+
+int rich_sweep(rich_sim *s, double t_end) { return launch_sweep(s, t_end, false); }
 
 int rich_sync(rich_sim *s, rich_step_info *info)
 {
@@ -580,23 +632,50 @@ int rich_sync(rich_sim *s, rich_step_info *info)
     return RICH_OK;
 }
 
+// One sweep of rich_step: while the device computes the gradients, fluxes
+// and update, the host builds the mesh of the moved points (which it reads
+// as soon as the point motion is done) unless the sweep ends the run at
+// t_end; after the sweep that mesh is uploaded.  A failed sweep leaves the
+// host mesh ahead of the device one: the next use tessellates again.
+static int pipelined_sweep(rich_sim *s, double t_end, rich_step_info *info)
+{
+    int rc = launch_sweep(s, t_end, true);
+    if (rc != RICH_OK) return rc;
+    const double t0 = now_ms();
+    CUDA_TRY(cudaEventSynchronize(s->ev_copied));
+    if (info) info->copy_ms += now_ms() - t0;
+    const double dt = s->hy()[s->n];
+    // the half-step points always get a mesh; after a full step, the points
+    // get one unless the step lands on t_end
+    const bool build = (s->time_centred() && s->tc_phase == 0) || dt < t_end - s->t;
+    int brc = RICH_OK;
+    if (build) {
+        s->tess_current = false;
+        brc = build_mesh(s, info);
+    }
+    rc = rich_sync(s, info);
+    if (rc != RICH_OK) return rc;
+    // (a mesh that could not be built is reported by the next step's
+    // tessellation of the same points, as without the early build)
+    if (!build || brc != RICH_OK) return RICH_OK;
+    return upload_mesh(s, info);
+}
+
 int rich_step(rich_sim *s, int32_t max_steps, double t_end, rich_step_info *info)
 {
     rich::Range range("rich step");
     if (!s) return fail(RICH_EINVAL, "NULL handle");
+    if (s->pending) return fail(RICH_ESTATE, "a sweep is pending; call rich_sync first");
     if (info) std::memset(info, 0, sizeof(*info));
     for (int32_t k = 0; k < max_steps; k++) {
         if (!(s->t < t_end)) break;
         int rc;
         if (!s->tess_current && (rc = tessellate(s, info, true)) != RICH_OK) return rc;
         double before = s->t;
-        if ((rc = rich_sweep(s, t_end)) != RICH_OK) return rc;
-        if ((rc = rich_sync(s, info)) != RICH_OK) return rc;
+        if ((rc = pipelined_sweep(s, t_end, info)) != RICH_OK) return rc;
         if (s->tc_phase == 1) {
-            // time-centred: the mesh of the half-step points, then the full step
-            if ((rc = tessellate(s, info, true)) != RICH_OK) return rc;
-            if ((rc = rich_sweep(s, t_end)) != RICH_OK) return rc;
-            if ((rc = rich_sync(s, info)) != RICH_OK) return rc;
+            // time-centred: the full step on the mesh of the half-step points
+            if ((rc = pipelined_sweep(s, t_end, info)) != RICH_OK) return rc;
         }
         if (s->last_dt >= t_end - before) s->t = t_end;  // landed on t_end
         if (info) info->t = s->t;
@@ -615,9 +694,12 @@ static int ensure_geometry(rich_sim *s)
         int rc = tessellate(s, nullptr, true);
         if (rc) return rc;
     }
-    for (int k = 0; k < rich::GEOMETRY_STAGES; k++) s->launch(k, nullptr);
+    for (int k = 0; k < rich::GEOMETRY_STAGES; k++) s->launch(k, nullptr, nullptr, false);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s->stream));
+    // the cell geometry and primitives now describe the current points
+    s->geometry_current = true;
+    s->diag_pts = s->pts();
     return RICH_OK;
 }
 
@@ -699,8 +781,9 @@ int rich_get_field(rich_sim *s, int32_t f, int64_t n, double *out)
     const size_t N = (size_t)s->n;
     std::vector<double> h, h2;
     int rc;
-    // the diagnostics refer to the points of the last sweep
-    const int prev = s->geometry_current && !s->tess_current ? s->diag_pts : s->pts();
+    // the diagnostics refer to the points of the last sweep (or of the last
+    // geometry pass on the current points)
+    const int prev = s->geometry_current ? s->diag_pts : s->pts();
     // gather component c of an array-of-structures field with `stride` values per cell
     auto comp_of = [&](const DBuf &b, int stride, int c) {
         int r2 = fetch_r(s, b.p, h2, stride * N);

@@ -20,6 +20,8 @@ namespace rich {
 namespace {
 
 constexpr int kBlock = 256;
+// threads per block of the point motion (a light, memory-bound pass)
+constexpr int kAdvanceBlock = 256;
 
 template <class R> __device__ __forceinline__ double px_of(const SweepParams<R> &p, int32_t q)
 {
@@ -137,6 +139,30 @@ __device__ __forceinline__ bool key_nonneg(float a) { return a >= 0.0f; }
 __device__ __forceinline__ bool key_nonpos(float a) { return a <= 0.0f; }
 __device__ __forceinline__ bool nonneg_less(float a, float b) { return a < b; }
 
+// Smallest non-negative cell time step of each simulation: a warp whose
+// cells all belong to one simulation reduces first and issues one atomic;
+// a mixed warp issues one atomic per lane.
+// The minimum is taken on the bits: non-negative doubles order like their
+// bit patterns, and a negative value, -0.0 or a negative NaN (negative as
+// an integer) is mapped past every candidate, as are +inf and positive NaNs
+// (above DBL_MAX's bits).
+__device__ __forceinline__ void warp_min_to(double v, int32_t inst, unsigned long long *dst)
+{
+    const long long kmax = __double_as_longlong(DBL_MAX);
+    long long k = __double_as_longlong(v);
+    if (k < 0) k = kmax;
+    const int32_t first = __shfl_sync(0xffffffffu, inst, 0);
+    if (__all_sync(0xffffffffu, inst == first)) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long q = __shfl_down_sync(0xffffffffu, k, o);
+            k = q < k ? q : k;
+        }
+        if ((threadIdx.x & 31) == 0 && k < kmax) atomicMin(dst + first, (unsigned long long)k);
+    } else if (k < kmax) {
+        atomicMin(dst + inst, (unsigned long long)k);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a1: circumcentre of every triangle touching a real cell (Voronoi vertices), FP64
 template <class R> __device__ __forceinline__ void stage_circumcentre(const SweepParams<R> &p, int32_t t)
@@ -151,9 +177,12 @@ template <class R> __device__ __forceinline__ void stage_circumcentre(const Swee
     p.ccy[t] = ay + (bx * c2 - cx * b2) * inv;
 }
 
+// (the first n_inst threads also clear the simulations' time-step minima,
+// which the geometry stage's cells then lower)
 template <class R> __global__ void k_circumcentre(SweepParams<R> p)
 {
     int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < p.n_inst) p.dtmin_bits[t] = 0x7f7f7f7f7f7f7f7full;
     if (t < p.T) stage_circumcentre(p, t);
 }
 
@@ -202,9 +231,12 @@ template <class R> __device__ __forceinline__ void stage_edge_geometry(const Swe
 
 
 // a1 + a2: area and centre of mass (shoelace about the generator, FP64),
-// then the primitive variables.  With init_W the conserved variables are set.
+// then the primitive variables; in a sweep also a5 (mesh velocity) and a6:
+// returns the cell's Courant time step R_i / (c_s + |v - w|) (DBL_MAX
+// outside a sweep).  With init_W the conserved variables are set.
 template <class R>
-__device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, const double *__restrict__ init_W, int32_t i)
+__device__ __forceinline__ double stage_cell_geometry(const SweepParams<R> &p, const double *__restrict__ init_W,
+                                                      int32_t i, int32_t &my_inst)
 {
     const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
     const double xi = p.x[i], yi = p.y[i];
@@ -255,23 +287,22 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
     // mass, d^2 > eta^2 A / pi (both sides non-negative, so no square roots).
     // Rounded cells settle at that distance, so the decision is taken in
     // FP64 in every precision.
-    {
-        const double eta = p.inst[inst_of(p, i)].eta;
-        p.rounding[i] = nonneg_less((eta * eta) * (A * (1.0 / M_PI)), ox * ox + oy * oy) ? 1 : 0;
-    }
+    my_inst = inst_of(p, i);
+    const InstParams &ip = p.inst[my_inst];
+    const bool rounding = nonneg_less((ip.eta * ip.eta) * (A * (1.0 / M_PI)), ox * ox + oy * oy);
+    p.rounding[i] = rounding ? 1 : 0;
     const int32_t n = p.n;
-    const InstParams &ip = p.inst[inst_of(p, i)];
     const double gamma = ip.gamma;
     const double gm1 = gamma - 1.0;
     if (init_W) {
-        if (!ip.init) return;
+        if (!ip.init) return DBL_MAX;
         double rho = init_W[i], vx = init_W[n + i], vy = init_W[2 * n + i], pr = init_W[3 * n + i];
         double m = rho * A;
         p.Un[i] = m;
         p.Un[n + i] = m * vx;
         p.Un[2 * n + i] = m * vy;
         p.Un[3 * n + i] = (pr / gm1 + 0.5 * rho * (vx * vx + vy * vy)) * A;
-        return;
+        return DBL_MAX;
     }
     double m = p.U[i], Px = p.U[n + i], Py = p.U[2 * n + i], E = p.U[3 * n + i];
     Vec4<R> W;
@@ -292,7 +323,29 @@ __device__ __forceinline__ void stage_cell_geometry(const SweepParams<R> &p, con
     p.W[i] = W;
     // c_s = sqrt(gamma p / rho) = gamma p / sqrt(gamma p rho): one reciprocal square root
     const R gp = to_R<R>(gamma) * W.w;
-    p.cs[i] = gp * rsqrt(gp * W.x);
+    const R cs = gp * rsqrt(gp * W.x);
+    p.cs[i] = cs;
+    if (!p.motion) return DBL_MAX;
+    // Section 6: mesh-generating point velocity, the fluid velocity plus,
+    // where the trigger is on, chi c_s towards the centre of mass
+    R wx = 0, wy = 0;
+    if (ip.motion == 0) {
+        wx = W.y;
+        wy = W.z;
+        if (rounding) {
+            const R oxr = to_R<R>(ox), oyr = to_R<R>(oy);
+            R f = to_R<R>(ip.chi) * cs * rsqrt(oxr * oxr + oyr * oyr);
+            wx += f * oxr;
+            wy += f * oyr;
+        }
+    }
+    p.w[i] = Vec2<R>{wx, wy};
+    // Courant step R_i / (c_s + |v - w|), R_i = sqrt(A/pi) = (A/pi) rsqrt(A/pi)
+    const R Api = to_R<R>(A) * (R(1) / R(M_PI));
+    const R Rad = Api * rsqrt(Api);
+    const R rx = W.y - wx, ry = W.z - wy;
+    const R speed = cs + sqrt_nonneg(rx * rx + ry * ry);
+    return to_d(Rad * recip(speed));
 }
 
 // a1 + a2 in one launch: the first edge_blocks blocks compute the edge
@@ -308,31 +361,11 @@ __global__ void k_geometry(SweepParams<R> p, const double *__restrict__ init_W, 
         if (e < p.E) stage_edge_geometry(p, e);
     } else {
         int32_t k = (blockIdx.x - edge_blocks) * blockDim.x + threadIdx.x;
-        if (k < p.n) stage_cell_geometry(p, init_W, cell_at(p, k));
-    }
-}
-
-// Smallest non-negative cell time step of each simulation: a warp whose
-// cells all belong to one simulation reduces first and issues one atomic;
-// a mixed warp issues one atomic per lane.
-// The minimum is taken on the bits: non-negative doubles order like their
-// bit patterns, and a negative value, -0.0 or a negative NaN (negative as
-// an integer) is mapped past every candidate, as are +inf and positive NaNs
-// (above DBL_MAX's bits).
-__device__ __forceinline__ void warp_min_to(double v, int32_t inst, unsigned long long *dst)
-{
-    const long long kmax = __double_as_longlong(DBL_MAX);
-    long long k = __double_as_longlong(v);
-    if (k < 0) k = kmax;
-    const int32_t first = __shfl_sync(0xffffffffu, inst, 0);
-    if (__all_sync(0xffffffffu, inst == first)) {
-        for (int o = 16; o > 0; o >>= 1) {
-            const long long q = __shfl_down_sync(0xffffffffu, k, o);
-            k = q < k ? q : k;
-        }
-        if ((threadIdx.x & 31) == 0 && k < kmax) atomicMin(dst + first, (unsigned long long)k);
-    } else if (k < kmax) {
-        atomicMin(dst + inst, (unsigned long long)k);
+        double dt_cell = DBL_MAX;
+        int32_t my_inst = 0;
+        if (k < p.n) dt_cell = stage_cell_geometry(p, init_W, cell_at(p, k), my_inst);
+        // (init_W and motion are the same for the whole grid)
+        if (!init_W && p.motion) warp_min_to(dt_cell, my_inst, p.dtmin_bits);
     }
 }
 
@@ -371,17 +404,15 @@ template <class R> struct GlobalSlots {
     }
 };
 
-// a3-a6: Green-Gauss gradient (Eq. 1), limiter with the shock switch
-// (Eqs. 3-8), cell-rounding mesh velocity (Section 6), per-cell time step,
-// for cell i whose ring slots are [lo, hi) of the accessor `sl`.
+// a3-a4: Green-Gauss gradient (Eq. 1), limiter with the shock switch
+// (Eqs. 3-8), and the cell terms of the half-step prediction, for cell i
+// whose ring slots are [lo, hi) of the accessor `sl`.
 template <class R, class Slots>
-__device__ __forceinline__ double stage_cell_gradient(const SweepParams<R> &p, int32_t i, int32_t lo, int32_t hi,
-                                                      const Slots &sl, int32_t &my_inst)
+__device__ __forceinline__ void stage_cell_gradient(const SweepParams<R> &p, int32_t i, int32_t lo, int32_t hi,
+                                                    const Slots &sl)
 {
-    double dt_cell = DBL_MAX;
     {
-        my_inst = inst_of(p, i);
-        const InstParams &ip = p.inst[my_inst];
+        const InstParams &ip = p.inst[inst_of(p, i)];
         const Vec4<R> W4 = p.W[i];
         const R Wi[4] = {W4.x, W4.y, W4.z, W4.w};
         R acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -512,28 +543,12 @@ __device__ __forceinline__ double stage_cell_gradient(const SweepParams<R> &p, i
                 else if (bd[v] > R(0) && tn < bd[v]) { an[v] = tn; ad[v] = bd[v]; lim[v] = true; }
             }
         }
-        // Section 6: mesh-generating point velocity
-        R wx = 0, wy = 0;
-        if (ip.motion == 0) {
-            wx = Wi[1];
-            wy = Wi[2];
-            if (p.rounding[i]) {
-                R f = to_R<R>(ip.chi) * cs * rsqrt(ox * ox + oy * oy);
-                wx += f * ox;
-                wy += f * oy;
-            }
-        }
-        p.w[i] = Vec2<R>{wx, wy};
-        const R rx = Wi[1] - wx, ry = Wi[2] - wy;
-        const R speed = cs + sqrt_nonneg(rx * rx + ry * ry);
-        // the cell's six quotients (alpha of each variable, 1/rho for the
-        // prediction terms, R_i over the Courant speed), each through one
-        // refined reciprocal
+        // the cell's five quotients (alpha of each variable, 1/rho for the
+        // prediction terms), each through one refined reciprocal
         R alpha[4];
 #pragma unroll
         for (int v = 0; v < 4; v++) alpha[v] = lim[v] ? an[v] * recip(ad[v]) : R(1);
         const R irho = recip(Wi[0]);
-        const R cdt = Rad * recip(speed);
         R lg[8];
 #pragma unroll
         for (int c = 0; c < 8; c++) lg[c] = alpha[c >> 1] * g[c];
@@ -551,9 +566,7 @@ __device__ __forceinline__ double stage_cell_gradient(const SweepParams<R> &p, i
             p.alpha[i] = Vec4<R>{alpha[0], alpha[1], alpha[2], alpha[3]};
             p.tess[i] = use_tess ? 1 : 0;
         }
-        dt_cell = to_d(cdt);
     }
-    return dt_cell;
 }
 
 // launched in blocks of 128 threads; six blocks per SM cap the FP64 build at
@@ -569,13 +582,10 @@ __device__ __forceinline__ double stage_cell_gradient(const SweepParams<R> &p, i
 template <class R> __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 9 : 6) k_cell_gradient(SweepParams<R> p)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    double dt_cell = DBL_MAX;
-    int32_t my_inst = 0;
     if (k < p.n) {
         const int32_t i = sizeof(R) == sizeof(double) ? cell_at(p, k) : k;
-        dt_cell = stage_cell_gradient(p, i, p.cell_ptr[i], p.cell_ptr[i + 1], GlobalSlots<R>{p}, my_inst);
+        stage_cell_gradient(p, i, p.cell_ptr[i], p.cell_ptr[i + 1], GlobalSlots<R>{p});
     }
-    warp_min_to(dt_cell, my_inst, p.dtmin_bits);
 }
 
 template <class R> __device__ __forceinline__ double step_dt(const SweepParams<R> &p, int32_t inst)
@@ -731,16 +741,59 @@ template <class R> __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 16 : 
     if (e < p.E) stage_edge_flux(p, e);
 }
 
-// a8 + a9: conservative update in FP64 (fixed CSR order, no atomics),
-// advance the generating points in FP64
+// a9: advance the generating points in FP64, x <- x0 + hdt w, wrapped
+// across a periodic box or mirrored back across a rigid wall.  The step's dt
+// is final once every cell's Courant candidate is in (after the geometry
+// stage); the first cell of each simulation records it.
+template <class R> __device__ __forceinline__ void stage_advance(const SweepParams<R> &p, int32_t i)
+{
+    const int32_t my_inst = inst_of(p, i);
+    const InstParams &ip = p.inst[my_inst];
+    const double dt = step_dt(p, my_inst);
+    if (ip.phase != 2 && (i == 0 || inst_of(p, i - 1) != my_inst)) p.dt_out[my_inst] = dt;
+    // the first sweep of the time-centred scheme moves the points half a step
+    const double hdt = ip.phase == 1 ? 0.5 * dt : dt;
+    // the box tests compare bit patterns on the integer pipe (dkey orders doubles)
+    int32_t st = 0;
+    const Vec2<R> w = p.w[i];
+    double xn = p.x0[i] + hdt * to_d(w.x), yn = p.y0[i] + hdt * to_d(w.y);
+    const long long kx0 = dkey0(ip.x0), kx1 = dkey0(ip.x1), ky0 = dkey0(ip.y0), ky1 = dkey0(ip.y1);
+    long long kx = dkey0(xn), ky = dkey0(yn);
+    if (ip.boundary == 1) {
+        const double Lx = ip.x1 - ip.x0, Ly = ip.y1 - ip.y0;
+        if (kx < kx0) xn += Lx;
+        else if (kx >= kx1) xn -= Lx;
+        if (ky < ky0) yn += Ly;
+        else if (ky >= ky1) yn -= Ly;
+    } else {
+        // a point that crossed a rigid wall comes back as its mirror image
+        if (kx <= kx0) xn = (ip.x0 + ip.x0) - xn;
+        else if (kx >= kx1) xn = (ip.x1 + ip.x1) - xn;
+        if (ky <= ky0) yn = (ip.y0 + ip.y0) - yn;
+        else if (ky >= ky1) yn = (ip.y1 + ip.y1) - yn;
+        kx = dkey0(xn);
+        ky = dkey0(yn);
+        if (!(kx > kx0 && kx < kx1 && ky > ky0 && ky < ky1)) st |= ST_LEFT_BOX;
+    }
+    p.xn[i] = xn;
+    p.yn[i] = yn;
+    if (st) atomicOr(p.status + my_inst, st);
+}
+
+template <class R> __global__ void __launch_bounds__(kAdvanceBlock) k_advance_points(SweepParams<R> p)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < p.n) stage_advance(p, i);
+}
+
+// a8: conservative update in FP64 (fixed CSR order, no atomics)
 template <class R> __device__ __forceinline__ void stage_cell_update(const SweepParams<R> &p, int32_t i)
 {
     const int32_t n = p.n;
     const int32_t my_inst = inst_of(p, i);
     const InstParams &ip = p.inst[my_inst];
     const double dt = step_dt(p, my_inst);
-    if (ip.phase != 2 && (i == 0 || inst_of(p, i - 1) != my_inst)) p.dt_out[my_inst] = dt;
-    // the first sweep of the time-centred scheme moves state and points half a step
+    // the first sweep of the time-centred scheme moves the state half a step
     const double hdt = ip.phase == 1 ? 0.5 * dt : dt;
     const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -766,9 +819,9 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
     p.Un[n + i] = Px;
     p.Un[2 * n + i] = Py;
     p.Un[3 * n + i] = E;
-    // the checks and the box tests compare bit patterns on the integer pipe:
-    // a double is not finite when its exponent bits are all set, positive
-    // when its bits are positive as an integer, and dkey orders doubles
+    // the checks compare bit patterns on the integer pipe: a double is not
+    // finite when its exponent bits are all set, positive when its bits are
+    // positive as an integer
     int32_t st = 0;
     {
         const long long bm = __double_as_longlong(m), bx = __double_as_longlong(Px);
@@ -777,28 +830,6 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
         if ((bm & ex) == ex || (bx & ex) == ex || (by & ex) == ex || (be & ex) == ex) st |= ST_NAN;
         else if (!(bm > 0) || !(__double_as_longlong(2.0 * m * E - (Px * Px + Py * Py)) > 0)) st |= ST_NEGATIVE;
     }
-    const Vec2<R> w = p.w[i];
-    double xn = p.x0[i] + hdt * to_d(w.x), yn = p.y0[i] + hdt * to_d(w.y);
-    const long long kx0 = dkey0(ip.x0), kx1 = dkey0(ip.x1), ky0 = dkey0(ip.y0), ky1 = dkey0(ip.y1);
-    long long kx = dkey0(xn), ky = dkey0(yn);
-    if (ip.boundary == 1) {
-        const double Lx = ip.x1 - ip.x0, Ly = ip.y1 - ip.y0;
-        if (kx < kx0) xn += Lx;
-        else if (kx >= kx1) xn -= Lx;
-        if (ky < ky0) yn += Ly;
-        else if (ky >= ky1) yn -= Ly;
-    } else {
-        // a point that crossed a rigid wall comes back as its mirror image
-        if (kx <= kx0) xn = (ip.x0 + ip.x0) - xn;
-        else if (kx >= kx1) xn = (ip.x1 + ip.x1) - xn;
-        if (ky <= ky0) yn = (ip.y0 + ip.y0) - yn;
-        else if (ky >= ky1) yn = (ip.y1 + ip.y1) - yn;
-        kx = dkey0(xn);
-        ky = dkey0(yn);
-        if (!(kx > kx0 && kx < kx1 && ky > ky0 && ky < ky1)) st |= ST_LEFT_BOX;
-    }
-    p.xn[i] = xn;
-    p.yn[i] = yn;
     if (st) atomicOr(p.status + my_inst, st);
 }
 
@@ -865,17 +896,19 @@ __global__ void __launch_bounds__(512) k_sweep_persistent(SweepParams<R> p, cons
     for (int32_t t = tid; t < p.T; t += stride) stage_circumcentre(p, t);
     if (!grid_sync(gs, nb, lim)) return;
     for (int32_t e = tid; e < p.E; e += stride) stage_edge_geometry(p, e);
-    for (int32_t k = tid; k < p.n; k += stride) stage_cell_geometry(p, (const double *)nullptr, cell_at(p, k));
-    if (!grid_sync(gs, nb, lim)) return;
+    // (whole warps through the cell loop, for the warp-wide dt minimum)
     for (int32_t base = blockIdx.x * blockDim.x; base < p.n; base += stride) {
         const int32_t k = base + threadIdx.x;
         double v = DBL_MAX;
         int32_t inst = 0;
-        if (k < p.n) {
-            const int32_t i = cell_at(p, k);
-            v = stage_cell_gradient(p, i, p.cell_ptr[i], p.cell_ptr[i + 1], GlobalSlots<R>{p}, inst);
-        }
+        if (k < p.n) v = stage_cell_geometry(p, (const double *)nullptr, cell_at(p, k), inst);
         warp_min_to(v, inst, p.dtmin_bits);
+    }
+    if (!grid_sync(gs, nb, lim)) return;
+    for (int32_t i = tid; i < p.n; i += stride) stage_advance(p, i);
+    for (int32_t k = tid; k < p.n; k += stride) {
+        const int32_t i = cell_at(p, k);
+        stage_cell_gradient(p, i, p.cell_ptr[i], p.cell_ptr[i + 1], GlobalSlots<R>{p});
     }
     if (!grid_sync(gs, nb, lim)) return;
     for (int32_t e = tid; e < p.E; e += stride) stage_edge_flux(p, e);
@@ -1022,7 +1055,7 @@ inline int blocks(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 // from 0.77x to 1.17x of the mean).  Chosen by timing 32, 64, 128 and 256 on
 // GB300 (Sedov, 262,144 cells): the gradient and flux stages, whose register
 // counts cap an SM at 16-21 warps, run best at 128, the others at 32.
-constexpr int kStageBlock[NUM_STAGES] = {32, 32, 0, 128, 128, 32};
+constexpr int kStageBlock[NUM_STAGES] = {32, 32, kAdvanceBlock, 128, 128, 32};
 static_assert(kStageBlock[K_CELL_GRADIENT] == 128 && kStageBlock[K_EDGE_FLUX] == 128,
               "the gradient's and flux's launch bounds assume 128 threads");
 inline int stage_block(int k) { return kStageBlock[k]; }
@@ -1032,7 +1065,7 @@ inline int nblk(int64_t n, int k) { return (int)((n + stage_block(k) - 1) / stag
 
 const char *stage_name(int k)
 {
-    static const char *names[NUM_STAGES] = {"k_circumcentre", "k_geometry", "dt_reset", "k_cell_gradient",
+    static const char *names[NUM_STAGES] = {"k_circumcentre", "k_geometry", "k_advance_points", "k_cell_gradient",
                                             "k_edge_flux", "k_cell_update"};
     return k >= 0 && k < NUM_STAGES ? names[k] : "";
 }
@@ -1040,16 +1073,18 @@ const char *stage_name(int k)
 template <class R> void launch_stage(int k, const SweepParams<R> &p, const double *init_W, cudaStream_t st)
 {
     switch (k) {
-    case K_CIRCUMCENTRE:
-        if (p.T > 0) k_circumcentre<R><<<nblk(p.T, K_CIRCUMCENTRE), stage_block(K_CIRCUMCENTRE), 0, st>>>(p);
+    case K_CIRCUMCENTRE: {
+        const int32_t m = p.T > p.n_inst ? p.T : p.n_inst;
+        if (m > 0) k_circumcentre<R><<<nblk(m, K_CIRCUMCENTRE), stage_block(K_CIRCUMCENTRE), 0, st>>>(p);
         break;
+    }
     case K_GEOMETRY: {
         const int eb = nblk(p.E, K_GEOMETRY), cb = nblk(p.n, K_GEOMETRY);
         if (eb + cb > 0) k_geometry<R><<<eb + cb, stage_block(K_GEOMETRY), 0, st>>>(p, init_W, eb);
         break;
     }
-    case K_DT_RESET:
-        cudaMemsetAsync(p.dtmin_bits, 0x7f, sizeof(unsigned long long) * p.n_inst, st);
+    case K_ADVANCE:
+        if (p.n > 0) k_advance_points<R><<<nblk(p.n, K_ADVANCE), stage_block(K_ADVANCE), 0, st>>>(p);
         break;
     case K_CELL_GRADIENT:
         if (p.n > 0) k_cell_gradient<R><<<nblk(p.n, K_CELL_GRADIENT), stage_block(K_CELL_GRADIENT), 0, st>>>(p);

@@ -75,6 +75,10 @@ template <class R> struct SweepParams {
     const InstParams *inst;
     const int32_t *cell_inst;
     int32_t n_inst, diagnostics;
+    // 1 in a sweep, where the geometry stage also takes the mesh velocity
+    // and the Courant candidates (a5, a6); 0 when only the geometry of the
+    // current points is wanted (the last sweep's velocities are kept)
+    int32_t motion;
     // sizes (all simulations together)
     int32_t n, ng, T, E, S;
     // points (current and next), FP64
@@ -118,16 +122,21 @@ template <class R> struct SweepParams {
 };
 
 // Stages of one step, in launch order.  GEOMETRY_STAGES = a1 + a2;
-// the remaining stages are a3-a9.
+// the remaining stages are a9 and a3-a8.  The points' motion needs only the
+// mesh velocity and the step's dt, both known once the geometry stage is
+// done, so the new points are written before the gradients and fluxes:
+// a caller can read them, and build the next mesh on the host, while the
+// rest of the sweep runs.
 enum Stage : int {
-    K_CIRCUMCENTRE = 0,   // a1 Voronoi vertices
+    K_CIRCUMCENTRE = 0,   // a1 Voronoi vertices (and clears the time-step minimum)
     K_GEOMETRY = 1,       // a1 + a2 in one launch: per-edge L, midpoint, normal,
                           // c_ij/|r_ij| (the first blocks) and per-cell area,
-                          // centre of mass, primitives (the rest)
-    K_DT_RESET = 2,       // clears the time-step minimum (memset, not a kernel)
-    K_CELL_GRADIENT = 3,  // a3-a6 gradients, limiter, mesh velocity, dt
+                          // centre of mass, primitives, then (in a sweep) a5
+                          // mesh velocity and a6 Courant candidates (the rest)
+    K_ADVANCE = 2,        // a9 point motion, dt recorded
+    K_CELL_GRADIENT = 3,  // a3-a4 gradients, limiter, prediction terms
     K_EDGE_FLUX = 4,      // a7 predicted edge states + HLLC
-    K_CELL_UPDATE = 5,    // a8 + a9 conservative update, point motion
+    K_CELL_UPDATE = 5,    // a8 conservative update
     NUM_STAGES = 6,
     GEOMETRY_STAGES = 2,
 };
@@ -157,7 +166,8 @@ struct GridSync {
 // The whole step a1-a9 in one cooperative launch of `grid` blocks of `block`
 // threads (grid <= co-resident blocks): grid-stride loops over triangles,
 // edges and cells, separated by four grid barriers whose waits give up after
-// about a second (GridSync::timeout).
+// about a second (GridSync::timeout); the point motion runs beside the
+// gradients, between the second and third barriers.
 template <class R>
 cudaError_t launch_persistent(const SweepParams<R> &p, const DeviceSizes *sizes, GridSync *sync, int block, int grid,
                               cudaStream_t st);

@@ -81,6 +81,12 @@ def test_sedov_fails_at_the_oracles_step(R):
     assert abs(t - t_before) <= 1e-12 * t_before, (t, t_before)
     c = sim.conserved()  # the last good state is kept
     assert np.all(c["m"] > 0)
+    # the failed step's moved points were read back and meshed on the host
+    # ahead of the device; a read of the state meshes the last good points
+    # again, and their cells tile the box
+    st = sim.state()
+    assert abs(float(np.sum(st["area"])) - 1.0) <= 1e-12
+    assert np.array_equal(st["x"], c["x"]) and np.array_equal(st["y"], c["y"])
     sim.close()
 
 
