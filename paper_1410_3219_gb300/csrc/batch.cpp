@@ -56,6 +56,9 @@ struct BatchSim {
     rich::MeshWork mw;           // (edge lists built on the device, packed)
     rich::HostMesh hm;
     int mesh_rc = 0;
+    // the mesh of its current points was built during the last step's sweep
+    // (mesh_rc is that build's result)
+    bool prebuilt = false;
     double t = 0.0, t_end = 0.0, last_dt = 0.0;
     int64_t steps = 0, max_steps = 0;
     int state = PENDING;
@@ -100,6 +103,12 @@ struct rich_batch {
     rich::ThreadPool *pool = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // early read of a staged sweep's moved points and time steps (copied on
+    // their own stream once the point motion is done) into page-locked
+    // memory: x, y of the packed cells, then dt per simulation
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_moved = nullptr, ev_copied = nullptr;
+    rich::HBuf h_moved;
     bool diagnostics = false;
     int cur = 0;
     // device
@@ -150,8 +159,12 @@ struct rich_batch {
             if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
             if (graph[k]) cudaGraphDestroy(graph[k]);
         }
+        if (copy_stream) cudaStreamSynchronize(copy_stream);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        if (ev_moved) cudaEventDestroy(ev_moved);
+        if (ev_copied) cudaEventDestroy(ev_copied);
+        if (copy_stream) cudaStreamDestroy(copy_stream);
         if (stream) cudaStreamDestroy(stream);
     }
 
@@ -223,8 +236,8 @@ rich::InstParams inst_params(const BatchSim &s, bool init)
 {
     rich::InstParams ip{};
     const rich_config &c = s.cfg;
-    ip.gamma = c.gamma; ip.igm1 = 1.0 / (c.gamma - 1.0); ip.cfl = c.cfl; ip.chi = c.chi; ip.eta = c.eta; ip.theta = c.theta;
-    ip.delta_v = c.delta_v; ip.delta_p = c.delta_p;
+    ip.gamma = c.gamma; ip.igm1 = 1.0 / (c.gamma - 1.0); ip.gamma_f = (float)ip.gamma; ip.igm1_f = (float)ip.igm1; ip.cfl = c.cfl; ip.chi = c.chi; ip.eta = c.eta; ip.theta = c.theta;
+    ip.delta_v = c.delta_v; ip.delta_p = c.delta_p; ip.chi_f = (float)ip.chi; ip.theta_f = (float)ip.theta; ip.delta_v_f = (float)ip.delta_v;
     ip.x0 = c.x0; ip.x1 = c.x1; ip.y0 = c.y0; ip.y1 = c.y1;
     ip.remaining = s.t_end - s.t;
     ip.boundary = c.boundary; ip.motion = c.motion; ip.limiter = c.limiter;
@@ -433,10 +446,25 @@ template <class R> int run_persistent(rich_batch *b, int block)
     return RICH_OK;
 }
 
-int run_staged(rich_batch *b)
+// The sweep stage by stage; with read_moved the moved points and each
+// simulation's dt are copied into h_moved as soon as the point motion is
+// done (ev_copied marks their arrival) while the other stages run.
+int run_staged(rich_batch *b, bool read_moved = false)
 {
     CUDA_TRY(cudaMemsetAsync(b->status.p, 0, b->status.cap, b->stream));
-    for (int k = 0; k < rich::NUM_STAGES; k++) b->launch(k, nullptr);
+    for (int k = 0; k < rich::NUM_STAGES; k++) {
+        b->launch(k, nullptr);
+        if (read_moved && k == rich::K_ADVANCE) {
+            const size_t N = (size_t)b->n_packed, I = b->packed.size();
+            double *h = b->h_moved.as<double>();
+            CUDA_TRY(cudaEventRecord(b->ev_moved, b->stream));
+            CUDA_TRY(cudaStreamWaitEvent(b->copy_stream, b->ev_moved, 0));
+            CUDA_TRY(cudaMemcpyAsync(h, b->x[1 - b->cur].p, N * 8, cudaMemcpyDeviceToHost, b->copy_stream));
+            CUDA_TRY(cudaMemcpyAsync(h + N, b->y[1 - b->cur].p, N * 8, cudaMemcpyDeviceToHost, b->copy_stream));
+            CUDA_TRY(cudaMemcpyAsync(h + 2 * N, b->dtout.p, I * 8, cudaMemcpyDeviceToHost, b->copy_stream));
+            CUDA_TRY(cudaEventRecord(b->ev_copied, b->copy_stream));
+        }
+    }
     CUDA_TRY(cudaGetLastError());
     b->staged_launches++;
     return RICH_OK;
@@ -494,7 +522,10 @@ int batch_create(int32_t precision, int64_t max_cells, int32_t host_threads, Thr
     b->precision = precision;
     b->max_cells = max_cells;
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_moved, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_copied, cudaEventDisableTiming) != cudaSuccess) {
         delete b;
         return fail(RICH_ECUDA, "stream or event creation failed");
     }
@@ -562,14 +593,47 @@ int rich_batch_add(rich_batch *b, const rich_config *cfg, int64_t n, const doubl
 // whole pool (four or more tiles of 16,384 points).
 constexpr int32_t kTiledMember = 65536;
 
+namespace {
+// a0 for the given simulations on the pool, from the points in their hx, hy
+// (results in mesh_rc): largest first, since the pool hands out tasks in
+// order, so the longest tessellations start first and the makespan stays
+// near the largest one (or the mean load per thread).  A simulation large
+// enough for several tiles is tessellated with the whole pool (its tiles in
+// parallel, as a single simulation is), one after another; the others in
+// parallel, one per pool thread.  The mesh the sweep sees does not depend
+// on the tiling.
+void tessellate_members(rich_batch *b, const std::vector<BatchSim *> &sims)
+{
+    rich::Range range("rich batch tessellate (a0)");
+    std::vector<BatchSim *> by_size(sims);
+    std::stable_sort(by_size.begin(), by_size.end(), [](const BatchSim *a, const BatchSim *c) { return a->n > c->n; });
+    size_t n_large = 0;
+    while (n_large < by_size.size() && by_size[n_large]->n >= kTiledMember) n_large++;
+    for (size_t k = 0; k < n_large; k++) {
+        BatchSim *s = by_size[k];
+        rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
+        s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm, b->pool);
+    }
+    b->pool->parallel_for((int64_t)(by_size.size() - n_large), [&](int64_t k) {
+        BatchSim *s = by_size[n_large + k];
+        rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
+        s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm);
+    });
+}
+
+}  // namespace
+
 int rich_batch_step(rich_batch *b, rich_step_info *info)
 {
     rich::Range range("rich batch step");
     if (!b) return fail(RICH_EINVAL, "NULL handle");
     if (info) std::memset(info, 0, sizeof(*info));
     const double t0 = now_ms();
-    // 1. points of the running simulations back to the host
-    if (b->n_packed > 0 && !b->packed.empty()) {
+    // 1. points of the running simulations back to the host (those whose
+    //    mesh was built during the last sweep have them already)
+    bool need_points = false;
+    for (BatchSim *s : b->packed) need_points |= s->state == RUNNING && !s->prebuilt;
+    if (b->n_packed > 0 && need_points) {
         // (kept between steps: a fresh vector would zero 16 B per cell first)
         std::vector<double> &hx = b->h_dlx, &hy = b->h_dly;
         if (hx.size() < (size_t)b->n_packed) {
@@ -582,7 +646,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
         // to each simulation's own arrays, on the pool
         b->pool->parallel_for((int64_t)b->packed.size(), [&](int64_t k) {
             BatchSim *s = b->packed[k];
-            if (s->state != RUNNING) return;
+            if (s->state != RUNNING || s->prebuilt) return;
             std::memcpy(s->hx.data(), &hx[s->cell_off], sizeof(double) * s->n);
             std::memcpy(s->hy.data(), &hy[s->cell_off], sizeof(double) * s->n);
         });
@@ -599,32 +663,15 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
         b->n_packed = 0;
         return RICH_OK;
     }
-    // 2. tessellations in parallel
+    // 2. tessellations in parallel (of the simulations without a mesh
+    //    built during the last sweep)
     const double t1 = now_ms();
-    // largest first: the pool hands out tasks in order, so the longest
-    // tessellations start first and the step's makespan stays near the
-    // largest one (or the mean load per thread)
-    std::vector<int32_t> by_size(list.size());
-    for (size_t k = 0; k < list.size(); k++) by_size[k] = (int32_t)k;
-    std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t c) { return list[a]->n > list[c]->n; });
     {
-        rich::Range range("rich batch tessellate (a0)");
-        // a simulation large enough for several tiles is tessellated with the
-        // whole pool (its tiles in parallel, as a single simulation is), one
-        // after another; the others in parallel, one per pool thread.  The
-        // mesh the sweep sees does not depend on the tiling.
-        size_t n_large = 0;
-        while (n_large < by_size.size() && list[by_size[n_large]]->n >= kTiledMember) n_large++;
-        for (size_t k = 0; k < n_large; k++) {
-            BatchSim *s = list[by_size[k]];
-            rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
-            s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm, b->pool);
-        }
-        b->pool->parallel_for((int64_t)(list.size() - n_large), [&](int64_t k) {
-            BatchSim *s = list[by_size[n_large + k]];
-            rich::BoxConfig box{s->cfg.boundary, s->cfg.x0, s->cfg.x1, s->cfg.y0, s->cfg.y1};
-            s->mesh_rc = rich::build_host_mesh(box, s->n, s->hx.data(), s->hy.data(), s->mw, s->hm);
-        });
+        std::vector<BatchSim *> todo;
+        for (BatchSim *s : list)
+            if (!s->prebuilt) todo.push_back(s);
+        tessellate_members(b, todo);
+        for (BatchSim *s : list) s->prebuilt = false;
     }
     const double t2 = now_ms();
     std::vector<BatchSim *> ok;
@@ -756,16 +803,43 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
         CUDA_TRY(upload(b->instp, b->h_inst, b->stream));
     }
     const double t3 = now_ms();
-    // 6. the sweep over every cell of every simulation
+    // 6. the sweep over every cell of every simulation; staged, its moved
+    //    points are read back once the point motion is done, and the host
+    //    tessellates them for the next step while the device finishes
     const LaunchShape shape = pick_shape(b);
+    if (!shape.persistent) CUDA_TRY(b->h_moved.ensure((2 * N + ok.size()) * sizeof(double)));
     CUDA_TRY(cudaEventRecord(b->ev0, b->stream));
     if (shape.persistent) {
         rc = b->precision == RICH_FP32_SPLIT ? run_persistent<float>(b, shape.block) : run_persistent<double>(b, shape.block);
     } else {
-        rc = run_staged(b);
+        rc = run_staged(b, true);
     }
     if (rc) return rc;
     CUDA_TRY(cudaEventRecord(b->ev1, b->stream));
+    double t_pre = 0.0;
+    if (!shape.persistent) {
+        CUDA_TRY(cudaEventSynchronize(b->ev_copied));
+        const double tp = now_ms();
+        const double *h = b->h_moved.as<double>();
+        // the simulations that go on after this step (the bookkeeping below
+        // takes the same decision), unless the step fails
+        std::vector<BatchSim *> next;
+        for (size_t k = 0; k < ok.size(); k++) {
+            BatchSim *s = ok[k];
+            const double dt = h[2 * N + k], rem = s->t_end - s->t;
+            const double tn = dt >= rem ? s->t_end : s->t + dt;
+            if (tn >= s->t_end || s->steps + 1 >= s->max_steps) continue;
+            next.push_back(s);
+        }
+        b->pool->parallel_for((int64_t)next.size(), [&](int64_t k) {
+            BatchSim *s = next[k];
+            std::memcpy(s->hx.data(), h + s->cell_off, sizeof(double) * s->n);
+            std::memcpy(s->hy.data(), h + N + s->cell_off, sizeof(double) * s->n);
+        });
+        tessellate_members(b, next);
+        for (BatchSim *s : next) s->prebuilt = true;
+        t_pre = now_ms() - tp;
+    }
     if (shape.persistent) {
         int32_t timeout = 0;
         CUDA_TRY(cudaMemcpyAsync(&timeout, (char *)b->gsync.p + offsetof(rich::GridSync, timeout), 4,
@@ -796,6 +870,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     for (size_t k = 0; k < ok.size(); k++) {
         BatchSim *s = ok[k];
         if (b->h_status[k]) {
+            s->prebuilt = false;
             s->err = (b->h_status[k] & rich::ST_NAN) ? RICH_ENAN : RICH_ENEGATIVE;
             s->err_msg = "step rejected (non-finite, non-positive mass or thermal energy, or a point left the box)";
             finish_copy_out(b, *s, b->cur);
@@ -820,7 +895,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     if (info) {
         info->steps_done = (int64_t)ok.size();
         info->sweep_ms = ms;
-        info->tess_ms = t2 - t1;
+        info->tess_ms = (t2 - t1) + t_pre;
         info->copy_ms = (t1 - t0) + (t3 - t2) + (now_ms() - tnow);
         info->n_ghost = b->nG;
         info->n_tri = b->nT;

@@ -189,8 +189,8 @@ struct rich_sim {
     {
         rich::InstParams ip{};
         ip.init = init ? 1 : 0;
-        ip.gamma = cfg.gamma; ip.igm1 = 1.0 / (cfg.gamma - 1.0); ip.cfl = cfg.cfl; ip.chi = cfg.chi; ip.eta = cfg.eta; ip.theta = cfg.theta;
-        ip.delta_v = cfg.delta_v; ip.delta_p = cfg.delta_p;
+        ip.gamma = cfg.gamma; ip.igm1 = 1.0 / (cfg.gamma - 1.0); ip.gamma_f = (float)ip.gamma; ip.igm1_f = (float)ip.igm1; ip.cfl = cfg.cfl; ip.chi = cfg.chi; ip.eta = cfg.eta; ip.theta = cfg.theta;
+        ip.delta_v = cfg.delta_v; ip.delta_p = cfg.delta_p; ip.chi_f = (float)ip.chi; ip.theta_f = (float)ip.theta; ip.delta_v_f = (float)ip.delta_v;
         ip.x0 = cfg.x0; ip.x1 = cfg.x1; ip.y0 = cfg.y0; ip.y1 = cfg.y1;
         ip.remaining = remaining;
         ip.boundary = cfg.boundary; ip.motion = cfg.motion; ip.limiter = cfg.limiter;

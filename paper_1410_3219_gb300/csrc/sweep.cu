@@ -23,6 +23,12 @@ constexpr int kBlock = 256;
 // threads per block of the point motion (a light, memory-bound pass)
 constexpr int kAdvanceBlock = 256;
 
+// A per-simulation constant in the reconstruction precision (the FP32 copy
+// rounded by the host: no conversion per thread)
+template <class R> __device__ __forceinline__ R inst_value(double d, float f);
+template <> __device__ __forceinline__ double inst_value<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float inst_value<float>(double, float f) { return f; }
+
 template <class R> __device__ __forceinline__ double px_of(const SweepParams<R> &p, int32_t q)
 {
     return q < p.n ? p.x[q] : p.gx[q - p.n];
@@ -322,7 +328,7 @@ __device__ __forceinline__ double stage_cell_geometry(const SweepParams<R> &p, c
     }
     p.W[i] = W;
     // c_s = sqrt(gamma p / rho) = gamma p / sqrt(gamma p rho): one reciprocal square root
-    const R gp = to_R<R>(gamma) * W.w;
+    const R gp = inst_value<R>(ip.gamma, ip.gamma_f) * W.w;
     const R cs = gp * rsqrt(gp * W.x);
     p.cs[i] = cs;
     if (!p.motion) return DBL_MAX;
@@ -334,7 +340,7 @@ __device__ __forceinline__ double stage_cell_geometry(const SweepParams<R> &p, c
         wy = W.z;
         if (rounding) {
             const R oxr = to_R<R>(ox), oyr = to_R<R>(oy);
-            R f = to_R<R>(ip.chi) * cs * rsqrt(oxr * oxr + oyr * oyr);
+            R f = inst_value<R>(ip.chi, ip.chi_f) * cs * rsqrt(oxr * oxr + oyr * oyr);
             wx += f * oxr;
             wy += f * oyr;
         }
@@ -473,7 +479,8 @@ __device__ __forceinline__ void stage_cell_gradient(const SweepParams<R> &p, int
         for (int c = 0; c < 8; c++) g[c] = acc[c] * invA;
         const R cs = p.cs[i];
         // Eq. 7: -div v > delta_v c_s / R_i, as (delta_v c_s) < -(div v) R_i
-        if (key_less(to_R<R>(ip.delta_v) * cs, flip((g[2] + g[5]) * Rad, 0x8000000000000000ull))) shock = true;
+        if (key_less(inst_value<R>(ip.delta_v, ip.delta_v_f) * cs, flip((g[2] + g[5]) * Rad, 0x8000000000000000ull)))
+            shock = true;
         const bool use_tess = ip.limiter == 2 || (ip.limiter == 0 && shock);
         const Vec2<R> oi = p.o[i];
         const R ox = oi.x, oy = oi.y;
@@ -538,7 +545,7 @@ __device__ __forceinline__ void stage_cell_gradient(const SweepParams<R> &p, int
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 // alpha = 0, or min(1, theta bn / bd)
-                const R tn = to_R<R>(ip.theta) * bn[v];
+                const R tn = inst_value<R>(ip.theta, ip.theta_f) * bn[v];
                 if (zero[v]) { an[v] = R(0); lim[v] = true; }
                 else if (bd[v] > R(0) && tn < bd[v]) { an[v] = tn; ad[v] = bd[v]; lim[v] = true; }
             }
@@ -558,7 +565,7 @@ __device__ __forceinline__ void stage_cell_gradient(const SweepParams<R> &p, int
             // cell-only terms of the half-step prediction (used by every edge
             // of the cell): rho div v, grad p / rho, gamma p div v
             const R ldiv = lg[2] + lg[5];
-            p.psrc[i] = Vec4<R>{Wi[0] * ldiv, lg[6] * irho, lg[7] * irho, to_R<R>(ip.gamma) * Wi[3] * ldiv};
+            p.psrc[i] = Vec4<R>{Wi[0] * ldiv, lg[6] * irho, lg[7] * irho, inst_value<R>(ip.gamma, ip.gamma_f) * Wi[3] * ldiv};
         }
         if (p.diagnostics) {
             p.g[2 * i] = Vec4<R>{g[0], g[1], g[2], g[3]};
@@ -598,6 +605,13 @@ template <class R> __device__ __forceinline__ double step_dt(const SweepParams<R
     // still sit stale in this SM's L1
     double dt = ip.cfl * __longlong_as_double((long long)__ldcg(p.dtmin_bits + inst));
     return nonneg_less(ip.remaining, dt) ? ip.remaining : dt;
+}
+
+// The step's dt in the stages after the point motion, which records it
+// (the same bits as step_dt, without its FP64 multiply per thread)
+template <class R> __device__ __forceinline__ double recorded_dt(const SweepParams<R> &p, int32_t inst)
+{
+    return __ldcg(p.dt_out + inst);
 }
 
 // half-step prediction of one side's edge state in the frame moving with wf:
@@ -676,7 +690,7 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
     // (the hardware converts FP64 -> R in this stage: the integer-pipe
     // conversions' extra registers cost it more than the FP64 issue slots
     // they save)
-    const R hdt = p.inst[li].phase == 0 ? R(0.5) * (R)step_dt(p, li) : R(0);
+    const R hdt = p.inst[li].phase == 0 ? R(0.5) * (R)recorded_dt(p, li) : R(0);
     int32_t xf;
     const int32_t k = src_of(p, p.edge_r[e], xf);
     // sign masks of a mirror image across an x wall, a y wall, and both
@@ -706,7 +720,7 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
     const R wfx = R(0.5) * (wlx + wrx) - dwc * nx;
     const R wfy = R(0.5) * (wly + wry) - dwc * ny;
     R Sl[4], Sr[4];
-    const R gam = (R)p.inst[li].gamma;
+    const R gam = inst_value<R>(p.inst[li].gamma, p.inst[li].gamma_f);
     const Vec4<R> sl4 = p.psrc[l], sr4 = p.psrc[k];
     // a mirrored source flips the pressure-gradient term of its axis
     const R srcL[4] = {sl4.x, sl4.y, sl4.z, sl4.w};
@@ -717,7 +731,7 @@ template <class R> __device__ __forceinline__ void stage_edge_flux(const SweepPa
     R WL[4] = {Sl[0], Sl[1] * nx + Sl[2] * ny, Sl[1] * tx + Sl[2] * ty, Sl[3]};
     R WR[4] = {Sr[0], Sr[1] * nx + Sr[2] * ny, Sr[1] * tx + Sr[2] * ty, Sr[3]};
     R Fe[4];
-    hllc(gam, (R)p.inst[li].igm1, WL, WR, Fe);
+    hllc(gam, inst_value<R>(p.inst[li].igm1, p.inst[li].igm1_f), WL, WR, Fe);
     if (xf && k == l) {
         // a wall: the cell faces its own mirror image.  The mirrored Riemann
         // problem has u* = 0 and the wall does not move normal to itself, so
@@ -752,20 +766,27 @@ template <class R> __device__ __forceinline__ void stage_advance(const SweepPara
     const double dt = step_dt(p, my_inst);
     if (ip.phase != 2 && (i == 0 || inst_of(p, i - 1) != my_inst)) p.dt_out[my_inst] = dt;
     // the first sweep of the time-centred scheme moves the points half a step
-    const double hdt = ip.phase == 1 ? 0.5 * dt : dt;
-    // the box tests compare bit patterns on the integer pipe (dkey orders doubles)
-    int32_t st = 0;
+    // (branches rather than selects: each FP64 instruction a warp issues
+    // costs 16 clocks of the SM's FP64 pipe, taken or not)
+    double hdt = dt;
+    if (ip.phase == 1) hdt = 0.5 * dt;
     const Vec2<R> w = p.w[i];
     double xn = p.x0[i] + hdt * to_d(w.x), yn = p.y0[i] + hdt * to_d(w.y);
+    // the box tests compare bit patterns on the integer pipe (dkey orders
+    // doubles); the few points that crossed an edge of the box take the
+    // FP64 corrections in a branch of their own
     const long long kx0 = dkey0(ip.x0), kx1 = dkey0(ip.x1), ky0 = dkey0(ip.y0), ky1 = dkey0(ip.y1);
     long long kx = dkey0(xn), ky = dkey0(yn);
+    int32_t st = 0;
     if (ip.boundary == 1) {
-        const double Lx = ip.x1 - ip.x0, Ly = ip.y1 - ip.y0;
-        if (kx < kx0) xn += Lx;
-        else if (kx >= kx1) xn -= Lx;
-        if (ky < ky0) yn += Ly;
-        else if (ky >= ky1) yn -= Ly;
-    } else {
+        if (kx < kx0 || kx >= kx1 || ky < ky0 || ky >= ky1) {
+            const double Lx = ip.x1 - ip.x0, Ly = ip.y1 - ip.y0;
+            if (kx < kx0) xn += Lx;
+            else if (kx >= kx1) xn -= Lx;
+            if (ky < ky0) yn += Ly;
+            else if (ky >= ky1) yn -= Ly;
+        }
+    } else if (kx <= kx0 || kx >= kx1 || ky <= ky0 || ky >= ky1) {
         // a point that crossed a rigid wall comes back as its mirror image
         if (kx <= kx0) xn = (ip.x0 + ip.x0) - xn;
         else if (kx >= kx1) xn = (ip.x1 + ip.x1) - xn;
@@ -792,9 +813,10 @@ template <class R> __device__ __forceinline__ void stage_cell_update(const Sweep
     const int32_t n = p.n;
     const int32_t my_inst = inst_of(p, i);
     const InstParams &ip = p.inst[my_inst];
-    const double dt = step_dt(p, my_inst);
+    const double dt = recorded_dt(p, my_inst);
     // the first sweep of the time-centred scheme moves the state half a step
-    const double hdt = ip.phase == 1 ? 0.5 * dt : dt;
+    double hdt = dt;
+    if (ip.phase == 1) hdt = 0.5 * dt;
     const int32_t lo = p.cell_ptr[i], hi = p.cell_ptr[i + 1];
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (int32_t s = lo; s < hi; s++) {

@@ -66,6 +66,9 @@ struct InstParams {
     // update); 2 its second sweep (spatial extrapolation only, the dt of
     // sweep 1 from dt_out, full update)
     int32_t phase;
+    // gamma, 1/(gamma - 1), chi, theta and delta_v rounded to FP32 (by the
+    // host), for the split-precision stages
+    float gamma_f, igm1_f, chi_f, theta_f, delta_v_f;
     int32_t pad;
 };
 
