@@ -212,9 +212,9 @@ int rich_set_diagnostics(rich_sim *s, int32_t on);
 /* Per-stage device times of the last synchronised sweep, from CUDA events
    recorded on the launching stream between the stages (enabled by
    rich_set_profiling; off by default).  Stages, in launch order:
-   k_circumcentre, k_geometry (edge and cell geometry with the primitives, in
-   one launch), dt_reset (a memset), k_cell_gradient, k_edge_flux,
-   k_cell_update.  *count receives the number of
+   k_circumcentre, k_geometry (edge and cell geometry with the primitives,
+   mesh velocity and Courant candidates, in one launch), k_advance_points,
+   k_cell_gradient, k_edge_flux, k_cell_update.  *count receives the number of
    stages; up to cap values (milliseconds) are written to ms. */
 int rich_set_profiling(rich_sim *s, int32_t on);
 int rich_kernel_times(rich_sim *s, int32_t cap, double *ms, int32_t *count);

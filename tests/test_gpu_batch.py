@@ -54,9 +54,15 @@ def test_batch_equals_solo_runs(R, precision):
     b.close()
 
 
-def test_batch_admission_mid_run_and_uneven_budgets(R):
+# launch mode 0 autotunes (staged and persistent trial steps); mode 1 runs
+# every step staged, where the meshes of the next step are built on the host
+# during each sweep from the points read back early
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_admission_mid_run_and_uneven_budgets(R, mode):
     wls = mix(W.FP64)
     b = R.Batch()
+    if mode:
+        b.set_launch(mode, 256)
     first = [b.add(wl, max_steps=4) for wl in wls[:2]]
     b.step()
     b.step()
@@ -103,12 +109,15 @@ def test_batch_launch_shapes_give_identical_results(R, mode, block):
     b.close()
 
 
-def test_batch_failure_is_isolated(R):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_failure_is_isolated(R, mode):
     good = W.sod(n_side=20, seed=3)
     bad = W.random_mixed(n=600, seed=3)
     bad["vx"] = np.where(bad["x"] < 0.5, -3.0, 3.0)
     bad["cfg"]["cfl"] = 40.0
     b = R.Batch()
+    if mode:
+        b.set_launch(mode, 256)
     g, f = b.add(good, max_steps=5), b.add(bad, max_steps=5)
     for _ in range(5):
         b.step()
