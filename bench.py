@@ -52,7 +52,7 @@ NUM_KERNELS = 6
 FLOPS = {
     "fp64": {
         "k_circumcentre": {"tri": {"fp64": 25}},
-        "k_geometry": {"edge": {"fp64": 34}, "cell": {"fp64": 52}, "slot": {"fp64": 11}},
+        "k_geometry": {"edge": {"fp64": 32}, "cell": {"fp64": 52}, "slot": {"fp64": 11}},
         "k_advance_points": {"cell": {"fp64": 5}},
         "k_cell_gradient": {"cell": {"fp64": 67}, "slot": {"fp64": 33}},
         "k_edge_flux": {"edge": {"fp64": 177}},
@@ -60,7 +60,7 @@ FLOPS = {
     },
     "split": {
         "k_circumcentre": {"tri": {"fp64": 25}},
-        "k_geometry": {"edge": {"fp64": 8, "fp32": 26}, "cell": {"fp64": 24, "fp32": 29}, "slot": {"fp64": 11}},
+        "k_geometry": {"edge": {"fp64": 6, "fp32": 26}, "cell": {"fp64": 24, "fp32": 29}, "slot": {"fp64": 11}},
         "k_advance_points": {"cell": {"fp64": 5}},
         "k_cell_gradient": {"cell": {"fp32": 67}, "slot": {"fp64": 1, "fp32": 32}},
         "k_edge_flux": {"edge": {"fp64": 1, "fp32": 176}},

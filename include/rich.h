@@ -259,9 +259,14 @@ int rich_batch_add(rich_batch *b, const rich_config *cfg, int64_t n, const doubl
                    const double *rho, const double *vx, const double *vy, const double *p, double t_end,
                    int64_t max_steps, int32_t *id);
 
-/* One step of every pending or running simulation.  info (nullable):
-   steps_done = simulations stepped, sweep_ms = device time of the sweep,
-   tess_ms = host tessellation wall time, copy_ms = other host time. */
+/* One step of every pending or running simulation.  With the staged
+   launch, the moved points are read back once the point motion is done and
+   the simulations that go on are tessellated for the next step while the
+   device finishes the sweep (the next call then tessellates only newly
+   admitted ones); results equal those without this overlap, bit for bit.
+   info (nullable): steps_done = simulations stepped, sweep_ms = device time
+   of the sweep, tess_ms = host tessellation wall time (both tessellations),
+   copy_ms = other host time outside the sweep. */
 int rich_batch_step(rich_batch *b, rich_step_info *info);
 
 /* State (RICH_SIM_*), error code of a failed simulation, its time and steps

@@ -198,13 +198,14 @@ template <class R> __device__ __forceinline__ void stage_edge_geometry(const Swe
 {
     int32_t l = p.edge_l[e], r = p.edge_r[e];
     double xl = p.x[l], yl = p.y[l];
-    const double ax64 = p.ccx[p.edge_ta[e]] - xl, ay64 = p.ccy[p.edge_ta[e]] - yl;
-    const double bx64 = p.ccx[p.edge_tb[e]] - xl, by64 = p.ccy[p.edge_tb[e]] - yl;
-    R ax = to_R<R>(ax64), ay = to_R<R>(ay64);
+    const int32_t ta = p.edge_ta[e], tb = p.edge_tb[e];
+    const double cax = p.ccx[ta], cay = p.ccy[ta];
+    R ax = to_R<R>(cax - xl), ay = to_R<R>(cay - yl);
     R dx = to_R<R>(px_of(p, r) - xl), dy = to_R<R>(py_of(p, r) - yl);
-    // the edge vector from the FP64 endpoints: a zero-length edge stays ~0
-    // instead of inheriting the rounding of two separately rounded endpoints
-    R ex = to_R<R>(bx64 - ax64), ey = to_R<R>(by64 - ay64);
+    // the edge vector as the FP64 difference of its two vertices: a
+    // zero-length edge stays ~0 instead of inheriting the rounding of two
+    // separately rounded endpoints (six FP64 subtractions per edge)
+    R ex = to_R<R>(p.ccx[tb] - cax), ey = to_R<R>(p.ccy[tb] - cay);
     R mx = ax + R(0.5) * ex, my = ay + R(0.5) * ey;
     // 1/|r_ij| with one reciprocal square root (a divide and a square root
     // each cost several FP64 issue slots on this part)

@@ -59,3 +59,26 @@ def test_pipelined_steps_equal_the_pieces_api(R, name, make, scheme, precision):
         assert np.array_equal(sa[f], sb[f]), f
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("scheme", [W.SCHEME_EXTRAPOLATED, W.SCHEME_TIME_CENTRED])
+def test_pipelined_run_lands_on_t_end_and_continues(R, scheme):
+    """A run to t_end: the step that lands on it builds no mesh ahead and
+    leaves the time at t_end exactly; a later call to a further t_end then
+    meshes the points itself, and a read of the state between the two calls
+    (which meshes them too) changes nothing that follows."""
+    wl = W.sod(n_side=24)
+    wl["cfg"]["scheme"] = scheme
+    a, c = R.Sim(wl), R.Sim(wl)
+    ia = a.step(1000, 0.01)
+    assert ia["t"] == 0.01 and R.rich_time(a.h) == 0.01
+    a.step(1000, 0.02)
+    assert R.rich_time(a.h) == 0.02
+    c.step(1000, 0.01)
+    c.state()
+    c.step(1000, 0.02)
+    ca, cc = a.conserved(), c.conserved()
+    for f in ("x", "y", "m", "px", "py", "E"):
+        assert np.array_equal(ca[f], cc[f]), f
+    a.close()
+    c.close()
