@@ -9,16 +9,23 @@
 // two-component expansions; GrowExpansion adds a double to an expansion
 // exactly, keeping the components non-overlapping and increasing in
 // magnitude, so the sign of an expansion is the sign of its last non-zero
-// component.  This file must be compiled without floating-point contraction.
+// component.  Expansions live in fixed arrays on the stack (nothing is
+// allocated on the exact path, which the mirror images of a walled box reach
+// at every wall-side edge: a point, its neighbour along the wall and their
+// two images are co-circular up to the rounding of the images).  This file
+// must be compiled without floating-point contraction.
 #include "predicates.h"
 
 #include <cmath>
-#include <vector>
 
 namespace rich {
 namespace {
 
-using Exp = std::vector<double>;
+// An expansion in a caller-provided array: components non-overlapping and
+// increasing in magnitude, zero components dropped (the value zero is the
+// single component 0).  Every routine writes into storage of its own; the
+// bounds on the lengths below follow from the operations of the in-circle
+// determinant, whose inputs are the two-component coordinate differences.
 
 inline void two_sum(double a, double b, double &s, double &e)
 {
@@ -34,90 +41,133 @@ inline void two_prod(double a, double b, double &p, double &e)
     e = std::fma(a, b, -p);
 }
 
-// h = e + b exactly
-Exp grow(const Exp &e, double b)
+// h[0, n) += b exactly, in place (room for n + 1); returns the new length.
+// Component i is read before anything is written at or beyond it.
+inline int grow(double *h, int n, double b)
 {
-    Exp h;
-    h.reserve(e.size() + 1);
     double q = b;
-    for (double ei : e) {
+    int k = 0;
+    for (int i = 0; i < n; i++) {
         double s, err;
-        two_sum(q, ei, s, err);
-        if (err != 0.0) h.push_back(err);
+        two_sum(q, h[i], s, err);
+        if (err != 0.0) h[k++] = err;
         q = s;
     }
-    if (q != 0.0 || h.empty()) h.push_back(q);
-    return h;
+    if (q != 0.0 || k == 0) h[k++] = q;
+    return k;
 }
 
-Exp add(const Exp &e, const Exp &f)
+// h = e + f (room for ne + nf)
+inline int add(const double *e, int ne, const double *f, int nf, double *h)
 {
-    Exp h = e;
-    for (double fi : f) h = grow(h, fi);
-    return h;
+    for (int i = 0; i < ne; i++) h[i] = e[i];
+    int n = ne;
+    for (int j = 0; j < nf; j++) n = grow(h, n, f[j]);
+    return n;
 }
 
-Exp neg(Exp e)
+// h = e * b (room for 2 ne + 1)
+inline int scale(const double *e, int ne, double b, double *h)
 {
-    for (double &v : e) v = -v;
-    return e;
-}
-
-Exp scale(const Exp &e, double b)
-{
-    Exp h{0.0};
-    for (double ei : e) {
+    h[0] = 0.0;
+    int n = 1;
+    for (int i = 0; i < ne; i++) {
         double p, err;
-        two_prod(ei, b, p, err);
-        h = grow(h, err);
-        h = grow(h, p);
+        two_prod(e[i], b, p, err);
+        n = grow(h, n, err);
+        n = grow(h, n, p);
     }
-    return h;
+    return n;
 }
 
-Exp mul(const Exp &e, const Exp &f)
+// h = e * f (room for 2 ne nf + 1; t: scratch of 2 ne + 1)
+inline int mul(const double *e, int ne, const double *f, int nf, double *h, double *t)
 {
-    Exp h{0.0};
-    for (double fi : f) h = add(h, scale(e, fi));
-    return h;
+    h[0] = 0.0;
+    int n = 1;
+    for (int j = 0; j < nf; j++) {
+        const int nt = scale(e, ne, f[j], t);
+        for (int i = 0; i < nt; i++) n = grow(h, n, t[i]);
+    }
+    return n;
 }
 
-Exp diff(double a, double b)
+inline int negate(double *e, int n)
+{
+    for (int i = 0; i < n; i++) e[i] = -e[i];
+    return n;
+}
+
+// a - b as two components
+inline int diff(double a, double b, double *h)
 {
     double s, e;
     two_sum(a, -b, s, e);
-    return Exp{e, s};
+    h[0] = e;
+    h[1] = s;
+    return 2;
 }
 
-int sign_of(const Exp &e)
+inline int sign_of(const double *e, int n)
 {
-    for (auto it = e.rbegin(); it != e.rend(); ++it)
-        if (*it != 0.0) return *it > 0.0 ? 1 : -1;
+    for (int i = n - 1; i >= 0; i--)
+        if (e[i] != 0.0) return e[i] > 0.0 ? 1 : -1;
     return 0;
+}
+
+// x*y - z*w for two-component x, y, z, w (room for 2 * 9)
+inline int cross(const double *x, const double *y, const double *z, const double *w, double *h)
+{
+    double a[9], b[9], t[5];
+    const int na = mul(x, 2, y, 2, a, t);
+    const int nb = negate(b, mul(z, 2, w, 2, b, t));
+    return add(a, na, b, nb, h);
+}
+
+// x*x + y*y for two-component x, y (room for 2 * 9)
+inline int norm2(const double *x, const double *y, double *h)
+{
+    double a[9], b[9], t[5];
+    const int na = mul(x, 2, x, 2, a, t);
+    const int nb = mul(y, 2, y, 2, b, t);
+    return add(a, na, b, nb, h);
 }
 
 }  // namespace
 
 int orient2d_exact(double ax, double ay, double bx, double by, double cx, double cy)
 {
-    Exp l = mul(diff(bx, ax), diff(cy, ay));
-    Exp r = mul(diff(by, ay), diff(cx, ax));
-    return sign_of(add(l, neg(r)));
+    double bax[2], cay[2], bay[2], cax[2], h[18];
+    diff(bx, ax, bax);
+    diff(cy, ay, cay);
+    diff(by, ay, bay);
+    diff(cx, ax, cax);
+    return sign_of(h, cross(bax, cay, bay, cax, h));
 }
 
 int incircle_exact(double ax, double ay, double bx, double by, double cx, double cy, double dx, double dy)
 {
-    Exp adx = diff(ax, dx), ady = diff(ay, dy);
-    Exp bdx = diff(bx, dx), bdy = diff(by, dy);
-    Exp cdx = diff(cx, dx), cdy = diff(cy, dy);
-    Exp la = add(mul(adx, adx), mul(ady, ady));
-    Exp lb = add(mul(bdx, bdx), mul(bdy, bdy));
-    Exp lc = add(mul(cdx, cdx), mul(cdy, cdy));
-    Exp ma = add(mul(bdx, cdy), neg(mul(cdx, bdy)));
-    Exp mb = add(mul(cdx, ady), neg(mul(adx, cdy)));
-    Exp mc = add(mul(adx, bdy), neg(mul(bdx, ady)));
-    Exp det = add(add(mul(la, ma), mul(lb, mb)), mul(lc, mc));
-    return sign_of(det);
+    double adx[2], ady[2], bdx[2], bdy[2], cdx[2], cdy[2];
+    diff(ax, dx, adx);
+    diff(ay, dy, ady);
+    diff(bx, dx, bdx);
+    diff(by, dy, bdy);
+    diff(cx, dx, cdx);
+    diff(cy, dy, cdy);
+    // lifted heights (up to 18 components) times the 2x2 minors (up to 18)
+    double la[18], lb[18], lc[18], ma[18], mb[18], mc[18];
+    const int nla = norm2(adx, ady, la), nlb = norm2(bdx, bdy, lb), nlc = norm2(cdx, cdy, lc);
+    const int nma = cross(bdx, cdy, cdx, bdy, ma);
+    const int nmb = cross(cdx, ady, adx, cdy, mb);
+    const int nmc = cross(adx, bdy, bdx, ady, mc);
+    // products up to 2 * 18 * 18 + 1 = 649 components, their sum up to 1947
+    double t[37], pa[649], pb[649], pc[649], det[1947];
+    const int npa = mul(la, nla, ma, nma, pa, t);
+    const int npb = mul(lb, nlb, mb, nmb, pb, t);
+    const int npc = mul(lc, nlc, mc, nmc, pc, t);
+    int n = add(pa, npa, pb, npb, det);
+    for (int i = 0; i < npc; i++) n = grow(det, n, pc[i]);
+    return sign_of(det, n);
 }
 
 namespace {

@@ -52,13 +52,22 @@ def _canon(tris, n):
     return {frozenset(t) for t in np.asarray(tris).tolist() if max(t) < n}
 
 
-@pytest.mark.parametrize("kind", ["random", "lattice", "near_lattice"])
+@pytest.mark.parametrize("kind", ["random", "lattice", "near_lattice", "mirrored"])
 def test_host_delaunay_matches_oracle(R, oracle, kind):
     rng = np.random.default_rng(4)
     if kind == "random":
         x, y = rng.random(3000), rng.random(3000)
     elif kind == "lattice":
         x, y = [a.ravel() * 0.125 for a in np.meshgrid(np.arange(20), np.arange(17))]
+    elif kind == "mirrored":
+        # points beside a wall at x = 0.3 and their mirror images (w + w) - x,
+        # as the ghosts of a walled box are made: every point, a neighbour
+        # along the wall and their two images are co-circular up to the
+        # rounding of the images, so the exact in-circle path and the
+        # tie-break decide the triangulation along the wall
+        w = 0.3
+        px, py = w + rng.random(1500) * 0.05, rng.random(1500)
+        x, y = np.concatenate([px, (w + w) - px]), np.concatenate([py, py])
     else:
         x, y = [a.ravel() * 0.125 + rng.uniform(-1, 1, a.size) * 1e-14 for a in np.meshgrid(np.arange(20), np.arange(17))]
     n = len(x)
@@ -71,6 +80,10 @@ def test_host_delaunay_matches_oracle(R, oracle, kind):
     touched = {v for t in a ^ b for v in t}
     interior_same = [v for v in range(n) if v not in touched]
     assert len(interior_same) > 0.8 * n
+    if kind == "mirrored":
+        # away from the hull, along the wall, the two agree triangle for triangle
+        near = lambda t: all(abs(x[v] - 0.3) < 0.02 and 0.05 < y[v] < 0.95 for v in t)
+        assert {t for t in a if near(t)} == {t for t in b if near(t)}
 
 
 def test_host_delaunay_duplicate(R):
