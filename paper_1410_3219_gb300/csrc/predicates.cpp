@@ -98,11 +98,15 @@ inline int negate(double *e, int n)
     return n;
 }
 
-// a - b as two components
+// a - b as one component when the difference is exact, else two
 inline int diff(double a, double b, double *h)
 {
     double s, e;
     two_sum(a, -b, s, e);
+    if (e == 0.0) {
+        h[0] = s;
+        return 1;
+    }
     h[0] = e;
     h[1] = s;
     return 2;
@@ -115,21 +119,28 @@ inline int sign_of(const double *e, int n)
     return 0;
 }
 
-// x*y - z*w for two-component x, y, z, w (room for 2 * 9)
-inline int cross(const double *x, const double *y, const double *z, const double *w, double *h)
+// A coordinate difference: one or two components.
+struct Diff {
+    double v[2];
+    int n;
+    Diff(double a, double b) { n = diff(a, b, v); }
+};
+
+// x*y - z*w (room for 2 * 8)
+inline int cross(const Diff &x, const Diff &y, const Diff &z, const Diff &w, double *h)
 {
     double a[9], b[9], t[5];
-    const int na = mul(x, 2, y, 2, a, t);
-    const int nb = negate(b, mul(z, 2, w, 2, b, t));
+    const int na = mul(x.v, x.n, y.v, y.n, a, t);
+    const int nb = negate(b, mul(z.v, z.n, w.v, w.n, b, t));
     return add(a, na, b, nb, h);
 }
 
-// x*x + y*y for two-component x, y (room for 2 * 9)
-inline int norm2(const double *x, const double *y, double *h)
+// x*x + y*y (room for 2 * 8)
+inline int norm2(const Diff &x, const Diff &y, double *h)
 {
     double a[9], b[9], t[5];
-    const int na = mul(x, 2, x, 2, a, t);
-    const int nb = mul(y, 2, y, 2, b, t);
+    const int na = mul(x.v, x.n, x.v, x.n, a, t);
+    const int nb = mul(y.v, y.n, y.v, y.n, b, t);
     return add(a, na, b, nb, h);
 }
 
@@ -137,23 +148,14 @@ inline int norm2(const double *x, const double *y, double *h)
 
 int orient2d_exact(double ax, double ay, double bx, double by, double cx, double cy)
 {
-    double bax[2], cay[2], bay[2], cax[2], h[18];
-    diff(bx, ax, bax);
-    diff(cy, ay, cay);
-    diff(by, ay, bay);
-    diff(cx, ax, cax);
+    const Diff bax(bx, ax), cay(cy, ay), bay(by, ay), cax(cx, ax);
+    double h[18];
     return sign_of(h, cross(bax, cay, bay, cax, h));
 }
 
 int incircle_exact(double ax, double ay, double bx, double by, double cx, double cy, double dx, double dy)
 {
-    double adx[2], ady[2], bdx[2], bdy[2], cdx[2], cdy[2];
-    diff(ax, dx, adx);
-    diff(ay, dy, ady);
-    diff(bx, dx, bdx);
-    diff(by, dy, bdy);
-    diff(cx, dx, cdx);
-    diff(cy, dy, cdy);
+    const Diff adx(ax, dx), ady(ay, dy), bdx(bx, dx), bdy(by, dy), cdx(cx, dx), cdy(cy, dy);
     // lifted heights (up to 18 components) times the 2x2 minors (up to 18)
     double la[18], lb[18], lc[18], ma[18], mb[18], mc[18];
     const int nla = norm2(adx, ady, la), nlb = norm2(bdx, bdy, lb), nlc = norm2(cdx, cdy, lc);
