@@ -443,7 +443,9 @@ def run_ours(args):
         # triangle and edge lists themselves are built on the device)
         h2d = (28 * info["n_ghost"] + 4 * (n + 1) + 4 * n + 4 * (n + 1) + 4 * (n + 1)
                + 4 * info["n_slots"])
-        d2h = 16 * n + 12 + 48 * n
+        # down: the moved points and dt read early, the mesh builds' two
+        # check flags, the step's dt and status, the conserved state read
+        d2h = (16 * n + 8) + 8 + 12 + 48 * n
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, ws)
     e2e_val = job_value(ws, n * e2e_steps, e2e_s)
