@@ -82,3 +82,22 @@ def test_pipelined_run_lands_on_t_end_and_continues(R, scheme):
         assert np.array_equal(ca[f], cc[f]), f
     a.close()
     c.close()
+
+
+def test_pipelined_steps_on_a_caller_stream(R):
+    """The early read of the moved points waits on the caller's stream when
+    the handle runs on one (rich_set_stream)."""
+    torch = pytest.importorskip("torch")
+    wl = W.kelvin_helmholtz(n_side=48, amp=0.1)
+    a, b = R.Sim(wl), R.Sim(wl)
+    st = torch.cuda.Stream()
+    a.set_stream(st.cuda_stream)
+    a.step(4)
+    for _ in range(4):
+        _pieces_step(R, b, W.SCHEME_EXTRAPOLATED)
+    ca, cb = a.conserved(), b.conserved()
+    for f in ("x", "y", "m", "px", "py", "E"):
+        assert np.array_equal(ca[f], cb[f]), f
+    a.set_stream(None)
+    a.close()
+    b.close()
