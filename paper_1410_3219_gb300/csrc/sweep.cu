@@ -579,9 +579,10 @@ __device__ __forceinline__ void stage_cell_gradient(const SweepParams<R> &p, int
 
 // launched in blocks of 128 threads; six blocks per SM cap the FP64 build at
 // 80 registers (from 94, with a few spilled to L1), 24 warps instead of 20;
-// nine cap the FP32 build at 56 (from 72, no spill), 36 warps instead of 28,
-// which hide more of its gather latency (0.102 -> 0.093 ms at 1M cells; ten
-// blocks spill and lose it again).
+// nine hold the FP32 build's 56 registers, 36 warps, which hide more of its
+// gather latency than 28 did (0.102 -> 0.093 ms at 1M cells, when the cap
+// took it from 72 registers, before the mesh velocity and the time step
+// moved to the geometry stage; ten blocks spilled and lost it again).
 // The FP64 build visits cells in the degree-sorted order (FP64 issue is per
 // warp instruction, so a warp should loop near the mean degree); the FP32
 // build, bound by its gathers, visits them in the Hilbert order itself, so
