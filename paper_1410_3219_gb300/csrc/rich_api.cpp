@@ -675,6 +675,8 @@ int rich_step(rich_sim *s, int32_t max_steps, double t_end, rich_step_info *info
         if ((rc = pipelined_sweep(s, t_end, info)) != RICH_OK) return rc;
         if (s->tc_phase == 1) {
             // time-centred: the full step on the mesh of the half-step points
+            // (meshed again here, to report its error, if the early build failed)
+            if (!s->tess_current && (rc = tessellate(s, info, true)) != RICH_OK) return rc;
             if ((rc = pipelined_sweep(s, t_end, info)) != RICH_OK) return rc;
         }
         if (s->last_dt >= t_end - before) s->t = t_end;  // landed on t_end
