@@ -807,7 +807,7 @@ int rich_batch_step(rich_batch *b, rich_step_info *info)
     //    points are read back once the point motion is done, and the host
     //    tessellates them for the next step while the device finishes
     const LaunchShape shape = pick_shape(b);
-    if (!shape.persistent) CUDA_TRY(b->h_moved.ensure((2 * N + ok.size()) * sizeof(double)));
+    if (!shape.persistent) CUDA_TRY(b->h_moved.ensure((2 * N + ok.size() + 1) * sizeof(double)));
     CUDA_TRY(cudaEventRecord(b->ev0, b->stream));
     if (shape.persistent) {
         rc = b->precision == RICH_FP32_SPLIT ? run_persistent<float>(b, shape.block) : run_persistent<double>(b, shape.block);
